@@ -1,0 +1,216 @@
+/*
+ * dash.h -- C ABI of libdash, the GB300 (sm_103a) implementation of the DASH
+ * 4D-hash deformation path (arXiv 2507.19141, Sec. 4.2-4.3, Eqs. 7-11).
+ *
+ * Conventions shared by every entry point
+ *   - All pointers are DEVICE pointers unless a comment says "host".
+ *   - The caller owns all memory.  Nothing here allocates device memory
+ *     except dash_batch_plan_create (inside the plan it returns).
+ *   - Every call is asynchronous on the CUDA stream passed as `void* stream`
+ *     (a cudaStream_t; NULL = the legacy default stream).  Nothing
+ *     synchronises; a kernel fault surfaces at the caller's next sync.
+ *   - Every call returns a dash_status.  No exception crosses the ABI.
+ *     dash_last_error() returns a thread-local message for the last failure.
+ *   - Gradient outputs are ACCUMULATED (+=); the caller zeroes them.
+ *   - Coordinates are normalised to [0,1]: values outside are clamped, NaN
+ *     maps to 0.
+ *   - Feature layout: f_h[i][l*F + f] (levels concatenated, Eq. 9).
+ *   - Table layout: entry-major [offset[L]][F]; level l occupies entries
+ *     [offset[l], offset[l] + size[l]).
+ *   - Decoder parameters (FP32, packed): W1 [H][D], b1 [H], W2 [H][H], b2 [H],
+ *     W3 [O][H], b3 [O] with D = L*F; gradients use the same packing.
+ *   - Deformation output: SoA delta[k][i], k = 0-2 position, 3-6 rotation,
+ *     7-9 scale (Sec. 4.2 multi-head decoder, Eq. 10).
+ */
+#ifndef DASH_H_
+#define DASH_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DASH_MAX_LEVELS 32
+
+typedef enum dash_status {
+  DASH_OK = 0,
+  DASH_ERR_INVALID_ARG = -1, /* null pointer, negative size, inconsistent shapes */
+  DASH_ERR_UNSUPPORTED = -2, /* valid but not implemented (F, L, MLP widths)     */
+  DASH_ERR_WORKSPACE = -3,   /* workspace missing or too small                   */
+  DASH_ERR_CUDA = -4,        /* a CUDA runtime call failed; see dash_last_error   */
+  DASH_ERR_BOUNDS = -5,      /* a device-side check found an out-of-range value  */
+  DASH_ERR_TIMEOUT = -6      /* a bounded device-side wait gave up               */
+} dash_status;
+
+typedef enum dash_dtype { DASH_F32 = 0, DASH_F16 = 1, DASH_BF16 = 2 } dash_dtype;
+
+/* Hash-grid hyper-parameters (Sec. 4.2): L levels, F features per level,
+ * hashed tables of T = 2^log2_T entries, coarsest/finest spatial (x, y, z)
+ * and temporal resolutions, and the four hash primes pi_i of Eq. 8. */
+typedef struct dash_hash4d_cfg {
+  int32_t L, F, log2_T, reserved;
+  double nmin_s, nmax_s, nmin_t, nmax_t;
+  uint32_t primes[4];
+} dash_hash4d_cfg;
+
+/* Level layout derived from a cfg by dash_hash4d_layout (host struct, passed
+ * to kernels by value).  res_*: N_l of Eq. 7; dense[l] != 0 when all
+ * (N_s+1)^3 (N_t+1) vertices fit in T (then indexed directly, x fastest),
+ * else hashed by Eq. 8 into T entries; size[l]: entries used; offset[l]:
+ * first entry of level l, a multiple of 8; offset[L]: entries to allocate. */
+typedef struct dash_layout {
+  int32_t L, F, log2_T, reserved;
+  uint32_t primes[4];
+  int32_t res_s[DASH_MAX_LEVELS];
+  int32_t res_t[DASH_MAX_LEVELS];
+  int32_t dense[DASH_MAX_LEVELS];
+  int64_t size[DASH_MAX_LEVELS];
+  int64_t offset[DASH_MAX_LEVELS + 1];
+} dash_layout;
+
+/* The points to encode: FP32 SoA coordinates of ALL Gaussians, indexed
+ * through idx (compact dynamic list, NULL = identity 0..n-1).  t_stride = 1
+ * reads t[j] per point, 0 broadcasts t[0] (one frame = one timestamp).
+ * n is the number of points, or the capacity when n_dev is set: then the
+ * kernels read the count from device memory (*n_dev, clamped to n), so a
+ * captured CUDA graph needs no host-side count. */
+typedef struct dash_points {
+  const float* x;
+  const float* y;
+  const float* z;
+  const float* t;
+  int64_t t_stride;
+  const int32_t* idx;
+  int64_t n;
+  const int64_t* n_dev;
+} dash_points;
+
+/* The decoder phi_d + heads (Sec. 4.2, Eq. 9): D = L*F -> H -> H -> O with
+ * ReLU after the two hidden layers; params is the packed FP32 vector. */
+typedef struct dash_mlp {
+  int32_t d_in, d_hidden, d_out, reserved;
+  const float* params;
+} dash_mlp;
+
+/* Optional Eq. 10 epilogue: attrs_out[k][j] = attrs_in[k][j] + delta[k][i]
+ * for j = idx[i] (SoA [O][n_all], FP32).  Only dynamic rows are written. */
+typedef struct dash_apply {
+  const float* attrs_in;
+  float* attrs_out;
+  int64_t n_all;
+} dash_apply;
+
+/* Optional smoothness term (Eq. 11): adds lambda_r * L_r with
+ * L_r = (1/n) sum_i |f(p_i) - f(p_i + e_s)|^2 + |f(p_i) - f(p_i + e_t)|^2,
+ * e_s = (eps_s[0], eps_s[1], eps_s[2], 0), e_t = (0, 0, 0, eps_t); perturbed
+ * coordinates are clamp(fl32(clamp(p) + e)).  The perturbed encodings are
+ * recomputed inside the backward kernel, never stored.  loss_out (device
+ * float, may be NULL) accumulates lambda_r * L_r. */
+typedef struct dash_smooth {
+  float lambda_r;
+  float eps_s[3];
+  float eps_t;
+  float* loss_out;
+} dash_smooth;
+
+/* ----------------------------------------------------------- utilities -- */
+
+/* Static string for a status code. */
+const char* dash_status_string(int status);
+/* Thread-local detail of the last failed call on this thread ("" if none). */
+const char* dash_last_error(void);
+/* ABI version (major * 100 + minor). */
+int dash_version(void);
+
+/* Eq. 7 (host): fills *out from *cfg.  N_l = floor(N_min * b^l + 1e-9),
+ * b = exp((ln N_max - ln N_min) / (L - 1)), separately for space and time.
+ * Errors: INVALID_ARG (null, N_min < 1, N_max < N_min), UNSUPPORTED
+ * (L > 32, F not in {1,2,4,8}, log2_T outside [4, 28]). */
+int dash_hash4d_layout(const dash_hash4d_cfg* cfg, dash_layout* out);
+
+/* ------------------------------------------------- a1: compaction ------ */
+
+/* Bytes of device workspace dash_compact_dynamic needs for n mask entries. */
+size_t dash_compact_workspace_size(int64_t n);
+
+/* Self-supervised split (Sec. 4.1): idx_out receives, in ascending order,
+ * every i < n with mask[i] != 0 (the dynamic set G_d), *count_out (device
+ * int64) its length.  idx_out must hold n entries.  ws: device scratch of
+ * dash_compact_workspace_size(n) bytes (contents need not be initialised).
+ * Errors: INVALID_ARG, WORKSPACE (ws too small), UNSUPPORTED (n >= 2^31). */
+int dash_compact_dynamic(const uint8_t* mask, int64_t n, int32_t* idx_out, int64_t* count_out,
+                         void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------- a2-a6: encoder (Eqs. 8-9) ---- */
+
+/* Debug view of Eq. 8/9: idx_out [n][L][16] level-local corner indices
+ * (corner b: bit d set = upper corner along axis d of x, y, z, t) and
+ * w_out [n][L][16] FP32 quadrilinear weights (either may be NULL). */
+int dash_hash4d_indices(const dash_layout* layout, const dash_points* pts,
+                        uint32_t* idx_out, float* w_out, void* stream);
+
+/* Eq. 9 encoder f_h = G_4D(x): feat_out [n][L*F] of feat_dtype (F32, F16 or
+ * BF16) from the table of table_dtype (F32 or F16), FP32 arithmetic. */
+int dash_hash4d_fwd(const dash_layout* layout, const dash_points* pts, const void* table,
+                    int table_dtype, void* feat_out, int feat_dtype, void* stream);
+
+/* Transpose of the encoder: table_grad[offset[l] + idx][f] += w * dfeat[i][l*F+f]
+ * over the 16 corners of every level.  dfeat [n][L*F] FP32, table_grad FP32
+ * [offset[L]][F].  Vector FP32 atomics; summation order is not deterministic. */
+int dash_hash4d_bwd(const dash_layout* layout, const dash_points* pts, const float* dfeat,
+                    float* table_grad, void* stream);
+
+/* ------------------------- a2-a8: fused deformation forward (Eqs. 8-10) -- */
+
+/* Encoder + decoder MLP (+ optional Eq. 10) in one kernel: gathers the
+ * tables (F32 or F16), interpolates in FP32, runs the three decoder layers on
+ * the tensor cores (tcgen05, BF16 operands as a hi+lo pair for activations,
+ * FP32 accumulation) and writes delta_out SoA [O][n] FP32.  feat_save
+ * (optional, BF16 [n][D]) keeps f_h for dash_deform_mlp_bwd.  apply may be
+ * NULL.  Supported: D = L*F <= 64, H = 64, O <= 16.
+ * Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+int dash_deform_mlp_fwd(const dash_layout* layout, const dash_points* pts,
+                        const void* table, int table_dtype, const dash_mlp* mlp,
+                        float* delta_out, void* feat_save, const dash_apply* apply,
+                        void* stream);
+
+/* ---------------------- a9-a11: fused deformation backward (+ Eq. 11) -- */
+
+/* Backward of dash_deform_mlp_fwd for upstream ddelta SoA [O][n] FP32:
+ * recomputes the decoder from feat_saved (BF16 [n][D] as written by the
+ * forward; NULL = re-encode from the table), back-propagates on the tensor
+ * cores, accumulates mlp_grad (FP32, packed like params) and scatters
+ * dL/df_h into table_grad (FP32 [offset[L]][F]) with vector atomics.  With
+ * smooth != NULL and lambda_r != 0 also adds the Eq. 11 term, re-encoding
+ * p, p + e_s and p + e_t in the kernel.  Supported shapes as the forward. */
+int dash_deform_mlp_bwd(const dash_layout* layout, const dash_points* pts,
+                        const void* table, int table_dtype, const dash_mlp* mlp,
+                        const float* ddelta, const void* feat_saved, float* table_grad,
+                        float* mlp_grad, const dash_smooth* smooth, void* stream);
+
+/* ------------------------ plain FP32 form (comparison baseline) -------- */
+/* One thread per point, FP32 tables, f_h stored in global memory, FP32
+ * CUDA-core decoder, scalar FP32 atomics.  Same semantics as above. */
+int dash_plain_hash4d_fwd(const dash_layout* layout, const dash_points* pts,
+                          const float* table, float* feat_out, void* stream);
+int dash_plain_hash4d_bwd(const dash_layout* layout, const dash_points* pts,
+                          const float* dfeat, float* table_grad, void* stream);
+/* feat [n][D] -> delta_out SoA [O][n]; n_dev optional device count. */
+int dash_plain_mlp_fwd(const dash_mlp* mlp, const float* feat, int64_t n, const int64_t* n_dev,
+                       float* delta_out, void* stream);
+/* Bytes of workspace dash_plain_mlp_bwd needs: the materialised h1, h2,
+ * dz1, dz2 (4 * H * n FP32). */
+size_t dash_plain_mlp_bwd_workspace_size(const dash_mlp* mlp, int64_t n);
+/* ddelta SoA [O][n] -> dfeat_out [n][D] (written), mlp_grad (accumulated).
+ * ws: device scratch of dash_plain_mlp_bwd_workspace_size bytes. */
+int dash_plain_mlp_bwd(const dash_mlp* mlp, const float* feat, int64_t n, const int64_t* n_dev,
+                       const float* ddelta, float* dfeat_out, float* mlp_grad, void* ws, size_t ws_bytes,
+                       void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DASH_H_ */

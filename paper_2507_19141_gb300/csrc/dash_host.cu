@@ -1,0 +1,148 @@
+// dash_host.cu -- host side of the libdash C ABI: status strings, the
+// thread-local error message, the Eq. 7 level layout and argument checks.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "dash_internal.cuh"
+
+namespace dash {
+
+static thread_local char g_last_error[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+  va_end(ap);
+}
+
+int fail(int status, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+  va_end(ap);
+  return status;
+}
+
+int cuda_status(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return DASH_OK;
+  return fail(DASH_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+int launch_status(const char* what) { return cuda_status(cudaGetLastError(), what); }
+
+int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  if (cached[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+    cached[dev] = v;
+  }
+  return cached[dev];
+}
+
+int make_geom(const dash_layout* lo, Geom* g) {
+  if (lo == nullptr || g == nullptr) return fail(DASH_ERR_INVALID_ARG, "layout is NULL");
+  if (lo->L < 1 || lo->L > DASH_MAX_LEVELS) return fail(DASH_ERR_UNSUPPORTED, "L=%d outside [1,32]", lo->L);
+  if (!(lo->F == 1 || lo->F == 2 || lo->F == 4 || lo->F == 8))
+    return fail(DASH_ERR_UNSUPPORTED, "F=%d not in {1,2,4,8}", lo->F);
+  if (lo->log2_T < 4 || lo->log2_T > 28) return fail(DASH_ERR_UNSUPPORTED, "log2_T=%d outside [4,28]", lo->log2_T);
+  memset(g, 0, sizeof(*g));
+  g->L = lo->L;
+  g->F = lo->F;
+  g->mask = (uint32_t)((1ull << lo->log2_T) - 1ull);
+  for (int i = 0; i < 4; ++i) g->primes[i] = lo->primes[i];
+  for (int l = 0; l < lo->L; ++l) {
+    if (lo->res_s[l] < 1 || lo->res_t[l] < 1) return fail(DASH_ERR_INVALID_ARG, "level %d has resolution < 1", l);
+    g->res_s[l] = lo->res_s[l];
+    g->res_t[l] = lo->res_t[l];
+    if (lo->dense[l]) g->dense_bits |= 1u << l;
+    g->offset[l] = lo->offset[l];
+  }
+  return DASH_OK;
+}
+
+int make_pts(const dash_points* p, Pts* out) {
+  if (p == nullptr) return fail(DASH_ERR_INVALID_ARG, "points is NULL");
+  if (p->n < 0) return fail(DASH_ERR_INVALID_ARG, "n=%lld < 0", (long long)p->n);
+  if (p->n > 0 && (p->x == nullptr || p->y == nullptr || p->z == nullptr || p->t == nullptr))
+    return fail(DASH_ERR_INVALID_ARG, "coordinate pointer is NULL");
+  if (p->t_stride < 0) return fail(DASH_ERR_INVALID_ARG, "t_stride < 0");
+  if (p->n >= (1ll << 31)) return fail(DASH_ERR_UNSUPPORTED, "n >= 2^31");
+  out->x = p->x;
+  out->y = p->y;
+  out->z = p->z;
+  out->t = p->t;
+  out->t_stride = p->t_stride;
+  out->idx = p->idx;
+  out->n = p->n;
+  out->n_dev = reinterpret_cast<const long long*>(p->n_dev);
+  return DASH_OK;
+}
+
+// Eq. 7: geometric progression of resolutions between N_min and N_max.
+static int32_t level_resolution(double nmin, double nmax, int L, int l) {
+  if (L == 1) return (int32_t)floor(nmin + 1e-9);
+  const double growth = exp((log(nmax) - log(nmin)) / (double)(L - 1));
+  return (int32_t)floor(nmin * pow(growth, (double)l) + 1e-9);
+}
+
+}  // namespace dash
+
+extern "C" {
+
+const char* dash_status_string(int s) {
+  switch (s) {
+    case DASH_OK: return "DASH_OK";
+    case DASH_ERR_INVALID_ARG: return "DASH_ERR_INVALID_ARG";
+    case DASH_ERR_UNSUPPORTED: return "DASH_ERR_UNSUPPORTED";
+    case DASH_ERR_WORKSPACE: return "DASH_ERR_WORKSPACE";
+    case DASH_ERR_CUDA: return "DASH_ERR_CUDA";
+    case DASH_ERR_BOUNDS: return "DASH_ERR_BOUNDS";
+    case DASH_ERR_TIMEOUT: return "DASH_ERR_TIMEOUT";
+    default: return "DASH_ERR_UNKNOWN";
+  }
+}
+
+const char* dash_last_error(void) { return dash::g_last_error; }
+
+int dash_version(void) { return 100; }
+
+int dash_hash4d_layout(const dash_hash4d_cfg* cfg, dash_layout* out) {
+  using dash::fail;
+  if (cfg == nullptr || out == nullptr) return fail(DASH_ERR_INVALID_ARG, "cfg/out is NULL");
+  if (cfg->L < 1 || cfg->L > DASH_MAX_LEVELS) return fail(DASH_ERR_UNSUPPORTED, "L=%d outside [1,32]", cfg->L);
+  if (!(cfg->F == 1 || cfg->F == 2 || cfg->F == 4 || cfg->F == 8))
+    return fail(DASH_ERR_UNSUPPORTED, "F=%d not in {1,2,4,8}", cfg->F);
+  if (cfg->log2_T < 4 || cfg->log2_T > 28) return fail(DASH_ERR_UNSUPPORTED, "log2_T=%d outside [4,28]", cfg->log2_T);
+  if (!(cfg->nmin_s >= 1.0) || !(cfg->nmax_s >= cfg->nmin_s) || !(cfg->nmin_t >= 1.0) ||
+      !(cfg->nmax_t >= cfg->nmin_t) || cfg->nmax_s > 65535.0 || cfg->nmax_t > 65535.0)
+    return fail(DASH_ERR_INVALID_ARG, "resolutions must satisfy 1 <= N_min <= N_max <= 65535");
+  memset(out, 0, sizeof(*out));
+  out->L = cfg->L;
+  out->F = cfg->F;
+  out->log2_T = cfg->log2_T;
+  for (int i = 0; i < 4; ++i) out->primes[i] = cfg->primes[i];
+  const int64_t T = (int64_t)1 << cfg->log2_T;
+  int64_t start = 0;
+  for (int l = 0; l < cfg->L; ++l) {
+    const int32_t ns = dash::level_resolution(cfg->nmin_s, cfg->nmax_s, cfg->L, l);
+    const int32_t nt = dash::level_resolution(cfg->nmin_t, cfg->nmax_t, cfg->L, l);
+    out->res_s[l] = ns;
+    out->res_t[l] = nt;
+    const int64_t r = (int64_t)ns + 1;
+    const int64_t vertices = r * r * r * ((int64_t)nt + 1);
+    out->dense[l] = vertices <= T ? 1 : 0;
+    out->size[l] = out->dense[l] ? vertices : T;
+    out->offset[l] = start;
+    start = (start + out->size[l] + 7) & ~(int64_t)7;  // next level on a multiple of 8 entries
+  }
+  out->offset[cfg->L] = start;
+  return DASH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,227 @@
+// encode.cu -- the multiresolution 4D hash encoder G_4D of Sec. 4.2 on its
+// own: forward f_h = G_4D(x) (Eqs. 8-9), its transpose (the table-gradient
+// scatter), the corner/weight debug view, and the plain FP32 forms used as
+// the comparison baseline.  One thread per point.
+#include "dash_internal.cuh"
+
+namespace dash {
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned grid_for(long long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+// f_h for point i: per level the weighted sum of the 16 corner entries.
+template <typename TT, int F, typename OT>
+__global__ void __launch_bounds__(kThreads) encode_fwd_kernel(Geom g, Pts pts, const TT* __restrict__ table,
+                                                              OT* __restrict__ out) {
+  const long long n = point_count(pts);
+  const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (i >= n) return;
+  const float4 p = load_point(pts, i);
+  OT* row = out + i * (long long)(g.L * F);
+  for (int l = 0; l < g.L; ++l) {
+    uint32_t idx[16];
+    float w[16];
+    level_corners(g, l, p, idx, w);
+    const TT* base = table + g.offset[l] * F;
+    float acc[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) acc[f] = 0.0f;
+#pragma unroll
+    for (int b = 0; b < 16; ++b) {
+      float v[F];
+      load_entry<TT, F>(base + (size_t)idx[b] * F, v);
+#pragma unroll
+      for (int f = 0; f < F; ++f) acc[f] = fmaf(w[b], v[f], acc[f]);
+    }
+#pragma unroll
+    for (int f = 0; f < F; ++f) row[l * F + f] = from_f32<OT>(acc[f]);
+  }
+}
+
+// Transpose of the encoder with vector FP32 reductions (F = 2: one 8-byte
+// red per corner; F = 4, 8: 16-byte reds; F = 1: scalar).
+template <int F>
+__global__ void __launch_bounds__(kThreads) encode_bwd_kernel(Geom g, Pts pts, const float* __restrict__ dfeat,
+                                                              float* __restrict__ grad) {
+  const long long n = point_count(pts);
+  const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (i >= n) return;
+  const float4 p = load_point(pts, i);
+  const float* drow = dfeat + i * (long long)(g.L * F);
+  for (int l = 0; l < g.L; ++l) {
+    uint32_t idx[16];
+    float w[16];
+    level_corners(g, l, p, idx, w);
+    float d[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) d[f] = __ldg(drow + l * F + f);
+    float* base = grad + g.offset[l] * F;
+#pragma unroll
+    for (int b = 0; b < 16; ++b) {
+      float* e = base + (size_t)idx[b] * F;
+      if constexpr (F == 1) {
+        atomicAdd(e, w[b] * d[0]);
+      } else if constexpr (F == 2) {
+        red_add_v2(e, w[b] * d[0], w[b] * d[1]);
+      } else {
+#pragma unroll
+        for (int f = 0; f < F; f += 4) red_add_v4(e + f, w[b] * d[f], w[b] * d[f + 1], w[b] * d[f + 2], w[b] * d[f + 3]);
+      }
+    }
+  }
+}
+
+// Plain form of the transpose: one scalar FP32 atomicAdd per feature.
+template <int F>
+__global__ void __launch_bounds__(kThreads) plain_bwd_kernel(Geom g, Pts pts, const float* __restrict__ dfeat,
+                                                             float* __restrict__ grad) {
+  const long long n = point_count(pts);
+  const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (i >= n) return;
+  const float4 p = load_point(pts, i);
+  const float* drow = dfeat + i * (long long)(g.L * F);
+  for (int l = 0; l < g.L; ++l) {
+    uint32_t idx[16];
+    float w[16];
+    level_corners(g, l, p, idx, w);
+    float* base = grad + g.offset[l] * F;
+#pragma unroll
+    for (int b = 0; b < 16; ++b)
+#pragma unroll
+      for (int f = 0; f < F; ++f) atomicAdd(base + (size_t)idx[b] * F + f, w[b] * drow[l * F + f]);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) indices_kernel(Geom g, Pts pts, uint32_t* __restrict__ idx_out,
+                                                           float* __restrict__ w_out) {
+  const long long n = point_count(pts);
+  const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (i >= n) return;
+  const float4 p = load_point(pts, i);
+  for (int l = 0; l < g.L; ++l) {
+    uint32_t idx[16];
+    float w[16];
+    level_corners(g, l, p, idx, w);
+    const long long o = (i * g.L + l) * 16;
+#pragma unroll
+    for (int b = 0; b < 16; ++b) {
+      if (idx_out) idx_out[o + b] = idx[b];
+      if (w_out) w_out[o + b] = w[b];
+    }
+  }
+}
+
+template <typename TT, typename OT>
+int launch_fwd_t(const Geom& g, const Pts& p, const void* table, void* out, cudaStream_t st) {
+  const unsigned grid = grid_for(p.n);
+  const TT* tb = static_cast<const TT*>(table);
+  OT* o = static_cast<OT*>(out);
+  switch (g.F) {
+    case 1: encode_fwd_kernel<TT, 1, OT><<<grid, kThreads, 0, st>>>(g, p, tb, o); break;
+    case 2: encode_fwd_kernel<TT, 2, OT><<<grid, kThreads, 0, st>>>(g, p, tb, o); break;
+    case 4: encode_fwd_kernel<TT, 4, OT><<<grid, kThreads, 0, st>>>(g, p, tb, o); break;
+    default: encode_fwd_kernel<TT, 8, OT><<<grid, kThreads, 0, st>>>(g, p, tb, o); break;
+  }
+  return launch_status("encode_fwd_kernel");
+}
+
+template <typename TT>
+int launch_fwd_out(const Geom& g, const Pts& p, const void* table, void* out, int feat_dtype, cudaStream_t st) {
+  switch (feat_dtype) {
+    case DASH_F32: return launch_fwd_t<TT, float>(g, p, table, out, st);
+    case DASH_F16: return launch_fwd_t<TT, __half>(g, p, table, out, st);
+    case DASH_BF16: return launch_fwd_t<TT, __nv_bfloat16>(g, p, table, out, st);
+    default: return fail(DASH_ERR_UNSUPPORTED, "feat_dtype %d", feat_dtype);
+  }
+}
+
+int prepare(const dash_layout* layout, const dash_points* pts, Geom* g, Pts* p) {
+  if (int s = make_geom(layout, g)) return s;
+  return make_pts(pts, p);
+}
+
+}  // namespace
+}  // namespace dash
+
+extern "C" {
+
+int dash_hash4d_fwd(const dash_layout* layout, const dash_points* pts, const void* table, int table_dtype,
+                    void* feat_out, int feat_dtype, void* stream) {
+  using namespace dash;
+  Geom g;
+  Pts p;
+  if (int s = prepare(layout, pts, &g, &p)) return s;
+  if (p.n == 0) return DASH_OK;
+  if (table == nullptr || feat_out == nullptr) return fail(DASH_ERR_INVALID_ARG, "table/feat_out is NULL");
+  switch (table_dtype) {
+    case DASH_F32: return launch_fwd_out<float>(g, p, table, feat_out, feat_dtype, as_stream(stream));
+    case DASH_F16: return launch_fwd_out<__half>(g, p, table, feat_out, feat_dtype, as_stream(stream));
+    default: return fail(DASH_ERR_UNSUPPORTED, "table_dtype %d (F32 or F16)", table_dtype);
+  }
+}
+
+int dash_hash4d_bwd(const dash_layout* layout, const dash_points* pts, const float* dfeat,
+                    float* table_grad, void* stream) {
+  using namespace dash;
+  Geom g;
+  Pts p;
+  if (int s = prepare(layout, pts, &g, &p)) return s;
+  if (p.n == 0) return DASH_OK;
+  if (dfeat == nullptr || table_grad == nullptr) return fail(DASH_ERR_INVALID_ARG, "dfeat/table_grad is NULL");
+  if ((reinterpret_cast<uintptr_t>(table_grad) & 15u) != 0)
+    return fail(DASH_ERR_INVALID_ARG, "table_grad must be 16-byte aligned");
+  const unsigned grid = grid_for(p.n);
+  cudaStream_t st = as_stream(stream);
+  switch (g.F) {
+    case 1: encode_bwd_kernel<1><<<grid, kThreads, 0, st>>>(g, p, dfeat, table_grad); break;
+    case 2: encode_bwd_kernel<2><<<grid, kThreads, 0, st>>>(g, p, dfeat, table_grad); break;
+    case 4: encode_bwd_kernel<4><<<grid, kThreads, 0, st>>>(g, p, dfeat, table_grad); break;
+    default: encode_bwd_kernel<8><<<grid, kThreads, 0, st>>>(g, p, dfeat, table_grad); break;
+  }
+  return launch_status("encode_bwd_kernel");
+}
+
+int dash_hash4d_indices(const dash_layout* layout, const dash_points* pts, uint32_t* idx_out, float* w_out,
+                        void* stream) {
+  using namespace dash;
+  Geom g;
+  Pts p;
+  if (int s = prepare(layout, pts, &g, &p)) return s;
+  if (p.n == 0) return DASH_OK;
+  indices_kernel<<<grid_for(p.n), kThreads, 0, as_stream(stream)>>>(g, p, idx_out, w_out);
+  return launch_status("indices_kernel");
+}
+
+int dash_plain_hash4d_fwd(const dash_layout* layout, const dash_points* pts, const float* table,
+                          float* feat_out, void* stream) {
+  using namespace dash;
+  Geom g;
+  Pts p;
+  if (int s = prepare(layout, pts, &g, &p)) return s;
+  if (p.n == 0) return DASH_OK;
+  if (table == nullptr || feat_out == nullptr) return fail(DASH_ERR_INVALID_ARG, "table/feat_out is NULL");
+  return launch_fwd_t<float, float>(g, p, table, feat_out, as_stream(stream));
+}
+
+int dash_plain_hash4d_bwd(const dash_layout* layout, const dash_points* pts, const float* dfeat,
+                          float* table_grad, void* stream) {
+  using namespace dash;
+  Geom g;
+  Pts p;
+  if (int s = prepare(layout, pts, &g, &p)) return s;
+  if (p.n == 0) return DASH_OK;
+  if (dfeat == nullptr || table_grad == nullptr) return fail(DASH_ERR_INVALID_ARG, "dfeat/table_grad is NULL");
+  const unsigned grid = grid_for(p.n);
+  cudaStream_t st = as_stream(stream);
+  switch (g.F) {
+    case 1: plain_bwd_kernel<1><<<grid, kThreads, 0, st>>>(g, p, dfeat, table_grad); break;
+    case 2: plain_bwd_kernel<2><<<grid, kThreads, 0, st>>>(g, p, dfeat, table_grad); break;
+    case 4: plain_bwd_kernel<4><<<grid, kThreads, 0, st>>>(g, p, dfeat, table_grad); break;
+    default: plain_bwd_kernel<8><<<grid, kThreads, 0, st>>>(g, p, dfeat, table_grad); break;
+  }
+  return launch_status("plain_bwd_kernel");
+}
+
+}  // extern "C"

@@ -1,0 +1,283 @@
+"""Thin Python binding of libdash (include/dash.h): the DASH 4D-hash
+deformation path of arXiv 2507.19141, Sec. 4.2-4.3.
+
+Functions carry the C entry points' names and only marshal arguments:
+torch tensors in, device pointers and the current CUDA stream out.  Every
+step of the path runs in libdash's CUDA kernels; there is no Python or CPU
+fallback.  Importing this module fails loudly if libdash.so is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libdash.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libdash.so not built ({LIB_PATH}); run `python -c 'import __graft_entry__ as g; g.build()'`")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+MAX_LEVELS = 32
+OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_WORKSPACE, ERR_CUDA, ERR_BOUNDS, ERR_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
+F32, F16, BF16 = 0, 1, 2
+_DTYPE_CODE = {torch.float32: F32, torch.float16: F16, torch.bfloat16: BF16}
+PRIMES = (1, 2654435761, 805459861, 3674653429)
+
+
+class DashError(RuntimeError):
+    def __init__(self, status, fn):
+        self.status = status
+        msg = _lib.dash_last_error().decode()
+        super().__init__(f"{fn}: {_lib.dash_status_string(status).decode()}: {msg}")
+
+
+# ------------------------------------------------------------------ structs --
+class dash_hash4d_cfg(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("F", ctypes.c_int32), ("log2_T", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("nmin_s", ctypes.c_double), ("nmax_s", ctypes.c_double),
+                ("nmin_t", ctypes.c_double), ("nmax_t", ctypes.c_double), ("primes", ctypes.c_uint32 * 4)]
+
+
+class dash_layout(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("F", ctypes.c_int32), ("log2_T", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("primes", ctypes.c_uint32 * 4),
+                ("res_s", ctypes.c_int32 * MAX_LEVELS), ("res_t", ctypes.c_int32 * MAX_LEVELS),
+                ("dense", ctypes.c_int32 * MAX_LEVELS), ("size", ctypes.c_int64 * MAX_LEVELS),
+                ("offset", ctypes.c_int64 * (MAX_LEVELS + 1))]
+
+    @property
+    def total(self) -> int:
+        return int(self.offset[self.L])
+
+    def as_dict(self) -> dict:
+        L = self.L
+        return {"L": L, "F": self.F, "log2_T": self.log2_T, "res_s": list(self.res_s[:L]),
+                "res_t": list(self.res_t[:L]), "dense": [bool(v) for v in self.dense[:L]],
+                "size": list(self.size[:L]), "offset": list(self.offset[:L + 1])}
+
+
+class dash_points(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p), ("t", ctypes.c_void_p),
+                ("t_stride", ctypes.c_int64), ("idx", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("n_dev", ctypes.c_void_p)]
+
+
+class dash_mlp(ctypes.Structure):
+    _fields_ = [("d_in", ctypes.c_int32), ("d_hidden", ctypes.c_int32), ("d_out", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("params", ctypes.c_void_p)]
+
+
+class dash_apply(ctypes.Structure):
+    _fields_ = [("attrs_in", ctypes.c_void_p), ("attrs_out", ctypes.c_void_p), ("n_all", ctypes.c_int64)]
+
+
+class dash_smooth(ctypes.Structure):
+    _fields_ = [("lambda_r", ctypes.c_float), ("eps_s", ctypes.c_float * 3), ("eps_t", ctypes.c_float),
+                ("loss_out", ctypes.c_void_p)]
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I = ctypes.c_int
+_SZ = ctypes.c_size_t
+_SIGS = {
+    "dash_status_string": ([_I], ctypes.c_char_p),
+    "dash_last_error": ([], ctypes.c_char_p),
+    "dash_version": ([], _I),
+    "dash_hash4d_layout": ([_P, _P], _I),
+    "dash_compact_workspace_size": ([_I64], _SZ),
+    "dash_compact_dynamic": ([_P, _I64, _P, _P, _P, _SZ, _P], _I),
+    "dash_hash4d_indices": ([_P, _P, _P, _P, _P], _I),
+    "dash_hash4d_fwd": ([_P, _P, _P, _I, _P, _I, _P], _I),
+    "dash_hash4d_bwd": ([_P, _P, _P, _P, _P], _I),
+    "dash_deform_mlp_fwd": ([_P, _P, _P, _I, _P, _P, _P, _P, _P], _I),
+    "dash_deform_mlp_bwd": ([_P, _P, _P, _I, _P, _P, _P, _P, _P, _P, _P], _I),
+    "dash_plain_hash4d_fwd": ([_P, _P, _P, _P, _P], _I),
+    "dash_plain_hash4d_bwd": ([_P, _P, _P, _P, _P], _I),
+    "dash_plain_mlp_fwd": ([_P, _P, _I64, _P, _P, _P], _I),
+    "dash_plain_mlp_bwd_workspace_size": ([_P, _I64], _SZ),
+    "dash_plain_mlp_bwd": ([_P, _P, _I64, _P, _P, _P, _P, _P, _SZ, _P], _I),
+}
+for _name, (_args, _ret) in _SIGS.items():
+    _f = getattr(_lib, _name, None)
+    if _f is not None:
+        _f.argtypes = _args
+        _f.restype = _ret
+
+
+def _check(status, fn):
+    if status != OK:
+        raise DashError(status, fn)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def exported_symbols():
+    return [n for n in _SIGS if hasattr(_lib, n)]
+
+
+# ------------------------------------------------------------ utilities --
+def dash_version() -> int:
+    return int(_lib.dash_version())
+
+
+def dash_hash4d_layout(L, F, log2_T, nmin_s, nmax_s, nmin_t, nmax_t, primes=PRIMES) -> dash_layout:
+    """Eq. 7 level layout (host call)."""
+    cfg = dash_hash4d_cfg(L, F, log2_T, 0, float(nmin_s), float(nmax_s), float(nmin_t), float(nmax_t),
+                          (ctypes.c_uint32 * 4)(*primes))
+    out = dash_layout()
+    _check(_lib.dash_hash4d_layout(ctypes.byref(cfg), ctypes.byref(out)), "dash_hash4d_layout")
+    return out
+
+
+def layout_from(grid) -> dash_layout:
+    """Layout from any object with L, F, log2_T, nmin_s, nmax_s, nmin_t, nmax_t, primes."""
+    return dash_hash4d_layout(grid.L, grid.F, grid.log2_T, grid.nmin_s, grid.nmax_s, grid.nmin_t, grid.nmax_t,
+                              grid.primes)
+
+
+class Points:
+    """Device coordinates (float32 CUDA tensors x, y, z of all Gaussians, t per
+    Gaussian or a 1-element tensor broadcast), optional int32 index list and
+    optional device int64 count (n is then a capacity)."""
+
+    def __init__(self, x, y, z, t, idx=None, n=None, n_dev=None):
+        for v in (x, y, z, t):
+            assert v.is_cuda and v.dtype == torch.float32 and v.is_contiguous()
+        if idx is not None:
+            assert idx.is_cuda and idx.dtype == torch.int32 and idx.is_contiguous()
+        if n_dev is not None:
+            assert n_dev.is_cuda and n_dev.dtype == torch.int64
+        self.x, self.y, self.z, self.t, self.idx, self.n_dev = x, y, z, t, idx, n_dev
+        if n is None:
+            n = idx.numel() if idx is not None else x.numel()
+        self.n = int(n)
+        self.t_stride = 0 if (t.numel() == 1 and x.numel() != 1) else 1
+        self.c = dash_points(x.data_ptr(), y.data_ptr(), z.data_ptr(), t.data_ptr(), self.t_stride,
+                             None if idx is None else idx.data_ptr(), self.n,
+                             None if n_dev is None else n_dev.data_ptr())
+
+    @property
+    def device(self):
+        return self.x.device
+
+
+def Mlp(params: torch.Tensor, d_in: int, d_hidden: int, d_out: int) -> dash_mlp:
+    assert params.is_cuda and params.dtype == torch.float32 and params.is_contiguous()
+    return dash_mlp(d_in, d_hidden, d_out, 0, params.data_ptr())
+
+
+def mlp_param_count(d_in, d_hidden, d_out) -> int:
+    return d_hidden * d_in + d_hidden + d_hidden * d_hidden + d_hidden + d_out * d_hidden + d_out
+
+
+# ------------------------------------------------------- a1: compaction --
+def dash_compact_workspace_size(n: int) -> int:
+    return int(_lib.dash_compact_workspace_size(n))
+
+
+def dash_compact_dynamic(mask: torch.Tensor, idx_out=None, count_out=None, ws=None):
+    """Ascending dynamic index list of a uint8 device mask; returns (idx int32 [n] buffer, count int64 [1])."""
+    assert mask.is_cuda and mask.dtype == torch.uint8 and mask.is_contiguous()
+    n = mask.numel()
+    dev = mask.device
+    idx_out = torch.empty(max(n, 1), dtype=torch.int32, device=dev) if idx_out is None else idx_out
+    count_out = torch.empty(1, dtype=torch.int64, device=dev) if count_out is None else count_out
+    need = dash_compact_workspace_size(n)
+    ws = torch.empty(need, dtype=torch.uint8, device=dev) if ws is None else ws
+    _check(_lib.dash_compact_dynamic(_ptr(mask), n, _ptr(idx_out), _ptr(count_out), _ptr(ws), ws.numel(),
+                                     _stream()), "dash_compact_dynamic")
+    return idx_out, count_out
+
+
+# ---------------------------------------------------------------- encoder --
+def dash_hash4d_indices(layout: dash_layout, pts: Points, want_weights=True):
+    idx = torch.empty((pts.n, layout.L, 16), dtype=torch.int32, device=pts.device)
+    w = torch.empty((pts.n, layout.L, 16), dtype=torch.float32, device=pts.device) if want_weights else None
+    _check(_lib.dash_hash4d_indices(ctypes.byref(layout), ctypes.byref(pts.c), _ptr(idx), _ptr(w), _stream()),
+           "dash_hash4d_indices")
+    return idx, w
+
+
+def dash_hash4d_fwd(layout: dash_layout, pts: Points, table: torch.Tensor, feat_dtype=torch.float32, out=None):
+    out = torch.empty((pts.n, layout.L * layout.F), dtype=feat_dtype, device=pts.device) if out is None else out
+    _check(_lib.dash_hash4d_fwd(ctypes.byref(layout), ctypes.byref(pts.c), _ptr(table), _DTYPE_CODE[table.dtype],
+                                _ptr(out), _DTYPE_CODE[out.dtype], _stream()), "dash_hash4d_fwd")
+    return out
+
+
+def dash_hash4d_bwd(layout: dash_layout, pts: Points, dfeat: torch.Tensor, table_grad: torch.Tensor):
+    assert dfeat.dtype == torch.float32 and table_grad.dtype == torch.float32
+    _check(_lib.dash_hash4d_bwd(ctypes.byref(layout), ctypes.byref(pts.c), _ptr(dfeat), _ptr(table_grad),
+                                _stream()), "dash_hash4d_bwd")
+    return table_grad
+
+
+# ------------------------------------------------------------ plain form --
+def dash_plain_hash4d_fwd(layout, pts, table, out=None):
+    assert table.dtype == torch.float32
+    out = torch.empty((pts.n, layout.L * layout.F), dtype=torch.float32, device=pts.device) if out is None else out
+    _check(_lib.dash_plain_hash4d_fwd(ctypes.byref(layout), ctypes.byref(pts.c), _ptr(table), _ptr(out), _stream()),
+           "dash_plain_hash4d_fwd")
+    return out
+
+
+def dash_plain_hash4d_bwd(layout, pts, dfeat, table_grad):
+    _check(_lib.dash_plain_hash4d_bwd(ctypes.byref(layout), ctypes.byref(pts.c), _ptr(dfeat), _ptr(table_grad),
+                                      _stream()), "dash_plain_hash4d_bwd")
+    return table_grad
+
+
+def dash_plain_mlp_fwd(mlp: dash_mlp, feat, n=None, n_dev=None, out=None):
+    n = feat.shape[0] if n is None else n
+    out = torch.empty((mlp.d_out, n), dtype=torch.float32, device=feat.device) if out is None else out
+    _check(_lib.dash_plain_mlp_fwd(ctypes.byref(mlp), _ptr(feat), n, _ptr(n_dev), _ptr(out), _stream()),
+           "dash_plain_mlp_fwd")
+    return out
+
+
+def dash_plain_mlp_bwd(mlp: dash_mlp, feat, ddelta, mlp_grad, n=None, n_dev=None, dfeat=None, ws=None):
+    n = feat.shape[0] if n is None else n
+    dfeat = torch.empty((n, mlp.d_in), dtype=torch.float32, device=feat.device) if dfeat is None else dfeat
+    need = int(_lib.dash_plain_mlp_bwd_workspace_size(ctypes.byref(mlp), n))
+    ws = torch.empty(max(need, 1), dtype=torch.uint8, device=feat.device) if ws is None else ws
+    _check(_lib.dash_plain_mlp_bwd(ctypes.byref(mlp), _ptr(feat), n, _ptr(n_dev), _ptr(ddelta), _ptr(dfeat),
+                                   _ptr(mlp_grad), _ptr(ws), ws.numel(), _stream()), "dash_plain_mlp_bwd")
+    return dfeat
+
+
+# ------------------------------------------------------------ fused form --
+def dash_deform_mlp_fwd(layout, pts, table, mlp: dash_mlp, delta_out=None, feat_save=None, apply=None):
+    """apply: optional (attrs_in [O][n_all], attrs_out [O][n_all]) float32 pair for Eq. 10."""
+    delta_out = torch.empty((mlp.d_out, pts.n), dtype=torch.float32, device=pts.device) if delta_out is None else delta_out
+    ap = None
+    if apply is not None:
+        ai, ao = apply
+        ap = dash_apply(ai.data_ptr(), ao.data_ptr(), ai.shape[1])
+    _check(_lib.dash_deform_mlp_fwd(ctypes.byref(layout), ctypes.byref(pts.c), _ptr(table), _DTYPE_CODE[table.dtype],
+                                    ctypes.byref(mlp), _ptr(delta_out), _ptr(feat_save),
+                                    None if ap is None else ctypes.byref(ap), _stream()), "dash_deform_mlp_fwd")
+    return delta_out
+
+
+def dash_deform_mlp_bwd(layout, pts, table, mlp: dash_mlp, ddelta, table_grad, mlp_grad, feat_saved=None,
+                        smooth=None):
+    """smooth: optional (lambda_r, (eps_x, eps_y, eps_z), eps_t, loss_out float32 [1] tensor or None)."""
+    sm = None
+    if smooth is not None:
+        lam, es, et, lo = smooth
+        sm = dash_smooth(float(lam), (ctypes.c_float * 3)(*es), float(et), None if lo is None else lo.data_ptr())
+    _check(_lib.dash_deform_mlp_bwd(ctypes.byref(layout), ctypes.byref(pts.c), _ptr(table), _DTYPE_CODE[table.dtype],
+                                    ctypes.byref(mlp), _ptr(ddelta), _ptr(feat_saved), _ptr(table_grad),
+                                    _ptr(mlp_grad), None if sm is None else ctypes.byref(sm), _stream()),
+           "dash_deform_mlp_bwd")

@@ -1,0 +1,75 @@
+"""CPU-side checks of the C ABI: libdash.so builds, loads without a GPU,
+exports every function include/dash.h declares, and its host-side Eq. 7
+layout equals the oracle's (two independent implementations)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import oracle
+from paper_2507_19141_gb300 import build as dash_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^\s*[A-Za-z_][\w\s\*]*?\b(dash_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = dash_build.build()
+    return ctypes.CDLL(path)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    assert len(names) >= 14
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_the_abi():
+    from paper_2507_19141_gb300 import dash
+    declared = set(_declared_functions())
+    assert set(dash.exported_symbols()) <= declared
+    for n in declared:
+        assert hasattr(dash._lib, n)
+
+
+def test_status_strings_and_version(lib):
+    lib.dash_status_string.restype = ctypes.c_char_p
+    assert lib.dash_status_string(0) == b"DASH_OK"
+    assert lib.dash_status_string(-3) == b"DASH_ERR_WORKSPACE"
+    assert lib.dash_version() >= 100
+
+
+@pytest.mark.parametrize("cfg", [(16, 2, 19, 16, 2048, 8, 150), (4, 2, 14, 16, 128, 8, 32), (1, 1, 10, 5, 5, 3, 3),
+                                 (8, 4, 16, 4, 300, 2, 60), (32, 1, 24, 2, 8192, 2, 512), (3, 8, 12, 7, 9, 1, 2)])
+def test_host_layout_equals_oracle(cfg):
+    from paper_2507_19141_gb300 import dash
+    L, F, lt, a, b, c, d = cfg
+    got = dash.dash_hash4d_layout(L, F, lt, a, b, c, d).as_dict()
+    ref = oracle.layout(L, F, lt, a, b, c, d).as_dict()
+    assert got == ref
+
+
+def test_host_layout_rejects_bad_arguments():
+    from paper_2507_19141_gb300 import dash
+    with pytest.raises(dash.DashError) as e:
+        dash.dash_hash4d_layout(33, 2, 19, 16, 2048, 8, 150)
+    assert e.value.status == dash.ERR_UNSUPPORTED
+    with pytest.raises(dash.DashError) as e:
+        dash.dash_hash4d_layout(4, 3, 19, 16, 2048, 8, 150)
+    assert e.value.status == dash.ERR_UNSUPPORTED
+    with pytest.raises(dash.DashError) as e:
+        dash.dash_hash4d_layout(4, 2, 19, 16, 8, 8, 150)
+    assert e.value.status == dash.ERR_INVALID_ARG

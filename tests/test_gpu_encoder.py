@@ -1,0 +1,140 @@
+"""GPU parity of compaction (a1) and the encoder (a2-a6, a10) against the
+FP64 oracle, through the C ABI.  Indices and compaction must match bit for
+bit; FP32 features and gradients within 1e-5 normwise."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2507_19141_gb300 import synth
+from gpu_helpers import edge_coords, oracle_grid, rel_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("n,p,offset", [(0, 0.5, 0), (1, 1.0, 0), (4095, 0.5, 0), (4096, 0.3, 0), (4097, 0.9, 1),
+                                         (100_003, 0.5, 3), (2_000_000, 0.5, 0), (300_000, 0.0, 0),
+                                         (300_000, 1.0, 5)])
+def test_compaction_bit_exact(dashlib, n, p, offset):
+    rng = np.random.default_rng(n + offset)
+    mask = (rng.random(n) < p).astype(np.uint8) * rng.integers(1, 256, size=n, dtype=np.uint8).clip(1)
+    ref_idx, ref_cnt = oracle.compact(mask)
+    buf = torch.zeros(n + offset, dtype=torch.uint8, device="cuda")
+    buf[offset:] = to_dev(mask)
+    m = buf[offset:]  # unaligned start when offset > 0
+    idx, cnt = dashlib.dash_compact_dynamic(m)
+    torch.cuda.synchronize()
+    assert int(cnt.item()) == ref_cnt
+    assert np.array_equal(idx[:ref_cnt].cpu().numpy(), ref_idx)
+
+
+def test_compaction_rejects_small_workspace(dashlib):
+    mask = torch.ones(10_000, dtype=torch.uint8, device="cuda")
+    ws = torch.empty(8, dtype=torch.uint8, device="cuda")
+    with pytest.raises(dashlib.DashError) as e:
+        dashlib.dash_compact_dynamic(mask, ws=ws)
+    assert e.value.status == dashlib.ERR_WORKSPACE
+
+
+def _points(dashlib, coords, idx=None):
+    x, y, z, t = (to_dev(c) for c in coords)
+    return dashlib.Points(x, y, z, t, idx=None if idx is None else to_dev(idx.astype(np.int32)))
+
+
+@pytest.mark.parametrize("grid", [synth.TINY_GRID, synth.PAPER_GRID])
+def test_indices_bit_exact_and_weights(dashlib, grid):
+    rng = np.random.default_rng(21)
+    n = 3000
+    coords = edge_coords(n, rng)
+    lay = dashlib.layout_from(grid)
+    idx, w = dashlib.dash_hash4d_indices(lay, _points(dashlib, coords))
+    g = oracle_grid(grid)
+    ridx, rw = oracle.corners(g, oracle.Points(*coords))
+    assert np.array_equal(idx.cpu().numpy().astype(np.uint32), ridx)
+    wn = w.cpu().numpy()
+    assert np.max(np.abs(wn - rw)) < 1e-6
+    assert np.max(np.abs(wn.sum(axis=2) - 1.0)) < 1e-6
+
+
+def test_indices_through_index_list_and_broadcast_t(dashlib):
+    rng = np.random.default_rng(22)
+    n_all = 5000
+    x, y, z, _ = synth.scene_coords(rng, n_all)
+    t = np.array([0.37], dtype=np.float32)
+    sel = np.flatnonzero(rng.random(n_all) < 0.4).astype(np.int32)
+    lay = dashlib.layout_from(synth.PAPER_GRID)
+    pts = dashlib.Points(to_dev(x), to_dev(y), to_dev(z), to_dev(t), idx=to_dev(sel))
+    assert pts.t_stride == 0
+    idx, _ = dashlib.dash_hash4d_indices(lay, pts)
+    ridx, _ = oracle.corners(oracle_grid(synth.PAPER_GRID), oracle.Points(x, y, z, t, idx=sel, t_stride=0))
+    assert np.array_equal(idx.cpu().numpy().astype(np.uint32), ridx)
+
+
+@pytest.mark.parametrize("grid,tdtype", [(synth.TINY_GRID, np.float32), (synth.PAPER_GRID, np.float32),
+                                         (synth.PAPER_GRID, np.float16)])
+def test_encoder_forward_parity(dashlib, grid, tdtype):
+    rng = np.random.default_rng(23)
+    n = 20_000
+    coords = edge_coords(n, rng)
+    g = oracle_grid(grid)
+    table = synth.table_values(rng, g.total, grid.F, tdtype)
+    lay = dashlib.layout_from(grid)
+    pts = _points(dashlib, coords)
+    tt = to_dev(table)
+    ref = oracle.encode(g, oracle.Points(*coords), table.astype(np.float64))
+    for odt, tol in ((torch.float32, 1e-6), (torch.float16, 1e-3), (torch.bfloat16, 8e-3)):
+        f = dashlib.dash_hash4d_fwd(lay, pts, tt, feat_dtype=odt)
+        assert rel_err(f.float().cpu().numpy(), ref) < tol, odt
+    if tdtype == np.float32:
+        fp = dashlib.dash_plain_hash4d_fwd(lay, pts, tt)
+        assert rel_err(fp.cpu().numpy(), ref) < 1e-6
+
+
+@pytest.mark.parametrize("grid", [synth.TINY_GRID, synth.PAPER_GRID])
+def test_encoder_backward_parity(dashlib, grid):
+    rng = np.random.default_rng(24)
+    n = 20_000
+    coords = edge_coords(n, rng)
+    g = oracle_grid(grid)
+    dfeat = rng.standard_normal((n, grid.L * grid.F)).astype(np.float32)
+    lay = dashlib.layout_from(grid)
+    pts = _points(dashlib, coords)
+    ref = oracle.encode_bwd(g, oracle.Points(*coords), dfeat.astype(np.float64))
+    for fn in (dashlib.dash_hash4d_bwd, dashlib.dash_plain_hash4d_bwd):
+        tg = torch.zeros((g.total, grid.F), dtype=torch.float32, device="cuda")
+        fn(lay, pts, to_dev(dfeat), tg)
+        assert rel_err(tg.cpu().numpy(), ref) < 1e-5, fn.__name__
+
+
+@pytest.mark.parametrize("D,H,O", [(8, 64, 10), (32, 64, 10), (16, 32, 7)])
+def test_plain_mlp_parity(dashlib, D, H, O):
+    rng = np.random.default_rng(25 + D)
+    n = 5000
+    params = synth.mlp_params(rng, synth.MlpCfg(D, H, O), bf16=False)
+    feat = rng.uniform(-1, 1, (n, D)).astype(np.float32)
+    dd = rng.standard_normal((O, n)).astype(np.float32)
+    mlp_t = to_dev(params)
+    mlp = dashlib.Mlp(mlp_t, D, H, O)
+    out = dashlib.dash_plain_mlp_fwd(mlp, to_dev(feat))
+    ref = oracle.mlp_fwd(D, H, O, params.astype(np.float64), feat.astype(np.float64))
+    assert rel_err(out.cpu().numpy(), ref) < 1e-5
+    grad = torch.zeros(len(params), dtype=torch.float32, device="cuda")
+    dfeat = dashlib.dash_plain_mlp_bwd(mlp, to_dev(feat), to_dev(dd), grad)
+    rdf, rpg = oracle.mlp_bwd(D, H, O, params.astype(np.float64), feat.astype(np.float64), dd.astype(np.float64))
+    assert rel_err(dfeat.cpu().numpy(), rdf) < 1e-5
+    assert rel_err(grad.cpu().numpy(), rpg) < 1e-5
+
+
+def test_empty_and_device_count(dashlib):
+    """n = 0 is a no-op; a device count below the capacity limits the work."""
+    lay = dashlib.layout_from(synth.TINY_GRID)
+    rng = np.random.default_rng(26)
+    coords = [to_dev(c) for c in synth.uniform_coords(rng, 100)]
+    empty = dashlib.Points(*coords, n=0)
+    dashlib.dash_hash4d_fwd(lay, empty, torch.zeros((65536, 2), device="cuda"))
+    cnt = torch.tensor([37], dtype=torch.int64, device="cuda")
+    pts = dashlib.Points(*coords, n=100, n_dev=cnt)
+    out = torch.full((100, 8), -7.0, device="cuda")
+    dashlib.dash_hash4d_fwd(lay, pts, torch.ones((65536, 2), device="cuda"), out=out)
+    o = out.cpu().numpy()
+    assert np.allclose(o[:37], 1.0, atol=1e-6) and np.all(o[37:] == -7.0)
