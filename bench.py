@@ -1,0 +1,487 @@
+#!/usr/bin/env python
+"""Benchmark of the DASH 4D-hash deformation hot path (arXiv 2507.19141,
+Sec. 4.2-4.3) on GB300.
+
+One step = one training pass of the path over one batch of seeded synthetic
+input resident in HBM: compaction of the static/dynamic mask (2M Gaussians,
+1M dynamic), the fused forward (Eqs. 8-10: encode, tensor-core decoder,
+Eq. 10 update, per-Gaussian state for the backward) and the fused backward (decoder gradients,
+table-gradient scatter into FP32 buffers).  Metric: dynamic Gaussians per
+second.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank processes its own shard of the same size (weak
+scaling; the path needs no data exchange), timed between barriers, max over
+ranks.  --impl reference times the FP64 CPU oracle on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "dynamic Gaussians/s, 4D hash enc+MLP fwd+bwd, N=1M L=16; % gather roofline"
+UNIT = "Gaussians/s"
+N_ALL = 2_000_000
+N_DYN = 1_000_000
+# algorithmic bytes per dynamic Gaussian (L=16, F=2, FP16 tables, 16 corners):
+#   forward : xyzt 16 + idx 4 + gather 16*16*4 = 1024 + delta 40 + state 80 (f_h BF16 + masks) + Eq. 10 in/out 80
+#   backward: xyzt 16 + idx 4 + state 80 + ddelta 40 + scatter 16*16*8 = 2048 (FP32 read-modify-write units)
+FWD_BYTES = 16 + 4 + 1024 + 40 + 80 + 80
+BWD_BYTES = 16 + 4 + 80 + 40 + 2048
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--n-dyn", type=int, default=N_DYN)
+    ap.add_argument("--n-all", type=int, default=N_ALL)
+    ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
+    ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (0 = calibrate to ~10 s)")
+    return ap.parse_args(argv)
+
+
+# ------------------------------------------------------------ distributed --
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def dist_init(backend):
+    import torch.distributed as dist
+    ws, rank, _ = dist_env()
+    if ws > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend, rank=rank, world_size=ws)
+    return ws, rank
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """Largest value over all ranks (the slowest rank's time)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons while running."""
+
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.5)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self):
+        return time.time()
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.3)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = [l for (ts, l) in self.lines if t0 <= ts <= t1 + 0.25]
+        if not rows:
+            rows = [l for (_, l) in self.lines]
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            f = [v.strip() for v in r.split(",")]
+            if len(f) < 10:
+                continue
+            try:
+                mhz.append(float(f[2]))
+                mx = float(f[3])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[6:10]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not mhz:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+def measured_hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            v = float(json.load(fh)["hbm_gbs"])
+            return v, "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ----------------------------------------------------------------- workload --
+class Workload:
+    """Seeded synthetic inputs of the precision/differentiation form: 2M
+    Gaussians, exactly 1M dynamic, scene-like coordinates, FP16 tables, BF16
+    decoder weights, N(0,1) upstream gradients; resident on the device."""
+
+    def __init__(self, seed, n_all, n_dyn, device):
+        import numpy as np
+        import torch
+        from paper_2507_19141_gb300 import dash, synth
+        self.np_rng = np.random.default_rng(seed)
+        rng = self.np_rng
+        self.grid, self.mlpc = synth.PAPER_GRID, synth.PAPER_MLP
+        self.n_all, self.n_dyn = n_all, n_dyn
+        self.layout = dash.layout_from(self.grid)
+        self.mask_h = synth.exact_count_mask(rng, n_all, n_dyn)
+        self.coords_h = synth.scene_coords(rng, n_all)
+        self.table_h = synth.table_values(rng, self.layout.total, self.grid.F, np.float16)
+        self.params_h = synth.mlp_params(rng, self.mlpc)
+        self.attrs_h = synth.gaussian_attrs(rng, n_all)
+        dd = synth.upstream_grad(rng, self.mlpc.d_out, n_dyn)
+        self.ddelta_h = dd
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+        self.mask = dev(self.mask_h)
+        self.x, self.y, self.z, self.t = (dev(c) for c in self.coords_h)
+        self.table = dev(self.table_h)
+        self.params = dev(self.params_h)
+        self.attrs_in = dev(self.attrs_h)
+        self.attrs_out = self.attrs_in.clone()
+        O = self.mlpc.d_out
+        # SoA buffers are sized by the capacity n_all; the device count selects the live prefix
+        self.ddelta = torch.zeros((O, n_all), dtype=torch.float32, device=device)
+        self.ddelta[:, :n_dyn] = dev(dd)
+        self.delta = torch.empty((O, n_all), dtype=torch.float32, device=device)
+        self.idx = torch.empty(n_all, dtype=torch.int32, device=device)
+        self.count = torch.zeros(1, dtype=torch.int64, device=device)
+        self.ws = torch.empty(dash.dash_compact_workspace_size(n_all), dtype=torch.uint8, device=device)
+        self.table_grad = torch.zeros((self.layout.total, self.grid.F), dtype=torch.float32, device=device)
+        self.mlp_grad = torch.zeros(self.mlpc.n_params, dtype=torch.float32, device=device)
+        self.mlp = dash.Mlp(self.params, self.mlpc.d_in, self.mlpc.d_hidden, self.mlpc.d_out)
+        self.fsave = dash.deform_state(self.mlp, n_all, device)
+        self.pts = dash.Points(self.x, self.y, self.z, self.t, idx=self.idx, n=n_all, n_dev=self.count)
+        self.dash = dash
+
+    def compact(self):
+        self.dash.dash_compact_dynamic(self.mask, idx_out=self.idx, count_out=self.count, ws=self.ws)
+
+    def forward(self):
+        self.dash.dash_deform_mlp_fwd(self.layout, self.pts, self.table, self.mlp, delta_out=self.delta,
+                                      fwd_state=self.fsave, apply=(self.attrs_in, self.attrs_out))
+
+    def backward(self, smooth=None):
+        self.dash.dash_deform_mlp_bwd(self.layout, self.pts, self.table, self.mlp, self.ddelta, self.table_grad,
+                                      self.mlp_grad, fwd_state=self.fsave, smooth=smooth)
+
+    def step(self):
+        self.compact()
+        self.forward()
+        self.backward()
+
+
+LAUNCHES_PER_STEP = 5  # compaction count/scan/write, fused forward, fused backward
+
+
+def time_steps(torch, fn, steps, stream):
+    """Times `steps` calls of fn with CUDA events on `stream`; returns ms per step."""
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(steps):
+        fn()
+    end.record(stream)
+    end.synchronize()
+    return start.elapsed_time(end) / steps
+
+
+def run_ours(args):
+    import torch
+    ws, rank = dist_init("nccl")
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    wl = Workload(seed=2 + rank, n_all=args.n_all, n_dyn=args.n_dyn, device=device)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(max(args.warmup, 3)):
+        wl.step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, per-kernel events, clocks sampled meanwhile
+    ev = {k: [] for k in ("compact", "fwd", "bwd")}
+    E = lambda: torch.cuda.Event(enable_timing=True)
+
+    def step_events():
+        marks = [E() for _ in range(4)]
+        marks[0].record(stream)
+        wl.compact()
+        marks[1].record(stream)
+        wl.forward()
+        marks[2].record(stream)
+        wl.backward()
+        marks[3].record(stream)
+        ev["compact"].append((marks[0], marks[1]))
+        ev["fwd"].append((marks[1], marks[2]))
+        ev["bwd"].append((marks[2], marks[3]))
+
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.time()
+        ms = time_steps(torch, step_events, args.steps, stream)
+        torch.cuda.synchronize()
+        barrier()
+        t1 = time.time()
+    ms = max_over_ranks(ms, device)
+    clocks = clk.summary(t0, t1)
+    per_kernel = {k: statistics.mean(a.elapsed_time(b) for a, b in v) for k, v in ev.items()}
+
+    n_units = args.n_dyn * ws
+    value = n_units / (ms / 1e3)
+    peak, peak_kind = measured_hbm_peak()
+    dom = max(("fwd", "bwd"), key=lambda k: per_kernel[k])
+    dom_bytes = (FWD_BYTES if dom == "fwd" else BWD_BYTES) * args.n_dyn
+    achieved = dom_bytes / (per_kernel[dom] / 1e3) / 1e9
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "fp16 tables / bf16 MLP / fp32 acc+grads",
+        "data": "synthetic (seeded; stands in for Neural 3D Video / Technicolor scenes)",
+        "config": {"workload": "DASH 4D-hash deformation step: compaction of 2M Gaussians (1M dynamic) + fused "
+                               "encoder/decoder forward (Eq. 10 applied, f_h saved) + fused backward; L=16 F=2 "
+                               "T=2^19 res 16->2048 / 8->150, decoder 32-64-64-10",
+                   "n_dynamic_per_gpu": args.n_dyn, "n_gaussians_per_gpu": args.n_all,
+                   "l2": "working set ~0.4 GB/step > 129 MB L2 (no flush); tables stay L2-warm as across frames",
+                   "parallelism": f"{ws} independent shard(s)"},
+        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+        "per_kernel_ms": per_kernel,
+        "roofline": {"bound": "hbm", "kernel": f"fused {dom}", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
+                     "algorithmic_bytes_per_gaussian": FWD_BYTES if dom == "fwd" else BWD_BYTES,
+                     "traffic": None},
+        "clocks": clocks,
+    }
+    if rank == 0:
+        out["e2e"] = run_e2e(torch, wl, args, stream)
+    if rank == 0 and not args.no_extras:
+        out["extras"] = run_extras(torch, wl, args, stream)
+        out["cpu_baseline"] = cpu_baseline(args, wl)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    barrier()
+
+
+def run_e2e(torch, wl, args, stream):
+    """Same step through the public API from pinned HOST buffers: H2D of the
+    mask, coordinates and upstream gradient, D2H of the offsets and decoder
+    gradient, inside the timed region."""
+    n, na = args.n_dyn, args.n_all
+    pin = lambda a: torch.from_numpy(a).pin_memory()
+    mask_h = pin(wl.mask_h)
+    xyzt_h = [pin(c) for c in wl.coords_h]
+    dd_h = pin(wl.ddelta_h)
+    delta_h = torch.empty((wl.mlpc.d_out, n), dtype=torch.float32).pin_memory()
+    grad_h = torch.empty(wl.mlpc.n_params, dtype=torch.float32).pin_memory()
+    h2d = mask_h.numel() + sum(c.numel() * 4 for c in xyzt_h) + dd_h.numel() * 4
+    d2h = delta_h.numel() * 4 + grad_h.numel() * 4
+
+    def e2e_step():
+        wl.mask.copy_(mask_h, non_blocking=True)
+        for d, h in zip((wl.x, wl.y, wl.z, wl.t), xyzt_h):
+            d.copy_(h, non_blocking=True)
+        wl.ddelta[:, :n].copy_(dd_h, non_blocking=True)
+        wl.step()
+        delta_h.copy_(wl.delta[:, :n], non_blocking=True)
+        grad_h.copy_(wl.mlp_grad, non_blocking=True)
+
+    steps = max(10, min(args.steps, 50))
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ms = time_steps(torch, e2e_step, steps, stream)
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t0) * 1e3 / steps
+    ms = max(ms, wall)
+    return {"value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+
+def run_extras(torch, wl, args, stream):
+    """Secondary rows: forward only, backward with the Eq. 11 term, the plain
+    FP32 GPU form at the same N, and a cold-L2 step."""
+    from paper_2507_19141_gb300 import dash
+    n = args.n_dyn
+    reps = 30
+    res = {}
+    for _ in range(3):
+        wl.forward()
+    res["fwd_ms"] = time_steps(torch, wl.forward, reps, stream)
+    loss = torch.zeros(1, dtype=torch.float32, device=wl.table.device)
+    smooth = (1.0, (1 / 2048, 1 / 2048, 1 / 2048), 1 / 300, loss)
+    wl.backward(smooth)
+    res["bwd_smooth_ms"] = time_steps(torch, lambda: wl.backward(smooth), reps, stream)
+    res["fwd_bwd_smooth_gaussians_per_s"] = n / ((res["fwd_ms"] + res["bwd_smooth_ms"]) / 1e3)
+    res["fwd_gaussians_per_s"] = n / (res["fwd_ms"] / 1e3)
+    # plain FP32 GPU form (baseline to beat): FP32 tables, f_h in HBM, CUDA-core decoder, scalar atomics
+    tab32 = wl.table.float()
+    grad32 = torch.zeros_like(wl.table_grad)
+    feat = torch.empty((n, wl.mlpc.d_in), dtype=torch.float32, device=wl.table.device)
+    dfeat = torch.empty_like(feat)
+    delta = torch.empty((wl.mlpc.d_out, n), dtype=torch.float32, device=wl.table.device)
+    dd = wl.ddelta[:, :n].contiguous()
+    mg = torch.zeros_like(wl.mlp_grad)
+    wsz = torch.empty(4 * wl.mlpc.d_hidden * n * 4, dtype=torch.uint8, device=wl.table.device)
+    torch.cuda.synchronize()
+    pts = dash.Points(wl.x, wl.y, wl.z, wl.t, idx=wl.idx[:n].contiguous(), n=n)
+
+    def plain():
+        dash.dash_compact_dynamic(wl.mask, idx_out=wl.idx, count_out=wl.count, ws=wl.ws)
+        dash.dash_plain_hash4d_fwd(wl.layout, pts, tab32, out=feat)
+        dash.dash_plain_mlp_fwd(wl.mlp, feat, out=delta)
+        dash.dash_plain_mlp_bwd(wl.mlp, feat, dd, mg, dfeat=dfeat, ws=wsz)
+        dash.dash_plain_hash4d_bwd(wl.layout, pts, dfeat, grad32)
+
+    for _ in range(3):
+        plain()
+    res["plain_fp32_step_ms"] = time_steps(torch, plain, 10, stream)
+    res["plain_fp32_gaussians_per_s"] = n / (res["plain_fp32_step_ms"] / 1e3)
+    # cold L2: write 512 MB before every step, time only the step
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=wl.table.device)
+    cold = []
+    for _ in range(10):
+        flush.fill_(1)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        wl.step()
+        b.record(stream)
+        b.synchronize()
+        cold.append(a.elapsed_time(b))
+    res["cold_l2_step_ms"] = statistics.median(cold)
+    res["cold_l2_gaussians_per_s"] = n / (res["cold_l2_step_ms"] / 1e3)
+    return res
+
+
+# ------------------------------------------------------------ CPU oracle --
+def oracle_rate(sample_n, seed=7):
+    """FP64 oracle forward + backward (one host thread) on `sample_n` Gaussians of
+    the same workload distribution; returns (Gaussians/s, seconds)."""
+    import numpy as np
+    import oracle
+    from paper_2507_19141_gb300 import synth
+    grid, mlpc = synth.PAPER_GRID, synth.PAPER_MLP
+    rng = np.random.default_rng(seed)
+    g = oracle.layout(grid.L, grid.F, grid.log2_T, grid.nmin_s, grid.nmax_s, grid.nmin_t, grid.nmax_t)
+    coords = synth.scene_coords(rng, sample_n)
+    table = synth.table_values(rng, g.total, grid.F, np.float16).astype(np.float64)
+    params = synth.mlp_params(rng, mlpc).astype(np.float64)
+    dd = synth.upstream_grad(rng, mlpc.d_out, sample_n).astype(np.float64)
+    pts = oracle.Points(*coords)
+    tg = np.zeros((g.total, grid.F))
+    t0 = time.perf_counter()
+    oracle.deform_fwd(g, pts, table, mlpc.d_hidden, mlpc.d_out, params)
+    oracle.deform_bwd(g, pts, table, mlpc.d_hidden, mlpc.d_out, params, dd, table_grad=tg)
+    dt = time.perf_counter() - t0
+    return sample_n / dt, dt
+
+
+def cpu_baseline(args, wl=None):
+    n = args.cpu_sample
+    if n <= 0:
+        rate, _ = oracle_rate(5000)
+        n = int(min(max(rate * 10.0, 5000), 1_000_000))
+    rate, dt = oracle_rate(n)
+    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} dynamic Gaussians of the same distribution, forward + backward, {dt:.1f} s, "
+                      f"1 host thread of {os.cpu_count()} cores"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist_init("gloo")
+        if rank != 0:
+            barrier()
+            return
+    rate, _ = oracle_rate(2000)
+    budget = 120.0  # seconds for the whole warmup + steps run
+    per_step = budget / max(1, args.steps + args.warmup)
+    sample = int(min(max(rate * per_step, 500), 100_000))
+    for i in range(args.warmup):
+        oracle_rate(sample, seed=100 + i)
+    total_t, total_n = 0.0, 0
+    for i in range(args.steps):
+        r, dt = oracle_rate(sample, seed=200 + i)
+        total_t += dt
+        total_n += sample
+    value = total_n / total_t
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_t / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded)",
+           "config": {"workload": "FP64 CPU oracle forward + backward of the DASH deformation path, same "
+                                  "distribution, bounded sample per step", "sample_per_step": sample},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"{sample} Gaussians per step x {args.steps} steps"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    if ws > 1:
+        barrier()
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -164,30 +164,37 @@ int dash_hash4d_bwd(const dash_layout* layout, const dash_points* pts, const flo
 
 /* ------------------------- a2-a8: fused deformation forward (Eqs. 8-10) -- */
 
+/* Bytes of forward state per Gaussian that dash_deform_mlp_fwd keeps for
+ * dash_deform_mlp_bwd: f_h in BF16 (2 * d_in bytes, padded to 16) followed by
+ * the two ReLU masks of the hidden layers (16 bytes). */
+size_t dash_deform_state_size(const dash_mlp* mlp);
+
 /* Encoder + decoder MLP (+ optional Eq. 10) in one kernel: gathers the
  * tables (F32 or F16), interpolates in FP32, runs the three decoder layers on
- * the tensor cores (tcgen05, BF16 operands as a hi+lo pair for activations,
- * FP32 accumulation) and writes delta_out SoA [O][n] FP32.  feat_save
- * (optional, BF16 [n][D]) keeps f_h for dash_deform_mlp_bwd.  apply may be
- * NULL.  Supported: D = L*F <= 64, H = 64, O <= 16.
+ * the tensor cores (tcgen05, BF16 operands with the activations split into a
+ * hi + lo pair, FP32 accumulation in TMEM) and writes delta_out SoA [O][n]
+ * FP32.  fwd_state (optional, 16-byte aligned, n * dash_deform_state_size
+ * bytes) receives what the backward needs.  apply may be NULL.
+ * Supported: D = L*F <= 64, H = 64, O <= 16.
  * Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
 int dash_deform_mlp_fwd(const dash_layout* layout, const dash_points* pts,
                         const void* table, int table_dtype, const dash_mlp* mlp,
-                        float* delta_out, void* feat_save, const dash_apply* apply,
+                        float* delta_out, void* fwd_state, const dash_apply* apply,
                         void* stream);
 
 /* ---------------------- a9-a11: fused deformation backward (+ Eq. 11) -- */
 
 /* Backward of dash_deform_mlp_fwd for upstream ddelta SoA [O][n] FP32:
- * recomputes the decoder from feat_saved (BF16 [n][D] as written by the
- * forward; NULL = re-encode from the table), back-propagates on the tensor
- * cores, accumulates mlp_grad (FP32, packed like params) and scatters
- * dL/df_h into table_grad (FP32 [offset[L]][F]) with vector atomics.  With
- * smooth != NULL and lambda_r != 0 also adds the Eq. 11 term, re-encoding
- * p, p + e_s and p + e_t in the kernel.  Supported shapes as the forward. */
+ * recomputes the decoder from fwd_state (as written by the forward, whose
+ * ReLU masks it reuses; NULL = re-encode f_h in FP32 and recompute the masks),
+ * back-propagates on the tensor cores (BF16 operands, FP32 accumulation),
+ * accumulates mlp_grad (FP32, packed like params) and scatters dL/df_h into
+ * table_grad (FP32 [offset[L]][F], 16-byte aligned) with vector atomics.
+ * With smooth != NULL and lambda_r != 0 also adds the Eq. 11 term,
+ * re-encoding p, p + e_s and p + e_t in the kernel.  Shapes as the forward. */
 int dash_deform_mlp_bwd(const dash_layout* layout, const dash_points* pts,
                         const void* table, int table_dtype, const dash_mlp* mlp,
-                        const float* ddelta, const void* feat_saved, float* table_grad,
+                        const float* ddelta, const void* fwd_state, float* table_grad,
                         float* mlp_grad, const dash_smooth* smooth, void* stream);
 
 /* ------------------------ plain FP32 form (comparison baseline) -------- */

@@ -1,0 +1,568 @@
+// deform_bwd.cu -- a9-a11 fused: backward of the deformation decoder and of
+// the 4D hash encoder (the learnable tables of Sec. 4.2), plus the Eq. 11
+// smoothness term, in one persistent kernel.
+//
+// Per group of 4 warps and tile of 128 Gaussians (thread r = Gaussian r =
+// TMEM lane r):
+//   1. f_h: the BF16 copy in the forward state, or, with the smoothness term
+//      on (or no state), a fresh FP32 encoding; the perturbed points
+//      p + e_s, p + e_t are encoded level by level and their gradient
+//      -2 lambda/n (f(p) - f(p+e)) scattered at once (never stored).
+//   2. z1 = [f_h | 1] [W1 | b1]^T, h1 = relu(z1); z2 likewise (tensor cores,
+//      hi + lo operands).  The ReLU masks come from the forward state (the
+//      forward's accurate pre-activations); without a state they are taken
+//      from this recompute, which is then fed FP32-accurate f_h.
+//   3. dh2 = ddelta W3, dz2 = dh2 * [z2 > 0]; dh1 = dz2 W2, dz1 = dh1 * [z1 > 0];
+//      df_h = dz1 W1 -- the weight tiles of the forward read with the
+//      transpose bit set.
+//   4. dW^T += A^T dZ with the Gaussians as the contraction axis: the
+//      activation tiles read MN-major; their constant-one column makes the
+//      row after the last feature the bias gradient.  Accumulated in TMEM
+//      over all tiles of the CTA and flushed with one atomic per weight.
+//   5. table_grad[corner] += w * (df_h + smoothness term) with vector FP32
+//      reductions (red.global.add.v2.f32 for F = 2).
+#include "deform_common.cuh"
+
+namespace dash {
+namespace fused {
+namespace {
+
+__device__ unsigned int g_bwd_flags;  // bit 0: an MMA completion wait gave up
+
+constexpr int kKH = kHidden + 16;        // h2 tile and W3 tile K: [h | 1, 0..]
+constexpr int kKH2 = 2 * kHidden + 16;   // h1 tile and W2 tile K: [hi | 1, 0.. | lo]
+constexpr int kKG = kHidden;             // dz tile K
+constexpr int kKO = kOutPad;             // ddelta tile K
+constexpr uint32_t kTmemCols = 256;      // S (64) | dW1 (64) | dW2 (64) | dW3 (16)
+constexpr uint32_t kColS = 0, kColW1 = 64, kColW2 = 128, kColW3 = 192;
+
+struct BwdArgs {
+  Geom g;
+  Pts pts;
+  const void* table;
+  const float* params;
+  int D, Dp, O;
+  const float* ddelta;
+  long long n_cap;
+  const uint8_t* state;
+  float* table_grad;
+  float* mlp_grad;
+  float lambda_r;
+  float eps_s[3];
+  float eps_t;
+  float* loss_out;
+  unsigned int* flags;
+  uint32_t off_w2, off_w3, off_f, off_h1, off_x, off_g3, off_bar, group_bytes;
+};
+
+__device__ __forceinline__ bool wait_mma(uint32_t bar, uint32_t phase, unsigned int* flags, volatile int* abort) {
+  if (tc::mbar_wait(bar, phase, kWaitIters)) return true;
+  atomicOr(flags, 1u);
+  *abort = 1;
+  return false;
+}
+
+// One MMA chain over K (step 16) with per-operand descriptor strides.
+struct Op {
+  uint32_t addr, lbo, sbo, kstep;  // kstep: start-address advance per 16 K
+};
+
+__device__ __forceinline__ void issue(uint32_t tmem, Op a, Op b, int K, uint32_t idesc, bool accumulate) {
+  for (int k = 0; k < K; k += 16) {
+    const uint32_t s = (uint32_t)(k / 16);
+    const uint64_t ad = tc::smem_desc(a.addr + s * a.kstep, a.lbo, a.sbo);
+    const uint64_t bd = tc::smem_desc(b.addr + s * b.kstep, b.lbo, b.sbo);
+    tc::mma_bf16(tmem, ad, bd, idesc, (accumulate || k > 0) ? 1u : 0u);
+  }
+}
+
+// K-major operand (rows = MN axis, tile K extent KE).
+__device__ __forceinline__ Op kmajor(const uint8_t* t, int KE) {
+  return Op{tc::smem_addr(t), 128u, (uint32_t)KE * 16u, 256u};
+}
+// The same tile read transposed: its rows become the K axis.
+__device__ __forceinline__ Op mnmajor(const uint8_t* t, int KE) {
+  return Op{tc::smem_addr(t), (uint32_t)KE * 16u, 128u, (uint32_t)KE * 32u};
+}
+
+template <int F>
+__device__ __forceinline__ void scatter_level(float* __restrict__ grad, long long off, const uint32_t idx[16],
+                                              const float w[16], const float d[F]) {
+  float* base = grad + off * F;
+#pragma unroll
+  for (int b = 0; b < 16; ++b) {
+    float* e = base + (size_t)idx[b] * F;
+    if constexpr (F == 1) {
+      atomicAdd(e, w[b] * d[0]);
+    } else if constexpr (F == 2) {
+      red_add_v2(e, w[b] * d[0], w[b] * d[1]);
+    } else {
+#pragma unroll
+      for (int f = 0; f < F; f += 4) red_add_v4(e + f, w[b] * d[f], w[b] * d[f + 1], w[b] * d[f + 2], w[b] * d[f + 3]);
+    }
+  }
+}
+
+template <typename TT, int F>
+__device__ __forceinline__ void gather_level(const TT* __restrict__ table, long long off, const uint32_t idx[16],
+                                             const float w[16], float acc[F]) {
+  const TT* base = table + off * F;
+#pragma unroll
+  for (int f = 0; f < F; ++f) acc[f] = 0.0f;
+#pragma unroll
+  for (int b = 0; b < 16; ++b) {
+    float e[F];
+    load_entry<TT, F>(base + (size_t)idx[b] * F, e);
+#pragma unroll
+    for (int f = 0; f < F; ++f) acc[f] = fmaf(w[b], e[f], acc[f]);
+  }
+}
+
+__device__ __forceinline__ float4 perturb(float4 p, float ex, float ey, float ez, float et) {
+  return make_float4(clamp01(__fadd_rn(p.x, ex)), clamp01(__fadd_rn(p.y, ey)), clamp01(__fadd_rn(p.z, ez)),
+                     clamp01(__fadd_rn(p.w, et)));
+}
+
+template <typename TT, int F>
+__global__ void __launch_bounds__(kRows, 1) deform_bwd_kernel(const __grid_constant__ BwdArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int r = threadIdx.x, q = r >> 5;
+  const int KF = 2 * a.Dp + 16;
+  uint8_t* w1 = smem;
+  uint8_t* w2 = smem + a.off_w2;
+  uint8_t* w3 = smem + a.off_w3;
+  uint8_t* Ft = smem + a.off_f;
+  uint8_t* H1 = smem + a.off_h1;  // later reused for dz1
+  uint8_t* X = smem + a.off_x;    // h2, later dz2
+  uint8_t* G3 = smem + a.off_g3;
+  uint64_t* bar_p = reinterpret_cast<uint64_t*>(smem + a.off_bar);
+  volatile uint32_t* holder = reinterpret_cast<volatile uint32_t*>(smem + a.off_bar + 8);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + a.off_bar + 12);
+
+  const float* W1 = a.params;
+  const float* b1 = W1 + kHidden * a.D;
+  const float* W2 = b1 + kHidden;
+  const float* b2 = W2 + kHidden * kHidden;
+  const float* W3 = b2 + kHidden;
+  const float* b3 = W3 + a.O * kHidden;
+  build_weight_tile(w1, kHidden, KF, a.Dp, true, a.D, kHidden, W1, b1, r, kRows);
+  build_weight_tile(w2, kHidden, kKH2, kHidden, true, kHidden, kHidden, W2, b2, r, kRows);
+  build_weight_tile(w3, kOutPad, kKH, kHidden, false, kHidden, a.O, W3, b3, r, kRows);
+  if (r == 0) {
+    tc::mbar_init(tc::smem_addr(bar_p), 1);
+    tc::mbar_init_fence();
+    *abort_flag = 0;
+  }
+  if (r < 32) tc::tmem_alloc(tc::smem_addr(const_cast<uint32_t*>(holder)), kTmemCols);
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *holder;
+  const uint32_t trow = tbase + ((uint32_t)(q * 32) << 16);
+  const uint32_t bar = tc::smem_addr(bar_p);
+  uint32_t phase = 0;
+
+  const TT* table = static_cast<const TT*>(a.table);
+  const long long n = point_count(a.pts);
+  const long long ntiles = (n + kRows - 1) / kRows;
+  const bool smooth = a.lambda_r != 0.0f;
+  const float scale = n > 0 ? 2.0f * a.lambda_r / (float)n : 0.0f;
+  float loss = 0.0f;
+  bool had_tile = false;
+
+  const uint32_t id_fwd = tc::idesc_bf16(kRows, kHidden, 0, 0);
+  const uint32_t id_dh = tc::idesc_bf16(kRows, kHidden, 0, 1);
+  const uint32_t id_df = tc::idesc_bf16(kRows, a.Dp, 0, 1);
+  const uint32_t id_w = tc::idesc_bf16(kRows, kHidden, 1, 1);
+  const uint32_t id_w3 = tc::idesc_bf16(kRows, kOutPad, 1, 1);
+
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long row = tile * kRows + r;
+    const bool valid = row < n;
+    const float4 p = valid ? load_point(a.pts, row) : make_float4(0.f, 0.f, 0.f, 0.f);
+
+    // ---- 1. f_h operand row [hi | 1 | lo], and the smoothness term's own scatters
+    float dreg[64];
+    constexpr int kLPC = 8 / F;
+    const bool encode = smooth || a.state == nullptr;
+    const uint8_t* srow = (valid && a.state != nullptr) ? a.state + row * state_stride(a.D) : nullptr;
+    for (int c = 0; c < a.Dp / 8; ++c) {
+      float v[8];
+      if (encode) {
+#pragma unroll
+        for (int j = 0; j < kLPC; ++j) {
+          const int l = c * kLPC + j;
+          float fp[F];
+#pragma unroll
+          for (int f = 0; f < F; ++f) fp[f] = 0.0f;
+          if (valid && l < a.g.L) {
+            uint32_t idx[16];
+            float w[16];
+            level_corners(a.g, l, p, idx, w);
+            gather_level<TT, F>(table, a.g.offset[l], idx, w, fp);
+            if (smooth) {
+              float dp[F];
+#pragma unroll
+              for (int f = 0; f < F; ++f) dp[f] = 0.0f;
+#pragma unroll
+              for (int e = 0; e < 2; ++e) {
+                const float4 pq = e == 0 ? perturb(p, a.eps_s[0], a.eps_s[1], a.eps_s[2], 0.0f)
+                                         : perturb(p, 0.0f, 0.0f, 0.0f, a.eps_t);
+                level_corners(a.g, l, pq, idx, w);
+                float fq[F], dq[F];
+                gather_level<TT, F>(table, a.g.offset[l], idx, w, fq);
+#pragma unroll
+                for (int f = 0; f < F; ++f) {
+                  const float diff = fp[f] - fq[f];
+                  loss = fmaf(diff, diff, loss);
+                  dp[f] = fmaf(scale, diff, dp[f]);
+                  dq[f] = -scale * diff;
+                }
+                scatter_level<F>(a.table_grad, a.g.offset[l], idx, w, dq);
+              }
+#pragma unroll
+              for (int f = 0; f < F; ++f) dreg[(c * kLPC + j) * F + f] = dp[f];
+            }
+          }
+          if (!(valid && l < a.g.L) && smooth) {
+#pragma unroll
+            for (int f = 0; f < F; ++f) dreg[(c * kLPC + j) * F + f] = 0.0f;
+          }
+#pragma unroll
+          for (int f = 0; f < F; ++f) v[j * F + f] = fp[f];
+        }
+      } else {
+        const __nv_bfloat16* fs = reinterpret_cast<const __nv_bfloat16*>(srow);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int k = 8 * c + j;
+          v[j] = (srow != nullptr && k < a.D) ? __bfloat162float(fs[k]) : 0.0f;
+        }
+      }
+      uint4 hi, lo;
+      split_hi_lo8(v, hi, lo);
+      *reinterpret_cast<uint4*>(Ft + tile_off(r, 8 * c, KF)) = hi;
+      *reinterpret_cast<uint4*>(Ft + tile_off(r, a.Dp + 16 + 8 * c, KF)) = lo;
+    }
+    write_ones(Ft, r, a.Dp, KF);
+    uint32_t m1[2] = {0u, 0u}, m2[2] = {0u, 0u};
+    if (srow != nullptr) {
+      const uint4 m = *reinterpret_cast<const uint4*>(srow + state_mask_off(a.D));
+      m1[0] = m.x;
+      m1[1] = m.y;
+      m2[0] = m.z;
+      m2[1] = m.w;
+    }
+    const bool own_masks = a.state == nullptr;
+    tc::fence_async_smem();
+    __syncthreads();
+    if (*abort_flag) break;
+    if (r == 0) {
+      tc::fence_after_sync();
+      issue(tbase + kColS, kmajor(Ft, KF), kmajor(w1, KF), KF, id_fwd, false);
+      tc::mma_commit(bar);
+    }
+    wait_mma(bar, phase, a.flags, abort_flag);
+    phase ^= 1u;
+    tc::fence_after_sync();
+
+    // ---- 2. h1 = relu(z1) -> H1 [hi | 1 | lo]
+#pragma unroll
+    for (int c = 0; c < kHidden / 16; ++c) {
+      float v[16];
+      tc::tmem_ld16(trow + kColS + 16 * c, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        if (own_masks && v[j] > 0.0f) m1[c >> 1] |= 1u << ((c & 1) * 16 + j);
+        v[j] = ((m1[c >> 1] >> ((c & 1) * 16 + j)) & 1u) ? fmaxf(v[j], 0.0f) : 0.0f;
+      }
+      uint4 h0, l0, h1, l1;
+      split_hi_lo8(v, h0, l0);
+      split_hi_lo8(v + 8, h1, l1);
+      *reinterpret_cast<uint4*>(H1 + tile_off(r, 16 * c, kKH2)) = h0;
+      *reinterpret_cast<uint4*>(H1 + tile_off(r, 16 * c + 8, kKH2)) = h1;
+      *reinterpret_cast<uint4*>(H1 + tile_off(r, kHidden + 16 + 16 * c, kKH2)) = l0;
+      *reinterpret_cast<uint4*>(H1 + tile_off(r, kHidden + 16 + 16 * c + 8, kKH2)) = l1;
+    }
+    write_ones(H1, r, kHidden, kKH2);
+    tc::fence_before_sync();
+    tc::fence_async_smem();
+    __syncthreads();
+    if (*abort_flag) break;
+    if (r == 0) {
+      tc::fence_after_sync();
+      issue(tbase + kColS, kmajor(H1, kKH2), kmajor(w2, kKH2), kKH2, id_fwd, false);
+      tc::mma_commit(bar);
+    }
+    wait_mma(bar, phase, a.flags, abort_flag);
+    phase ^= 1u;
+    tc::fence_after_sync();
+
+    // ---- 3. h2 = relu(z2) -> X [h2 | 1]; ddelta -> G3
+#pragma unroll
+    for (int c = 0; c < kHidden / 16; ++c) {
+      float v[16];
+      tc::tmem_ld16(trow + kColS + 16 * c, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        if (own_masks && v[j] > 0.0f) m2[c >> 1] |= 1u << ((c & 1) * 16 + j);
+        v[j] = ((m2[c >> 1] >> ((c & 1) * 16 + j)) & 1u) ? fmaxf(v[j], 0.0f) : 0.0f;
+      }
+      uint32_t h[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) h[j] = pack_bf16x2(v[2 * j], v[2 * j + 1]);
+      *reinterpret_cast<uint4*>(X + tile_off(r, 16 * c, kKH)) = make_uint4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<uint4*>(X + tile_off(r, 16 * c + 8, kKH)) = make_uint4(h[4], h[5], h[6], h[7]);
+    }
+    write_ones(X, r, kHidden, kKH);
+    {
+      float d[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) d[j] = (valid && j < a.O) ? __ldg(a.ddelta + (long long)j * a.n_cap + row) : 0.0f;
+      uint32_t h[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) h[j] = pack_bf16x2(d[2 * j], d[2 * j + 1]);
+      *reinterpret_cast<uint4*>(G3 + tile_off(r, 0, kKO)) = make_uint4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<uint4*>(G3 + tile_off(r, 8, kKO)) = make_uint4(h[4], h[5], h[6], h[7]);
+    }
+    tc::fence_before_sync();
+    tc::fence_async_smem();
+    __syncthreads();
+    if (*abort_flag) break;
+    if (r == 0) {
+      tc::fence_after_sync();
+      // dh2 = ddelta W3  (B = W3 tile transposed: N = hidden unit, K = output)
+      issue(tbase + kColS, kmajor(G3, kKO), mnmajor(w3, kKH), kKO, id_dh, false);
+      // [dW3 | db3]^T += [h2 | 1]^T ddelta
+      issue(tbase + kColW3, mnmajor(X, kKH), mnmajor(G3, kKO), kRows, id_w3, had_tile);
+      tc::mma_commit(bar);
+    }
+    wait_mma(bar, phase, a.flags, abort_flag);
+    phase ^= 1u;
+    tc::fence_after_sync();
+
+    // ---- 4. dz2 = dh2 * m2 -> X
+#pragma unroll
+    for (int c = 0; c < kHidden / 16; ++c) {
+      float v[16];
+      tc::tmem_ld16(trow + kColS + 16 * c, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = ((m2[c >> 1] >> ((c & 1) * 16 + j)) & 1u) ? v[j] : 0.0f;
+      uint32_t h[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) h[j] = pack_bf16x2(v[2 * j], v[2 * j + 1]);
+      *reinterpret_cast<uint4*>(X + tile_off(r, 16 * c, kKG)) = make_uint4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<uint4*>(X + tile_off(r, 16 * c + 8, kKG)) = make_uint4(h[4], h[5], h[6], h[7]);
+    }
+    tc::fence_before_sync();
+    tc::fence_async_smem();
+    __syncthreads();
+    if (*abort_flag) break;
+    if (r == 0) {
+      tc::fence_after_sync();
+      issue(tbase + kColS, kmajor(X, kKG), mnmajor(w2, kKH2), kKG, id_dh, false);           // dh1 = dz2 W2
+      issue(tbase + kColW2, mnmajor(H1, kKH2), mnmajor(X, kKG), kRows, id_w, had_tile);     // dW2^T += [h1|1]^T dz2
+      tc::mma_commit(bar);
+    }
+    wait_mma(bar, phase, a.flags, abort_flag);
+    phase ^= 1u;
+    tc::fence_after_sync();
+
+    // ---- 5. dz1 = dh1 * m1 -> H1
+#pragma unroll
+    for (int c = 0; c < kHidden / 16; ++c) {
+      float v[16];
+      tc::tmem_ld16(trow + kColS + 16 * c, v);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = ((m1[c >> 1] >> ((c & 1) * 16 + j)) & 1u) ? v[j] : 0.0f;
+      uint32_t h[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) h[j] = pack_bf16x2(v[2 * j], v[2 * j + 1]);
+      *reinterpret_cast<uint4*>(H1 + tile_off(r, 16 * c, kKG)) = make_uint4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<uint4*>(H1 + tile_off(r, 16 * c + 8, kKG)) = make_uint4(h[4], h[5], h[6], h[7]);
+    }
+    tc::fence_before_sync();
+    tc::fence_async_smem();
+    __syncthreads();
+    if (*abort_flag) break;
+    if (r == 0) {
+      tc::fence_after_sync();
+      issue(tbase + kColS, kmajor(H1, kKG), mnmajor(w1, KF), kKG, id_df, false);            // df_h = dz1 W1
+      issue(tbase + kColW1, mnmajor(Ft, KF), mnmajor(H1, kKG), kRows, id_w, had_tile);     // dW1^T += [f|1]^T dz1
+      tc::mma_commit(bar);
+    }
+    wait_mma(bar, phase, a.flags, abort_flag);
+    phase ^= 1u;
+    tc::fence_after_sync();
+    had_tile = true;
+
+    // ---- 6. scatter df_h (+ smoothness gradient at p) into the tables
+    float df[64];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      if (16 * c < a.Dp) {
+        float v[16];
+        tc::tmem_ld16(trow + kColS + 16 * c, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) df[16 * c + j] = v[j];
+      }
+    }
+    tc::fence_before_sync();
+    if (valid) {
+      for (int l = 0; l < a.g.L; ++l) {
+        uint32_t idx[16];
+        float w[16];
+        level_corners(a.g, l, p, idx, w);
+        float d[F];
+#pragma unroll
+        for (int f = 0; f < F; ++f) d[f] = df[l * F + f] + (smooth ? dreg[l * F + f] : 0.0f);
+        scatter_level<F>(a.table_grad, a.g.offset[l], idx, w, d);
+      }
+    }
+  }
+
+  // ---- flush the CTA's weight gradients (rows = input unit, columns = output unit)
+  __syncthreads();
+  tc::fence_after_sync();
+  if (had_tile && !*abort_flag) {
+    float* gW1 = a.mlp_grad;
+    float* gb1 = gW1 + kHidden * a.D;
+    float* gW2 = gb1 + kHidden;
+    float* gb2 = gW2 + kHidden * kHidden;
+    float* gW3 = gb2 + kHidden;
+    float* gb3 = gW3 + a.O * kHidden;
+#pragma unroll 1
+    for (int c = 0; c < 4; ++c) {
+      float v[16];
+      tc::tmem_ld16(trow + kColW1 + 16 * c, v);
+      for (int j = 0; j < 16; ++j) {
+        const int o = 16 * c + j;
+        if (r < a.D) atomicAdd(gW1 + o * a.D + r, v[j]);
+        else if (r == a.Dp) atomicAdd(gb1 + o, v[j]);
+      }
+      tc::tmem_ld16(trow + kColW2 + 16 * c, v);
+      for (int j = 0; j < 16; ++j) {
+        const int o = 16 * c + j;
+        if (r < kHidden) atomicAdd(gW2 + o * kHidden + r, v[j]);
+        else if (r == kHidden) atomicAdd(gb2 + o, v[j]);
+      }
+    }
+    {
+      float v[16];
+      tc::tmem_ld16(trow + kColW3, v);
+      for (int j = 0; j < a.O; ++j) {
+        if (r < kHidden) atomicAdd(gW3 + j * kHidden + r, v[j]);
+        else if (r == kHidden) atomicAdd(gb3 + j, v[j]);
+      }
+    }
+  }
+  if (smooth && a.loss_out != nullptr) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
+    if ((r & 31) == 0 && n > 0) atomicAdd(a.loss_out, a.lambda_r * loss / (float)n);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (r < 32) tc::tmem_dealloc(tbase, kTmemCols);
+}
+
+template <typename TT, int F>
+int launch(BwdArgs a, cudaStream_t st) {
+  // Tiles read transposed with M = 128 rows (F, H1, X) run past their own
+  // end into the next region; G3 comes last and is read within its bounds.
+  const int KF = 2 * a.Dp + 16;
+  uint32_t off = (uint32_t)kHidden * KF * 2;
+  a.off_w2 = (off + 127) & ~127u;
+  a.off_w3 = a.off_w2 + (uint32_t)kHidden * kKH2 * 2;
+  off = a.off_w3 + (uint32_t)kOutPad * kKH * 2;
+  a.off_f = (off + 127) & ~127u;
+  a.off_h1 = a.off_f + (uint32_t)kRows * KF * 2;
+  a.off_x = a.off_h1 + (uint32_t)kRows * kKH2 * 2;
+  a.off_g3 = a.off_x + (uint32_t)kRows * kKH * 2;
+  a.off_bar = a.off_g3 + (uint32_t)kRows * kKO * 2;
+  const size_t smem = a.off_bar + 64;
+  auto kern = deform_bwd_kernel<TT, F>;
+  if (int s = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                          "cudaFuncSetAttribute(deform_bwd)"))
+    return s;
+  int per_sm = 0;
+  if (int s = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRows, smem),
+                          "occupancy(deform_bwd)"))
+    return s;
+  per_sm = per_sm < 1 ? 1 : per_sm;
+  while (per_sm * (int)kTmemCols > 512) --per_sm;
+  const long long ntiles = (a.n_cap + kRows - 1) / kRows;
+  const long long cap = (long long)per_sm * sm_count();
+  const long long grid = ntiles < cap ? ntiles : cap;
+  kern<<<(unsigned)grid, kRows, smem, st>>>(a);
+  return launch_status("deform_bwd_kernel");
+}
+
+template <typename TT>
+int dispatch(int F, BwdArgs& a, cudaStream_t st) {
+  switch (F) {
+    case 1: return launch<TT, 1>(a, st);
+    case 2: return launch<TT, 2>(a, st);
+    case 4: return launch<TT, 4>(a, st);
+    default: return launch<TT, 8>(a, st);
+  }
+}
+
+}  // namespace
+
+int check_fused_mlp(const dash_mlp* mlp, int D);
+
+unsigned int* bwd_flags_ptr() {
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_bwd_flags) != cudaSuccess) return nullptr;
+  return static_cast<unsigned int*>(p);
+}
+
+}  // namespace fused
+}  // namespace dash
+
+extern "C" int dash_deform_mlp_bwd(const dash_layout* layout, const dash_points* pts, const void* table,
+                                   int table_dtype, const dash_mlp* mlp, const float* ddelta, const void* fwd_state,
+                                   float* table_grad, float* mlp_grad, const dash_smooth* smooth, void* stream) {
+  using namespace dash;
+  using namespace dash::fused;
+  BwdArgs a;
+  memset(&a, 0, sizeof(a));
+  if (int s = make_geom(layout, &a.g)) return s;
+  if (int s = make_pts(pts, &a.pts)) return s;
+  const int D = a.g.L * a.g.F;
+  if (int s = check_fused_mlp(mlp, D)) return s;
+  if (a.pts.n == 0) return DASH_OK;
+  if (table == nullptr || ddelta == nullptr || table_grad == nullptr || mlp_grad == nullptr)
+    return fail(DASH_ERR_INVALID_ARG, "table/ddelta/table_grad/mlp_grad is NULL");
+  if ((reinterpret_cast<uintptr_t>(table_grad) & 15u) != 0)
+    return fail(DASH_ERR_INVALID_ARG, "table_grad must be 16-byte aligned");
+  a.table = table;
+  a.params = mlp->params;
+  a.D = D;
+  a.Dp = pad16(D);
+  a.O = mlp->d_out;
+  a.ddelta = ddelta;
+  a.n_cap = a.pts.n;
+  a.state = static_cast<const uint8_t*>(fwd_state);
+  if (fwd_state != nullptr && (reinterpret_cast<uintptr_t>(fwd_state) & 15u) != 0)
+    return fail(DASH_ERR_INVALID_ARG, "fwd_state must be 16-byte aligned");
+  a.table_grad = table_grad;
+  a.mlp_grad = mlp_grad;
+  if (smooth != nullptr) {
+    a.lambda_r = smooth->lambda_r;
+    for (int i = 0; i < 3; ++i) a.eps_s[i] = smooth->eps_s[i];
+    a.eps_t = smooth->eps_t;
+    a.loss_out = smooth->loss_out;
+  }
+  a.flags = bwd_flags_ptr();
+  if (a.flags == nullptr) return fail(DASH_ERR_CUDA, "cannot resolve the device flag word");
+  cudaStream_t st = as_stream(stream);
+  switch (table_dtype) {
+    case DASH_F32: return dispatch<float>(a.g.F, a, st);
+    case DASH_F16: return dispatch<__half>(a.g.F, a, st);
+    default: return fail(DASH_ERR_UNSUPPORTED, "table_dtype %d (F32 or F16)", table_dtype);
+  }
+}

@@ -8,9 +8,11 @@
 // Activation tiles hold 128 rows (one per Gaussian of the tile).  A decoder
 // layer  z = W a + b  is evaluated as one K-major MMA chain by appending a
 // constant-one column to the activations and the bias as an extra weight
-// column.  In the forward pass activations are split into a BF16 "hi" part
+// column.  Where the pre-activations must be accurate (they decide the ReLU
+// masks the backward pass uses) activations are split into a BF16 "hi" part
 // and a BF16 "lo" remainder (a = hi + lo to ~16 bits) that both multiply the
-// same weights:  K = [hi (Kd) | lo (Kd) | 1, 0 x 15].
+// same weights:  K = [hi (Kd) | 1, 0 x 15 | lo (Kd)].  The ones column sits
+// right after hi so that, read transposed (rows = K slots), it is row Kd < 128.
 #pragma once
 
 #include "dash_internal.cuh"
@@ -23,6 +25,12 @@ constexpr int kRows = 128;        // Gaussians per tile = MMA M
 constexpr int kHidden = 64;       // H of the decoder
 constexpr int kOutPad = 16;       // O padded to the MMA N granule
 constexpr uint32_t kWaitIters = 1u << 22;
+
+// Per-Gaussian forward state kept for the backward pass: f_h as BF16 (D
+// values) and the two ReLU masks of the forward's accurate pre-activations
+// (2 x 64 bits) at byte offset state_mask_off(D); row stride state_stride(D).
+__host__ __device__ constexpr int state_mask_off(int D) { return (2 * D + 15) / 16 * 16; }
+__host__ __device__ constexpr int state_stride(int D) { return state_mask_off(D) + 16; }
 
 __host__ __device__ constexpr int pad16(int v) { return (v + 15) / 16 * 16; }
 
@@ -59,24 +67,21 @@ __device__ __forceinline__ void write_ones(uint8_t* tile, int r, int kones, int 
 }
 
 // Builds a weight tile B[n][k] (N rows x KB) of  z = W a + b:
-//   k < Kd: W[n][k] (0 beyond the real width kin), repeated at k + Kd when
-//   `dup` (hi/lo operand), bias b[n] at the ones column, zeros elsewhere;
-//   rows n >= nout are zero.  W is row-major [nout][kin] FP32.
+//   k < Kd: W[n][k] (0 beyond the real width kin); k = Kd: bias b[n];
+//   Kd < k < Kd + 16: 0; with `dup`, Kd + 16 <= k < 2 Kd + 16 repeats W for
+//   the lo operand part.  Rows n >= nout are zero.  W is row-major [nout][kin].
 __device__ __forceinline__ void build_weight_tile(uint8_t* tile, int N, int KB, int Kd, bool dup, int kin, int nout,
                                                   const float* __restrict__ W, const float* __restrict__ b,
                                                   int tid, int nthreads) {
-  const int kones = dup ? 2 * Kd : Kd;
   for (int e = tid; e < N * KB; e += nthreads) {
     const int n = e / KB, k = e % KB;
     float v = 0.0f;
     if (n < nout) {
-      int kk = k;
-      if (dup && kk >= Kd && kk < 2 * Kd) kk -= Kd;
-      if (kk < Kd) {
-        v = kk < kin ? __ldg(W + (size_t)n * kin + kk) : 0.0f;
-      } else if (k == kones) {
-        v = __ldg(b + n);
-      }
+      int kk = -1;
+      if (k < Kd) kk = k;
+      else if (dup && k >= Kd + 16 && k < 2 * Kd + 16) kk = k - Kd - 16;
+      if (kk >= 0) v = kk < kin ? __ldg(W + (size_t)n * kin + kk) : 0.0f;
+      else if (k == Kd) v = __ldg(b + n);
     }
     *reinterpret_cast<__nv_bfloat16*>(tile + tile_off(n, k, KB)) = __float2bfloat16_rn(v);
   }

@@ -1,0 +1,343 @@
+// deform_fwd.cu -- a2-a8 fused: 4D hash encoding (Eqs. 8-9) of a tile of
+// 128 dynamic Gaussians, the decoder phi_d + heads (Sec. 4.2) on the 5th-gen
+// tensor cores, and the optional Eq. 10 update, in one persistent kernel.
+//
+// A CTA holds G independent groups of 4 warps.  In a group, thread r owns
+// Gaussian r of the tile and TMEM lane r: it gathers and interpolates the
+// 16 corners of every level in FP32, writes f_h as a BF16 hi+lo operand row
+// to shared memory, and after each layer reads its own accumulator row back
+// (tcgen05.ld 32x32b), applies ReLU and writes the next operand row.  Thread
+// 0 of the group issues the MMAs (M = 128, N = 64 / 64 / 16, BF16 x BF16 ->
+// FP32 in TMEM) and commits them to the group's mbarrier.
+#include "deform_common.cuh"
+
+namespace dash {
+namespace fused {
+namespace {
+
+__device__ unsigned int g_fwd_flags;  // bit 0: an MMA completion wait gave up
+
+constexpr int kKH = 2 * kHidden + 16;                    // hidden-layer operand K (hi | lo | ones)
+constexpr uint32_t kATileBytes = kRows * kKH * 2;        // 36,864 B per group
+
+struct FwdArgs {
+  Geom g;
+  Pts pts;
+  const void* table;
+  const float* params;
+  int D, Dp, O;
+  float* delta;
+  long long n_cap;
+  uint8_t* state;  // optional per-Gaussian forward state (row stride state_stride(D))
+  const float* attrs_in;
+  float* attrs_out;
+  long long n_all;
+  unsigned int* flags;
+  uint32_t off_w2, off_w3, off_a, off_bar;
+};
+
+__device__ __forceinline__ bool wait_mma(uint32_t bar, uint32_t phase, unsigned int* flags, volatile int* abort) {
+  if (tc::mbar_wait(bar, phase, kWaitIters)) return true;
+  atomicOr(flags, 1u);
+  *abort = 1;
+  return false;
+}
+
+// Encodes Gaussian `row` (Eqs. 8-9) into operand row r: K = [hi | 1 | lo],
+// and keeps a BF16 copy of f_h in the forward state.
+template <typename TT, int F>
+__device__ __forceinline__ void encode_row(const FwdArgs& a, bool valid, long long row, uint8_t* A, int r) {
+  const int KA = 2 * a.Dp + 16;
+  const float4 p = valid ? load_point(a.pts, row) : make_float4(0.f, 0.f, 0.f, 0.f);
+  const TT* table = static_cast<const TT*>(a.table);
+  constexpr int kLevelsPerChunk = 8 / F;
+  const int nchunks = a.Dp / 8;
+  for (int c = 0; c < nchunks; ++c) {
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < kLevelsPerChunk; ++j) {
+      const int l = c * kLevelsPerChunk + j;
+      float acc[F];
+#pragma unroll
+      for (int f = 0; f < F; ++f) acc[f] = 0.0f;
+      if (valid && l < a.g.L) {
+        uint32_t idx[16];
+        float w[16];
+        level_corners(a.g, l, p, idx, w);
+        const TT* base = table + a.g.offset[l] * F;
+#pragma unroll
+        for (int b = 0; b < 16; ++b) {
+          float e[F];
+          load_entry<TT, F>(base + (size_t)idx[b] * F, e);
+#pragma unroll
+          for (int f = 0; f < F; ++f) acc[f] = fmaf(w[b], e[f], acc[f]);
+        }
+      }
+#pragma unroll
+      for (int f = 0; f < F; ++f) v[j * F + f] = acc[f];
+    }
+    uint4 hi, lo;
+    split_hi_lo8(v, hi, lo);
+    *reinterpret_cast<uint4*>(A + tile_off(r, 8 * c, KA)) = hi;
+    *reinterpret_cast<uint4*>(A + tile_off(r, a.Dp + 16 + 8 * c, KA)) = lo;
+    if (valid && a.state != nullptr && 8 * c < a.D) {
+      __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(a.state + row * state_stride(a.D)) + 8 * c;
+      if ((a.D & 7) == 0) {
+        *reinterpret_cast<uint4*>(dst) = hi;
+      } else {
+        const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&hi);
+        for (int j = 0; j < 8 && 8 * c + j < a.D; ++j) dst[j] = h[j];
+      }
+    }
+  }
+  write_ones(A, r, a.Dp, KA);
+}
+
+// Reads this thread's 64 hidden pre-activations, records their ReLU mask
+// (bit j of mask[j / 32]), applies ReLU and writes the next layer's operand
+// row [hi | 1 | lo].
+__device__ __forceinline__ void hidden_epilogue(uint32_t trow, uint8_t* A, int r, uint32_t mask[2]) {
+  mask[0] = mask[1] = 0u;
+#pragma unroll
+  for (int c = 0; c < kHidden / 16; ++c) {
+    float v[16];
+    tc::tmem_ld16(trow + 16 * c, v);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (v[j] > 0.0f) mask[c >> 1] |= 1u << ((c & 1) * 16 + j);
+      v[j] = fmaxf(v[j], 0.0f);
+    }
+    uint4 h0, l0, h1, l1;
+    split_hi_lo8(v, h0, l0);
+    split_hi_lo8(v + 8, h1, l1);
+    *reinterpret_cast<uint4*>(A + tile_off(r, 16 * c, kKH)) = h0;
+    *reinterpret_cast<uint4*>(A + tile_off(r, 16 * c + 8, kKH)) = h1;
+    *reinterpret_cast<uint4*>(A + tile_off(r, kHidden + 16 + 16 * c, kKH)) = l0;
+    *reinterpret_cast<uint4*>(A + tile_off(r, kHidden + 16 + 16 * c + 8, kKH)) = l1;
+  }
+  write_ones(A, r, kHidden, kKH);
+}
+
+template <typename TT, int F, int G>
+__global__ void __launch_bounds__(G * kRows, 1) deform_fwd_kernel(const __grid_constant__ FwdArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int tid = threadIdx.x, grp = tid / kRows, r = tid % kRows, q = (tid >> 5) & 3;
+  const int KB1 = 2 * a.Dp + 16;
+  uint8_t* w1 = smem;
+  uint8_t* w2 = smem + a.off_w2;
+  uint8_t* w3 = smem + a.off_w3;
+  uint8_t* A = smem + a.off_a + grp * kATileBytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + a.off_bar);
+  volatile uint32_t* holder = reinterpret_cast<volatile uint32_t*>(smem + a.off_bar + 8 * G);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + a.off_bar + 8 * G + 16);
+
+  // decoder weights -> BF16 operand tiles (bias folded in as an extra column)
+  const float* W1 = a.params;
+  const float* b1 = W1 + kHidden * a.D;
+  const float* W2 = b1 + kHidden;
+  const float* b2 = W2 + kHidden * kHidden;
+  const float* W3 = b2 + kHidden;
+  const float* b3 = W3 + a.O * kHidden;
+  build_weight_tile(w1, kHidden, KB1, a.Dp, true, a.D, kHidden, W1, b1, tid, blockDim.x);
+  build_weight_tile(w2, kHidden, kKH, kHidden, true, kHidden, kHidden, W2, b2, tid, blockDim.x);
+  build_weight_tile(w3, kOutPad, kKH, kHidden, true, kHidden, a.O, W3, b3, tid, blockDim.x);
+  if (tid < G) {
+    tc::mbar_init(tc::smem_addr(&bars[tid]), 1);
+    abort_flag[tid] = 0;
+  }
+  if (tid == 0) tc::mbar_init_fence();
+  if (tid < 32) tc::tmem_alloc(tc::smem_addr(const_cast<uint32_t*>(holder)), G * 64);
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *holder;
+  const uint32_t tgrp = tbase + (uint32_t)grp * 64u;
+  const uint32_t trow = tgrp + ((uint32_t)(q * 32) << 16);
+  const uint32_t bar = tc::smem_addr(&bars[grp]);
+  uint32_t phase = 0;
+
+  const long long n = point_count(a.pts);
+  const long long ntiles = (n + kRows - 1) / kRows;
+  for (long long tile = (long long)blockIdx.x * G + grp; tile < ntiles; tile += (long long)gridDim.x * G) {
+    const long long row = tile * kRows + r;
+    const bool valid = row < n;
+    encode_row<TT, F>(a, valid, row, A, r);
+    tc::fence_async_smem();
+    tc::named_sync(1 + grp, kRows);
+    if (abort_flag[grp]) break;
+    if (r == 0) {
+      tc::fence_after_sync();
+      mma_chain(tgrp, A, KB1, w1, KB1, KB1, kHidden);
+      tc::mma_commit(bar);
+    }
+    wait_mma(bar, phase, a.flags, abort_flag + grp);
+    phase ^= 1u;
+    tc::fence_after_sync();
+    uint32_t m1[2], m2[2];
+    hidden_epilogue(trow, A, r, m1);
+    tc::fence_before_sync();
+    tc::fence_async_smem();
+    tc::named_sync(1 + grp, kRows);
+    if (abort_flag[grp]) break;
+    if (r == 0) {
+      tc::fence_after_sync();
+      mma_chain(tgrp, A, kKH, w2, kKH, kKH, kHidden);
+      tc::mma_commit(bar);
+    }
+    wait_mma(bar, phase, a.flags, abort_flag + grp);
+    phase ^= 1u;
+    tc::fence_after_sync();
+    hidden_epilogue(trow, A, r, m2);
+    if (valid && a.state != nullptr)
+      *reinterpret_cast<uint4*>(a.state + row * state_stride(a.D) + state_mask_off(a.D)) =
+          make_uint4(m1[0], m1[1], m2[0], m2[1]);
+    tc::fence_before_sync();
+    tc::fence_async_smem();
+    tc::named_sync(1 + grp, kRows);
+    if (abort_flag[grp]) break;
+    if (r == 0) {
+      tc::fence_after_sync();
+      mma_chain(tgrp, A, kKH, w3, kKH, kKH, kOutPad);
+      tc::mma_commit(bar);
+    }
+    wait_mma(bar, phase, a.flags, abort_flag + grp);
+    phase ^= 1u;
+    tc::fence_after_sync();
+    float o[16];
+    tc::tmem_ld16(trow, o);
+    if (valid) {
+      for (int j = 0; j < a.O; ++j) a.delta[(long long)j * a.n_cap + row] = o[j];
+      if (a.attrs_out != nullptr) {
+        const long long gi = point_row(a.pts, row);
+        for (int j = 0; j < a.O; ++j)
+          a.attrs_out[(long long)j * a.n_all + gi] = a.attrs_in[(long long)j * a.n_all + gi] + o[j];
+      }
+    }
+    tc::fence_before_sync();
+  }
+  __syncthreads();
+  tc::fence_after_sync();
+  if (tid < 32) tc::tmem_dealloc(tbase, G * 64);
+}
+
+struct Plan {
+  size_t smem;
+  uint32_t off_w2, off_w3, off_a, off_bar;
+};
+
+template <int G>
+Plan plan_for(int Dp) {
+  Plan p;
+  const uint32_t w1 = (uint32_t)kHidden * (2 * Dp + 16) * 2;
+  p.off_w2 = (w1 + 127) & ~127u;
+  p.off_w3 = p.off_w2 + (uint32_t)kHidden * kKH * 2;
+  p.off_a = (p.off_w3 + (uint32_t)kOutPad * kKH * 2 + 127) & ~127u;
+  p.off_bar = p.off_a + (uint32_t)G * kATileBytes;
+  p.smem = p.off_bar + 8 * G + 16 + 4 * G + 16;
+  return p;
+}
+
+template <typename TT, int F, int G>
+int launch(FwdArgs a, cudaStream_t st) {
+  const Plan p = plan_for<G>(a.Dp);
+  a.off_w2 = p.off_w2;
+  a.off_w3 = p.off_w3;
+  a.off_a = p.off_a;
+  a.off_bar = p.off_bar;
+  auto kern = deform_fwd_kernel<TT, F, G>;
+  if (int s = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem),
+                          "cudaFuncSetAttribute(deform_fwd)"))
+    return s;
+  int per_sm = 0;
+  if (int s = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G * kRows, p.smem),
+                          "occupancy(deform_fwd)"))
+    return s;
+  per_sm = per_sm < 1 ? 1 : per_sm;
+  while (per_sm * G * 64 > 512) --per_sm;  // TMEM columns per SM
+  const long long ntiles = (a.n_cap + kRows - 1) / kRows;
+  long long grid = (ntiles + G - 1) / G;
+  const long long cap = (long long)per_sm * sm_count();
+  grid = grid < cap ? grid : cap;
+  kern<<<(unsigned)grid, G * kRows, p.smem, st>>>(a);
+  return launch_status("deform_fwd_kernel");
+}
+
+template <typename TT>
+int dispatch_f(int F, int G, FwdArgs& a, cudaStream_t st) {
+  switch (F) {
+    case 1: return launch<TT, 1, 2>(a, st);
+    case 2:
+      if (G == 1) return launch<TT, 2, 1>(a, st);
+      if (G == 4) return launch<TT, 2, 4>(a, st);
+      return launch<TT, 2, 2>(a, st);
+    case 4: return launch<TT, 4, 2>(a, st);
+    default: return launch<TT, 8, 2>(a, st);
+  }
+}
+
+}  // namespace
+
+int fused_groups_fwd = 2;  // groups (4-warp units) per CTA; set by the tuner
+
+unsigned int* fwd_flags_ptr() {
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_fwd_flags) != cudaSuccess) return nullptr;
+  return static_cast<unsigned int*>(p);
+}
+
+int check_fused_mlp(const dash_mlp* mlp, int D) {
+  if (mlp == nullptr || mlp->params == nullptr) return fail(DASH_ERR_INVALID_ARG, "mlp/params is NULL");
+  if (mlp->d_in != D) return fail(DASH_ERR_INVALID_ARG, "mlp d_in=%d but L*F=%d", mlp->d_in, D);
+  if (D > 64 || mlp->d_hidden != kHidden || mlp->d_out < 1 || mlp->d_out > kOutPad)
+    return fail(DASH_ERR_UNSUPPORTED, "fused decoder supports L*F <= 64, H = 64, 1 <= O <= 16");
+  return DASH_OK;
+}
+
+}  // namespace fused
+}  // namespace dash
+
+extern "C" size_t dash_deform_state_size(const dash_mlp* mlp) {
+  if (mlp == nullptr || mlp->d_in < 1) return 0;
+  return (size_t)dash::fused::state_stride(mlp->d_in);
+}
+
+extern "C" int dash_deform_mlp_fwd(const dash_layout* layout, const dash_points* pts, const void* table,
+                                   int table_dtype, const dash_mlp* mlp, float* delta_out, void* fwd_state,
+                                   const dash_apply* apply, void* stream) {
+  using namespace dash;
+  using namespace dash::fused;
+  FwdArgs a;
+  memset(&a, 0, sizeof(a));
+  if (int s = make_geom(layout, &a.g)) return s;
+  if (int s = make_pts(pts, &a.pts)) return s;
+  const int D = a.g.L * a.g.F;
+  if (int s = check_fused_mlp(mlp, D)) return s;
+  if (a.pts.n == 0) return DASH_OK;
+  if (table == nullptr || delta_out == nullptr) return fail(DASH_ERR_INVALID_ARG, "table/delta_out is NULL");
+  if (fwd_state != nullptr && (reinterpret_cast<uintptr_t>(fwd_state) & 15u) != 0)
+    return fail(DASH_ERR_INVALID_ARG, "fwd_state must be 16-byte aligned");
+  if (apply != nullptr && (apply->attrs_in == nullptr || apply->attrs_out == nullptr || apply->n_all < 1))
+    return fail(DASH_ERR_INVALID_ARG, "apply needs attrs_in, attrs_out and n_all >= 1");
+  a.table = table;
+  a.params = mlp->params;
+  a.D = D;
+  a.Dp = pad16(D);
+  a.O = mlp->d_out;
+  a.delta = delta_out;
+  a.n_cap = a.pts.n;
+  a.state = static_cast<uint8_t*>(fwd_state);
+  if (apply != nullptr) {
+    a.attrs_in = apply->attrs_in;
+    a.attrs_out = apply->attrs_out;
+    a.n_all = apply->n_all;
+  }
+  a.flags = fwd_flags_ptr();
+  if (a.flags == nullptr) return fail(DASH_ERR_CUDA, "cannot resolve the device flag word");
+  cudaStream_t st = as_stream(stream);
+  switch (table_dtype) {
+    case DASH_F32: return dispatch_f<float>(a.g.F, fused_groups_fwd, a, st);
+    case DASH_F16: return dispatch_f<__half>(a.g.F, fused_groups_fwd, a, st);
+    default: return fail(DASH_ERR_UNSUPPORTED, "table_dtype %d (F32 or F16)", table_dtype);
+  }
+}

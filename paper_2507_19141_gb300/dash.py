@@ -94,6 +94,7 @@ _SIGS = {
     "dash_hash4d_indices": ([_P, _P, _P, _P, _P], _I),
     "dash_hash4d_fwd": ([_P, _P, _P, _I, _P, _I, _P], _I),
     "dash_hash4d_bwd": ([_P, _P, _P, _P, _P], _I),
+    "dash_deform_state_size": ([_P], _SZ),
     "dash_deform_mlp_fwd": ([_P, _P, _P, _I, _P, _P, _P, _P, _P], _I),
     "dash_deform_mlp_bwd": ([_P, _P, _P, _I, _P, _P, _P, _P, _P, _P, _P], _I),
     "dash_plain_hash4d_fwd": ([_P, _P, _P, _P, _P], _I),
@@ -172,9 +173,16 @@ class Points:
         return self.x.device
 
 
-def Mlp(params: torch.Tensor, d_in: int, d_hidden: int, d_out: int) -> dash_mlp:
-    assert params.is_cuda and params.dtype == torch.float32 and params.is_contiguous()
-    return dash_mlp(d_in, d_hidden, d_out, 0, params.data_ptr())
+class Mlp:
+    """Decoder description: packed FP32 parameters (a CUDA tensor this object
+    keeps alive) and the widths D -> H -> H -> O."""
+
+    def __init__(self, params: torch.Tensor, d_in: int, d_hidden: int, d_out: int):
+        assert params.is_cuda and params.dtype == torch.float32 and params.is_contiguous()
+        assert params.numel() == mlp_param_count(d_in, d_hidden, d_out)
+        self.params = params
+        self.d_in, self.d_hidden, self.d_out = d_in, d_hidden, d_out
+        self.c = dash_mlp(d_in, d_hidden, d_out, 0, params.data_ptr())
 
 
 def mlp_param_count(d_in, d_hidden, d_out) -> int:
@@ -238,26 +246,35 @@ def dash_plain_hash4d_bwd(layout, pts, dfeat, table_grad):
     return table_grad
 
 
-def dash_plain_mlp_fwd(mlp: dash_mlp, feat, n=None, n_dev=None, out=None):
+def dash_plain_mlp_fwd(mlp: Mlp, feat, n=None, n_dev=None, out=None):
     n = feat.shape[0] if n is None else n
     out = torch.empty((mlp.d_out, n), dtype=torch.float32, device=feat.device) if out is None else out
-    _check(_lib.dash_plain_mlp_fwd(ctypes.byref(mlp), _ptr(feat), n, _ptr(n_dev), _ptr(out), _stream()),
+    _check(_lib.dash_plain_mlp_fwd(ctypes.byref(mlp.c), _ptr(feat), n, _ptr(n_dev), _ptr(out), _stream()),
            "dash_plain_mlp_fwd")
     return out
 
 
-def dash_plain_mlp_bwd(mlp: dash_mlp, feat, ddelta, mlp_grad, n=None, n_dev=None, dfeat=None, ws=None):
+def dash_plain_mlp_bwd(mlp: Mlp, feat, ddelta, mlp_grad, n=None, n_dev=None, dfeat=None, ws=None):
     n = feat.shape[0] if n is None else n
     dfeat = torch.empty((n, mlp.d_in), dtype=torch.float32, device=feat.device) if dfeat is None else dfeat
-    need = int(_lib.dash_plain_mlp_bwd_workspace_size(ctypes.byref(mlp), n))
+    need = int(_lib.dash_plain_mlp_bwd_workspace_size(ctypes.byref(mlp.c), n))
     ws = torch.empty(max(need, 1), dtype=torch.uint8, device=feat.device) if ws is None else ws
-    _check(_lib.dash_plain_mlp_bwd(ctypes.byref(mlp), _ptr(feat), n, _ptr(n_dev), _ptr(ddelta), _ptr(dfeat),
+    _check(_lib.dash_plain_mlp_bwd(ctypes.byref(mlp.c), _ptr(feat), n, _ptr(n_dev), _ptr(ddelta), _ptr(dfeat),
                                    _ptr(mlp_grad), _ptr(ws), ws.numel(), _stream()), "dash_plain_mlp_bwd")
     return dfeat
 
 
 # ------------------------------------------------------------ fused form --
-def dash_deform_mlp_fwd(layout, pts, table, mlp: dash_mlp, delta_out=None, feat_save=None, apply=None):
+def dash_deform_state_size(mlp: Mlp) -> int:
+    return int(_lib.dash_deform_state_size(ctypes.byref(mlp.c)))
+
+
+def deform_state(mlp: Mlp, n: int, device) -> torch.Tensor:
+    """Buffer for the per-Gaussian forward state (uint8 [n][state_size])."""
+    return torch.empty((n, dash_deform_state_size(mlp)), dtype=torch.uint8, device=device)
+
+
+def dash_deform_mlp_fwd(layout, pts, table, mlp: Mlp, delta_out=None, fwd_state=None, apply=None):
     """apply: optional (attrs_in [O][n_all], attrs_out [O][n_all]) float32 pair for Eq. 10."""
     delta_out = torch.empty((mlp.d_out, pts.n), dtype=torch.float32, device=pts.device) if delta_out is None else delta_out
     ap = None
@@ -265,19 +282,59 @@ def dash_deform_mlp_fwd(layout, pts, table, mlp: dash_mlp, delta_out=None, feat_
         ai, ao = apply
         ap = dash_apply(ai.data_ptr(), ao.data_ptr(), ai.shape[1])
     _check(_lib.dash_deform_mlp_fwd(ctypes.byref(layout), ctypes.byref(pts.c), _ptr(table), _DTYPE_CODE[table.dtype],
-                                    ctypes.byref(mlp), _ptr(delta_out), _ptr(feat_save),
+                                    ctypes.byref(mlp.c), _ptr(delta_out), _ptr(fwd_state),
                                     None if ap is None else ctypes.byref(ap), _stream()), "dash_deform_mlp_fwd")
     return delta_out
 
 
-def dash_deform_mlp_bwd(layout, pts, table, mlp: dash_mlp, ddelta, table_grad, mlp_grad, feat_saved=None,
-                        smooth=None):
+def dash_deform_mlp_bwd(layout, pts, table, mlp: Mlp, ddelta, table_grad, mlp_grad, fwd_state=None, smooth=None):
     """smooth: optional (lambda_r, (eps_x, eps_y, eps_z), eps_t, loss_out float32 [1] tensor or None)."""
     sm = None
     if smooth is not None:
         lam, es, et, lo = smooth
         sm = dash_smooth(float(lam), (ctypes.c_float * 3)(*es), float(et), None if lo is None else lo.data_ptr())
     _check(_lib.dash_deform_mlp_bwd(ctypes.byref(layout), ctypes.byref(pts.c), _ptr(table), _DTYPE_CODE[table.dtype],
-                                    ctypes.byref(mlp), _ptr(ddelta), _ptr(feat_saved), _ptr(table_grad),
+                                    ctypes.byref(mlp.c), _ptr(ddelta), _ptr(fwd_state), _ptr(table_grad),
                                     _ptr(mlp_grad), None if sm is None else ctypes.byref(sm), _stream()),
            "dash_deform_mlp_bwd")
+
+
+# ------------------------------------------------------------- autograd --
+class DashDeform(torch.autograd.Function):
+    """delta = D(G_4D(x)) for the dynamic Gaussians (Sec. 4.2), differentiable
+    with respect to the hash tables and the decoder parameters.
+
+    forward runs dash_deform_mlp_fwd (keeping the per-Gaussian state); backward
+    runs dash_deform_mlp_bwd.  With `smooth = (lambda_r, eps_s, eps_t,
+    loss_out)` the backward also adds the gradient of lambda_r * L_r (Eq. 11)
+    and accumulates its value into loss_out.  The table gradient is computed
+    in FP32: with `table_grad` (an FP32 buffer shaped like the table) it is
+    accumulated there and None is returned for the table; otherwise it is
+    returned in the table's dtype."""
+
+    @staticmethod
+    def forward(ctx, table, params, layout, pts, dims, smooth=None, table_grad=None):
+        mlp = Mlp(params, *dims)
+        fsave = deform_state(mlp, pts.n, table.device)
+        delta = dash_deform_mlp_fwd(layout, pts, table, mlp, fwd_state=fsave)
+        ctx.save_for_backward(table, params, fsave)
+        ctx.layout, ctx.pts, ctx.dims, ctx.smooth, ctx.table_grad = layout, pts, dims, smooth, table_grad
+        return delta
+
+    @staticmethod
+    def backward(ctx, ddelta):
+        table, params, fsave = ctx.saved_tensors
+        mlp = Mlp(params, *ctx.dims)
+        tg = ctx.table_grad
+        if tg is None:
+            tg = torch.zeros(table.shape, dtype=torch.float32, device=table.device)
+        pg = torch.zeros_like(params)
+        dash_deform_mlp_bwd(ctx.layout, ctx.pts, table, mlp, ddelta.contiguous().float(), tg, pg,
+                            fwd_state=fsave, smooth=ctx.smooth)
+        gtab = None if ctx.table_grad is not None else tg.to(table.dtype)
+        return gtab, pg, None, None, None, None, None
+
+
+def deform(table, params, layout, pts, dims=(32, 64, 10), smooth=None, table_grad=None):
+    """Differentiable deformation offsets SoA [O][n] (see DashDeform)."""
+    return DashDeform.apply(table, params, layout, pts, tuple(dims), smooth, table_grad)

@@ -1,0 +1,224 @@
+"""GPU parity of the fused deformation path (encoder + tensor-core decoder,
+Eqs. 8-10; backward and Eq. 11) against the FP64 oracle through the C ABI.
+Targets: outputs within 1e-3 normwise relative error per head, gradients
+within 1e-2."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2507_19141_gb300 import synth
+from gpu_helpers import edge_coords, oracle_grid, rel_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+HEADS = ((0, 3), (3, 7), (7, 10))
+
+
+def _case(grid, mlpc, n, tdtype, seed, coords=None, n_all=None):
+    rng = np.random.default_rng(seed)
+    g = oracle_grid(grid)
+    if coords is None:
+        if n_all is None:
+            coords = synth.scene_coords(rng, n)
+            idx = None
+        else:
+            mask = synth.exact_count_mask(rng, n_all, n)
+            coords = synth.scene_coords(rng, n_all)
+            idx = np.flatnonzero(mask).astype(np.int32)
+    else:
+        idx = None
+    table = synth.table_values(rng, g.total, grid.F, tdtype)
+    params = synth.mlp_params(rng, mlpc)
+    dd = synth.upstream_grad(rng, mlpc.d_out, n)
+    return g, coords, idx, table, params, dd
+
+
+def _dev_points(dashlib, coords, idx, n):
+    x, y, z, t = (to_dev(c) for c in coords)
+    return dashlib.Points(x, y, z, t, idx=None if idx is None else to_dev(idx), n=n)
+
+
+@pytest.mark.parametrize("grid,mlpc,n,tdtype", [
+    (synth.TINY_GRID, synth.TINY_MLP, 10_000, np.float32),
+    (synth.PAPER_GRID, synth.PAPER_MLP, 20_000, np.float16),
+    (synth.PAPER_GRID, synth.PAPER_MLP, 20_000, np.float32),
+    (synth.PAPER_GRID, synth.PAPER_MLP, 300, np.float16),      # one ragged tile pair
+    (synth.PAPER_GRID, synth.PAPER_MLP, 1, np.float16),
+])
+def test_fused_forward_parity(dashlib, grid, mlpc, n, tdtype):
+    g, coords, idx, table, params, _ = _case(grid, mlpc, n, tdtype, seed=31 + n)
+    lay = dashlib.layout_from(grid)
+    pts = _dev_points(dashlib, coords, idx, n)
+    mlp = dashlib.Mlp(to_dev(params), mlpc.d_in, mlpc.d_hidden, mlpc.d_out)
+    fsave = dashlib.deform_state(dashlib.Mlp(to_dev(params), mlpc.d_in, mlpc.d_hidden, mlpc.d_out), n, "cuda")
+    delta = dashlib.dash_deform_mlp_fwd(lay, pts, to_dev(table), mlp, fwd_state=fsave).cpu().numpy()
+    ref = oracle.deform_fwd(g, oracle.Points(*coords), table.astype(np.float64), mlpc.d_hidden, mlpc.d_out,
+                            params.astype(np.float64))
+    for a, b in HEADS:
+        assert rel_err(delta[a:b], ref[a:b]) < 1e-3, (a, b, rel_err(delta[a:b], ref[a:b]))
+    fh = oracle.encode(g, oracle.Points(*coords), table.astype(np.float64))
+    fstate = fsave[:, :2 * mlpc.d_in].contiguous().view(torch.bfloat16)  # BF16 copy of f_h in the state
+    assert rel_err(fstate.float().cpu().numpy(), fh) < 8e-3
+
+
+def test_fused_forward_index_list_apply_and_edges(dashlib):
+    grid, mlpc = synth.PAPER_GRID, synth.PAPER_MLP
+    rng = np.random.default_rng(33)
+    n_all = 7000
+    coords = list(edge_coords(n_all, rng))
+    mask = synth.bernoulli_mask(rng, n_all, 0.45)
+    mask[:10] = 1  # keep the degenerate coordinates dynamic
+    idx = np.flatnonzero(mask).astype(np.int32)
+    n = len(idx)
+    g = oracle_grid(grid)
+    table = synth.table_values(rng, g.total, grid.F, np.float16)
+    params = synth.mlp_params(rng, mlpc)
+    attrs = synth.gaussian_attrs(rng, n_all)
+    lay = dashlib.layout_from(grid)
+    pts = _dev_points(dashlib, coords, idx, n)
+    mlp = dashlib.Mlp(to_dev(params), mlpc.d_in, mlpc.d_hidden, mlpc.d_out)
+    ai = to_dev(attrs)
+    ao = ai.clone()
+    delta = dashlib.dash_deform_mlp_fwd(lay, pts, to_dev(table), mlp, apply=(ai, ao)).cpu().numpy()
+    rdelta, rout = oracle.deform_fwd(g, oracle.Points(*coords, idx=idx), table.astype(np.float64), mlpc.d_hidden,
+                                     mlpc.d_out, params.astype(np.float64), attrs_in=attrs)
+    for a, b in HEADS:
+        assert rel_err(delta[a:b], rdelta[a:b]) < 1e-3
+    out = ao.cpu().numpy()
+    assert np.array_equal(out[:, mask == 0], attrs[:, mask == 0])  # static Gaussians untouched
+    assert np.max(np.abs(out[:, idx] - rout[:, idx])) < 1e-3
+
+
+def test_fused_forward_device_count(dashlib):
+    """The kernel reads the dynamic count from device memory (graph-safe)."""
+    grid, mlpc = synth.PAPER_GRID, synth.PAPER_MLP
+    g, coords, _, table, params, _ = _case(grid, mlpc, 5000, np.float16, seed=34)
+    lay = dashlib.layout_from(grid)
+    x, y, z, t = (to_dev(c) for c in coords)
+    cnt = torch.tensor([3001], dtype=torch.int64, device="cuda")
+    pts = dashlib.Points(x, y, z, t, n=5000, n_dev=cnt)
+    mlp = dashlib.Mlp(to_dev(params), mlpc.d_in, mlpc.d_hidden, mlpc.d_out)
+    out = torch.full((10, 5000), 123.0, device="cuda")
+    dashlib.dash_deform_mlp_fwd(lay, pts, to_dev(table), mlp, delta_out=out)
+    o = out.cpu().numpy()
+    ref = oracle.deform_fwd(g, oracle.Points(*[c[:3001] for c in coords]), table.astype(np.float64), 64, 10,
+                            params.astype(np.float64))
+    assert rel_err(o[:, :3001], ref) < 1e-3
+    assert np.all(o[:, 3001:] == 123.0)
+
+
+def test_fused_forward_rejects_unsupported(dashlib):
+    grid = synth.PAPER_GRID
+    lay = dashlib.layout_from(grid)
+    rng = np.random.default_rng(35)
+    coords = [to_dev(c) for c in synth.uniform_coords(rng, 10)]
+    pts = dashlib.Points(*coords)
+    p = torch.zeros(synth.MlpCfg(32, 32, 10).n_params, device="cuda")
+    with pytest.raises(dashlib.DashError) as e:
+        dashlib.dash_deform_mlp_fwd(lay, pts, torch.zeros((10, 2), device="cuda"), dashlib.Mlp(p, 32, 32, 10))
+    assert e.value.status == dashlib.ERR_UNSUPPORTED
+
+
+def _grad_errors(dashlib, grid, mlpc, n, tdtype, seed, use_saved, smooth=None, n_all=None):
+    g, coords, idx, table, params, dd = _case(grid, mlpc, n, tdtype, seed, n_all=n_all)
+    lay = dashlib.layout_from(grid)
+    pts = _dev_points(dashlib, coords, idx, n)
+    mlp = dashlib.Mlp(to_dev(params), mlpc.d_in, mlpc.d_hidden, mlpc.d_out)
+    tab = to_dev(table)
+    fsave = dashlib.deform_state(dashlib.Mlp(to_dev(params), mlpc.d_in, mlpc.d_hidden, mlpc.d_out), n, "cuda")
+    dashlib.dash_deform_mlp_fwd(lay, pts, tab, mlp, fwd_state=fsave)
+    tg = torch.zeros((g.total, grid.F), dtype=torch.float32, device="cuda")
+    pg = torch.zeros(mlpc.n_params, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    sm = None if smooth is None else (smooth[0], smooth[1], smooth[2], loss)
+    dashlib.dash_deform_mlp_bwd(lay, pts, tab, mlp, to_dev(dd), tg, pg, fwd_state=fsave if use_saved else None,
+                                smooth=sm)
+    lam, es, et = smooth if smooth is not None else (0.0, (0.0, 0.0, 0.0), 0.0)
+    rtg, rpg, rl = oracle.deform_bwd(g, oracle.Points(*coords, idx=idx), table.astype(np.float64), mlpc.d_hidden,
+                                     mlpc.d_out, params.astype(np.float64), dd.astype(np.float64), lam, es, et)
+    D, H, O = mlpc.d_in, mlpc.d_hidden, mlpc.d_out
+    bounds = np.cumsum([0, H * D, H, H * H, H, O * H, O])
+    pgn = pg.cpu().numpy()
+    errs = {"table": rel_err(tg.cpu().numpy(), rtg)}
+    for name, a, b in zip(("W1", "b1", "W2", "b2", "W3", "b3"), bounds[:-1], bounds[1:]):
+        errs[name] = rel_err(pgn[a:b], rpg[a:b])
+    if smooth is not None:
+        errs["loss"] = abs(float(loss.item()) - rl) / abs(rl)
+    return errs
+
+
+@pytest.mark.parametrize("grid,mlpc,n,tdtype,use_saved", [
+    (synth.TINY_GRID, synth.TINY_MLP, 10_000, np.float32, True),
+    (synth.PAPER_GRID, synth.PAPER_MLP, 20_000, np.float16, True),
+    (synth.PAPER_GRID, synth.PAPER_MLP, 20_000, np.float16, False),
+    (synth.PAPER_GRID, synth.PAPER_MLP, 300, np.float32, True),
+])
+def test_fused_backward_parity(dashlib, grid, mlpc, n, tdtype, use_saved):
+    errs = _grad_errors(dashlib, grid, mlpc, n, tdtype, 41 + n, use_saved)
+    assert all(v < 1e-2 for v in errs.values()), errs
+
+
+def test_fused_backward_with_index_list(dashlib):
+    errs = _grad_errors(dashlib, synth.PAPER_GRID, synth.PAPER_MLP, 6000, np.float16, 42, True, n_all=13_000)
+    assert all(v < 1e-2 for v in errs.values()), errs
+
+
+@pytest.mark.parametrize("grid,mlpc,tdtype", [(synth.TINY_GRID, synth.TINY_MLP, np.float32),
+                                              (synth.PAPER_GRID, synth.PAPER_MLP, np.float16)])
+def test_fused_backward_smoothness_term(dashlib, grid, mlpc, tdtype):
+    """Eq. 11 with the paper-shaped perturbations dx = 1/2048, dt = 1/300."""
+    smooth = (1.0, (1 / 2048, 1 / 2048, 1 / 2048), 1 / 300)
+    errs = _grad_errors(dashlib, grid, mlpc, 8000, tdtype, 43, True, smooth=smooth)
+    assert all(v < 1e-2 for v in errs.values()), errs
+
+
+def test_fused_backward_finite_differences(dashlib):
+    """Table gradient of Loss = sum(ddelta * delta) + lambda L_r from the GPU
+    backward against central differences of the GPU forward (FP32 tables)."""
+    grid, mlpc = synth.TINY_GRID, synth.TINY_MLP
+    n = 512
+    g, coords, _, table, params, dd = _case(grid, mlpc, n, np.float32, 44)
+    lay = dashlib.layout_from(grid)
+    pts = _dev_points(dashlib, coords, None, n)
+    mlp = dashlib.Mlp(to_dev(params), mlpc.d_in, mlpc.d_hidden, mlpc.d_out)
+    tab = to_dev(table)
+    ddt = to_dev(dd)
+    lam, es, et = 0.5, (1 / 2048, 1 / 2048, 1 / 2048), 1 / 300
+    tg = torch.zeros((g.total, 2), dtype=torch.float32, device="cuda")
+    pg = torch.zeros(mlpc.n_params, dtype=torch.float32, device="cuda")
+    dashlib.dash_deform_mlp_bwd(lay, pts, tab, mlp, ddt, tg, pg, smooth=(lam, es, et, None))
+    tgn = tg.cpu().numpy()
+
+    def loss(t):
+        delta = dashlib.dash_deform_mlp_fwd(lay, pts, t, mlp).double()
+        lr = torch.zeros(1, dtype=torch.float32, device="cuda")
+        scratch = torch.zeros_like(tg)
+        dashlib.dash_deform_mlp_bwd(lay, pts, t, mlp, torch.zeros_like(ddt), scratch, torch.zeros_like(pg),
+                                    smooth=(lam, es, et, lr))
+        return float((delta * ddt.double()).sum().item()) + float(lr.item())
+
+    order = np.argsort(-np.abs(tgn).max(axis=1))[:12]
+    h = 1e-2
+    for e in order:
+        for f in range(2):
+            tp = tab.clone(); tp[e, f] += h
+            tm = tab.clone(); tm[e, f] -= h
+            fd = (loss(tp) - loss(tm)) / (2 * h)
+            assert abs(fd - tgn[e, f]) < 2e-2 * max(1.0, abs(fd)), (e, f, fd, tgn[e, f])
+
+
+def test_autograd_function_matches_oracle(dashlib):
+    grid, mlpc = synth.PAPER_GRID, synth.PAPER_MLP
+    n = 4000
+    g, coords, _, table, params, dd = _case(grid, mlpc, n, np.float32, 45)
+    lay = dashlib.layout_from(grid)
+    pts = _dev_points(dashlib, coords, None, n)
+    tab = to_dev(table).requires_grad_(True)
+    par = to_dev(params).requires_grad_(True)
+    delta = dashlib.deform(tab, par, lay, pts)
+    (delta * to_dev(dd)).sum().backward()
+    rtg, rpg, _ = oracle.deform_bwd(g, oracle.Points(*coords), table.astype(np.float64), 64, 10,
+                                    params.astype(np.float64), dd.astype(np.float64))
+    assert rel_err(tab.grad.cpu().numpy(), rtg) < 1e-2
+    assert rel_err(par.grad.cpu().numpy(), rpg) < 1e-2
