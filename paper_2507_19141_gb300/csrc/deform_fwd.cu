@@ -17,7 +17,7 @@ namespace {
 
 __device__ unsigned int g_fwd_flags;  // bit 0: an MMA completion wait gave up
 
-constexpr int kKH = 2 * kHidden + 16;                    // hidden-layer operand K (hi | lo | ones)
+constexpr int kKH = 2 * kHidden + 16;                    // hidden-layer operand K (hi | ones | lo)
 constexpr uint32_t kATileBytes = kRows * kKH * 2;        // 36,864 B per group
 
 struct FwdArgs {
@@ -221,6 +221,189 @@ __global__ void __launch_bounds__(G * kRows, 1) deform_fwd_kernel(const __grid_c
   if (tid < 32) tc::tmem_dealloc(tbase, G * 64);
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialised form.  Warps 0-3 (the consumer, whose thread r owns TMEM
+// lane r) run the decoder: wait for a stage of the ring, issue layer 1 from
+// it (the MMA's completion releases the stage), then the epilogues and layers
+// 2-3 on a private operand tile.  P producer groups of 4 warps gather and
+// interpolate: producer group g fills the ring stage of every P-th tile.  The
+// latency-bound gathers of the producers overlap the consumer's MMA chain.
+// ---------------------------------------------------------------------------
+struct WsPlan {
+  size_t smem;
+  uint32_t off_w2, off_w3, off_ring, off_a2, off_bar, stage_bytes;
+};
+
+template <int P, int S>
+WsPlan ws_plan(int Dp) {
+  WsPlan p;
+  const uint32_t KA = 2 * Dp + 16;
+  const uint32_t w1 = (uint32_t)kHidden * KA * 2;
+  p.off_w2 = (w1 + 127) & ~127u;
+  p.off_w3 = p.off_w2 + (uint32_t)kHidden * kKH * 2;
+  p.off_ring = (p.off_w3 + (uint32_t)kOutPad * kKH * 2 + 127) & ~127u;
+  p.stage_bytes = (uint32_t)kRows * KA * 2;
+  p.off_a2 = p.off_ring + S * p.stage_bytes;
+  p.off_bar = p.off_a2 + kATileBytes;
+  p.smem = p.off_bar + 8 * (2 * S + 1) + 16;
+  return p;
+}
+
+template <typename TT, int F, int P, int S>
+__global__ void __launch_bounds__((P + 1) * kRows, 1) deform_fwd_ws_kernel(const __grid_constant__ FwdArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int tid = threadIdx.x;
+  const int KB1 = 2 * a.Dp + 16;
+  uint8_t* w1 = smem;
+  uint8_t* w2 = smem + a.off_w2;
+  uint8_t* w3 = smem + a.off_w3;
+  uint8_t* ring = smem + a.off_a;  // S stages of stage_bytes
+  uint8_t* A2 = smem + a.off_a + S * (uint32_t)kRows * KB1 * 2;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + a.off_bar);
+  uint64_t* empty = full + S;
+  uint64_t* mma_bar = empty + S;
+  volatile uint32_t* holder = reinterpret_cast<volatile uint32_t*>(mma_bar + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(mma_bar + 1) + 1;
+  const uint32_t stage_bytes = (uint32_t)kRows * KB1 * 2;
+
+  const float* W1 = a.params;
+  const float* b1 = W1 + kHidden * a.D;
+  const float* W2 = b1 + kHidden;
+  const float* b2 = W2 + kHidden * kHidden;
+  const float* W3 = b2 + kHidden;
+  const float* b3 = W3 + a.O * kHidden;
+  build_weight_tile(w1, kHidden, KB1, a.Dp, true, a.D, kHidden, W1, b1, tid, blockDim.x);
+  build_weight_tile(w2, kHidden, kKH, kHidden, true, kHidden, kHidden, W2, b2, tid, blockDim.x);
+  build_weight_tile(w3, kOutPad, kKH, kHidden, true, kHidden, a.O, W3, b3, tid, blockDim.x);
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      tc::mbar_init(tc::smem_addr(&full[s]), kRows);
+      tc::mbar_init(tc::smem_addr(&empty[s]), 1);
+    }
+    tc::mbar_init(tc::smem_addr(mma_bar), 1);
+    tc::mbar_init_fence();
+    *abort_flag = 0;
+  }
+  if (tid < 32) tc::tmem_alloc(tc::smem_addr(const_cast<uint32_t*>(holder)), 64);
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *holder;
+
+  const long long n = point_count(a.pts);
+  const long long ntiles = (n + kRows - 1) / kRows;
+  const long long my_tiles = ntiles > blockIdx.x ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+
+  if (tid < kRows) {
+    // ------------------------------------------------ consumer: the decoder
+    const int r = tid, q = tid >> 5;
+    const uint32_t trow = tbase + ((uint32_t)(q * 32) << 16);
+    const uint32_t mb = tc::smem_addr(mma_bar);
+    uint32_t phase = 0;
+    for (long long j = 0; j < my_tiles; ++j) {
+      const int s = (int)(j % S);
+      const uint32_t round = (uint32_t)(j / S);
+      const long long row = (blockIdx.x + j * gridDim.x) * kRows + r;
+      const bool valid = row < n;
+      if (!tc::mbar_wait(tc::smem_addr(&full[s]), round & 1u, kWaitIters)) {
+        atomicOr(a.flags, 1u);
+        *abort_flag = 1;
+      }
+      tc::named_sync(1, kRows);
+      if (*abort_flag) break;
+      if (r == 0) {
+        tc::fence_after_sync();
+        mma_chain(tbase, ring + s * stage_bytes, KB1, w1, KB1, KB1, kHidden);
+        tc::mma_commit(tc::smem_addr(&empty[s]));  // stage free once layer 1 has read it
+        tc::mma_commit(mb);
+      }
+      wait_mma(mb, phase, a.flags, abort_flag);
+      phase ^= 1u;
+      tc::fence_after_sync();
+      uint32_t m1[2], m2[2];
+      hidden_epilogue(trow, A2, r, m1);
+      tc::fence_before_sync();
+      tc::fence_async_smem();
+      tc::named_sync(1, kRows);
+      if (*abort_flag) break;
+      if (r == 0) {
+        tc::fence_after_sync();
+        mma_chain(tbase, A2, kKH, w2, kKH, kKH, kHidden);
+        tc::mma_commit(mb);
+      }
+      wait_mma(mb, phase, a.flags, abort_flag);
+      phase ^= 1u;
+      tc::fence_after_sync();
+      hidden_epilogue(trow, A2, r, m2);
+      if (valid && a.state != nullptr)
+        *reinterpret_cast<uint4*>(a.state + row * state_stride(a.D) + state_mask_off(a.D)) =
+            make_uint4(m1[0], m1[1], m2[0], m2[1]);
+      tc::fence_before_sync();
+      tc::fence_async_smem();
+      tc::named_sync(1, kRows);
+      if (*abort_flag) break;
+      if (r == 0) {
+        tc::fence_after_sync();
+        mma_chain(tbase, A2, kKH, w3, kKH, kKH, kOutPad);
+        tc::mma_commit(mb);
+      }
+      wait_mma(mb, phase, a.flags, abort_flag);
+      phase ^= 1u;
+      tc::fence_after_sync();
+      float o[16];
+      tc::tmem_ld16(trow, o);
+      if (valid) {
+        for (int k = 0; k < a.O; ++k) a.delta[(long long)k * a.n_cap + row] = o[k];
+        if (a.attrs_out != nullptr) {
+          const long long gi = point_row(a.pts, row);
+          for (int k = 0; k < a.O; ++k)
+            a.attrs_out[(long long)k * a.n_all + gi] = a.attrs_in[(long long)k * a.n_all + gi] + o[k];
+        }
+      }
+      tc::fence_before_sync();
+    }
+  } else {
+    // ------------------------------------------- producers: Eqs. 8-9 gathers
+    const int pg = tid / kRows - 1, r = tid % kRows;
+    for (long long j = pg; j < my_tiles; j += P) {
+      const int s = (int)(j % S);
+      const uint32_t round = (uint32_t)(j / S);
+      if (!tc::mbar_wait(tc::smem_addr(&empty[s]), (round & 1u) ^ 1u, kWaitIters)) {
+        atomicOr(a.flags, 1u);
+        *abort_flag = 1;
+      }
+      if (*abort_flag) break;
+      const long long row = (blockIdx.x + j * gridDim.x) * kRows + r;
+      encode_row<TT, F>(a, row < n, row, ring + s * stage_bytes, r);
+      tc::fence_async_smem();
+      tc::mbar_arrive(tc::smem_addr(&full[s]));
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (tid < 32) tc::tmem_dealloc(tbase, 64);
+}
+
+template <typename TT, int F, int P, int S>
+int launch_ws(FwdArgs a, cudaStream_t st) {
+  const WsPlan p = ws_plan<P, S>(a.Dp);
+  a.off_w2 = p.off_w2;
+  a.off_w3 = p.off_w3;
+  a.off_a = p.off_ring;
+  a.off_bar = p.off_bar;
+  auto kern = deform_fwd_ws_kernel<TT, F, P, S>;
+  if (int s = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem),
+                          "cudaFuncSetAttribute(deform_fwd_ws)"))
+    return s;
+  const long long ntiles = (a.n_cap + kRows - 1) / kRows;
+  long long grid = sm_count();  // one persistent CTA per SM (shared memory allows one)
+  grid = ntiles < grid ? (ntiles > 0 ? ntiles : 1) : grid;
+  kern<<<(unsigned)grid, (P + 1) * kRows, p.smem, st>>>(a);
+  return launch_status("deform_fwd_ws_kernel");
+}
+
 struct Plan {
   size_t smem;
   uint32_t off_w2, off_w3, off_a, off_bar;
@@ -264,12 +447,30 @@ int launch(FwdArgs a, cudaStream_t st) {
 }
 
 template <typename TT>
-int dispatch_f(int F, int G, FwdArgs& a, cudaStream_t st) {
+int dispatch_f(int F, int Dp, int variant, FwdArgs& a, cudaStream_t st) {
+  // variant 0: warp-specialised (3 producer groups; 6-stage ring, 3 stages when D > 32);
+  // 1, 2, 4: the simple form with that many independent groups per CTA
+  if (variant == 0) {
+    if (Dp > 32) {
+      switch (F) {
+        case 1: return launch_ws<TT, 1, 3, 3>(a, st);
+        case 2: return launch_ws<TT, 2, 3, 3>(a, st);
+        case 4: return launch_ws<TT, 4, 3, 3>(a, st);
+        default: return launch_ws<TT, 8, 3, 3>(a, st);
+      }
+    }
+    switch (F) {
+      case 1: return launch_ws<TT, 1, 3, 6>(a, st);
+      case 2: return launch_ws<TT, 2, 3, 6>(a, st);
+      case 4: return launch_ws<TT, 4, 3, 6>(a, st);
+      default: return launch_ws<TT, 8, 3, 6>(a, st);
+    }
+  }
   switch (F) {
     case 1: return launch<TT, 1, 2>(a, st);
     case 2:
-      if (G == 1) return launch<TT, 2, 1>(a, st);
-      if (G == 4) return launch<TT, 2, 4>(a, st);
+      if (variant == 1) return launch<TT, 2, 1>(a, st);
+      if (variant == 4) return launch<TT, 2, 4>(a, st);
       return launch<TT, 2, 2>(a, st);
     case 4: return launch<TT, 4, 2>(a, st);
     default: return launch<TT, 8, 2>(a, st);
@@ -278,7 +479,7 @@ int dispatch_f(int F, int G, FwdArgs& a, cudaStream_t st) {
 
 }  // namespace
 
-int fused_groups_fwd = 2;  // groups (4-warp units) per CTA; set by the tuner
+int fwd_variant = 0;  // kernel form of the fused forward (see dispatch_f)
 
 unsigned int* fwd_flags_ptr() {
   void* p = nullptr;
@@ -336,8 +537,8 @@ extern "C" int dash_deform_mlp_fwd(const dash_layout* layout, const dash_points*
   if (a.flags == nullptr) return fail(DASH_ERR_CUDA, "cannot resolve the device flag word");
   cudaStream_t st = as_stream(stream);
   switch (table_dtype) {
-    case DASH_F32: return dispatch_f<float>(a.g.F, fused_groups_fwd, a, st);
-    case DASH_F16: return dispatch_f<__half>(a.g.F, fused_groups_fwd, a, st);
+    case DASH_F32: return dispatch_f<float>(a.g.F, a.Dp, fwd_variant, a, st);
+    case DASH_F16: return dispatch_f<__half>(a.g.F, a.Dp, fwd_variant, a, st);
     default: return fail(DASH_ERR_UNSUPPORTED, "table_dtype %d (F32 or F16)", table_dtype);
   }
 }

@@ -63,6 +63,11 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
 
 __device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
+// One arrival (release semantics at CTA scope) on an mbarrier.
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(mbar) : "memory");
+}
+
 // Waits for completion of the phase with the given parity; gives up after
 // max_iters polls and returns false.
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32_t max_iters) {
