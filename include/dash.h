@@ -143,6 +143,23 @@ size_t dash_compact_workspace_size(int64_t n);
 int dash_compact_dynamic(const uint8_t* mask, int64_t n, int32_t* idx_out, int64_t* count_out,
                          void* ws, size_t ws_bytes, void* stream);
 
+/* dash_compact_dynamic without a workspace and without allocating anything.
+ * The paper has no counterpart: this serves callers that must not allocate
+ * device memory while they run (a render loop that owns all device memory
+ * and gives its plug-ins only buffers it allocated up front, or code running
+ * inside a memory allocator's own callbacks, where cudaMalloc would re-enter
+ * that allocator).  The per-CTA scratch is a 256 KB array built into the
+ * library, held by every GPU that loads it until the process exits; n is
+ * limited to 268,435,456 mask entries (DASH_ERR_UNSUPPORTED beyond).  The
+ * first call on a device resolves the array's device address (one
+ * cudaGetSymbolAddress, with that device current), so make that first call
+ * before any stream capture.  All calls share the array: calls whose kernels
+ * overlap on the GPU (other streams, other host threads) race and corrupt
+ * each other's results; serialise them.  Output and errors as
+ * dash_compact_dynamic. */
+int dash_compact_dynamic_noalloc(const uint8_t* mask, int64_t n, int32_t* idx_out,
+                                 int64_t* count_out, void* stream);
+
 /* ---------------------------------------- a2-a6: encoder (Eqs. 8-9) ---- */
 
 /* Debug view of Eq. 8/9: idx_out [n][L][16] level-local corner indices

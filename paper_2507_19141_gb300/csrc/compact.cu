@@ -194,3 +194,62 @@ int dash_compact_dynamic(const uint8_t* mask, int64_t n, int32_t* idx_out, int64
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Compaction without any allocation.  For callers that must not allocate
+// device memory once they are running -- for example a render loop that owns
+// all device memory and hands its plug-ins only the buffers it allocated up
+// front, or code that runs inside a memory allocator's own callbacks, where a
+// cudaMalloc would re-enter that allocator.  The per-CTA counts live in this
+// file-scope array instead of a caller workspace; every GPU that loads the
+// library holds it (256 KB) until the process exits.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace dash {
+namespace {
+
+constexpr long long kNoAllocMaxCtas = 65536;                 // 256 KB of int32 counts
+constexpr long long kNoAllocMaxN = kNoAllocMaxCtas * kChunk;  // 268,435,456 mask entries
+
+static __device__ __align__(256) int g_noalloc_cta_counts[kNoAllocMaxCtas];
+
+std::mutex g_noalloc_mutex;
+int* g_noalloc_ptr[64] = {nullptr};
+
+// Device address of the array on the current device, resolved once per
+// device (host code cannot use the symbol itself: on the host it names a
+// stand-in, not device memory).
+int noalloc_scratch(int** out) {
+  int dev = 0;
+  if (int s = cuda_status(cudaGetDevice(&dev), "cudaGetDevice")) return s;
+  if (dev < 0 || dev >= 64) return fail(DASH_ERR_UNSUPPORTED, "device ordinal %d >= 64", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (g_noalloc_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    if (int s = cuda_status(cudaGetSymbolAddress(&p, g_noalloc_cta_counts), "cudaGetSymbolAddress")) return s;
+    g_noalloc_ptr[dev] = static_cast<int*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return DASH_OK;
+}
+
+}  // namespace
+}  // namespace dash
+
+extern "C" int dash_compact_dynamic_noalloc(const uint8_t* mask, int64_t n, int32_t* idx_out, int64_t* count_out,
+                                            void* stream) {
+  using dash::fail;
+  if (n < 0) return fail(DASH_ERR_INVALID_ARG, "n=%lld < 0", (long long)n);
+  if (n > dash::kNoAllocMaxN)
+    return fail(DASH_ERR_UNSUPPORTED, "n=%lld exceeds the %lld-entry limit of the built-in scratch array",
+                (long long)n, dash::kNoAllocMaxN);
+  if (count_out == nullptr) return fail(DASH_ERR_INVALID_ARG, "count_out is NULL");
+  if (n > 0 && (mask == nullptr || idx_out == nullptr)) return fail(DASH_ERR_INVALID_ARG, "mask/idx_out is NULL");
+  int* scratch = nullptr;
+  if (int s = dash::noalloc_scratch(&scratch)) return s;
+  // The count pass writes every slot that the scan and write passes read, so
+  // what earlier calls left in the array never needs clearing.
+  return dash::compact_launch(mask, n, idx_out, reinterpret_cast<long long*>(count_out), scratch,
+                              dash::as_stream(stream));
+}

@@ -91,6 +91,7 @@ _SIGS = {
     "dash_hash4d_layout": ([_P, _P], _I),
     "dash_compact_workspace_size": ([_I64], _SZ),
     "dash_compact_dynamic": ([_P, _I64, _P, _P, _P, _SZ, _P], _I),
+    "dash_compact_dynamic_noalloc": ([_P, _I64, _P, _P, _P], _I),
     "dash_hash4d_indices": ([_P, _P, _P, _P, _P], _I),
     "dash_hash4d_fwd": ([_P, _P, _P, _I, _P, _I, _P], _I),
     "dash_hash4d_bwd": ([_P, _P, _P, _P, _P], _I),
@@ -205,6 +206,15 @@ def dash_compact_dynamic(mask: torch.Tensor, idx_out=None, count_out=None, ws=No
     ws = torch.empty(need, dtype=torch.uint8, device=dev) if ws is None else ws
     _check(_lib.dash_compact_dynamic(_ptr(mask), n, _ptr(idx_out), _ptr(count_out), _ptr(ws), ws.numel(),
                                      _stream()), "dash_compact_dynamic")
+    return idx_out, count_out
+
+
+def dash_compact_dynamic_noalloc(mask: torch.Tensor, idx_out: torch.Tensor, count_out: torch.Tensor):
+    """Like dash_compact_dynamic, with the library's built-in scratch array
+    instead of a workspace; the caller passes the (pre-allocated) outputs."""
+    assert mask.is_cuda and mask.dtype == torch.uint8 and mask.is_contiguous()
+    _check(_lib.dash_compact_dynamic_noalloc(_ptr(mask), mask.numel(), _ptr(idx_out), _ptr(count_out), _stream()),
+           "dash_compact_dynamic_noalloc")
     return idx_out, count_out
 
 
