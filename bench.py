@@ -51,6 +51,8 @@ def parse_args(argv=None):
     ap.add_argument("--n-all", type=int, default=N_ALL)
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (0 = calibrate to ~10 s)")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run the small profiling case (1M points, two launches of each kernel) and exit")
     return ap.parse_args(argv)
 
 
@@ -475,8 +477,43 @@ def run_reference(args):
         barrier()
 
 
+def profile_case(n):
+    """Small case for ncu captures: n dynamic Gaussians (no compaction), about
+    0.6 GB on the device, two launches of the encoder forward/backward and of
+    the fused forward/backward."""
+    import numpy as np
+    import torch
+    from paper_2507_19141_gb300 import dash, synth
+    grid, mlpc = synth.PAPER_GRID, synth.PAPER_MLP
+    rng = np.random.default_rng(2)
+    x, y, z, t = synth.scene_coords(rng, n)
+    lay = dash.layout_from(grid)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    table = dev(synth.table_values(rng, lay.total, grid.F, np.float16))
+    mlp = dash.Mlp(dev(synth.mlp_params(rng, mlpc)), mlpc.d_in, mlpc.d_hidden, mlpc.d_out)
+    pts = dash.Points(dev(x), dev(y), dev(z), dev(t))
+    delta = torch.empty((mlpc.d_out, n), device="cuda")
+    state = dash.deform_state(mlp, n, "cuda")
+    feat = torch.empty((n, mlpc.d_in), dtype=torch.bfloat16, device="cuda")
+    tg = torch.zeros((lay.total, grid.F), device="cuda")
+    pg = torch.zeros(mlpc.n_params, device="cuda")
+    dd = dev(synth.upstream_grad(rng, mlpc.d_out, n))
+    dfeat = dev(rng.standard_normal((n, mlpc.d_in)).astype(np.float32))
+    for _ in range(2):
+        dash.dash_hash4d_fwd(lay, pts, table, torch.bfloat16, out=feat)
+        dash.dash_hash4d_bwd(lay, pts, dfeat, tg)
+        dash.dash_deform_mlp_fwd(lay, pts, table, mlp, delta_out=delta, fwd_state=state)
+        dash.dash_deform_mlp_bwd(lay, pts, table, mlp, dd, tg, pg, fwd_state=state)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": n, "delta_abs_mean": float(delta.abs().mean()),
+                      "grad_abs_sum": float(tg.abs().sum())}))
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.profile_case:
+        profile_case(args.n_dyn)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

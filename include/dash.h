@@ -124,6 +124,16 @@ const char* dash_last_error(void);
 /* ABI version (major * 100 + minor). */
 int dash_version(void);
 
+/* Process-wide kernel-form options (host; take effect at the next launch).
+ * DASH_OPT_FWD_FORM selects the fused forward kernel: 0 = warp-specialised
+ * (one decoder group fed by three gather groups through a shared-memory
+ * ring; default), 1 / 2 / 4 = that many independent gather+decoder groups
+ * per CTA.  Results are identical across forms.  dash_get_option returns
+ * the current value (negative status for an unknown option). */
+enum dash_option { DASH_OPT_FWD_FORM = 1 };
+int dash_set_option(int option, int value);
+int dash_get_option(int option);
+
 /* Eq. 7 (host): fills *out from *cfg.  N_l = floor(N_min * b^l + 1e-9),
  * b = exp((ln N_max - ln N_min) / (L - 1)), separately for space and time.
  * Errors: INVALID_ARG (null, N_min < 1, N_max < N_min), UNSUPPORTED

@@ -11,6 +11,8 @@ namespace dash {
 
 static thread_local char g_last_error[512] = "";
 
+int g_opt_fwd_form = 0;
+
 void set_error(const char* fmt, ...) {
   va_list ap;
   va_start(ap, fmt);
@@ -111,6 +113,24 @@ const char* dash_status_string(int s) {
 const char* dash_last_error(void) { return dash::g_last_error; }
 
 int dash_version(void) { return 100; }
+
+int dash_set_option(int option, int value) {
+  switch (option) {
+    case DASH_OPT_FWD_FORM:
+      if (!(value == 0 || value == 1 || value == 2 || value == 4))
+        return dash::fail(DASH_ERR_INVALID_ARG, "forward form %d not in {0, 1, 2, 4}", value);
+      dash::g_opt_fwd_form = value;
+      return DASH_OK;
+    default: return dash::fail(DASH_ERR_INVALID_ARG, "unknown option %d", option);
+  }
+}
+
+int dash_get_option(int option) {
+  switch (option) {
+    case DASH_OPT_FWD_FORM: return dash::g_opt_fwd_form;
+    default: return dash::fail(DASH_ERR_INVALID_ARG, "unknown option %d", option);
+  }
+}
 
 int dash_hash4d_layout(const dash_hash4d_cfg* cfg, dash_layout* out) {
   using dash::fail;

@@ -25,6 +25,9 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 // Number of SMs of the current device (cached per device).
 int sm_count();
 
+// Kernel-form options (dash_set_option).
+extern int g_opt_fwd_form;
+
 // ------------------------------------------------ kernel-side geometry ----
 // Level layout in the form the kernels read it (by-value kernel argument).
 struct Geom {
@@ -68,17 +71,18 @@ __device__ __forceinline__ long long point_count(const Pts& p) {
 __device__ __forceinline__ float clamp01(float v) { return fminf(fmaxf(v, 0.0f), 1.0f); }
 
 __device__ __forceinline__ long long point_row(const Pts& p, long long i) {
-  return p.idx != nullptr ? (long long)__ldg(p.idx + i) : i;
+  return p.idx != nullptr ? (long long)__ldcs(p.idx + i) : i;
 }
 
 // Clamped (x, y, z, t) of compact point i.
 __device__ __forceinline__ float4 load_point(const Pts& p, long long i) {
   const long long j = point_row(p, i);
   float4 r;
-  r.x = clamp01(__ldg(p.x + j));
-  r.y = clamp01(__ldg(p.y + j));
-  r.z = clamp01(__ldg(p.z + j));
-  r.w = clamp01(p.t_stride != 0 ? __ldg(p.t + j * p.t_stride) : __ldg(p.t));
+  // coordinates are read once per kernel: streaming loads (evict first)
+  r.x = clamp01(__ldcs(p.x + j));
+  r.y = clamp01(__ldcs(p.y + j));
+  r.z = clamp01(__ldcs(p.z + j));
+  r.w = clamp01(p.t_stride != 0 ? __ldcs(p.t + j * p.t_stride) : __ldg(p.t));
   return r;
 }
 
@@ -170,15 +174,95 @@ __device__ __forceinline__ void load_entry(const TT* __restrict__ p, float v[F])
   }
 }
 
-// Vector FP32 reductions into global memory (fire-and-forget, no return).
+// Vector FP32 reductions into global memory (fire-and-forget, no return),
+// with an evict-last L2 policy: the gradient buffer is updated from every tile
+// and should not be pushed out of L2 by the streaming inputs.
 __device__ __forceinline__ void red_add_v2(float* addr, float a, float b) {
-  asm volatile("red.relaxed.gpu.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(a), "f"(b)
-               : "memory");
+  asm volatile(
+      "{\n.reg .b64 pol;\ncreatepolicy.fractional.L2::evict_last.b64 pol, 1.0;\n"
+      "red.relaxed.gpu.global.add.L2::cache_hint.v2.f32 [%0], {%1, %2}, pol;\n}" ::"l"(addr),
+      "f"(a), "f"(b)
+      : "memory");
 }
 __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d) {
-  asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a),
-               "f"(b), "f"(c), "f"(d)
-               : "memory");
+  asm volatile(
+      "{\n.reg .b64 pol;\ncreatepolicy.fractional.L2::evict_last.b64 pol, 1.0;\n"
+      "red.relaxed.gpu.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, pol;\n}" ::"l"(addr),
+      "f"(a), "f"(b), "f"(c), "f"(d)
+      : "memory");
+}
+
+// ------------------------------------------- corner-pair merged access ----
+// Corners b and b|1 differ only in x.  With pi_x = 1 (and on dense levels)
+// their entries are neighbours: c and c+1 along x hash to indices that differ
+// in the low bits only, unless c ends in many one-bits.  One aligned 16-byte
+// load then serves both corners, which halves the distinct addresses a warp
+// presents to L1 for those pairs.  Level offsets are multiples of 8 entries
+// and tables are 16-byte aligned, so the aligned group never straddles a level.
+
+// F = 2 entry k of a 16-byte group, widened to FP32.
+template <typename TT>
+__device__ __forceinline__ float2 entry_in16(const uint4& v, uint32_t k);
+template <>
+__device__ __forceinline__ float2 entry_in16<__half>(const uint4& v, uint32_t k) {
+  const uint32_t lo = (k & 1u) ? v.y : v.x;
+  const uint32_t hi = (k & 1u) ? v.w : v.z;
+  const uint32_t word = (k & 2u) ? hi : lo;
+  return __half22float2(*reinterpret_cast<const __half2*>(&word));
+}
+template <>
+__device__ __forceinline__ float2 entry_in16<float>(const uint4& v, uint32_t k) {
+  return (k & 1u) ? make_float2(__uint_as_float(v.z), __uint_as_float(v.w))
+                  : make_float2(__uint_as_float(v.x), __uint_as_float(v.y));
+}
+
+// acc[0..2) = sum_b w[b] * table[base + idx[b]] for F = 2 (same summation
+// order as corner by corner).
+template <typename TT>
+__device__ __forceinline__ void gather2_pairs(const TT* __restrict__ base, const uint32_t idx[16], const float w[16],
+                                              float acc[2]) {
+  constexpr uint32_t kGroup = 16u / (2u * sizeof(TT));  // entries per 16 bytes: 4 (FP16) or 2 (FP32)
+  float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    const uint32_t i0 = idx[2 * p], i1 = idx[2 * p + 1];
+    const uint32_t g = i0 & ~(kGroup - 1u);
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(base + (size_t)g * 2));
+    const float2 e0 = entry_in16<TT>(v, i0 & (kGroup - 1u));
+    float2 e1;
+    if ((i1 & ~(kGroup - 1u)) == g) {
+      e1 = entry_in16<TT>(v, i1 & (kGroup - 1u));
+    } else {
+      float t[2];
+      load_entry<TT, 2>(base + (size_t)i1 * 2, t);
+      e1 = make_float2(t[0], t[1]);
+    }
+    a0 = fmaf(w[2 * p], e0.x, a0);
+    a1 = fmaf(w[2 * p], e0.y, a1);
+    a0 = fmaf(w[2 * p + 1], e1.x, a0);
+    a1 = fmaf(w[2 * p + 1], e1.y, a1);
+  }
+  acc[0] = a0;
+  acc[1] = a1;
+}
+
+// grad[base + idx[b]] += w[b] * d for F = 2 FP32 gradients: a 16-byte
+// reduction when a pair's two entries form one aligned 16-byte group.
+__device__ __forceinline__ void scatter2_pairs(float* __restrict__ base, const uint32_t idx[16], const float w[16],
+                                               float d0, float d1) {
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    const uint32_t i0 = idx[2 * p], i1 = idx[2 * p + 1];
+    const float u0 = w[2 * p] * d0, u1 = w[2 * p] * d1;
+    const float v0 = w[2 * p + 1] * d0, v1 = w[2 * p + 1] * d1;
+    if ((i0 ^ i1) == 1u) {
+      if (i0 < i1) red_add_v4(base + (size_t)i0 * 2, u0, u1, v0, v1);
+      else red_add_v4(base + (size_t)i1 * 2, v0, v1, u0, u1);
+    } else {
+      red_add_v2(base + (size_t)i0 * 2, u0, u1);
+      red_add_v2(base + (size_t)i1 * 2, v0, v1);
+    }
+  }
 }
 
 }  // namespace dash

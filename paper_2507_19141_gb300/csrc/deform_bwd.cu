@@ -89,13 +89,15 @@ template <int F>
 __device__ __forceinline__ void scatter_level(float* __restrict__ grad, long long off, const uint32_t idx[16],
                                               const float w[16], const float d[F]) {
   float* base = grad + off * F;
+  if constexpr (F == 2) {
+    scatter2_pairs(base, idx, w, d[0], d[1]);
+    return;
+  }
 #pragma unroll
   for (int b = 0; b < 16; ++b) {
     float* e = base + (size_t)idx[b] * F;
     if constexpr (F == 1) {
       atomicAdd(e, w[b] * d[0]);
-    } else if constexpr (F == 2) {
-      red_add_v2(e, w[b] * d[0], w[b] * d[1]);
     } else {
 #pragma unroll
       for (int f = 0; f < F; f += 4) red_add_v4(e + f, w[b] * d[f], w[b] * d[f + 1], w[b] * d[f + 2], w[b] * d[f + 3]);
@@ -107,6 +109,10 @@ template <typename TT, int F>
 __device__ __forceinline__ void gather_level(const TT* __restrict__ table, long long off, const uint32_t idx[16],
                                              const float w[16], float acc[F]) {
   const TT* base = table + off * F;
+  if constexpr (F == 2) {
+    gather2_pairs<TT>(base, idx, w, acc);
+    return;
+  }
 #pragma unroll
   for (int f = 0; f < F; ++f) acc[f] = 0.0f;
 #pragma unroll
@@ -237,7 +243,7 @@ __global__ void __launch_bounds__(kRows, 1) deform_bwd_kernel(const __grid_const
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int k = 8 * c + j;
-          v[j] = (srow != nullptr && k < a.D) ? __bfloat162float(fs[k]) : 0.0f;
+          v[j] = (srow != nullptr && k < a.D) ? __bfloat162float(__ldcs(fs + k)) : 0.0f;
         }
       }
       uint4 hi, lo;
@@ -248,7 +254,7 @@ __global__ void __launch_bounds__(kRows, 1) deform_bwd_kernel(const __grid_const
     write_ones(Ft, r, a.Dp, KF);
     uint32_t m1[2] = {0u, 0u}, m2[2] = {0u, 0u};
     if (srow != nullptr) {
-      const uint4 m = *reinterpret_cast<const uint4*>(srow + state_mask_off(a.D));
+      const uint4 m = __ldcs(reinterpret_cast<const uint4*>(srow + state_mask_off(a.D)));
       m1[0] = m.x;
       m1[1] = m.y;
       m2[0] = m.z;
@@ -319,7 +325,7 @@ __global__ void __launch_bounds__(kRows, 1) deform_bwd_kernel(const __grid_const
     {
       float d[16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) d[j] = (valid && j < a.O) ? __ldg(a.ddelta + (long long)j * a.n_cap + row) : 0.0f;
+      for (int j = 0; j < 16; ++j) d[j] = (valid && j < a.O) ? __ldcs(a.ddelta + (long long)j * a.n_cap + row) : 0.0f;
       uint32_t h[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) h[j] = pack_bf16x2(d[2 * j], d[2 * j + 1]);
@@ -487,6 +493,10 @@ int launch(BwdArgs a, cudaStream_t st) {
   if (int s = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                           "cudaFuncSetAttribute(deform_bwd)"))
     return s;
+  if (int s = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                               (int)cudaSharedmemCarveoutMaxShared),
+                          "carveout"))
+    return s;
   int per_sm = 0;
   if (int s = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRows, smem),
                           "occupancy(deform_bwd)"))
@@ -539,6 +549,7 @@ extern "C" int dash_deform_mlp_bwd(const dash_layout* layout, const dash_points*
     return fail(DASH_ERR_INVALID_ARG, "table/ddelta/table_grad/mlp_grad is NULL");
   if ((reinterpret_cast<uintptr_t>(table_grad) & 15u) != 0)
     return fail(DASH_ERR_INVALID_ARG, "table_grad must be 16-byte aligned");
+  if ((reinterpret_cast<uintptr_t>(table) & 15u) != 0) return fail(DASH_ERR_INVALID_ARG, "table must be 16-byte aligned");
   a.table = table;
   a.params = mlp->params;
   a.D = D;

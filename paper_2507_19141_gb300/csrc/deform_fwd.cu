@@ -65,12 +65,16 @@ __device__ __forceinline__ void encode_row(const FwdArgs& a, bool valid, long lo
         float w[16];
         level_corners(a.g, l, p, idx, w);
         const TT* base = table + a.g.offset[l] * F;
+        if constexpr (F == 2) {
+          gather2_pairs<TT>(base, idx, w, acc);
+        } else {
 #pragma unroll
-        for (int b = 0; b < 16; ++b) {
-          float e[F];
-          load_entry<TT, F>(base + (size_t)idx[b] * F, e);
+          for (int b = 0; b < 16; ++b) {
+            float e[F];
+            load_entry<TT, F>(base + (size_t)idx[b] * F, e);
 #pragma unroll
-          for (int f = 0; f < F; ++f) acc[f] = fmaf(w[b], e[f], acc[f]);
+            for (int f = 0; f < F; ++f) acc[f] = fmaf(w[b], e[f], acc[f]);
+          }
         }
       }
 #pragma unroll
@@ -83,7 +87,7 @@ __device__ __forceinline__ void encode_row(const FwdArgs& a, bool valid, long lo
     if (valid && a.state != nullptr && 8 * c < a.D) {
       __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(a.state + row * state_stride(a.D)) + 8 * c;
       if ((a.D & 7) == 0) {
-        *reinterpret_cast<uint4*>(dst) = hi;
+        __stcs(reinterpret_cast<uint4*>(dst), hi);
       } else {
         const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&hi);
         for (int j = 0; j < 8 && 8 * c + j < a.D; ++j) dst[j] = h[j];
@@ -337,8 +341,8 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_fwd_ws_kernel(const
       tc::fence_after_sync();
       hidden_epilogue(trow, A2, r, m2);
       if (valid && a.state != nullptr)
-        *reinterpret_cast<uint4*>(a.state + row * state_stride(a.D) + state_mask_off(a.D)) =
-            make_uint4(m1[0], m1[1], m2[0], m2[1]);
+        __stcs(reinterpret_cast<uint4*>(a.state + row * state_stride(a.D) + state_mask_off(a.D)),
+               make_uint4(m1[0], m1[1], m2[0], m2[1]));
       tc::fence_before_sync();
       tc::fence_async_smem();
       tc::named_sync(1, kRows);
@@ -354,11 +358,11 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_fwd_ws_kernel(const
       float o[16];
       tc::tmem_ld16(trow, o);
       if (valid) {
-        for (int k = 0; k < a.O; ++k) a.delta[(long long)k * a.n_cap + row] = o[k];
+        for (int k = 0; k < a.O; ++k) __stcs(a.delta + (long long)k * a.n_cap + row, o[k]);
         if (a.attrs_out != nullptr) {
           const long long gi = point_row(a.pts, row);
           for (int k = 0; k < a.O; ++k)
-            a.attrs_out[(long long)k * a.n_all + gi] = a.attrs_in[(long long)k * a.n_all + gi] + o[k];
+            __stcs(a.attrs_out + (long long)k * a.n_all + gi, __ldcs(a.attrs_in + (long long)k * a.n_all + gi) + o[k]);
         }
       }
       tc::fence_before_sync();
@@ -432,6 +436,10 @@ int launch(FwdArgs a, cudaStream_t st) {
   if (int s = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem),
                           "cudaFuncSetAttribute(deform_fwd)"))
     return s;
+  if (int s = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                               (int)cudaSharedmemCarveoutMaxShared),
+                          "carveout"))
+    return s;
   int per_sm = 0;
   if (int s = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G * kRows, p.smem),
                           "occupancy(deform_fwd)"))
@@ -479,8 +487,6 @@ int dispatch_f(int F, int Dp, int variant, FwdArgs& a, cudaStream_t st) {
 
 }  // namespace
 
-int fwd_variant = 0;  // kernel form of the fused forward (see dispatch_f)
-
 unsigned int* fwd_flags_ptr() {
   void* p = nullptr;
   if (cudaGetSymbolAddress(&p, g_fwd_flags) != cudaSuccess) return nullptr;
@@ -516,6 +522,7 @@ extern "C" int dash_deform_mlp_fwd(const dash_layout* layout, const dash_points*
   if (int s = check_fused_mlp(mlp, D)) return s;
   if (a.pts.n == 0) return DASH_OK;
   if (table == nullptr || delta_out == nullptr) return fail(DASH_ERR_INVALID_ARG, "table/delta_out is NULL");
+  if ((reinterpret_cast<uintptr_t>(table) & 15u) != 0) return fail(DASH_ERR_INVALID_ARG, "table must be 16-byte aligned");
   if (fwd_state != nullptr && (reinterpret_cast<uintptr_t>(fwd_state) & 15u) != 0)
     return fail(DASH_ERR_INVALID_ARG, "fwd_state must be 16-byte aligned");
   if (apply != nullptr && (apply->attrs_in == nullptr || apply->attrs_out == nullptr || apply->n_all < 1))
@@ -537,8 +544,8 @@ extern "C" int dash_deform_mlp_fwd(const dash_layout* layout, const dash_points*
   if (a.flags == nullptr) return fail(DASH_ERR_CUDA, "cannot resolve the device flag word");
   cudaStream_t st = as_stream(stream);
   switch (table_dtype) {
-    case DASH_F32: return dispatch_f<float>(a.g.F, a.Dp, fwd_variant, a, st);
-    case DASH_F16: return dispatch_f<__half>(a.g.F, a.Dp, fwd_variant, a, st);
+    case DASH_F32: return dispatch_f<float>(a.g.F, a.Dp, g_opt_fwd_form, a, st);
+    case DASH_F16: return dispatch_f<__half>(a.g.F, a.Dp, g_opt_fwd_form, a, st);
     default: return fail(DASH_ERR_UNSUPPORTED, "table_dtype %d (F32 or F16)", table_dtype);
   }
 }

@@ -11,8 +11,9 @@ constexpr int kThreads = 256;
 
 inline unsigned grid_for(long long n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
-// f_h for point i: per level the weighted sum of the 16 corner entries.
-template <typename TT, int F, typename OT>
+// f_h for point i: per level the weighted sum of the 16 corner entries
+// (kPairs: F = 2 corner pairs fetched with one 16-byte load where possible).
+template <typename TT, int F, typename OT, bool kPairs>
 __global__ void __launch_bounds__(kThreads) encode_fwd_kernel(Geom g, Pts pts, const TT* __restrict__ table,
                                                               OT* __restrict__ out) {
   const long long n = point_count(pts);
@@ -26,14 +27,18 @@ __global__ void __launch_bounds__(kThreads) encode_fwd_kernel(Geom g, Pts pts, c
     level_corners(g, l, p, idx, w);
     const TT* base = table + g.offset[l] * F;
     float acc[F];
+    if constexpr (kPairs && F == 2) {
+      gather2_pairs<TT>(base, idx, w, acc);
+    } else {
 #pragma unroll
-    for (int f = 0; f < F; ++f) acc[f] = 0.0f;
+      for (int f = 0; f < F; ++f) acc[f] = 0.0f;
 #pragma unroll
-    for (int b = 0; b < 16; ++b) {
-      float v[F];
-      load_entry<TT, F>(base + (size_t)idx[b] * F, v);
+      for (int b = 0; b < 16; ++b) {
+        float v[F];
+        load_entry<TT, F>(base + (size_t)idx[b] * F, v);
 #pragma unroll
-      for (int f = 0; f < F; ++f) acc[f] = fmaf(w[b], v[f], acc[f]);
+        for (int f = 0; f < F; ++f) acc[f] = fmaf(w[b], v[f], acc[f]);
+      }
     }
 #pragma unroll
     for (int f = 0; f < F; ++f) row[l * F + f] = from_f32<OT>(acc[f]);
@@ -58,13 +63,15 @@ __global__ void __launch_bounds__(kThreads) encode_bwd_kernel(Geom g, Pts pts, c
 #pragma unroll
     for (int f = 0; f < F; ++f) d[f] = __ldg(drow + l * F + f);
     float* base = grad + g.offset[l] * F;
+    if constexpr (F == 2) {
+      scatter2_pairs(base, idx, w, d[0], d[1]);
+      continue;
+    }
 #pragma unroll
     for (int b = 0; b < 16; ++b) {
       float* e = base + (size_t)idx[b] * F;
       if constexpr (F == 1) {
         atomicAdd(e, w[b] * d[0]);
-      } else if constexpr (F == 2) {
-        red_add_v2(e, w[b] * d[0], w[b] * d[1]);
       } else {
 #pragma unroll
         for (int f = 0; f < F; f += 4) red_add_v4(e + f, w[b] * d[f], w[b] * d[f + 1], w[b] * d[f + 2], w[b] * d[f + 3]);
@@ -113,16 +120,16 @@ __global__ void __launch_bounds__(kThreads) indices_kernel(Geom g, Pts pts, uint
   }
 }
 
-template <typename TT, typename OT>
+template <typename TT, typename OT, bool kPairs = true>
 int launch_fwd_t(const Geom& g, const Pts& p, const void* table, void* out, cudaStream_t st) {
   const unsigned grid = grid_for(p.n);
   const TT* tb = static_cast<const TT*>(table);
   OT* o = static_cast<OT*>(out);
   switch (g.F) {
-    case 1: encode_fwd_kernel<TT, 1, OT><<<grid, kThreads, 0, st>>>(g, p, tb, o); break;
-    case 2: encode_fwd_kernel<TT, 2, OT><<<grid, kThreads, 0, st>>>(g, p, tb, o); break;
-    case 4: encode_fwd_kernel<TT, 4, OT><<<grid, kThreads, 0, st>>>(g, p, tb, o); break;
-    default: encode_fwd_kernel<TT, 8, OT><<<grid, kThreads, 0, st>>>(g, p, tb, o); break;
+    case 1: encode_fwd_kernel<TT, 1, OT, kPairs><<<grid, kThreads, 0, st>>>(g, p, tb, o); break;
+    case 2: encode_fwd_kernel<TT, 2, OT, kPairs><<<grid, kThreads, 0, st>>>(g, p, tb, o); break;
+    case 4: encode_fwd_kernel<TT, 4, OT, kPairs><<<grid, kThreads, 0, st>>>(g, p, tb, o); break;
+    default: encode_fwd_kernel<TT, 8, OT, kPairs><<<grid, kThreads, 0, st>>>(g, p, tb, o); break;
   }
   return launch_status("encode_fwd_kernel");
 }
@@ -155,6 +162,7 @@ int dash_hash4d_fwd(const dash_layout* layout, const dash_points* pts, const voi
   if (int s = prepare(layout, pts, &g, &p)) return s;
   if (p.n == 0) return DASH_OK;
   if (table == nullptr || feat_out == nullptr) return fail(DASH_ERR_INVALID_ARG, "table/feat_out is NULL");
+  if ((reinterpret_cast<uintptr_t>(table) & 15u) != 0) return fail(DASH_ERR_INVALID_ARG, "table must be 16-byte aligned");
   switch (table_dtype) {
     case DASH_F32: return launch_fwd_out<float>(g, p, table, feat_out, feat_dtype, as_stream(stream));
     case DASH_F16: return launch_fwd_out<__half>(g, p, table, feat_out, feat_dtype, as_stream(stream));
@@ -202,7 +210,7 @@ int dash_plain_hash4d_fwd(const dash_layout* layout, const dash_points* pts, con
   if (int s = prepare(layout, pts, &g, &p)) return s;
   if (p.n == 0) return DASH_OK;
   if (table == nullptr || feat_out == nullptr) return fail(DASH_ERR_INVALID_ARG, "table/feat_out is NULL");
-  return launch_fwd_t<float, float>(g, p, table, feat_out, as_stream(stream));
+  return launch_fwd_t<float, float, false>(g, p, table, feat_out, as_stream(stream));
 }
 
 int dash_plain_hash4d_bwd(const dash_layout* layout, const dash_points* pts, const float* dfeat,

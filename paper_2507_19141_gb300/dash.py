@@ -88,6 +88,8 @@ _SIGS = {
     "dash_status_string": ([_I], ctypes.c_char_p),
     "dash_last_error": ([], ctypes.c_char_p),
     "dash_version": ([], _I),
+    "dash_set_option": ([_I, _I], _I),
+    "dash_get_option": ([_I], _I),
     "dash_hash4d_layout": ([_P, _P], _I),
     "dash_compact_workspace_size": ([_I64], _SZ),
     "dash_compact_dynamic": ([_P, _I64, _P, _P, _P, _SZ, _P], _I),
@@ -131,6 +133,20 @@ def exported_symbols():
 # ------------------------------------------------------------ utilities --
 def dash_version() -> int:
     return int(_lib.dash_version())
+
+
+OPT_FWD_FORM = 1
+
+
+def dash_set_option(option: int, value: int) -> None:
+    _check(_lib.dash_set_option(option, value), "dash_set_option")
+
+
+def dash_get_option(option: int) -> int:
+    v = int(_lib.dash_get_option(option))
+    if v < 0:
+        raise DashError(v, "dash_get_option")
+    return v
 
 
 def dash_hash4d_layout(L, F, log2_T, nmin_s, nmax_s, nmin_t, nmax_t, primes=PRIMES) -> dash_layout:

@@ -222,3 +222,31 @@ def test_autograd_function_matches_oracle(dashlib):
                                     params.astype(np.float64), dd.astype(np.float64))
     assert rel_err(tab.grad.cpu().numpy(), rtg) < 1e-2
     assert rel_err(par.grad.cpu().numpy(), rpg) < 1e-2
+
+
+@pytest.mark.parametrize("grid,mlpc,tdtype", [(synth.PAPER_GRID, synth.PAPER_MLP, np.float16),
+                                              (synth.TINY_GRID, synth.TINY_MLP, np.float32)])
+def test_forward_kernel_forms_agree(dashlib, grid, mlpc, tdtype):
+    """Every fused-forward form (warp-specialised, 1/2/4 groups per CTA)
+    computes the same offsets and state bit for bit."""
+    n = 70_001
+    g, coords, _, table, params, _ = _case(grid, mlpc, n, tdtype, 46)
+    lay = dashlib.layout_from(grid)
+    pts = _dev_points(dashlib, coords, None, n)
+    mlp = dashlib.Mlp(to_dev(params), mlpc.d_in, mlpc.d_hidden, mlpc.d_out)
+    tab = to_dev(table)
+    outs = []
+    old = dashlib.dash_get_option(dashlib.OPT_FWD_FORM)
+    try:
+        for form in (0, 1, 2, 4):
+            dashlib.dash_set_option(dashlib.OPT_FWD_FORM, form)
+            st = dashlib.deform_state(mlp, n, "cuda")
+            d = dashlib.dash_deform_mlp_fwd(lay, pts, tab, mlp, fwd_state=st)
+            outs.append((d.cpu(), st.cpu()))
+    finally:
+        dashlib.dash_set_option(dashlib.OPT_FWD_FORM, old)
+    for d, st in outs[1:]:
+        assert torch.equal(d, outs[0][0]) and torch.equal(st, outs[0][1])
+    ref = oracle.deform_fwd(g, oracle.Points(*coords), table.astype(np.float64), mlpc.d_hidden, mlpc.d_out,
+                            params.astype(np.float64))
+    assert rel_err(outs[0][0].numpy(), ref) < 1e-3
