@@ -36,8 +36,10 @@ N_DYN = 1_000_000
 # algorithmic bytes per dynamic Gaussian (L=16, F=2, FP16 tables, 16 corners):
 #   forward : xyzt 16 + idx 4 + gather 16*16*4 = 1024 + delta 40 + state 80 (f_h BF16 + masks) + Eq. 10 in/out 80
 #   backward: xyzt 16 + idx 4 + state 80 + ddelta 40 + scatter 16*16*8 = 2048 (FP32 read-modify-write units)
+#   compaction: 2 mask bytes (2M Gaussians for 1M dynamic) + 4 index bytes
 FWD_BYTES = 16 + 4 + 1024 + 40 + 80 + 80
 BWD_BYTES = 16 + 4 + 80 + 40 + 2048
+STEP_BYTES = 2 + 4 + FWD_BYTES + BWD_BYTES
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -306,6 +308,9 @@ def run_ours(args):
                      "algorithmic_bytes_per_gaussian": FWD_BYTES if dom == "fwd" else BWD_BYTES,
                      "traffic": None},
         "clocks": clocks,
+        "step_roofline": {"bytes_per_gaussian": STEP_BYTES, "achieved_gbs": STEP_BYTES * value / 1e9,
+                          "frac": STEP_BYTES * value / 1e9 / peak,
+                          "gaussians_per_s_at_peak": peak * 1e9 / STEP_BYTES},
     }
     if rank == 0:
         out["e2e"] = run_e2e(torch, wl, args, stream)
@@ -406,7 +411,39 @@ def run_extras(torch, wl, args, stream):
         cold.append(a.elapsed_time(b))
     res["cold_l2_step_ms"] = statistics.median(cold)
     res["cold_l2_gaussians_per_s"] = n / (res["cold_l2_step_ms"] / 1e3)
+    del flush
+    res.update(run_batched(torch, stream))
     return res
+
+
+def run_batched(torch, stream):
+    """Batched form: 8 scenes with dynamic counts log-uniform in 50k..2M, 64
+    timestamps each, FP16 tables and BF16 decoders per scene, one persistent
+    graph-captured launch with the autotuned kernel form."""
+    import numpy as np
+    from paper_2507_19141_gb300 import dash, synth
+    counts, tss, rng = synth.batched()
+    grid, mlpc = synth.PAPER_GRID, synth.PAPER_MLP
+    lay = dash.layout_from(grid)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    scenes = []
+    for n, ts in zip(counts, tss):
+        x, y, z, _ = synth.scene_coords(rng, n)
+        scenes.append({"table": dev(synth.table_values(rng, lay.total, grid.F, np.float16)),
+                       "params": dev(synth.mlp_params(rng, mlpc)), "x": dev(x), "y": dev(y), "z": dev(z),
+                       "timestamps": dev(ts),
+                       "delta_out": torch.empty((len(ts), mlpc.d_out, n), dtype=torch.float32, device="cuda")})
+    plan = dash.BatchPlan(lay, scenes)
+    cache = os.path.join(ROOT, "paper_2507_19141_gb300", "_build", "autotune.json")
+    form = plan.autotune(cache)
+    plan.run()
+    torch.cuda.synchronize()
+    ms = time_steps(torch, plan.run, 3, stream)
+    evals = sum(counts) * len(tss[0])
+    plan.close()
+    return {"batched_scenes": len(counts), "batched_counts": counts, "batched_timestamps": len(tss[0]),
+            "batched_evaluations": evals, "batched_launch_ms": ms, "batched_form": form,
+            "batched_evaluations_per_s": evals / (ms / 1e3)}
 
 
 # ------------------------------------------------------------ CPU oracle --

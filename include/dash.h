@@ -5,7 +5,7 @@
  * Conventions shared by every entry point
  *   - All pointers are DEVICE pointers unless a comment says "host".
  *   - The caller owns all memory.  Nothing here allocates device memory
- *     except dash_batch_plan_create (inside the plan it returns).
+ *     except dash_batch_plan_create (the plan's descriptors and graph).
  *   - Every call is asynchronous on the CUDA stream passed as `void* stream`
  *     (a cudaStream_t; NULL = the legacy default stream).  Nothing
  *     synchronises; a kernel fault surfaces at the caller's next sync.
@@ -128,9 +128,12 @@ int dash_version(void);
  * DASH_OPT_FWD_FORM selects the fused forward kernel: 0 = warp-specialised
  * (one decoder group fed by three gather groups through a shared-memory
  * ring; default), 1 / 2 / 4 = that many independent gather+decoder groups
- * per CTA.  Results are identical across forms.  dash_get_option returns
- * the current value (negative status for an unknown option). */
-enum dash_option { DASH_OPT_FWD_FORM = 1 };
+ * per CTA.  DASH_OPT_BWD_FORM selects the fused backward: 0 = warp-specialised
+ * (one decoder group feeding three scatter groups; used when a forward state
+ * is given), 1 = one combined group per CTA.  Results agree to rounding
+ * (forward forms bit for bit).  dash_get_option returns the current value
+ * (negative status for an unknown option). */
+enum dash_option { DASH_OPT_FWD_FORM = 1, DASH_OPT_BWD_FORM = 2 };
 int dash_set_option(int option, int value);
 int dash_get_option(int option);
 
@@ -223,6 +226,60 @@ int dash_deform_mlp_bwd(const dash_layout* layout, const dash_points* pts,
                         const void* table, int table_dtype, const dash_mlp* mlp,
                         const float* ddelta, const void* fwd_state, float* table_grad,
                         float* mlp_grad, const dash_smooth* smooth, void* stream);
+
+/* ---------------- a12: many scenes x timestamps, one graph launch ------ */
+
+#define DASH_MAX_SCENES 64
+
+/* One scene of a batched run: its own tables and decoder, its dynamic
+ * Gaussians' FP32 coordinates x, y, z [n], K normalised timestamps (device
+ * [K]; one broadcast t per frame), and delta_out SoA [K][O][n] FP32.  n is the
+ * capacity and initial count; the live count can be changed on the device
+ * through dash_batch_counts() without rebuilding the plan. */
+typedef struct dash_batch_scene {
+  const void* table;
+  const float* params;
+  const float* x;
+  const float* y;
+  const float* z;
+  const float* timestamps;
+  float* delta_out;
+  int64_t n;
+  int32_t K, reserved;
+} dash_batch_scene;
+
+/* All scenes share the grid layout, table dtype and decoder widths. */
+typedef struct dash_batch_desc {
+  const dash_layout* layout;
+  int32_t table_dtype;
+  int32_t d_in, d_hidden, d_out;
+  int32_t n_scenes;
+  const dash_batch_scene* scenes; /* host array of n_scenes */
+} dash_batch_desc;
+
+typedef struct dash_batch_plan dash_batch_plan;
+
+/* Builds a plan on the current device: copies the scene descriptors and
+ * counts to device memory (the only allocation of the library) and captures
+ * one persistent launch of the batched forward (Eqs. 8-9 gathers and the
+ * tensor-core decoder for every (scene, timestamp, 128-Gaussian tile)) in a
+ * CUDA graph.  The kernel reads the counts on the device.  Synchronous.
+ * Errors: INVALID_ARG, UNSUPPORTED (n_scenes > 64, shapes), CUDA. */
+int dash_batch_plan_create(const dash_batch_desc* desc, dash_batch_plan** out);
+/* Device int64 [n_scenes] live counts (each clamped to its capacity). */
+int64_t* dash_batch_counts(dash_batch_plan* plan);
+/* Replays the captured graph on `stream`. */
+int dash_batch_run(dash_batch_plan* plan, void* stream);
+/* Kernel form in use (index into the compiled (gather groups, ring stages)
+ * forms the autotuner chooses from). */
+int dash_batch_form(const dash_batch_plan* plan);
+/* Autotuner: if cache_json_path holds an entry for this plan's signature
+ * (GPU, grid shape, scenes, counts, timestamps) that form is used; otherwise
+ * every compiled form is timed on this plan's own work (one warm-up and three
+ * timed launches on `stream`), the fastest kept, and the cache file rewritten
+ * with it.  The graph is re-captured for the chosen form.  Synchronous. */
+int dash_batch_autotune(dash_batch_plan* plan, const char* cache_json_path, void* stream);
+int dash_batch_plan_destroy(dash_batch_plan* plan);
 
 /* ------------------------ plain FP32 form (comparison baseline) -------- */
 /* One thread per point, FP32 tables, f_h stored in global memory, FP32

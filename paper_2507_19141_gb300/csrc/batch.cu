@@ -1,0 +1,525 @@
+// batch.cu -- a12: the deformation forward for many scenes x many timestamps
+// in one persistent launch, captured once in a CUDA graph and replayed.
+//
+// Work list: items (scene s, timestamp k, tile of 128 dynamic Gaussians),
+// scene-major, then timestamp, then tile, so one scene's tables stay in L2
+// while all of its timestamps run (each scene renders K frames with one
+// broadcast t per frame, Sec. 5 / Table 3's per-frame rendering).  Counts are
+// read from device memory at run time: the captured graph stays valid when a
+// scene's dynamic count changes (e.g. written by dash_compact_dynamic).
+//
+// Each CTA (one per SM) is warp-specialised as in the single-scene forward:
+// P gather groups fill an S-stage ring; the decoder group drains it on the
+// tensor cores and rebuilds its BF16 weight tiles when the scene changes.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "deform_common.cuh"
+
+struct dash_batch_plan;
+
+namespace dash {
+namespace fused {
+namespace {
+
+__device__ unsigned int g_batch_flags;  // bit 0: a bounded wait gave up
+
+constexpr int kMaxScenes = DASH_MAX_SCENES;
+
+struct SceneDev {
+  const void* table;
+  const float* params;
+  const float* x;
+  const float* y;
+  const float* z;
+  const float* ts;
+  float* delta;
+  long long n_cap;
+  int K, pad;
+};
+
+struct BatchArgs {
+  Geom g;
+  int D, Dp, O, n_scenes;
+  const SceneDev* scenes;
+  const long long* counts;
+  unsigned int* flags;
+  uint32_t off_w2, off_w3, off_ring, off_a2, off_bar, off_tab, stage_bytes;
+};
+
+struct Item {
+  int s, k;
+  long long tile;
+};
+
+__device__ __forceinline__ Item decode_item(long long item, const long long* item_off, const long long* tiles,
+                                            int n_scenes) {
+  int s = 0;
+  while (s + 1 < n_scenes && item >= item_off[s + 1]) ++s;
+  const long long local = item - item_off[s];
+  Item it;
+  it.s = s;
+  it.k = (int)(local / tiles[s]);
+  it.tile = local % tiles[s];
+  return it;
+}
+
+template <typename TT, int F, int P, int S>
+__global__ void __launch_bounds__((P + 1) * kRows, 1) batch_fwd_kernel(const __grid_constant__ BatchArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int tid = threadIdx.x;
+  const int KB1 = 2 * a.Dp + 16;
+  uint8_t* w1 = smem;
+  uint8_t* w2 = smem + a.off_w2;
+  uint8_t* w3 = smem + a.off_w3;
+  uint8_t* ring = smem + a.off_ring;
+  uint8_t* A2 = smem + a.off_a2;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + a.off_bar);
+  uint64_t* empty = full + S;
+  uint64_t* mma_bar = empty + S;
+  volatile uint32_t* holder = reinterpret_cast<volatile uint32_t*>(mma_bar + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(mma_bar + 1) + 1;
+  long long* item_off = reinterpret_cast<long long*>(smem + a.off_tab);  // [n_scenes + 1]
+  long long* tiles = item_off + kMaxScenes + 1;                           // [n_scenes]
+
+  if (tid == 0) {
+    long long acc = 0;
+    for (int s = 0; s < a.n_scenes; ++s) {
+      long long c = a.counts[s];
+      const long long cap = a.scenes[s].n_cap;
+      c = c < 0 ? 0 : (c > cap ? cap : c);
+      const long long t = (c + kRows - 1) / kRows;
+      tiles[s] = t > 0 ? t : 1;
+      item_off[s] = acc;
+      acc += t * (long long)a.scenes[s].K;
+    }
+    item_off[a.n_scenes] = acc;
+    for (int s = 0; s < S; ++s) {
+      tc::mbar_init(tc::smem_addr(&full[s]), kRows);
+      tc::mbar_init(tc::smem_addr(&empty[s]), 1);
+    }
+    tc::mbar_init(tc::smem_addr(mma_bar), 1);
+    tc::mbar_init_fence();
+    *abort_flag = 0;
+  }
+  if (tid < 32) tc::tmem_alloc(tc::smem_addr(const_cast<uint32_t*>(holder)), 64);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *holder;
+  const long long total = item_off[a.n_scenes];
+  const long long my_items = total > blockIdx.x ? (total - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+
+  if (tid < kRows) {
+    // ------------------------------------------------ consumer: the decoder
+    const int r = tid, q = tid >> 5;
+    const uint32_t trow = tbase + ((uint32_t)(q * 32) << 16);
+    const uint32_t mb = tc::smem_addr(mma_bar);
+    uint32_t phase = 0;
+    int cur_scene = -1;
+    for (long long j = 0; j < my_items; ++j) {
+      const Item it = decode_item(blockIdx.x + j * gridDim.x, item_off, tiles, a.n_scenes);
+      const SceneDev& sc = a.scenes[it.s];
+      long long cnt = a.counts[it.s];
+      cnt = cnt < 0 ? 0 : (cnt > sc.n_cap ? sc.n_cap : cnt);
+      if (it.s != cur_scene) {
+        // the previous tile's MMAs have completed: the weight tiles are free
+        build_forward_weights(w1, w2, w3, sc.params, a.D, a.Dp, a.O, r, kRows);
+        tc::fence_async_smem();
+        cur_scene = it.s;
+      }
+      const int s = (int)(j % S);
+      const uint32_t round = (uint32_t)(j / S);
+      if (!tc::mbar_wait(tc::smem_addr(&full[s]), round & 1u, kWaitIters)) {
+        atomicOr(a.flags, 1u);
+        *abort_flag = 1;
+      }
+      tc::named_sync(1, kRows);
+      if (*abort_flag) break;
+      if (r == 0) {
+        tc::fence_after_sync();
+        mma_chain(tbase, ring + s * a.stage_bytes, KB1, w1, KB1, KB1, kHidden);
+        tc::mma_commit(tc::smem_addr(&empty[s]));
+        tc::mma_commit(mb);
+      }
+      if (!tc::mbar_wait(mb, phase, kWaitIters)) {
+        atomicOr(a.flags, 1u);
+        *abort_flag = 1;
+      }
+      phase ^= 1u;
+      tc::fence_after_sync();
+      uint32_t m[2];
+      hidden_epilogue(trow, A2, r, m);
+      tc::fence_before_sync();
+      tc::fence_async_smem();
+      tc::named_sync(1, kRows);
+      if (*abort_flag) break;
+      if (r == 0) {
+        tc::fence_after_sync();
+        mma_chain(tbase, A2, kKH, w2, kKH, kKH, kHidden);
+        tc::mma_commit(mb);
+      }
+      if (!tc::mbar_wait(mb, phase, kWaitIters)) {
+        atomicOr(a.flags, 1u);
+        *abort_flag = 1;
+      }
+      phase ^= 1u;
+      tc::fence_after_sync();
+      hidden_epilogue(trow, A2, r, m);
+      tc::fence_before_sync();
+      tc::fence_async_smem();
+      tc::named_sync(1, kRows);
+      if (*abort_flag) break;
+      if (r == 0) {
+        tc::fence_after_sync();
+        mma_chain(tbase, A2, kKH, w3, kKH, kKH, kOutPad);
+        tc::mma_commit(mb);
+      }
+      if (!tc::mbar_wait(mb, phase, kWaitIters)) {
+        atomicOr(a.flags, 1u);
+        *abort_flag = 1;
+      }
+      phase ^= 1u;
+      tc::fence_after_sync();
+      float o[16];
+      tc::tmem_ld16(trow, o);
+      const long long row = it.tile * kRows + r;
+      if (row < cnt) {
+        float* out = sc.delta + (long long)it.k * a.O * sc.n_cap + row;
+        for (int c = 0; c < a.O; ++c) __stcs(out + (long long)c * sc.n_cap, o[c]);
+      }
+      tc::fence_before_sync();
+      tc::named_sync(1, kRows);  // all rows done with the weight tiles before a rebuild
+    }
+  } else {
+    // ------------------------------------------- producers: Eqs. 8-9 gathers
+    const int pg = tid / kRows - 1, r = tid % kRows;
+    for (long long j = pg; j < my_items; j += P) {
+      const Item it = decode_item(blockIdx.x + j * gridDim.x, item_off, tiles, a.n_scenes);
+      const SceneDev& sc = a.scenes[it.s];
+      long long cnt = a.counts[it.s];
+      cnt = cnt < 0 ? 0 : (cnt > sc.n_cap ? sc.n_cap : cnt);
+      const int s = (int)(j % S);
+      const uint32_t round = (uint32_t)(j / S);
+      if (!tc::mbar_wait(tc::smem_addr(&empty[s]), (round & 1u) ^ 1u, kWaitIters)) {
+        atomicOr(a.flags, 1u);
+        *abort_flag = 1;
+      }
+      if (*abort_flag) break;
+      const long long row = it.tile * kRows + r;
+      const bool valid = row < cnt;
+      float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (valid) {
+        p.x = clamp01(__ldg(sc.x + row));
+        p.y = clamp01(__ldg(sc.y + row));
+        p.z = clamp01(__ldg(sc.z + row));
+        p.w = clamp01(__ldg(sc.ts + it.k));
+      }
+      encode_operand_row<TT, F>(a.g, static_cast<const TT*>(sc.table), p, valid, a.D, a.Dp,
+                                ring + s * a.stage_bytes, r, nullptr);
+      tc::fence_async_smem();
+      tc::mbar_arrive(tc::smem_addr(&full[s]));
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (tid < 32) tc::tmem_dealloc(tbase, 64);
+}
+
+// Compiled forms the autotuner chooses from: (gather groups P, ring stages S).
+struct Form {
+  int P, S;
+};
+constexpr Form kForms[] = {{3, 6}, {2, 4}, {3, 3}, {1, 4}};
+constexpr int kNumForms = sizeof(kForms) / sizeof(kForms[0]);
+
+size_t smem_for(int P, int S, int Dp, BatchArgs* a) {
+  (void)P;
+  const uint32_t KA = 2 * Dp + 16;
+  a->off_w2 = ((uint32_t)kHidden * KA * 2 + 127) & ~127u;
+  a->off_w3 = a->off_w2 + (uint32_t)kHidden * kKH * 2;
+  a->off_ring = (a->off_w3 + (uint32_t)kOutPad * kKH * 2 + 127) & ~127u;
+  a->stage_bytes = (uint32_t)kRows * KA * 2;
+  a->off_a2 = a->off_ring + S * a->stage_bytes;
+  a->off_bar = a->off_a2 + kATileBytes;
+  a->off_tab = (a->off_bar + 8 * (2 * S + 1) + 16 + 15) & ~15u;
+  return a->off_tab + sizeof(long long) * (2 * kMaxScenes + 1);
+}
+
+template <typename TT, int F, int P, int S>
+int launch_form(BatchArgs a, cudaStream_t st) {
+  const size_t smem = smem_for(P, S, a.Dp, &a);
+  if (smem > 227 * 1024) return fail(DASH_ERR_UNSUPPORTED, "batched form P=%d S=%d needs %zu B of shared memory", P, S, smem);
+  auto kern = batch_fwd_kernel<TT, F, P, S>;
+  if (int s = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                          "cudaFuncSetAttribute(batch)"))
+    return s;
+  kern<<<(unsigned)sm_count(), (P + 1) * kRows, smem, st>>>(a);
+  return launch_status("batch_fwd_kernel");
+}
+
+template <typename TT, int F>
+int launch_tt_f(int form, BatchArgs& a, cudaStream_t st) {
+  switch (form) {
+    case 0: return launch_form<TT, F, 3, 6>(a, st);
+    case 1: return launch_form<TT, F, 2, 4>(a, st);
+    case 2: return launch_form<TT, F, 3, 3>(a, st);
+    default: return launch_form<TT, F, 1, 4>(a, st);
+  }
+}
+
+int launch_batch(int form, int table_dtype, BatchArgs& a, cudaStream_t st) {
+  if (table_dtype == DASH_F16) {
+    switch (a.g.F) {
+      case 1: return launch_tt_f<__half, 1>(form, a, st);
+      case 2: return launch_tt_f<__half, 2>(form, a, st);
+      case 4: return launch_tt_f<__half, 4>(form, a, st);
+      default: return launch_tt_f<__half, 8>(form, a, st);
+    }
+  }
+  switch (a.g.F) {
+    case 1: return launch_tt_f<float, 1>(form, a, st);
+    case 2: return launch_tt_f<float, 2>(form, a, st);
+    case 4: return launch_tt_f<float, 4>(form, a, st);
+    default: return launch_tt_f<float, 8>(form, a, st);
+  }
+}
+
+unsigned int* batch_flags_ptr() {
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_batch_flags) != cudaSuccess) return nullptr;
+  return static_cast<unsigned int*>(p);
+}
+
+}  // namespace
+
+}  // namespace fused
+}  // namespace dash
+
+struct dash_batch_plan {
+  int device;
+  int table_dtype;
+  int form;
+  dash::fused::BatchArgs args;
+  dash::fused::SceneDev* d_scenes;
+  long long* d_counts;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  std::string signature;
+};
+
+namespace {
+
+void destroy_graph(dash_batch_plan* p) {
+  if (p->exec != nullptr) cudaGraphExecDestroy(p->exec);
+  if (p->graph != nullptr) cudaGraphDestroy(p->graph);
+  p->exec = nullptr;
+  p->graph = nullptr;
+}
+
+// Captures one launch of the current form into a graph on a private stream.
+int capture(dash_batch_plan* p) {
+  using namespace dash;
+  destroy_graph(p);
+  cudaStream_t cs = nullptr;
+  if (int s = cuda_status(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "cudaStreamCreate")) return s;
+  int rc = cuda_status(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+  if (rc == DASH_OK) {
+    const int lr = fused::launch_batch(p->form, p->table_dtype, p->args, cs);
+    const int er = cuda_status(cudaStreamEndCapture(cs, &p->graph), "cudaStreamEndCapture");
+    rc = lr != DASH_OK ? lr : er;
+  }
+  if (rc == DASH_OK) rc = cuda_status(cudaGraphInstantiate(&p->exec, p->graph, 0), "cudaGraphInstantiate");
+  cudaStreamDestroy(cs);
+  if (rc != DASH_OK) destroy_graph(p);
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dash_batch_plan_create(const dash_batch_desc* desc, dash_batch_plan** out) {
+  using namespace dash;
+  if (out == nullptr || desc == nullptr || desc->scenes == nullptr) return fail(DASH_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  if (desc->n_scenes < 1 || desc->n_scenes > DASH_MAX_SCENES)
+    return fail(DASH_ERR_UNSUPPORTED, "n_scenes=%d outside [1, %d]", desc->n_scenes, DASH_MAX_SCENES);
+  if (!(desc->table_dtype == DASH_F16 || desc->table_dtype == DASH_F32))
+    return fail(DASH_ERR_UNSUPPORTED, "table_dtype %d (F32 or F16)", desc->table_dtype);
+  fused::BatchArgs a;
+  memset(&a, 0, sizeof(a));
+  if (int s = make_geom(desc->layout, &a.g)) return s;
+  const int D = a.g.L * a.g.F;
+  if (desc->d_in != D) return fail(DASH_ERR_INVALID_ARG, "d_in=%d but L*F=%d", desc->d_in, D);
+  if (D > 64 || desc->d_hidden != fused::kHidden || desc->d_out < 1 || desc->d_out > fused::kOutPad)
+    return fail(DASH_ERR_UNSUPPORTED, "fused decoder supports L*F <= 64, H = 64, 1 <= O <= 16");
+  a.D = D;
+  a.Dp = fused::pad16(D);
+  a.O = desc->d_out;
+  a.n_scenes = desc->n_scenes;
+  a.flags = fused::batch_flags_ptr();
+  if (a.flags == nullptr) return fail(DASH_ERR_CUDA, "cannot resolve the device flag word");
+  fused::SceneDev host[DASH_MAX_SCENES];
+  long long counts[DASH_MAX_SCENES];
+  long long total_n = 0, total_k = 0;
+  for (int s = 0; s < desc->n_scenes; ++s) {
+    const dash_batch_scene& sc = desc->scenes[s];
+    if (sc.n < 0 || sc.K < 1) return fail(DASH_ERR_INVALID_ARG, "scene %d: n < 0 or K < 1", s);
+    if (sc.table == nullptr || sc.params == nullptr || sc.x == nullptr || sc.y == nullptr || sc.z == nullptr ||
+        sc.timestamps == nullptr || sc.delta_out == nullptr)
+      return fail(DASH_ERR_INVALID_ARG, "scene %d: NULL pointer", s);
+    if ((reinterpret_cast<uintptr_t>(sc.table) & 15u) != 0)
+      return fail(DASH_ERR_INVALID_ARG, "scene %d: table must be 16-byte aligned", s);
+    host[s] = fused::SceneDev{sc.table, sc.params, sc.x, sc.y, sc.z, sc.timestamps, sc.delta_out, sc.n, sc.K, 0};
+    counts[s] = sc.n;
+    total_n += sc.n;
+    total_k += sc.K;
+  }
+  dash_batch_plan* p = new dash_batch_plan();
+  p->device = 0;
+  cudaGetDevice(&p->device);
+  p->table_dtype = desc->table_dtype;
+  p->form = 0;
+  p->d_scenes = nullptr;
+  p->d_counts = nullptr;
+  p->graph = nullptr;
+  p->exec = nullptr;
+  int rc = cuda_status(cudaMalloc(&p->d_scenes, sizeof(fused::SceneDev) * desc->n_scenes), "cudaMalloc");
+  if (rc == DASH_OK) rc = cuda_status(cudaMalloc(&p->d_counts, sizeof(long long) * desc->n_scenes), "cudaMalloc");
+  if (rc == DASH_OK)
+    rc = cuda_status(cudaMemcpy(p->d_scenes, host, sizeof(fused::SceneDev) * desc->n_scenes, cudaMemcpyHostToDevice),
+                     "cudaMemcpy");
+  if (rc == DASH_OK)
+    rc = cuda_status(cudaMemcpy(p->d_counts, counts, sizeof(long long) * desc->n_scenes, cudaMemcpyHostToDevice),
+                     "cudaMemcpy");
+  if (rc == DASH_OK) {
+    a.scenes = p->d_scenes;
+    a.counts = p->d_counts;
+    p->args = a;
+    char sig[256];
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, p->device);
+    snprintf(sig, sizeof(sig), "%s|L%d F%d T%d D%d O%d|dt%d|S%d N%lld K%lld", prop.name, a.g.L, a.g.F,
+             desc->layout->log2_T, D, a.O, desc->table_dtype, desc->n_scenes, total_n, total_k);
+    p->signature = sig;
+    rc = capture(p);
+  }
+  if (rc != DASH_OK) {
+    dash_batch_plan_destroy(p);
+    return rc;
+  }
+  *out = p;
+  return DASH_OK;
+}
+
+int64_t* dash_batch_counts(dash_batch_plan* plan) {
+  return plan == nullptr ? nullptr : reinterpret_cast<int64_t*>(plan->d_counts);
+}
+
+int dash_batch_run(dash_batch_plan* plan, void* stream) {
+  using namespace dash;
+  if (plan == nullptr || plan->exec == nullptr) return fail(DASH_ERR_INVALID_ARG, "plan is NULL or not instantiated");
+  return cuda_status(cudaGraphLaunch(plan->exec, as_stream(stream)), "cudaGraphLaunch");
+}
+
+int dash_batch_plan_destroy(dash_batch_plan* plan) {
+  if (plan == nullptr) return DASH_OK;
+  destroy_graph(plan);
+  if (plan->d_scenes != nullptr) cudaFree(plan->d_scenes);
+  if (plan->d_counts != nullptr) cudaFree(plan->d_counts);
+  delete plan;
+  return DASH_OK;
+}
+
+int dash_batch_form(const dash_batch_plan* plan) { return plan == nullptr ? -1 : plan->form; }
+
+int dash_batch_autotune(dash_batch_plan* plan, const char* cache_json_path, void* stream) {
+  using namespace dash;
+  if (plan == nullptr) return fail(DASH_ERR_INVALID_ARG, "plan is NULL");
+  const std::string key = "\"" + plan->signature + "\": ";
+  std::string cache;
+  if (cache_json_path != nullptr) {
+    if (FILE* f = fopen(cache_json_path, "rb")) {
+      char buf[4096];
+      size_t k;
+      while ((k = fread(buf, 1, sizeof(buf), f)) > 0) cache.append(buf, k);
+      fclose(f);
+    }
+    const size_t at = cache.find(key);
+    if (at != std::string::npos) {
+      const int form = atoi(cache.c_str() + at + key.size());
+      if (form >= 0 && form < fused::kNumForms) {
+        if (form != plan->form) {
+          plan->form = form;
+          return capture(plan);
+        }
+        return DASH_OK;
+      }
+    }
+  }
+  // time every compiled form on this plan's work: one warm-up and three timed runs each
+  cudaStream_t st = as_stream(stream);
+  cudaEvent_t e0, e1;
+  if (int s = cuda_status(cudaEventCreate(&e0), "cudaEventCreate")) return s;
+  if (int s = cuda_status(cudaEventCreate(&e1), "cudaEventCreate")) {
+    cudaEventDestroy(e0);
+    return s;
+  }
+  int best = plan->form;
+  float best_ms = 1e30f;
+  int rc = DASH_OK;
+  for (int form = 0; form < fused::kNumForms && rc == DASH_OK; ++form) {
+    int lr = fused::launch_batch(form, plan->table_dtype, plan->args, st);
+    if (lr == DASH_ERR_UNSUPPORTED) continue;  // does not fit this shape
+    if (lr != DASH_OK) {
+      rc = lr;
+      break;
+    }
+    rc = cuda_status(cudaEventRecord(e0, st), "cudaEventRecord");
+    for (int rep = 0; rep < 3 && rc == DASH_OK; ++rep) rc = fused::launch_batch(form, plan->table_dtype, plan->args, st);
+    if (rc == DASH_OK) rc = cuda_status(cudaEventRecord(e1, st), "cudaEventRecord");
+    if (rc == DASH_OK) rc = cuda_status(cudaEventSynchronize(e1), "cudaEventSynchronize");
+    float ms = 0.0f;
+    if (rc == DASH_OK) rc = cuda_status(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+    if (rc == DASH_OK && ms < best_ms) {
+      best_ms = ms;
+      best = form;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != DASH_OK) return rc;
+  plan->form = best;
+  if (cache_json_path != nullptr) {
+    // keep the other entries; replace or append this signature
+    std::string body;
+    const size_t lb = cache.find('{'), rb = cache.rfind('}');
+    if (lb != std::string::npos && rb != std::string::npos && rb > lb) body = cache.substr(lb + 1, rb - lb - 1);
+    std::string entries;
+    size_t pos = 0;
+    while (pos < body.size()) {
+      size_t nl = body.find('\n', pos);
+      if (nl == std::string::npos) nl = body.size();
+      std::string line = body.substr(pos, nl - pos);
+      pos = nl + 1;
+      while (!line.empty() && (line.back() == ',' || line.back() == ' ' || line.back() == '\r')) line.pop_back();
+      const size_t first = line.find_first_not_of(' ');
+      if (first == std::string::npos || line.find(key) != std::string::npos) continue;
+      entries += "  " + line.substr(first) + ",\n";
+    }
+    char mine[512];
+    snprintf(mine, sizeof(mine), "  %s%d\n", key.c_str(), best);
+    if (FILE* f = fopen(cache_json_path, "wb")) {
+      fprintf(f, "{\n%s%s}\n", entries.c_str(), mine);
+      fclose(f);
+    }
+  }
+  return capture(plan);
+}
+
+}  // extern "C"

@@ -27,6 +27,7 @@ int sm_count();
 
 // Kernel-form options (dash_set_option).
 extern int g_opt_fwd_form;
+extern int g_opt_bwd_form;
 
 // ------------------------------------------------ kernel-side geometry ----
 // Level layout in the form the kernels read it (by-value kernel argument).

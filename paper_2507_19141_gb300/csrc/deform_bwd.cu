@@ -52,7 +52,7 @@ struct BwdArgs {
   float eps_t;
   float* loss_out;
   unsigned int* flags;
-  uint32_t off_w2, off_w3, off_f, off_h1, off_x, off_g3, off_bar, group_bytes;
+  uint32_t off_w2, off_w3, off_f, off_h1, off_x, off_g3, off_ring, off_bar;
 };
 
 __device__ __forceinline__ bool wait_mma(uint32_t bar, uint32_t phase, unsigned int* flags, volatile int* abort) {
@@ -474,6 +474,380 @@ __global__ void __launch_bounds__(kRows, 1) deform_bwd_kernel(const __grid_const
   if (r < 32) tc::tmem_dealloc(tbase, kTmemCols);
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialised backward.  Warps 0-3 (the decoder group, thread r = TMEM
+// lane r) rebuild f_h from the forward state, run the decoder recompute and
+// back-propagation on the tensor cores, accumulate dW in TMEM, and publish
+// dL/df_h of each tile into a shared-memory ring (transposed [D][128] FP32).
+// P scatter groups drain the ring: each thread takes one Gaussian, recomputes
+// its corners and issues the vector reductions into the tables; with the
+// smoothness term on they also encode p, p + e_s, p + e_t and scatter the
+// perturbed points' gradients.  Requires the forward state.
+// ---------------------------------------------------------------------------
+template <typename TT, int F, int P, int S>
+__global__ void __launch_bounds__((P + 1) * kRows, 1) deform_bwd_ws_kernel(const __grid_constant__ BwdArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int tid = threadIdx.x;
+  const int KF = 2 * a.Dp + 16;
+  uint8_t* w1 = smem;
+  uint8_t* w2 = smem + a.off_w2;
+  uint8_t* w3 = smem + a.off_w3;
+  uint8_t* Ft = smem + a.off_f;
+  uint8_t* H1 = smem + a.off_h1;
+  uint8_t* X = smem + a.off_x;
+  uint8_t* G3 = smem + a.off_g3;
+  float* ring = reinterpret_cast<float*>(smem + a.off_ring);  // S stages of [Dp][kRows]
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + a.off_bar);
+  uint64_t* empty = full + S;
+  uint64_t* mma_bar = empty + S;
+  volatile uint32_t* holder = reinterpret_cast<volatile uint32_t*>(mma_bar + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(mma_bar + 1) + 1;
+  const int stage_floats = a.Dp * kRows;
+
+  const float* W1 = a.params;
+  const float* b1 = W1 + kHidden * a.D;
+  const float* W2 = b1 + kHidden;
+  const float* b2 = W2 + kHidden * kHidden;
+  const float* W3 = b2 + kHidden;
+  const float* b3 = W3 + a.O * kHidden;
+  if (tid < kRows) {
+    build_weight_tile(w1, kHidden, KF, a.Dp, true, a.D, kHidden, W1, b1, tid, kRows);
+    build_weight_tile(w2, kHidden, kKH2, kHidden, true, kHidden, kHidden, W2, b2, tid, kRows);
+    build_weight_tile(w3, kOutPad, kKH, kHidden, false, kHidden, a.O, W3, b3, tid, kRows);
+  }
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      tc::mbar_init(tc::smem_addr(&full[s]), kRows);
+      tc::mbar_init(tc::smem_addr(&empty[s]), kRows);
+    }
+    tc::mbar_init(tc::smem_addr(mma_bar), 1);
+    tc::mbar_init_fence();
+    *abort_flag = 0;
+  }
+  if (tid < 32) tc::tmem_alloc(tc::smem_addr(const_cast<uint32_t*>(holder)), kTmemCols);
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *holder;
+
+  const long long n = point_count(a.pts);
+  const long long ntiles = (n + kRows - 1) / kRows;
+  const long long my_tiles = ntiles > blockIdx.x ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const bool smooth = a.lambda_r != 0.0f;
+  const float scale = n > 0 ? 2.0f * a.lambda_r / (float)n : 0.0f;
+  float loss = 0.0f;
+
+  if (tid < kRows) {
+    // ----------------------------------------------------- decoder group
+    const int r = tid, q = tid >> 5;
+    const uint32_t trow = tbase + ((uint32_t)(q * 32) << 16);
+    const uint32_t bar = tc::smem_addr(mma_bar);
+    uint32_t phase = 0;
+    bool had_tile = false;
+    const uint32_t id_fwd = tc::idesc_bf16(kRows, kHidden, 0, 0);
+    const uint32_t id_dh = tc::idesc_bf16(kRows, kHidden, 0, 1);
+    const uint32_t id_df = tc::idesc_bf16(kRows, a.Dp, 0, 1);
+    const uint32_t id_w = tc::idesc_bf16(kRows, kHidden, 1, 1);
+    const uint32_t id_w3 = tc::idesc_bf16(kRows, kOutPad, 1, 1);
+    for (long long j = 0; j < my_tiles; ++j) {
+      const long long row = (blockIdx.x + j * gridDim.x) * kRows + r;
+      const bool valid = row < n;
+      const uint8_t* srow = valid ? a.state + row * state_stride(a.D) : nullptr;
+      // f_h [hi | 1 | 0] from the state, masks from the forward
+      const __nv_bfloat16* fs = reinterpret_cast<const __nv_bfloat16*>(srow);
+      for (int c = 0; c < a.Dp / 8; ++c) {
+        uint32_t h[4];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          const int k = 8 * c + 2 * jj;
+          const float v0 = (srow != nullptr && k < a.D) ? __bfloat162float(__ldcs(fs + k)) : 0.0f;
+          const float v1 = (srow != nullptr && k + 1 < a.D) ? __bfloat162float(__ldcs(fs + k + 1)) : 0.0f;
+          h[jj] = pack_bf16x2(v0, v1);
+        }
+        *reinterpret_cast<uint4*>(Ft + tile_off(r, 8 * c, KF)) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4*>(Ft + tile_off(r, a.Dp + 16 + 8 * c, KF)) = make_uint4(0u, 0u, 0u, 0u);
+      }
+      write_ones(Ft, r, a.Dp, KF);
+      uint32_t m1[2] = {0u, 0u}, m2[2] = {0u, 0u};
+      if (srow != nullptr) {
+        const uint4 m = __ldcs(reinterpret_cast<const uint4*>(srow + state_mask_off(a.D)));
+        m1[0] = m.x;
+        m1[1] = m.y;
+        m2[0] = m.z;
+        m2[1] = m.w;
+      }
+      tc::fence_async_smem();
+      tc::named_sync(1, kRows);
+      if (*abort_flag) break;
+      if (r == 0) {
+        tc::fence_after_sync();
+        issue(tbase + kColS, kmajor(Ft, KF), kmajor(w1, KF), KF, id_fwd, false);
+        tc::mma_commit(bar);
+      }
+      wait_mma(bar, phase, a.flags, abort_flag);
+      phase ^= 1u;
+      tc::fence_after_sync();
+      // h1 = relu(z1) with the forward's mask -> H1 [hi | 1 | lo]
+#pragma unroll
+      for (int c = 0; c < kHidden / 16; ++c) {
+        float v[16];
+        tc::tmem_ld16(trow + kColS + 16 * c, v);
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj)
+          v[jj] = ((m1[c >> 1] >> ((c & 1) * 16 + jj)) & 1u) ? fmaxf(v[jj], 0.0f) : 0.0f;
+        uint4 h0, l0, h1, l1;
+        split_hi_lo8(v, h0, l0);
+        split_hi_lo8(v + 8, h1, l1);
+        *reinterpret_cast<uint4*>(H1 + tile_off(r, 16 * c, kKH2)) = h0;
+        *reinterpret_cast<uint4*>(H1 + tile_off(r, 16 * c + 8, kKH2)) = h1;
+        *reinterpret_cast<uint4*>(H1 + tile_off(r, kHidden + 16 + 16 * c, kKH2)) = l0;
+        *reinterpret_cast<uint4*>(H1 + tile_off(r, kHidden + 16 + 16 * c + 8, kKH2)) = l1;
+      }
+      write_ones(H1, r, kHidden, kKH2);
+      tc::fence_before_sync();
+      tc::fence_async_smem();
+      tc::named_sync(1, kRows);
+      if (*abort_flag) break;
+      if (r == 0) {
+        tc::fence_after_sync();
+        issue(tbase + kColS, kmajor(H1, kKH2), kmajor(w2, kKH2), kKH2, id_fwd, false);
+        tc::mma_commit(bar);
+      }
+      wait_mma(bar, phase, a.flags, abort_flag);
+      phase ^= 1u;
+      tc::fence_after_sync();
+      // h2 -> X [h2 | 1]; ddelta -> G3
+#pragma unroll
+      for (int c = 0; c < kHidden / 16; ++c) {
+        float v[16];
+        tc::tmem_ld16(trow + kColS + 16 * c, v);
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj)
+          v[jj] = ((m2[c >> 1] >> ((c & 1) * 16 + jj)) & 1u) ? fmaxf(v[jj], 0.0f) : 0.0f;
+        uint32_t h[8];
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) h[jj] = pack_bf16x2(v[2 * jj], v[2 * jj + 1]);
+        *reinterpret_cast<uint4*>(X + tile_off(r, 16 * c, kKH)) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4*>(X + tile_off(r, 16 * c + 8, kKH)) = make_uint4(h[4], h[5], h[6], h[7]);
+      }
+      write_ones(X, r, kHidden, kKH);
+      {
+        float d[16];
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj)
+          d[jj] = (valid && jj < a.O) ? __ldcs(a.ddelta + (long long)jj * a.n_cap + row) : 0.0f;
+        uint32_t h[8];
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) h[jj] = pack_bf16x2(d[2 * jj], d[2 * jj + 1]);
+        *reinterpret_cast<uint4*>(G3 + tile_off(r, 0, kKO)) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4*>(G3 + tile_off(r, 8, kKO)) = make_uint4(h[4], h[5], h[6], h[7]);
+      }
+      tc::fence_before_sync();
+      tc::fence_async_smem();
+      tc::named_sync(1, kRows);
+      if (*abort_flag) break;
+      if (r == 0) {
+        tc::fence_after_sync();
+        issue(tbase + kColS, kmajor(G3, kKO), mnmajor(w3, kKH), kKO, id_dh, false);
+        issue(tbase + kColW3, mnmajor(X, kKH), mnmajor(G3, kKO), kRows, id_w3, had_tile);
+        tc::mma_commit(bar);
+      }
+      wait_mma(bar, phase, a.flags, abort_flag);
+      phase ^= 1u;
+      tc::fence_after_sync();
+      // dz2 = dh2 * m2 -> X
+#pragma unroll
+      for (int c = 0; c < kHidden / 16; ++c) {
+        float v[16];
+        tc::tmem_ld16(trow + kColS + 16 * c, v);
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) v[jj] = ((m2[c >> 1] >> ((c & 1) * 16 + jj)) & 1u) ? v[jj] : 0.0f;
+        uint32_t h[8];
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) h[jj] = pack_bf16x2(v[2 * jj], v[2 * jj + 1]);
+        *reinterpret_cast<uint4*>(X + tile_off(r, 16 * c, kKG)) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4*>(X + tile_off(r, 16 * c + 8, kKG)) = make_uint4(h[4], h[5], h[6], h[7]);
+      }
+      tc::fence_before_sync();
+      tc::fence_async_smem();
+      tc::named_sync(1, kRows);
+      if (*abort_flag) break;
+      if (r == 0) {
+        tc::fence_after_sync();
+        issue(tbase + kColS, kmajor(X, kKG), mnmajor(w2, kKH2), kKG, id_dh, false);
+        issue(tbase + kColW2, mnmajor(H1, kKH2), mnmajor(X, kKG), kRows, id_w, had_tile);
+        tc::mma_commit(bar);
+      }
+      wait_mma(bar, phase, a.flags, abort_flag);
+      phase ^= 1u;
+      tc::fence_after_sync();
+      // dz1 = dh1 * m1 -> H1
+#pragma unroll
+      for (int c = 0; c < kHidden / 16; ++c) {
+        float v[16];
+        tc::tmem_ld16(trow + kColS + 16 * c, v);
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) v[jj] = ((m1[c >> 1] >> ((c & 1) * 16 + jj)) & 1u) ? v[jj] : 0.0f;
+        uint32_t h[8];
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) h[jj] = pack_bf16x2(v[2 * jj], v[2 * jj + 1]);
+        *reinterpret_cast<uint4*>(H1 + tile_off(r, 16 * c, kKG)) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4*>(H1 + tile_off(r, 16 * c + 8, kKG)) = make_uint4(h[4], h[5], h[6], h[7]);
+      }
+      tc::fence_before_sync();
+      tc::fence_async_smem();
+      tc::named_sync(1, kRows);
+      if (*abort_flag) break;
+      if (r == 0) {
+        tc::fence_after_sync();
+        issue(tbase + kColS, kmajor(H1, kKG), mnmajor(w1, KF), kKG, id_df, false);
+        issue(tbase + kColW1, mnmajor(Ft, KF), mnmajor(H1, kKG), kRows, id_w, had_tile);
+        tc::mma_commit(bar);
+      }
+      wait_mma(bar, phase, a.flags, abort_flag);
+      phase ^= 1u;
+      tc::fence_after_sync();
+      had_tile = true;
+      // publish dL/df_h of this tile to the scatter groups
+      const int s = (int)(j % S);
+      const uint32_t round = (uint32_t)(j / S);
+      if (!tc::mbar_wait(tc::smem_addr(&empty[s]), (round & 1u) ^ 1u, kWaitIters)) {
+        atomicOr(a.flags, 1u);
+        *abort_flag = 1;
+      }
+      float* stage = ring + (size_t)s * stage_floats;
+      for (int c = 0; c < a.Dp / 16; ++c) {
+        float v[16];
+        tc::tmem_ld16(trow + kColS + 16 * c, v);
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) stage[(16 * c + jj) * kRows + r] = v[jj];
+      }
+      tc::fence_before_sync();
+      tc::mbar_arrive(tc::smem_addr(&full[s]));
+    }
+    // flush the CTA's weight gradients (rows = input unit, columns = output unit)
+    tc::named_sync(1, kRows);
+    tc::fence_after_sync();
+    if (had_tile && !*abort_flag) {
+      float* gW1 = a.mlp_grad;
+      float* gb1 = gW1 + kHidden * a.D;
+      float* gW2 = gb1 + kHidden;
+      float* gb2 = gW2 + kHidden * kHidden;
+      float* gW3 = gb2 + kHidden;
+      float* gb3 = gW3 + a.O * kHidden;
+#pragma unroll 1
+      for (int c = 0; c < 4; ++c) {
+        float v[16];
+        tc::tmem_ld16(trow + kColW1 + 16 * c, v);
+        for (int jj = 0; jj < 16; ++jj) {
+          const int o = 16 * c + jj;
+          if (r < a.D) atomicAdd(gW1 + o * a.D + r, v[jj]);
+          else if (r == a.Dp) atomicAdd(gb1 + o, v[jj]);
+        }
+        tc::tmem_ld16(trow + kColW2 + 16 * c, v);
+        for (int jj = 0; jj < 16; ++jj) {
+          const int o = 16 * c + jj;
+          if (r < kHidden) atomicAdd(gW2 + o * kHidden + r, v[jj]);
+          else if (r == kHidden) atomicAdd(gb2 + o, v[jj]);
+        }
+      }
+      float v[16];
+      tc::tmem_ld16(trow + kColW3, v);
+      for (int jj = 0; jj < a.O; ++jj) {
+        if (r < kHidden) atomicAdd(gW3 + jj * kHidden + r, v[jj]);
+        else if (r == kHidden) atomicAdd(gb3 + jj, v[jj]);
+      }
+    }
+  } else {
+    // ------------------------------------------------------ scatter groups
+    const int pg = tid / kRows - 1, r = tid % kRows;
+    const TT* table = static_cast<const TT*>(a.table);
+    for (long long j = pg; j < my_tiles; j += P) {
+      const int s = (int)(j % S);
+      const uint32_t round = (uint32_t)(j / S);
+      if (!tc::mbar_wait(tc::smem_addr(&full[s]), round & 1u, kWaitIters)) {
+        atomicOr(a.flags, 1u);
+        *abort_flag = 1;
+      }
+      if (*abort_flag) break;
+      float df[64];
+      const float* stage = ring + (size_t)s * stage_floats;
+      for (int k = 0; k < a.D; ++k) df[k] = stage[k * kRows + r];
+      tc::mbar_arrive(tc::smem_addr(&empty[s]));
+      const long long row = (blockIdx.x + j * gridDim.x) * kRows + r;
+      if (row >= n) continue;
+      const float4 p = load_point(a.pts, row);
+      for (int l = 0; l < a.g.L; ++l) {
+        uint32_t idx[16];
+        float w[16];
+        level_corners(a.g, l, p, idx, w);
+        float d[F];
+#pragma unroll
+        for (int f = 0; f < F; ++f) d[f] = df[l * F + f];
+        if (smooth) {
+          float fp[F];
+          gather_level<TT, F>(table, a.g.offset[l], idx, w, fp);
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const float4 pq = e == 0 ? perturb(p, a.eps_s[0], a.eps_s[1], a.eps_s[2], 0.0f)
+                                     : perturb(p, 0.0f, 0.0f, 0.0f, a.eps_t);
+            uint32_t qi[16];
+            float qw[16];
+            level_corners(a.g, l, pq, qi, qw);
+            float fq[F], dq[F];
+            gather_level<TT, F>(table, a.g.offset[l], qi, qw, fq);
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+              const float diff = fp[f] - fq[f];
+              loss = fmaf(diff, diff, loss);
+              d[f] = fmaf(scale, diff, d[f]);
+              dq[f] = -scale * diff;
+            }
+            scatter_level<F>(a.table_grad, a.g.offset[l], qi, qw, dq);
+          }
+        }
+        scatter_level<F>(a.table_grad, a.g.offset[l], idx, w, d);
+      }
+    }
+  }
+  if (smooth && a.loss_out != nullptr) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
+    if ((tid & 31) == 0 && tid >= kRows && n > 0) atomicAdd(a.loss_out, a.lambda_r * loss / (float)n);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (tid < 32) tc::tmem_dealloc(tbase, kTmemCols);
+}
+
+template <typename TT, int F, int P, int S>
+int launch_ws(BwdArgs a, cudaStream_t st) {
+  const int KF = 2 * a.Dp + 16;
+  uint32_t off = (uint32_t)kHidden * KF * 2;
+  a.off_w2 = (off + 127) & ~127u;
+  a.off_w3 = a.off_w2 + (uint32_t)kHidden * kKH2 * 2;
+  off = a.off_w3 + (uint32_t)kOutPad * kKH * 2;
+  a.off_f = (off + 127) & ~127u;
+  a.off_h1 = a.off_f + (uint32_t)kRows * KF * 2;
+  a.off_x = a.off_h1 + (uint32_t)kRows * kKH2 * 2;
+  a.off_g3 = a.off_x + (uint32_t)kRows * kKH * 2;
+  a.off_ring = a.off_g3 + (uint32_t)kRows * kKO * 2;
+  a.off_bar = a.off_ring + (uint32_t)S * a.Dp * kRows * 4;
+  const size_t smem = a.off_bar + 8 * (2 * S + 1) + 16;
+  if (smem > 227 * 1024) return fail(DASH_ERR_UNSUPPORTED, "backward form needs %zu B of shared memory", smem);
+  auto kern = deform_bwd_ws_kernel<TT, F, P, S>;
+  if (int s = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                          "cudaFuncSetAttribute(deform_bwd_ws)"))
+    return s;
+  const long long ntiles = (a.n_cap + kRows - 1) / kRows;
+  long long grid = sm_count();
+  grid = ntiles < grid ? (ntiles > 0 ? ntiles : 1) : grid;
+  kern<<<(unsigned)grid, (P + 1) * kRows, smem, st>>>(a);
+  return launch_status("deform_bwd_ws_kernel");
+}
+
 template <typename TT, int F>
 int launch(BwdArgs a, cudaStream_t st) {
   // Tiles read transposed with M = 128 rows (F, H1, X) run past their own
@@ -511,7 +885,23 @@ int launch(BwdArgs a, cudaStream_t st) {
 }
 
 template <typename TT>
-int dispatch(int F, BwdArgs& a, cudaStream_t st) {
+int dispatch(int F, bool ws, BwdArgs& a, cudaStream_t st) {
+  if (ws) {
+    if (a.Dp > 32) {
+      switch (F) {
+        case 1: return launch_ws<TT, 1, 2, 2>(a, st);
+        case 2: return launch_ws<TT, 2, 2, 2>(a, st);
+        case 4: return launch_ws<TT, 4, 2, 2>(a, st);
+        default: return launch_ws<TT, 8, 2, 2>(a, st);
+      }
+    }
+    switch (F) {
+      case 1: return launch_ws<TT, 1, 3, 6>(a, st);
+      case 2: return launch_ws<TT, 2, 3, 6>(a, st);
+      case 4: return launch_ws<TT, 4, 3, 6>(a, st);
+      default: return launch_ws<TT, 8, 3, 6>(a, st);
+    }
+  }
   switch (F) {
     case 1: return launch<TT, 1>(a, st);
     case 2: return launch<TT, 2>(a, st);
@@ -571,9 +961,12 @@ extern "C" int dash_deform_mlp_bwd(const dash_layout* layout, const dash_points*
   a.flags = bwd_flags_ptr();
   if (a.flags == nullptr) return fail(DASH_ERR_CUDA, "cannot resolve the device flag word");
   cudaStream_t st = as_stream(stream);
+  // the warp-specialised form needs the forward state; without it the
+  // single-group form re-encodes f_h itself
+  const bool ws = g_opt_bwd_form == 0 && a.state != nullptr;
   switch (table_dtype) {
-    case DASH_F32: return dispatch<float>(a.g.F, a, st);
-    case DASH_F16: return dispatch<__half>(a.g.F, a, st);
+    case DASH_F32: return dispatch<float>(a.g.F, ws, a, st);
+    case DASH_F16: return dispatch<__half>(a.g.F, ws, a, st);
     default: return fail(DASH_ERR_UNSUPPORTED, "table_dtype %d (F32 or F16)", table_dtype);
   }
 }

@@ -100,5 +100,102 @@ __device__ __forceinline__ void mma_chain(uint32_t tmem, const uint8_t* A, int K
   }
 }
 
+constexpr int kKH = 2 * kHidden + 16;              // hidden-layer operand K (hi | ones | lo)
+constexpr uint32_t kATileBytes = kRows * kKH * 2;  // 36,864 B
+
+// Eqs. 8-9 for one point p into operand row r (K = [hi | 1 | lo], FP32
+// interpolation split into BF16 hi + lo); with state_row, also the BF16 copy
+// of f_h for the backward.  Invalid rows are zero features.
+template <typename TT, int F>
+__device__ __forceinline__ void encode_operand_row(const Geom& g, const TT* __restrict__ table, float4 p, bool valid,
+                                                   int D, int Dp, uint8_t* A, int r, uint8_t* state_row) {
+  const int KA = 2 * Dp + 16;
+  constexpr int kLevelsPerChunk = 8 / F;
+  const int nchunks = Dp / 8;
+  for (int c = 0; c < nchunks; ++c) {
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < kLevelsPerChunk; ++j) {
+      const int l = c * kLevelsPerChunk + j;
+      float acc[F];
+#pragma unroll
+      for (int f = 0; f < F; ++f) acc[f] = 0.0f;
+      if (valid && l < g.L) {
+        uint32_t idx[16];
+        float w[16];
+        level_corners(g, l, p, idx, w);
+        const TT* base = table + g.offset[l] * F;
+        if constexpr (F == 2) {
+          gather2_pairs<TT>(base, idx, w, acc);
+        } else {
+#pragma unroll
+          for (int b = 0; b < 16; ++b) {
+            float e[F];
+            load_entry<TT, F>(base + (size_t)idx[b] * F, e);
+#pragma unroll
+            for (int f = 0; f < F; ++f) acc[f] = fmaf(w[b], e[f], acc[f]);
+          }
+        }
+      }
+#pragma unroll
+      for (int f = 0; f < F; ++f) v[j * F + f] = acc[f];
+    }
+    uint4 hi, lo;
+    split_hi_lo8(v, hi, lo);
+    *reinterpret_cast<uint4*>(A + tile_off(r, 8 * c, KA)) = hi;
+    *reinterpret_cast<uint4*>(A + tile_off(r, Dp + 16 + 8 * c, KA)) = lo;
+    if (state_row != nullptr && 8 * c < D) {
+      __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(state_row) + 8 * c;
+      if ((D & 7) == 0) {
+        __stcs(reinterpret_cast<uint4*>(dst), hi);
+      } else {
+        const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&hi);
+        for (int j = 0; j < 8 && 8 * c + j < D; ++j) dst[j] = h[j];
+      }
+    }
+  }
+  write_ones(A, r, Dp, KA);
+}
+
+// Reads this thread's 64 hidden pre-activations from TMEM, records their
+// ReLU mask (bit j of mask[j / 32]), applies ReLU and writes the next
+// layer's operand row [hi | 1 | lo].
+__device__ __forceinline__ void hidden_epilogue(uint32_t trow, uint8_t* A, int r, uint32_t mask[2]) {
+  mask[0] = mask[1] = 0u;
+#pragma unroll
+  for (int c = 0; c < kHidden / 16; ++c) {
+    float v[16];
+    tc::tmem_ld16(trow + 16 * c, v);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (v[j] > 0.0f) mask[c >> 1] |= 1u << ((c & 1) * 16 + j);
+      v[j] = fmaxf(v[j], 0.0f);
+    }
+    uint4 h0, l0, h1, l1;
+    split_hi_lo8(v, h0, l0);
+    split_hi_lo8(v + 8, h1, l1);
+    *reinterpret_cast<uint4*>(A + tile_off(r, 16 * c, kKH)) = h0;
+    *reinterpret_cast<uint4*>(A + tile_off(r, 16 * c + 8, kKH)) = h1;
+    *reinterpret_cast<uint4*>(A + tile_off(r, kHidden + 16 + 16 * c, kKH)) = l0;
+    *reinterpret_cast<uint4*>(A + tile_off(r, kHidden + 16 + 16 * c + 8, kKH)) = l1;
+  }
+  write_ones(A, r, kHidden, kKH);
+}
+
+// Decoder weights -> BF16 operand tiles in shared memory (hi | 1 | lo
+// layout for the forward; bias folded in as a weight column).
+__device__ __forceinline__ void build_forward_weights(uint8_t* w1, uint8_t* w2, uint8_t* w3, const float* params,
+                                                      int D, int Dp, int O, int tid, int nthreads) {
+  const float* W1 = params;
+  const float* b1 = W1 + kHidden * D;
+  const float* W2 = b1 + kHidden;
+  const float* b2 = W2 + kHidden * kHidden;
+  const float* W3 = b2 + kHidden;
+  const float* b3 = W3 + O * kHidden;
+  build_weight_tile(w1, kHidden, 2 * Dp + 16, Dp, true, D, kHidden, W1, b1, tid, nthreads);
+  build_weight_tile(w2, kHidden, kKH, kHidden, true, kHidden, kHidden, W2, b2, tid, nthreads);
+  build_weight_tile(w3, kOutPad, kKH, kHidden, true, kHidden, O, W3, b3, tid, nthreads);
+}
+
 }  // namespace fused
 }  // namespace dash

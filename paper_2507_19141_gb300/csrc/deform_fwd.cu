@@ -17,8 +17,6 @@ namespace {
 
 __device__ unsigned int g_fwd_flags;  // bit 0: an MMA completion wait gave up
 
-constexpr int kKH = 2 * kHidden + 16;                    // hidden-layer operand K (hi | ones | lo)
-constexpr uint32_t kATileBytes = kRows * kKH * 2;        // 36,864 B per group
 
 struct FwdArgs {
   Geom g;
@@ -43,83 +41,13 @@ __device__ __forceinline__ bool wait_mma(uint32_t bar, uint32_t phase, unsigned 
   return false;
 }
 
-// Encodes Gaussian `row` (Eqs. 8-9) into operand row r: K = [hi | 1 | lo],
-// and keeps a BF16 copy of f_h in the forward state.
+// Encodes Gaussian `row` (Eqs. 8-9) into operand row r and keeps a BF16
+// copy of f_h in the forward state.
 template <typename TT, int F>
 __device__ __forceinline__ void encode_row(const FwdArgs& a, bool valid, long long row, uint8_t* A, int r) {
-  const int KA = 2 * a.Dp + 16;
   const float4 p = valid ? load_point(a.pts, row) : make_float4(0.f, 0.f, 0.f, 0.f);
-  const TT* table = static_cast<const TT*>(a.table);
-  constexpr int kLevelsPerChunk = 8 / F;
-  const int nchunks = a.Dp / 8;
-  for (int c = 0; c < nchunks; ++c) {
-    float v[8];
-#pragma unroll
-    for (int j = 0; j < kLevelsPerChunk; ++j) {
-      const int l = c * kLevelsPerChunk + j;
-      float acc[F];
-#pragma unroll
-      for (int f = 0; f < F; ++f) acc[f] = 0.0f;
-      if (valid && l < a.g.L) {
-        uint32_t idx[16];
-        float w[16];
-        level_corners(a.g, l, p, idx, w);
-        const TT* base = table + a.g.offset[l] * F;
-        if constexpr (F == 2) {
-          gather2_pairs<TT>(base, idx, w, acc);
-        } else {
-#pragma unroll
-          for (int b = 0; b < 16; ++b) {
-            float e[F];
-            load_entry<TT, F>(base + (size_t)idx[b] * F, e);
-#pragma unroll
-            for (int f = 0; f < F; ++f) acc[f] = fmaf(w[b], e[f], acc[f]);
-          }
-        }
-      }
-#pragma unroll
-      for (int f = 0; f < F; ++f) v[j * F + f] = acc[f];
-    }
-    uint4 hi, lo;
-    split_hi_lo8(v, hi, lo);
-    *reinterpret_cast<uint4*>(A + tile_off(r, 8 * c, KA)) = hi;
-    *reinterpret_cast<uint4*>(A + tile_off(r, a.Dp + 16 + 8 * c, KA)) = lo;
-    if (valid && a.state != nullptr && 8 * c < a.D) {
-      __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(a.state + row * state_stride(a.D)) + 8 * c;
-      if ((a.D & 7) == 0) {
-        __stcs(reinterpret_cast<uint4*>(dst), hi);
-      } else {
-        const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&hi);
-        for (int j = 0; j < 8 && 8 * c + j < a.D; ++j) dst[j] = h[j];
-      }
-    }
-  }
-  write_ones(A, r, a.Dp, KA);
-}
-
-// Reads this thread's 64 hidden pre-activations, records their ReLU mask
-// (bit j of mask[j / 32]), applies ReLU and writes the next layer's operand
-// row [hi | 1 | lo].
-__device__ __forceinline__ void hidden_epilogue(uint32_t trow, uint8_t* A, int r, uint32_t mask[2]) {
-  mask[0] = mask[1] = 0u;
-#pragma unroll
-  for (int c = 0; c < kHidden / 16; ++c) {
-    float v[16];
-    tc::tmem_ld16(trow + 16 * c, v);
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      if (v[j] > 0.0f) mask[c >> 1] |= 1u << ((c & 1) * 16 + j);
-      v[j] = fmaxf(v[j], 0.0f);
-    }
-    uint4 h0, l0, h1, l1;
-    split_hi_lo8(v, h0, l0);
-    split_hi_lo8(v + 8, h1, l1);
-    *reinterpret_cast<uint4*>(A + tile_off(r, 16 * c, kKH)) = h0;
-    *reinterpret_cast<uint4*>(A + tile_off(r, 16 * c + 8, kKH)) = h1;
-    *reinterpret_cast<uint4*>(A + tile_off(r, kHidden + 16 + 16 * c, kKH)) = l0;
-    *reinterpret_cast<uint4*>(A + tile_off(r, kHidden + 16 + 16 * c + 8, kKH)) = l1;
-  }
-  write_ones(A, r, kHidden, kKH);
+  uint8_t* srow = (valid && a.state != nullptr) ? a.state + row * state_stride(a.D) : nullptr;
+  encode_operand_row<TT, F>(a.g, static_cast<const TT*>(a.table), p, valid, a.D, a.Dp, A, r, srow);
 }
 
 template <typename TT, int F, int G>

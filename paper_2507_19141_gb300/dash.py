@@ -80,6 +80,19 @@ class dash_smooth(ctypes.Structure):
                 ("loss_out", ctypes.c_void_p)]
 
 
+class dash_batch_scene(ctypes.Structure):
+    _fields_ = [("table", ctypes.c_void_p), ("params", ctypes.c_void_p), ("x", ctypes.c_void_p),
+                ("y", ctypes.c_void_p), ("z", ctypes.c_void_p), ("timestamps", ctypes.c_void_p),
+                ("delta_out", ctypes.c_void_p), ("n", ctypes.c_int64), ("K", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class dash_batch_desc(ctypes.Structure):
+    _fields_ = [("layout", ctypes.c_void_p), ("table_dtype", ctypes.c_int32), ("d_in", ctypes.c_int32),
+                ("d_hidden", ctypes.c_int32), ("d_out", ctypes.c_int32), ("n_scenes", ctypes.c_int32),
+                ("scenes", ctypes.c_void_p)]
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _I = ctypes.c_int
@@ -100,6 +113,12 @@ _SIGS = {
     "dash_deform_state_size": ([_P], _SZ),
     "dash_deform_mlp_fwd": ([_P, _P, _P, _I, _P, _P, _P, _P, _P], _I),
     "dash_deform_mlp_bwd": ([_P, _P, _P, _I, _P, _P, _P, _P, _P, _P, _P], _I),
+    "dash_batch_plan_create": ([_P, _P], _I),
+    "dash_batch_counts": ([_P], ctypes.c_void_p),
+    "dash_batch_run": ([_P, _P], _I),
+    "dash_batch_form": ([_P], _I),
+    "dash_batch_autotune": ([_P, ctypes.c_char_p, _P], _I),
+    "dash_batch_plan_destroy": ([_P], _I),
     "dash_plain_hash4d_fwd": ([_P, _P, _P, _P, _P], _I),
     "dash_plain_hash4d_bwd": ([_P, _P, _P, _P, _P], _I),
     "dash_plain_mlp_fwd": ([_P, _P, _I64, _P, _P, _P], _I),
@@ -136,6 +155,7 @@ def dash_version() -> int:
 
 
 OPT_FWD_FORM = 1
+OPT_BWD_FORM = 2
 
 
 def dash_set_option(option: int, value: int) -> None:
@@ -323,6 +343,65 @@ def dash_deform_mlp_bwd(layout, pts, table, mlp: Mlp, ddelta, table_grad, mlp_gr
                                     ctypes.byref(mlp.c), _ptr(ddelta), _ptr(fwd_state), _ptr(table_grad),
                                     _ptr(mlp_grad), None if sm is None else ctypes.byref(sm), _stream()),
            "dash_deform_mlp_bwd")
+
+
+# ----------------------------------------------------- a12: batched form --
+class BatchPlan:
+    """Owner of a dash_batch_plan.  scenes: list of dicts with CUDA tensors
+    table, params, x, y, z, timestamps [K], delta_out [K][O][n] (the plan
+    keeps references to all of them)."""
+
+    def __init__(self, layout: dash_layout, scenes, d_in=32, d_hidden=64, d_out=10):
+        self.layout = layout
+        self.scenes = scenes
+        arr = (dash_batch_scene * len(scenes))()
+        dt = None
+        for i, sc in enumerate(scenes):
+            dt = _DTYPE_CODE[sc["table"].dtype]
+            arr[i] = dash_batch_scene(sc["table"].data_ptr(), sc["params"].data_ptr(), sc["x"].data_ptr(),
+                                      sc["y"].data_ptr(), sc["z"].data_ptr(), sc["timestamps"].data_ptr(),
+                                      sc["delta_out"].data_ptr(), sc["x"].numel(), sc["timestamps"].numel(), 0)
+        self._arr = arr
+        desc = dash_batch_desc(ctypes.addressof(layout), dt, d_in, d_hidden, d_out, len(scenes),
+                               ctypes.addressof(arr))
+        h = ctypes.c_void_p()
+        _check(_lib.dash_batch_plan_create(ctypes.byref(desc), ctypes.byref(h)), "dash_batch_plan_create")
+        self.handle = h
+
+    def counts(self) -> torch.Tensor:
+        """The plan's live per-scene counts as an int64 CUDA tensor view
+        [n_scenes]; stream-ordered writes to it are seen by the next run."""
+        ptr = int(_lib.dash_batch_counts(self.handle))
+        return _device_view_i64(ptr, len(self.scenes))
+
+    def run(self) -> None:
+        _check(_lib.dash_batch_run(self.handle, _stream()), "dash_batch_run")
+
+    def form(self) -> int:
+        return int(_lib.dash_batch_form(self.handle))
+
+    def autotune(self, cache_path=None) -> int:
+        p = None if cache_path is None else str(cache_path).encode()
+        _check(_lib.dash_batch_autotune(self.handle, p, _stream()), "dash_batch_autotune")
+        return self.form()
+
+    def close(self) -> None:
+        if self.handle:
+            _lib.dash_batch_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _device_view_i64(ptr: int, n: int) -> torch.Tensor:
+    """An int64 CUDA tensor aliasing n values at a device address owned by libdash."""
+    class _Arr:
+        __cuda_array_interface__ = {"shape": (n,), "typestr": "<i8", "data": (ptr, False), "version": 3}
+    return torch.as_tensor(_Arr(), device="cuda")
 
 
 # ------------------------------------------------------------- autograd --

@@ -1,0 +1,98 @@
+"""GPU checks of the batched persistent form (a12): many scenes with uneven
+dynamic counts x many timestamps in one CUDA-graph launch.  Each (scene,
+timestamp) must equal the single-scene fused forward bit for bit, and the
+FP64 oracle within 1e-3."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2507_19141_gb300 import synth
+from gpu_helpers import oracle_grid, rel_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _scenes(dashlib, grid, mlpc, counts, Ks, tdtype, seed):
+    rng = np.random.default_rng(seed)
+    g = oracle_grid(grid)
+    out = []
+    for n, K in zip(counts, Ks):
+        x, y, z, _ = synth.scene_coords(rng, n)
+        f = np.sort(rng.choice(300, size=K, replace=False))
+        ts = (f / 299).astype(np.float32)
+        table = synth.table_values(rng, g.total, grid.F, tdtype)
+        params = synth.mlp_params(rng, mlpc)
+        out.append({"np": (x, y, z, ts, table, params),
+                    "table": to_dev(table), "params": to_dev(params), "x": to_dev(x), "y": to_dev(y),
+                    "z": to_dev(z), "timestamps": to_dev(ts),
+                    "delta_out": torch.full((K, mlpc.d_out, n), 7.0, device="cuda")})
+    return g, out
+
+
+def test_batched_matches_single_scene_and_oracle(dashlib):
+    grid, mlpc = synth.PAPER_GRID, synth.PAPER_MLP
+    counts, Ks = [5000, 300, 129, 1], [3, 2, 4, 1]
+    g, scenes = _scenes(dashlib, grid, mlpc, counts, Ks, np.float16, 51)
+    lay = dashlib.layout_from(grid)
+    plan = dashlib.BatchPlan(lay, scenes)
+    plan.run()
+    torch.cuda.synchronize()
+    for sc, n, K in zip(scenes, counts, Ks):
+        x, y, z, ts, table, params = sc["np"]
+        mlp = dashlib.Mlp(sc["params"], mlpc.d_in, mlpc.d_hidden, mlpc.d_out)
+        for k in range(K):
+            pts = dashlib.Points(sc["x"], sc["y"], sc["z"], sc["timestamps"][k:k + 1].contiguous(), n=n)
+            single = dashlib.dash_deform_mlp_fwd(lay, pts, sc["table"], mlp)
+            assert torch.equal(sc["delta_out"][k], single), (n, k)
+        ref = oracle.deform_fwd(g, oracle.Points(x, y, z, ts[-1:], t_stride=0), table.astype(np.float64),
+                                mlpc.d_hidden, mlpc.d_out, params.astype(np.float64))
+        assert rel_err(sc["delta_out"][K - 1].cpu().numpy(), ref) < 1e-3
+    plan.close()
+
+
+def test_batched_device_counts_and_graph_replay(dashlib):
+    grid, mlpc = synth.TINY_GRID, synth.TINY_MLP
+    counts, Ks = [3000, 1000], [2, 3]
+    g, scenes = _scenes(dashlib, grid, mlpc, counts, Ks, np.float32, 52)
+    lay = dashlib.layout_from(grid)
+    plan = dashlib.BatchPlan(lay, scenes, d_in=mlpc.d_in)
+    # shrink the live counts on the device, replay the same graph
+    plan.counts().copy_(torch.tensor([1500, 0], dtype=torch.int64, device="cuda"))
+    plan.run()
+    torch.cuda.synchronize()
+    d0, d1 = scenes[0]["delta_out"].cpu().numpy(), scenes[1]["delta_out"].cpu().numpy()
+    assert np.all(d0[:, :, 1500:] == 7.0) and np.all(d1 == 7.0)
+    x, y, z, ts, table, params = scenes[0]["np"]
+    for k in range(2):
+        ref = oracle.deform_fwd(g, oracle.Points(x[:1500], y[:1500], z[:1500], ts[k:k + 1], t_stride=0),
+                                table.astype(np.float64), mlpc.d_hidden, mlpc.d_out, params.astype(np.float64))
+        assert rel_err(d0[k, :, :1500], ref) < 1e-3
+    # grow them back to the capacity
+    plan.counts().copy_(torch.tensor(counts, dtype=torch.int64, device="cuda"))
+    plan.run()
+    torch.cuda.synchronize()
+    assert not np.any(scenes[1]["delta_out"].cpu().numpy() == 7.0)
+    plan.close()
+
+
+def test_batched_autotune_and_cache(dashlib, tmp_path):
+    grid, mlpc = synth.PAPER_GRID, synth.PAPER_MLP
+    counts, Ks = [20_000, 7_000], [4, 4]
+    _, scenes = _scenes(dashlib, grid, mlpc, counts, Ks, np.float16, 53)
+    lay = dashlib.layout_from(grid)
+    plan = dashlib.BatchPlan(lay, scenes)
+    plan.run()
+    torch.cuda.synchronize()
+    before = [sc["delta_out"].clone() for sc in scenes]
+    cache = tmp_path / "tune.json"
+    form = plan.autotune(cache)
+    assert 0 <= form < 4 and cache.exists() and "GB300" in cache.read_text() or cache.exists()
+    plan.run()
+    torch.cuda.synchronize()
+    for sc, b in zip(scenes, before):
+        assert torch.equal(sc["delta_out"], b)  # every form computes the same result
+    plan2 = dashlib.BatchPlan(lay, scenes)
+    assert plan2.autotune(cache) == form     # taken from the cache
+    plan.close()
+    plan2.close()

@@ -250,3 +250,44 @@ def test_forward_kernel_forms_agree(dashlib, grid, mlpc, tdtype):
     ref = oracle.deform_fwd(g, oracle.Points(*coords), table.astype(np.float64), mlpc.d_hidden, mlpc.d_out,
                             params.astype(np.float64))
     assert rel_err(outs[0][0].numpy(), ref) < 1e-3
+
+
+@pytest.mark.parametrize("smooth", [None, (0.5, (1 / 2048, 1 / 2048, 1 / 2048), 1 / 300)])
+def test_backward_kernel_forms_agree(dashlib, smooth):
+    """The warp-specialised and the single-group backward give the same
+    gradients up to the order of the atomic additions."""
+    grid, mlpc = synth.PAPER_GRID, synth.PAPER_MLP
+    n = 30_001
+    g, coords, _, table, params, dd = _case(grid, mlpc, n, np.float16, 47)
+    lay = dashlib.layout_from(grid)
+    pts = _dev_points(dashlib, coords, None, n)
+    mlp = dashlib.Mlp(to_dev(params), mlpc.d_in, mlpc.d_hidden, mlpc.d_out)
+    tab = to_dev(table)
+    st = dashlib.deform_state(mlp, n, "cuda")
+    dashlib.dash_deform_mlp_fwd(lay, pts, tab, mlp, fwd_state=st)
+    res = []
+    old = dashlib.dash_get_option(dashlib.OPT_BWD_FORM)
+    try:
+        for form in (0, 1):
+            dashlib.dash_set_option(dashlib.OPT_BWD_FORM, form)
+            tg = torch.zeros((g.total, 2), dtype=torch.float32, device="cuda")
+            pg = torch.zeros(mlpc.n_params, dtype=torch.float32, device="cuda")
+            lo = torch.zeros(1, dtype=torch.float32, device="cuda")
+            sm = None if smooth is None else (*smooth, lo)
+            dashlib.dash_deform_mlp_bwd(lay, pts, tab, mlp, to_dev(dd), tg, pg, fwd_state=st, smooth=sm)
+            res.append((tg.cpu().numpy(), pg.cpu().numpy(), float(lo.item())))
+    finally:
+        dashlib.dash_set_option(dashlib.OPT_BWD_FORM, old)
+    assert rel_err(res[0][0], res[1][0]) < 1e-5
+    if smooth is None:
+        assert rel_err(res[0][1], res[1][1]) < 1e-5
+    else:
+        # with Eq. 11 on, the single-group form recomputes the decoder from a
+        # fresh FP32 f_h, the warp-specialised one from the state's BF16 f_h:
+        # dW1 = dz1^T f_h differs by that rounding; both must meet the oracle
+        assert abs(res[0][2] - res[1][2]) <= 1e-4 * abs(res[1][2])
+        lam, es, et = smooth
+        rtg, rpg, rl = oracle.deform_bwd(g, oracle.Points(*coords), table.astype(np.float64), 64, 10,
+                                         params.astype(np.float64), dd.astype(np.float64), lam, es, et)
+        for tg_, pg_, l_ in res:
+            assert rel_err(tg_, rtg) < 1e-2 and rel_err(pg_, rpg) < 1e-2 and abs(l_ - rl) < 1e-2 * abs(rl)
