@@ -126,12 +126,16 @@ int dash_version(void);
 
 /* Process-wide kernel-form options (host; take effect at the next launch).
  * DASH_OPT_FWD_FORM selects the fused forward kernel: 0 = warp-specialised
- * (one decoder group fed by three gather groups through a shared-memory
- * ring; default), 1 / 2 / 4 = that many independent gather+decoder groups
- * per CTA.  DASH_OPT_BWD_FORM selects the fused backward: 0 = warp-specialised
- * (one decoder group feeding three scatter groups; used when a forward state
- * is given), 1 = one combined group per CTA.  Results agree to rounding
- * (forward forms bit for bit).  dash_get_option returns the current value
+ * (one decoder group fed by gather groups through a shared-memory ring;
+ * default, four groups x four stages for F = 2, L*F <= 32), 1 / 2 / 4 = that
+ * many independent gather+decoder groups per CTA, and for F = 2, L*F <= 32
+ * the warp-specialised shapes (gather groups, ring stages) 10 = (3, 6),
+ * 11 = (3, 3), 12 = (2, 4), 13 = (5, 5).  DASH_OPT_BWD_FORM selects the fused
+ * backward: 0 = warp-specialised (a decoder group feeding scatter groups;
+ * three groups, or four with the Eq. 11 term; used when a forward state is
+ * given), 1 = one combined group per CTA, 10..13 = the shapes (3, 6), (4, 4),
+ * (2, 4), (5, 5).  Forward forms agree bit for bit, backward forms up to the
+ * order of the atomic additions.  dash_get_option returns the current value
  * (negative status for an unknown option). */
 enum dash_option { DASH_OPT_FWD_FORM = 1, DASH_OPT_BWD_FORM = 2 };
 int dash_set_option(int option, int value);

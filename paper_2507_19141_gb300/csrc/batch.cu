@@ -234,7 +234,7 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) batch_fwd_kernel(const __g
 struct Form {
   int P, S;
 };
-constexpr Form kForms[] = {{3, 6}, {2, 4}, {3, 3}, {1, 4}};
+constexpr Form kForms[] = {{4, 4}, {3, 6}, {3, 3}, {2, 4}};
 constexpr int kNumForms = sizeof(kForms) / sizeof(kForms[0]);
 
 size_t smem_for(int P, int S, int Dp, BatchArgs* a) {
@@ -265,10 +265,10 @@ int launch_form(BatchArgs a, cudaStream_t st) {
 template <typename TT, int F>
 int launch_tt_f(int form, BatchArgs& a, cudaStream_t st) {
   switch (form) {
-    case 0: return launch_form<TT, F, 3, 6>(a, st);
-    case 1: return launch_form<TT, F, 2, 4>(a, st);
+    case 0: return launch_form<TT, F, 4, 4>(a, st);
+    case 1: return launch_form<TT, F, 3, 6>(a, st);
     case 2: return launch_form<TT, F, 3, 3>(a, st);
-    default: return launch_form<TT, F, 1, 4>(a, st);
+    default: return launch_form<TT, F, 2, 4>(a, st);
   }
 }
 

@@ -766,6 +766,9 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_bwd_ws_kernel(const
     for (long long j = pg; j < my_tiles; j += P) {
       const int s = (int)(j % S);
       const uint32_t round = (uint32_t)(j / S);
+      const long long row = (blockIdx.x + j * gridDim.x) * kRows + r;
+      // the point's loads are in flight while this group waits for the tile's gradients
+      const float4 p = row < n ? load_point(a.pts, row) : make_float4(0.f, 0.f, 0.f, 0.f);
       if (!tc::mbar_wait(tc::smem_addr(&full[s]), round & 1u, kWaitIters)) {
         atomicOr(a.flags, 1u);
         *abort_flag = 1;
@@ -775,9 +778,7 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_bwd_ws_kernel(const
       const float* stage = ring + (size_t)s * stage_floats;
       for (int k = 0; k < a.D; ++k) df[k] = stage[k * kRows + r];
       tc::mbar_arrive(tc::smem_addr(&empty[s]));
-      const long long row = (blockIdx.x + j * gridDim.x) * kRows + r;
       if (row >= n) continue;
-      const float4 p = load_point(a.pts, row);
       for (int l = 0; l < a.g.L; ++l) {
         uint32_t idx[16];
         float w[16];
@@ -867,10 +868,6 @@ int launch(BwdArgs a, cudaStream_t st) {
   if (int s = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                           "cudaFuncSetAttribute(deform_bwd)"))
     return s;
-  if (int s = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                               (int)cudaSharedmemCarveoutMaxShared),
-                          "carveout"))
-    return s;
   int per_sm = 0;
   if (int s = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRows, smem),
                           "occupancy(deform_bwd)"))
@@ -886,6 +883,18 @@ int launch(BwdArgs a, cudaStream_t st) {
 
 template <typename TT>
 int dispatch(int F, bool ws, BwdArgs& a, cudaStream_t st) {
+  if (ws && F == 2 && a.Dp <= 32) {
+    // warp-specialised shapes (scatter groups, ring stages); 0 = the measured best:
+    // three groups without the smoothness term, four with its extra gathers and scatters
+    switch (g_opt_bwd_form) {
+      case 0: return a.lambda_r != 0.0f ? launch_ws<TT, 2, 4, 4>(a, st) : launch_ws<TT, 2, 3, 3>(a, st);
+      case 10: return launch_ws<TT, 2, 3, 6>(a, st);
+      case 11: return launch_ws<TT, 2, 4, 4>(a, st);
+      case 12: return launch_ws<TT, 2, 2, 4>(a, st);
+      case 13: return launch_ws<TT, 2, 5, 5>(a, st);
+      default: break;
+    }
+  }
   if (ws) {
     if (a.Dp > 32) {
       switch (F) {
@@ -963,7 +972,7 @@ extern "C" int dash_deform_mlp_bwd(const dash_layout* layout, const dash_points*
   cudaStream_t st = as_stream(stream);
   // the warp-specialised form needs the forward state; without it the
   // single-group form re-encodes f_h itself
-  const bool ws = g_opt_bwd_form == 0 && a.state != nullptr;
+  const bool ws = g_opt_bwd_form != 1 && a.state != nullptr;
   switch (table_dtype) {
     case DASH_F32: return dispatch<float>(a.g.F, ws, a, st);
     case DASH_F16: return dispatch<__half>(a.g.F, ws, a, st);

@@ -301,13 +301,18 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_fwd_ws_kernel(const
     for (long long j = pg; j < my_tiles; j += P) {
       const int s = (int)(j % S);
       const uint32_t round = (uint32_t)(j / S);
+      const long long row = (blockIdx.x + j * gridDim.x) * kRows + r;
+      const bool valid = row < n;
+      // the point's loads are in flight while this group waits for its stage
+      const float4 p = valid ? load_point(a.pts, row) : make_float4(0.f, 0.f, 0.f, 0.f);
       if (!tc::mbar_wait(tc::smem_addr(&empty[s]), (round & 1u) ^ 1u, kWaitIters)) {
         atomicOr(a.flags, 1u);
         *abort_flag = 1;
       }
       if (*abort_flag) break;
-      const long long row = (blockIdx.x + j * gridDim.x) * kRows + r;
-      encode_row<TT, F>(a, row < n, row, ring + s * stage_bytes, r);
+      uint8_t* srow = (valid && a.state != nullptr) ? a.state + row * state_stride(a.D) : nullptr;
+      encode_operand_row<TT, F>(a.g, static_cast<const TT*>(a.table), p, valid, a.D, a.Dp, ring + s * stage_bytes, r,
+                                srow);
       tc::fence_async_smem();
       tc::mbar_arrive(tc::smem_addr(&full[s]));
     }
@@ -364,10 +369,6 @@ int launch(FwdArgs a, cudaStream_t st) {
   if (int s = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem),
                           "cudaFuncSetAttribute(deform_fwd)"))
     return s;
-  if (int s = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                               (int)cudaSharedmemCarveoutMaxShared),
-                          "carveout"))
-    return s;
   int per_sm = 0;
   if (int s = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G * kRows, p.smem),
                           "occupancy(deform_fwd)"))
@@ -386,7 +387,18 @@ template <typename TT>
 int dispatch_f(int F, int Dp, int variant, FwdArgs& a, cudaStream_t st) {
   // variant 0: warp-specialised (3 producer groups; 6-stage ring, 3 stages when D > 32);
   // 1, 2, 4: the simple form with that many independent groups per CTA
-  if (variant == 0) {
+  if (F == 2 && Dp <= 32) {
+    // warp-specialised shapes (gather groups, ring stages); 0 = the measured best
+    switch (variant) {
+      case 0: return launch_ws<TT, 2, 4, 4>(a, st);
+      case 10: return launch_ws<TT, 2, 3, 6>(a, st);
+      case 11: return launch_ws<TT, 2, 3, 3>(a, st);
+      case 12: return launch_ws<TT, 2, 2, 4>(a, st);
+      case 13: return launch_ws<TT, 2, 5, 5>(a, st);
+      default: break;
+    }
+  }
+  if (variant == 0 || variant >= 10) {
     if (Dp > 32) {
       switch (F) {
         case 1: return launch_ws<TT, 1, 3, 3>(a, st);
