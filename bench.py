@@ -322,40 +322,96 @@ def run_ours(args):
     barrier()
 
 
+class Slot:
+    """One in-flight step's device buffers (mask, coordinates, upstream
+    gradient, index list, state, offsets); the model (tables, decoder) and
+    its gradients are shared with the workload."""
+
+    def __init__(self, torch, wl):
+        from paper_2507_19141_gb300 import dash
+        self.wl, self.dash = wl, dash
+        self.mask = torch.empty_like(wl.mask)
+        self.x, self.y, self.z, self.t = (torch.empty_like(v) for v in (wl.x, wl.y, wl.z, wl.t))
+        self.ddelta = torch.zeros_like(wl.ddelta)
+        self.delta = torch.empty_like(wl.delta)
+        self.idx = torch.empty_like(wl.idx)
+        self.count = torch.zeros_like(wl.count)
+        self.ws = torch.empty_like(wl.ws)
+        self.state = torch.empty_like(wl.fsave)
+        self.pts = dash.Points(self.x, self.y, self.z, self.t, idx=self.idx, n=wl.n_all, n_dev=self.count)
+
+    def step(self):
+        wl, d = self.wl, self.dash
+        d.dash_compact_dynamic(self.mask, idx_out=self.idx, count_out=self.count, ws=self.ws)
+        d.dash_deform_mlp_fwd(wl.layout, self.pts, wl.table, wl.mlp, delta_out=self.delta, fwd_state=self.state,
+                              apply=(wl.attrs_in, wl.attrs_out))
+        d.dash_deform_mlp_bwd(wl.layout, self.pts, wl.table, wl.mlp, self.ddelta, wl.table_grad, wl.mlp_grad,
+                              fwd_state=self.state)
+
+
 def run_e2e(torch, wl, args, stream):
-    """Same step through the public API from pinned HOST buffers: H2D of the
-    mask, coordinates and upstream gradient, D2H of the offsets and decoder
-    gradient, inside the timed region."""
-    n, na = args.n_dyn, args.n_all
+    """Same step through the public API from pinned HOST buffers: every step
+    uploads its mask, coordinates and upstream gradient and downloads its
+    offsets and the decoder gradient, all inside the timed region.  Two
+    buffer slots and two copy streams let step k+1's upload and step k-1's
+    download overlap step k's kernels."""
+    n = args.n_dyn
     pin = lambda a: torch.from_numpy(a).pin_memory()
     mask_h = pin(wl.mask_h)
     xyzt_h = [pin(c) for c in wl.coords_h]
     dd_h = pin(wl.ddelta_h)
-    delta_h = torch.empty((wl.mlpc.d_out, n), dtype=torch.float32).pin_memory()
-    grad_h = torch.empty(wl.mlpc.n_params, dtype=torch.float32).pin_memory()
+    delta_h = [torch.empty((wl.mlpc.d_out, n), dtype=torch.float32).pin_memory() for _ in range(2)]
+    grad_h = [torch.empty(wl.mlpc.n_params, dtype=torch.float32).pin_memory() for _ in range(2)]
     h2d = mask_h.numel() + sum(c.numel() * 4 for c in xyzt_h) + dd_h.numel() * 4
-    d2h = delta_h.numel() * 4 + grad_h.numel() * 4
+    d2h = delta_h[0].numel() * 4 + grad_h[0].numel() * 4
+    slots = [Slot(torch, wl), Slot(torch, wl)]
+    up, down = torch.cuda.Stream(), torch.cuda.Stream()
+    done = [None, None]
 
-    def e2e_step():
-        wl.mask.copy_(mask_h, non_blocking=True)
-        for d, h in zip((wl.x, wl.y, wl.z, wl.t), xyzt_h):
-            d.copy_(h, non_blocking=True)
-        wl.ddelta[:, :n].copy_(dd_h, non_blocking=True)
-        wl.step()
-        delta_h.copy_(wl.delta[:, :n], non_blocking=True)
-        grad_h.copy_(wl.mlp_grad, non_blocking=True)
+    def e2e_step(k):
+        s = slots[k % 2]
+        with torch.cuda.stream(up):
+            if done[k % 2] is not None:
+                up.wait_event(done[k % 2])  # slot free: step k-2 has finished computing
+            s.mask.copy_(mask_h, non_blocking=True)
+            for dv, hv in zip((s.x, s.y, s.z, s.t), xyzt_h):
+                dv.copy_(hv, non_blocking=True)
+            for j in range(dd_h.shape[0]):  # contiguous rows of the SoA layout: plain async copies
+                s.ddelta[j, :n].copy_(dd_h[j], non_blocking=True)
+            uploaded = torch.cuda.Event()
+            uploaded.record(up)
+        stream.wait_event(uploaded)
+        s.step()
+        computed = torch.cuda.Event()
+        computed.record(stream)
+        done[k % 2] = computed
+        with torch.cuda.stream(down):
+            down.wait_event(computed)
+            for j in range(delta_h[k % 2].shape[0]):
+                delta_h[k % 2][j].copy_(s.delta[j, :n], non_blocking=True)
+            grad_h[k % 2].copy_(wl.mlp_grad, non_blocking=True)
 
-    steps = max(10, min(args.steps, 50))
-    for _ in range(3):
-        e2e_step()
+    steps = max(10, min(args.steps, 100))
+    for k in range(4):
+        e2e_step(k)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ms = time_steps(torch, e2e_step, steps, stream)
-    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    up.wait_event(start)
+    for k in range(steps):
+        e2e_step(k)
+    stream.wait_stream(up)
+    stream.wait_stream(down)
+    end.record(stream)
+    end.synchronize()
     wall = (time.perf_counter() - t0) * 1e3 / steps
-    ms = max(ms, wall)
+    ms = max(start.elapsed_time(end) / steps, wall)
+    torch.cuda.synchronize()
     return {"value": n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
-            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "overlap": "two buffer slots; uploads and downloads on their own streams overlap the kernels"}
 
 
 def run_extras(torch, wl, args, stream):
