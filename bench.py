@@ -468,6 +468,22 @@ def run_extras(torch, wl, args, stream):
     res["cold_l2_step_ms"] = statistics.median(cold)
     res["cold_l2_gaussians_per_s"] = n / (res["cold_l2_step_ms"] / 1e3)
     del flush
+    # the table-gradient scatter alone: FP32 buffers (the form the backward uses) and the
+    # reduced-precision FP16 variant (half2 vector atomics), with the FP16 error against FP32
+    dfeat = torch.randn((n, wl.mlpc.d_in), dtype=torch.float32, device=wl.table.device) * 0.05
+    pts_c = dash.Points(wl.x, wl.y, wl.z, wl.t, idx=wl.idx[:n].contiguous(), n=n)
+    g32 = torch.zeros_like(wl.table_grad)
+    g16 = torch.zeros(wl.table_grad.shape, dtype=torch.float16, device=wl.table.device)
+    res["scatter_fp32_ms"] = time_steps(torch, lambda: dash.dash_hash4d_bwd(wl.layout, pts_c, dfeat, g32), 10, stream)
+    res["scatter_fp16_ms"] = time_steps(torch, lambda: dash.dash_hash4d_bwd_half(wl.layout, pts_c, dfeat, g16), 10,
+                                        stream)
+    g32.zero_()
+    g16.zero_()
+    dash.dash_hash4d_bwd(wl.layout, pts_c, dfeat, g32)
+    dash.dash_hash4d_bwd_half(wl.layout, pts_c, dfeat, g16)
+    torch.cuda.synchronize()
+    res["scatter_fp16_rel_err_vs_fp32"] = float((g16.float() - g32).norm() / g32.norm())
+    del g32, g16, dfeat
     res.update(run_batched(torch, stream))
     return res
 

@@ -196,6 +196,14 @@ int dash_hash4d_fwd(const dash_layout* layout, const dash_points* pts, const voi
 int dash_hash4d_bwd(const dash_layout* layout, const dash_points* pts, const float* dfeat,
                     float* table_grad, void* stream);
 
+/* The same transpose into FP16 gradients (F = 2 only): table_grad is
+ * [offset[L]][2] FP16, accumulated with half2 vector atomics (an x-adjacent
+ * corner pair within one aligned 16-byte group is one 16-byte reduction).
+ * A reduced-precision variant: FP16 accumulation loses accuracy on entries
+ * that receive many updates; the FP32 form above is the reference. */
+int dash_hash4d_bwd_half(const dash_layout* layout, const dash_points* pts, const float* dfeat,
+                         void* table_grad, void* stream);
+
 /* ------------------------- a2-a8: fused deformation forward (Eqs. 8-10) -- */
 
 /* Bytes of forward state per Gaussian that dash_deform_mlp_fwd keeps for

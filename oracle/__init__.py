@@ -78,9 +78,21 @@ def build(force: bool = False) -> str:
 
 def _load():
     global _lib
-    if _lib is not None:
-        return _lib
-    lib = ctypes.CDLL(build())
+    if _lib is None:
+        _lib = configure(ctypes.CDLL(build()))
+    return _lib
+
+
+def compile_variant(src_path: str, out_path: str) -> str:
+    """Compiles another copy of the oracle source (the mutation tests plant
+    mistakes in copies to show the pins catch them)."""
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", out_path, src_path,
+                    "-lm"], check=True)
+    return out_path
+
+
+def configure(lib):
+    """Declares the argument and result types of the oracle entry points on a loaded library."""
     P = ctypes.c_void_p
     i64 = ctypes.c_int64
     i32 = ctypes.c_int
@@ -112,7 +124,6 @@ def _load():
     lib.orc_deform_bwd.restype = ctypes.c_double
     lib.orc_smooth_loss.argtypes = [G] + pts + [P, ctypes.c_float, P, ctypes.c_float]
     lib.orc_smooth_loss.restype = ctypes.c_double
-    _lib = lib
     return lib
 
 

@@ -101,6 +101,56 @@ __global__ void __launch_bounds__(kThreads) plain_bwd_kernel(Geom g, Pts pts, co
   }
 }
 
+// FP16-gradient variant of the transpose (F = 2): table_grad holds one
+// f16x2 word per entry.  An x-adjacent corner pair whose two entries share an
+// aligned 16-byte group goes out as one 16-byte reduction (the group's other
+// entries receive +0), otherwise as two 4-byte reductions.
+__device__ __forceinline__ uint32_t h2_bits(float a, float b) {
+  __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+__device__ __forceinline__ void red_h2(__half* addr, uint32_t v) {
+  asm volatile("red.relaxed.gpu.global.add.noftz.f16x2 [%0], %1;" ::"l"(addr), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void red_h2x4(__half* addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("red.relaxed.gpu.global.add.noftz.v4.f16x2 [%0], {%1, %2, %3, %4};" ::"l"(addr), "r"(a), "r"(b),
+               "r"(c), "r"(d)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(kThreads) encode_bwd_half_kernel(Geom g, Pts pts, const float* __restrict__ dfeat,
+                                                                   __half* __restrict__ grad) {
+  const long long n = point_count(pts);
+  const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (i >= n) return;
+  const float4 p = load_point(pts, i);
+  const float* drow = dfeat + i * (long long)(g.L * 2);
+  for (int l = 0; l < g.L; ++l) {
+    uint32_t idx[16];
+    float w[16];
+    level_corners(g, l, p, idx, w);
+    const float d0 = __ldg(drow + 2 * l), d1 = __ldg(drow + 2 * l + 1);
+    __half* base = grad + g.offset[l] * 2;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const uint32_t i0 = idx[2 * q], i1 = idx[2 * q + 1];
+      const uint32_t u = h2_bits(w[2 * q] * d0, w[2 * q] * d1);
+      const uint32_t v = h2_bits(w[2 * q + 1] * d0, w[2 * q + 1] * d1);
+      if ((i0 & ~3u) == (i1 & ~3u)) {
+        uint32_t word[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) word[k] = ((i0 & 3u) == (uint32_t)k ? u : 0u) | ((i1 & 3u) == (uint32_t)k ? v : 0u);
+        red_h2x4(base + (size_t)(i0 & ~3u) * 2, word[0], word[1], word[2], word[3]);
+      } else {
+        red_h2(base + (size_t)i0 * 2, u);
+        red_h2(base + (size_t)i1 * 2, v);
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) indices_kernel(Geom g, Pts pts, uint32_t* __restrict__ idx_out,
                                                            float* __restrict__ w_out) {
   const long long n = point_count(pts);
@@ -189,6 +239,22 @@ int dash_hash4d_bwd(const dash_layout* layout, const dash_points* pts, const flo
     default: encode_bwd_kernel<8><<<grid, kThreads, 0, st>>>(g, p, dfeat, table_grad); break;
   }
   return launch_status("encode_bwd_kernel");
+}
+
+int dash_hash4d_bwd_half(const dash_layout* layout, const dash_points* pts, const float* dfeat, void* table_grad,
+                         void* stream) {
+  using namespace dash;
+  Geom g;
+  Pts p;
+  if (int s = prepare(layout, pts, &g, &p)) return s;
+  if (g.F != 2) return fail(DASH_ERR_UNSUPPORTED, "the FP16-gradient scatter supports F = 2");
+  if (p.n == 0) return DASH_OK;
+  if (dfeat == nullptr || table_grad == nullptr) return fail(DASH_ERR_INVALID_ARG, "dfeat/table_grad is NULL");
+  if ((reinterpret_cast<uintptr_t>(table_grad) & 15u) != 0)
+    return fail(DASH_ERR_INVALID_ARG, "table_grad must be 16-byte aligned");
+  encode_bwd_half_kernel<<<grid_for(p.n), kThreads, 0, as_stream(stream)>>>(g, p, dfeat,
+                                                                            static_cast<__half*>(table_grad));
+  return launch_status("encode_bwd_half_kernel");
 }
 
 int dash_hash4d_indices(const dash_layout* layout, const dash_points* pts, uint32_t* idx_out, float* w_out,

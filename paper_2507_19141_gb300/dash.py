@@ -110,6 +110,7 @@ _SIGS = {
     "dash_hash4d_indices": ([_P, _P, _P, _P, _P], _I),
     "dash_hash4d_fwd": ([_P, _P, _P, _I, _P, _I, _P], _I),
     "dash_hash4d_bwd": ([_P, _P, _P, _P, _P], _I),
+    "dash_hash4d_bwd_half": ([_P, _P, _P, _P, _P], _I),
     "dash_deform_state_size": ([_P], _SZ),
     "dash_deform_mlp_fwd": ([_P, _P, _P, _I, _P, _P, _P, _P, _P], _I),
     "dash_deform_mlp_bwd": ([_P, _P, _P, _I, _P, _P, _P, _P, _P, _P, _P], _I),
@@ -274,6 +275,14 @@ def dash_hash4d_bwd(layout: dash_layout, pts: Points, dfeat: torch.Tensor, table
     assert dfeat.dtype == torch.float32 and table_grad.dtype == torch.float32
     _check(_lib.dash_hash4d_bwd(ctypes.byref(layout), ctypes.byref(pts.c), _ptr(dfeat), _ptr(table_grad),
                                 _stream()), "dash_hash4d_bwd")
+    return table_grad
+
+
+def dash_hash4d_bwd_half(layout: dash_layout, pts: Points, dfeat: torch.Tensor, table_grad: torch.Tensor):
+    """FP16-gradient variant of dash_hash4d_bwd (F = 2); table_grad float16 [offset[L]][2]."""
+    assert dfeat.dtype == torch.float32 and table_grad.dtype == torch.float16
+    _check(_lib.dash_hash4d_bwd_half(ctypes.byref(layout), ctypes.byref(pts.c), _ptr(dfeat), _ptr(table_grad),
+                                     _stream()), "dash_hash4d_bwd_half")
     return table_grad
 
 

@@ -138,3 +138,27 @@ def test_empty_and_device_count(dashlib):
     dashlib.dash_hash4d_fwd(lay, pts, torch.ones((65536, 2), device="cuda"), out=out)
     o = out.cpu().numpy()
     assert np.allclose(o[:37], 1.0, atol=1e-6) and np.all(o[37:] == -7.0)
+
+
+def test_fp16_gradient_variant_error(dashlib):
+    """The half2-atomic FP16-gradient scatter is a reduced-precision variant:
+    its error against the FP64 oracle is reported, and bounded, separately
+    from the FP32 form (which stays within 1e-5)."""
+    grid = synth.PAPER_GRID
+    rng = np.random.default_rng(27)
+    n = 50_000
+    coords = synth.scene_coords(rng, n)
+    g = oracle_grid(grid)
+    dfeat = (rng.standard_normal((n, grid.L * grid.F)) * 0.05).astype(np.float32)
+    lay = dashlib.layout_from(grid)
+    pts = _points(dashlib, coords)
+    ref = oracle.encode_bwd(g, oracle.Points(*coords), dfeat.astype(np.float64))
+    t16 = torch.zeros((g.total, 2), dtype=torch.float16, device="cuda")
+    dashlib.dash_hash4d_bwd_half(lay, pts, to_dev(dfeat), t16)
+    t32 = torch.zeros((g.total, 2), dtype=torch.float32, device="cuda")
+    dashlib.dash_hash4d_bwd(lay, pts, to_dev(dfeat), t32)
+    e16 = rel_err(t16.float().cpu().numpy(), ref)
+    e32 = rel_err(t32.cpu().numpy(), ref)
+    print(f"table-gradient error vs oracle: FP16 buffers {e16:.2e}, FP32 buffers {e32:.2e}")
+    assert e32 < 1e-5
+    assert e16 < 1e-2

@@ -1,0 +1,107 @@
+"""The oracle's pins must catch plausible mistakes.  Each case plants one
+mistake in a copy of the oracle's C source (a dropped exponent, a swapped
+axis, a wrong sign, a transposed operand, ...), compiles that copy on the CPU,
+points the oracle binding at it, and requires at least one pin to fail."""
+import ctypes
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+from paper_2507_19141_gb300 import synth
+
+MUTATIONS = [
+    ("Eq. 7 level exponent dropped",
+     "return (int32_t)floor(nmin * pow(b, (double)l) + 1e-9);",
+     "return (int32_t)floor(nmin * b + 1e-9);",
+     [("test_layout_paper_shape_golden", {})]),
+    ("Eq. 7 rounding guard dropped",
+     "return (int32_t)floor(nmin * pow(b, (double)l) + 1e-9);",
+     "return (int32_t)floor(nmin * pow(b, (double)l));",
+     [("test_layout_endpoints_and_monotone", dict(L=8, nmin=2, nmax=512)),
+      ("test_layout_endpoints_and_monotone", dict(L=12, nmin=16, nmax=4096))]),
+    ("temporal axis given the spatial resolution",
+     "int64_t res[4] = {g->res_s[l], g->res_s[l], g->res_s[l], g->res_t[l]};",
+     "int64_t res[4] = {g->res_s[l], g->res_s[l], g->res_s[l], g->res_s[l]};",
+     [("test_hash_big_integer_brute_force", {})]),
+    ("lower corner rounded instead of floored",
+     "int64_t c = (int64_t)floor(pos);",
+     "int64_t c = (int64_t)floor(pos + 0.5);",
+     [("test_weights_partition_of_unity", dict(cfg=synth.TINY_GRID)), ("test_multilinear_matches_scipy_regular_grid", {})]),
+    ("corner weights swapped",
+     "wb *= up ? frac[d] : (1.0 - frac[d]);",
+     "wb *= up ? (1.0 - frac[d]) : frac[d];",
+     [("test_multilinear_matches_scipy_regular_grid", {}), ("test_vertex_reproduction_exact", {})]),
+    ("y and z corner bits swapped",
+     "int up = (b >> d) & 1;",
+     "int up = (b >> (d == 1 ? 2 : (d == 2 ? 1 : d))) & 1;",
+     [("test_hash_reduces_to_bit_packing_with_power_of_two_primes", {})]),
+    ("Eq. 8 XOR replaced by addition",
+     "h ^= ((uint64_t)c[d] * (uint64_t)g->primes[d]) & 0xFFFFFFFFull;",
+     "h += ((uint64_t)c[d] * (uint64_t)g->primes[d]) & 0xFFFFFFFFull;",
+     [("test_hash_big_integer_brute_force", {})]),
+    ("dense stride N instead of N + 1",
+     "int64_t R = res[0] + 1;",
+     "int64_t R = res[0];",
+     [("test_dense_level_is_bijection_onto_table", {})]),
+    ("features stored feature-major",
+     "f_h[l * F + f] = acc;",
+     "f_h[f * g->L + l] = acc;",
+     [("test_vertex_reproduction_exact", {})]),
+    ("compaction keeps only mask bytes equal to 1",
+     "if (mask[i] != 0) idx_out[count++] = (int32_t)i;",
+     "if (mask[i] == 1) idx_out[count++] = (int32_t)i;",
+     [("test_compaction_is_flatnonzero", dict(n=100_003, p=0.5))]),
+    ("second ReLU dropped",
+     "h2[j] = a > 0.0 ? a : 0.0;",
+     "h2[j] = a;",
+     [("test_mlp_forward_and_backward_match_torch_autograd", dict(D=8, H=64, O=10))]),
+    ("W2 transposed in back-propagation",
+     "for (int j = 0; j < H; ++j) a += m->W2[(size_t)j * H + k] * dz2[j];",
+     "for (int j = 0; j < H; ++j) a += m->W2[(size_t)k * H + j] * dz2[j];",
+     [("test_mlp_forward_and_backward_match_torch_autograd", dict(D=8, H=64, O=10))]),
+    ("Eq. 10 subtracts the offset",
+     "(double)attrs_in[j * n_all + gi] + o[j];",
+     "(double)attrs_in[j * n_all + gi] - o[j];",
+     [("test_deform_forward_composes_encoder_mlp_and_eq10", {})]),
+    ("Eq. 11 gradient of the perturbed point with the wrong sign",
+     "dq[k] = -scale * diff;",
+     "dq[k] = scale * diff;",
+     [("test_full_backward_finite_difference_with_smoothness", {})]),
+    ("Eq. 11 gradient missing the factor 2",
+     "const double scale = 2.0 * (double)lambda_r / (double)(n > 0 ? n : 1);",
+     "const double scale = (double)lambda_r / (double)(n > 0 ? n : 1);",
+     [("test_full_backward_finite_difference_with_smoothness", {})]),
+    ("Eq. 11 temporal perturbation applied to x",
+     "const float e_t[4] = {0.f, 0.f, 0.f, eps_t};",
+     "const float e_t[4] = {eps_t, 0.f, 0.f, 0.f};",
+     [("test_smoothness_closed_form_on_affine_tables", {})]),
+]
+
+
+@pytest.mark.parametrize("name,old,new,checks", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_planted_mistake(tmp_path, monkeypatch, name, old, new, checks):
+    src = open(oracle._SRC).read()
+    assert old in src, f"mutation anchor not found: {old}"
+    (tmp_path / "mutant.c").write_text(src.replace(old, new))
+    lib = oracle.configure(ctypes.CDLL(oracle.compile_variant(str(tmp_path / "mutant.c"),
+                                                              str(tmp_path / "mutant.so"))))
+    monkeypatch.setattr(oracle, "_lib", lib)
+    caught = []
+    for fname, kwargs in checks:
+        try:
+            getattr(pins, fname)(**kwargs)
+        except (AssertionError, ValueError):
+            caught.append(fname)
+    assert caught, f"no pin caught: {name}"
+
+
+def test_unmutated_copy_passes_the_same_checks(tmp_path, monkeypatch):
+    """Control: the same procedure on an unchanged copy fails nothing."""
+    src = open(oracle._SRC).read()
+    (tmp_path / "copy.c").write_text(src)
+    lib = oracle.configure(ctypes.CDLL(oracle.compile_variant(str(tmp_path / "copy.c"), str(tmp_path / "copy.so"))))
+    monkeypatch.setattr(oracle, "_lib", lib)
+    for _, _, _, checks in MUTATIONS:
+        for fname, kwargs in checks:
+            getattr(pins, fname)(**kwargs)
