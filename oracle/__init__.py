@@ -124,6 +124,16 @@ def configure(lib):
     lib.orc_deform_bwd.restype = ctypes.c_double
     lib.orc_smooth_loss.argtypes = [G] + pts + [P, ctypes.c_float, P, ctypes.c_float]
     lib.orc_smooth_loss.restype = ctypes.c_double
+    lib.orc_layout3.argtypes = [G, i32, i32, i32, ctypes.c_double, ctypes.c_double, P]
+    lib.orc_layout3.restype = i32
+    lib.orc_cell3.argtypes = [G, i32, P, P, P]
+    lib.orc_cell3.restype = None
+    lib.orc_encode3.argtypes = [G, P, P, P, i64, P, P]
+    lib.orc_encode3.restype = None
+    lib.orc_decomp_fwd.argtypes = [G, P, P, P, i64, P, i32, P, P, P]
+    lib.orc_decomp_fwd.restype = i32
+    lib.orc_topk_mask.argtypes = [P, i64, ctypes.c_double, P]
+    lib.orc_topk_mask.restype = ctypes.c_double
     return lib
 
 
@@ -276,3 +286,52 @@ def smooth_loss(g: Grid, pts: Points, table, lambda_r, eps_s, eps_t) -> float:
     es = np.asarray(eps_s, dtype=np.float32)
     return float(_load().orc_smooth_loss(ctypes.byref(g), *pts.args(), _ptr(tab),
                                          float(lambda_r), _ptr(es), float(eps_t)))
+
+
+# ------------------------------------------------ decomposition (Sec. 4.1) --
+def layout3(L, F, log2_T, nmin, nmax, primes=DEFAULT_PRIMES) -> Grid:
+    """3-D level layout of G_3D (Eq. 7 progression, (N+1)^3 dense vertices)."""
+    g = Grid()
+    pr = np.asarray(primes, dtype=np.uint32)
+    if _load().orc_layout3(ctypes.byref(g), L, F, log2_T, float(nmin), float(nmax), _ptr(pr)) != 0:
+        raise ValueError("invalid hash-grid configuration")
+    return g
+
+
+def cell3(g: Grid, l: int, p):
+    pf = np.asarray(p, dtype=np.float32)
+    idx = np.zeros(8, dtype=np.uint32)
+    w = np.zeros(8, dtype=np.float64)
+    _load().orc_cell3(ctypes.byref(g), l, _ptr(pf), _ptr(idx), _ptr(w))
+    return idx, w
+
+
+def encode3(g: Grid, x, y, z, table) -> np.ndarray:
+    xs, ys, zs = (_c(v, np.float32) for v in (x, y, z))
+    tab = _c(table, np.float64)
+    n = len(xs)
+    out = np.zeros((n, g.L * g.F), dtype=np.float64)
+    _load().orc_encode3(ctypes.byref(g), _ptr(xs), _ptr(ys), _ptr(zs), n, _ptr(tab), _ptr(out))
+    return out
+
+
+def decomp_fwd(g: Grid, x, y, z, table, H, params):
+    """Returns (dp SoA [3][n], norm [n]) of Eqs. 3-4's positional deformation."""
+    xs, ys, zs = (_c(v, np.float32) for v in (x, y, z))
+    tab = _c(table, np.float64)
+    p = _c(params, np.float64)
+    n = len(xs)
+    dp = np.zeros((3, n), dtype=np.float64)
+    norm = np.zeros(n, dtype=np.float64)
+    if _load().orc_decomp_fwd(ctypes.byref(g), _ptr(xs), _ptr(ys), _ptr(zs), n, _ptr(tab), H, _ptr(p), _ptr(dp),
+                              _ptr(norm)) != 0:
+        raise ValueError("unsupported MLP shape")
+    return dp, norm
+
+
+def topk_mask(values, k_percent):
+    """(mask uint8 [n], tau): dynamic iff value > tau, tau the (m+1)-th largest, m = floor(k n / 100)."""
+    v = _c(values, np.float64)
+    mask = np.zeros(max(len(v), 1), dtype=np.uint8)
+    tau = _load().orc_topk_mask(_ptr(v), len(v), float(k_percent), _ptr(mask))
+    return mask[:len(v)].copy(), float(tau)

@@ -442,3 +442,146 @@ double orc_smooth_loss(const orc_grid* g, const float* x, const float* y, const 
   }
   return (double)lambda_r * loss / (double)(n > 0 ? n : 1);
 }
+
+/* =========================================================================
+ * Self-supervised decomposition (Sec. 4.1, Eqs. 3-4): the 3-D hash encoder
+ * G_3D of the Gaussian positions, the MLPs phi_p and phi_l giving the
+ * positional deformation dp, its norm, and the top-k % threshold tau.
+ * Readings: G_3D uses the Eq. 7 progression of the spatial resolutions and
+ * the Eq. 8 hash with the first three primes, (N+1)^3 vertices per dense
+ * level; phi_p is one ReLU layer D -> H (f_3D), phi_l one linear layer
+ * H -> 3 (dp).  tau is the (m+1)-th largest norm with m = floor(k N / 100);
+ * Gaussians with norm > tau are dynamic, so ties at tau are static.
+ * ========================================================================= */
+
+/* 3-D level layout; the grid's res_t entries are 0 and `reserved` holds 3. */
+int orc_layout3(orc_grid* g, int L, int F, int log2_T, double nmin, double nmax, const uint32_t* primes) {
+  if (L < 1 || L > ORC_MAX_LEVELS || F < 1 || log2_T < 1 || log2_T > 30) return -1;
+  if (!(nmin >= 1.0) || !(nmax >= nmin)) return -1;
+  memset(g, 0, sizeof(*g));
+  g->L = L;
+  g->F = F;
+  g->log2_T = log2_T;
+  g->reserved = 3;
+  for (int i = 0; i < 3; ++i) g->primes[i] = primes[i];
+  const int64_t T = (int64_t)1 << log2_T;
+  int64_t off = 0;
+  for (int l = 0; l < L; ++l) {
+    int32_t ns = orc_level_res(nmin, nmax, L, l);
+    g->res_s[l] = ns;
+    int64_t verts = (int64_t)(ns + 1) * (ns + 1) * (ns + 1);
+    g->dense[l] = verts <= T;
+    g->size[l] = g->dense[l] ? verts : T;
+    g->offset[l] = off;
+    off += g->size[l];
+    off = (off + 7) / 8 * 8;
+  }
+  g->offset[L] = off;
+  return 0;
+}
+
+/* The 8 corners of the level-l voxel around p (x, y, z) and their trilinear
+ * weights; corner b: bit d set = upper corner along axis d. */
+void orc_cell3(const orc_grid* g, int l, const float p[3], uint32_t idx[8], double w[8]) {
+  const int64_t N = g->res_s[l];
+  int64_t i0[3];
+  double frac[3];
+  for (int d = 0; d < 3; ++d) {
+    double pos = (double)(float)((double)p[d] * (double)N);
+    int64_t c = (int64_t)floor(pos);
+    if (c > N - 1) c = N - 1;
+    i0[d] = c;
+    frac[d] = pos - (double)c;
+  }
+  const uint32_t mask = (uint32_t)((((uint64_t)1) << g->log2_T) - 1);
+  for (int b = 0; b < 8; ++b) {
+    int64_t c[3];
+    double wb = 1.0;
+    for (int d = 0; d < 3; ++d) {
+      int up = (b >> d) & 1;
+      c[d] = i0[d] + up;
+      wb *= up ? frac[d] : (1.0 - frac[d]);
+    }
+    w[b] = wb;
+    if (g->dense[l]) {
+      int64_t R = N + 1;
+      idx[b] = (uint32_t)(c[0] + R * (c[1] + R * c[2]));
+    } else {
+      uint64_t h = 0;
+      for (int d = 0; d < 3; ++d) h ^= ((uint64_t)c[d] * (uint64_t)g->primes[d]) & 0xFFFFFFFFull;
+      idx[b] = (uint32_t)h & mask;
+    }
+  }
+}
+
+/* G_3D(p) for points (x, y, z)[n] (clamped to [0,1]): feat [n][L*F]. */
+void orc_encode3(const orc_grid* g, const float* x, const float* y, const float* z, int64_t n,
+                 const double* table, double* feat) {
+  const int F = g->F, LF = g->L * g->F;
+  for (int64_t i = 0; i < n; ++i) {
+    const float p[3] = {orc_clamp01(x[i]), orc_clamp01(y[i]), orc_clamp01(z[i])};
+    for (int l = 0; l < g->L; ++l) {
+      uint32_t idx[8];
+      double w[8];
+      orc_cell3(g, l, p, idx, w);
+      for (int f = 0; f < F; ++f) {
+        double acc = 0.0;
+        for (int b = 0; b < 8; ++b) acc += w[b] * table[(g->offset[l] + idx[b]) * F + f];
+        feat[i * LF + l * F + f] = acc;
+      }
+    }
+  }
+}
+
+/* dp = phi_l(phi_p(G_3D(p))) and its Euclidean norm.  params packs
+ * W1 [H][D], b1 [H], W2 [3][H], b2 [3]; dp SoA [3][n] (may be NULL). */
+int orc_decomp_fwd(const orc_grid* g, const float* x, const float* y, const float* z, int64_t n,
+                   const double* table, int H, const double* params, double* dp, double* norm) {
+  const int D = g->L * g->F;
+  if (D > 256 || H > 256) return -1;
+  const double* W1 = params;
+  const double* b1 = W1 + (size_t)H * D;
+  const double* W2 = b1 + H;
+  const double* b2 = W2 + (size_t)3 * H;
+  double f[256], h[256];
+  for (int64_t i = 0; i < n; ++i) {
+    orc_encode3(g, x + i, y + i, z + i, 1, table, f);
+    for (int j = 0; j < H; ++j) {
+      double a = b1[j];
+      for (int k = 0; k < D; ++k) a += W1[(size_t)j * D + k] * f[k];
+      h[j] = a > 0.0 ? a : 0.0;
+    }
+    double s = 0.0;
+    for (int j = 0; j < 3; ++j) {
+      double a = b2[j];
+      for (int k = 0; k < H; ++k) a += W2[(size_t)j * H + k] * h[k];
+      if (dp) dp[j * n + i] = a;
+      s += a * a;
+    }
+    norm[i] = sqrt(s);
+  }
+  return 0;
+}
+
+static int orc_cmp_desc(const void* a, const void* b) {
+  const double x = *(const double*)a, y = *(const double*)b;
+  return x < y ? 1 : (x > y ? -1 : 0);
+}
+
+/* Top-k % split: tau is the (m+1)-th largest of the n values (m = floor(k n /
+ * 100)); mask[i] = values[i] > tau.  m = 0 marks nothing, m >= n marks
+ * everything (tau = -1; the values are norms, never negative).  Returns tau. */
+double orc_topk_mask(const double* values, int64_t n, double k_percent, uint8_t* mask) {
+  int64_t m = (int64_t)floor(k_percent * (double)n / 100.0);
+  if (m < 0) m = 0;
+  double tau = -1.0;
+  if (m < n && n > 0) {
+    double* s = (double*)malloc(sizeof(double) * (size_t)n);
+    memcpy(s, values, sizeof(double) * (size_t)n);
+    qsort(s, (size_t)n, sizeof(double), orc_cmp_desc);
+    tau = s[m];
+    free(s);
+  }
+  for (int64_t i = 0; i < n; ++i) mask[i] = values[i] > tau;
+  return tau;
+}
