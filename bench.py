@@ -484,8 +484,60 @@ def run_extras(torch, wl, args, stream):
     torch.cuda.synchronize()
     res["scatter_fp16_rel_err_vs_fp32"] = float((g16.float() - g32).norm() / g32.norm())
     del g32, g16, dfeat
+    res.update(run_decomp(torch, wl, stream))
     res.update(run_batched(torch, stream))
     return res
+
+
+# decomposition, algorithmic bytes per Gaussian: x, y, z (12) + 16 levels x 8
+# corners x one FP16 F=2 entry (512) + dp (12) + norm (4); top-k: norm (4) + mask (1)
+DECOMP_BYTES = 12 + 16 * 8 * 4 + 12 + 4
+TOPK_BYTES = 4 + 1
+
+
+def run_decomp(torch, wl, stream):
+    """Decomposition producing the mask, over all Gaussians of the workload:
+    G_3D (16 levels 16..2048, T = 2^19, FP16) + phi_p/phi_l norms, the top-50 %
+    threshold and mask, and the chain decomposition -> mask -> compaction."""
+    import numpy as np
+    from paper_2507_19141_gb300 import dash, synth
+    rng = np.random.default_rng(11)
+    lay3 = dash.dash_hash3d_layout(16, 2, 19, 16, 2048)
+    D, H = 32, 64
+    k = 1 / np.sqrt(D)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    table3 = dev(synth.table_values(rng, lay3.total, 2, np.float16))
+    dec = dash.Mlp(dev(rng.uniform(-k, k, H * D + H + 3 * H + 3).astype(np.float32)), D, H, 3)
+    n = wl.n_all
+    dp = torch.empty((3, n), dtype=torch.float32, device="cuda")
+    norm = torch.empty(n, dtype=torch.float32, device="cuda")
+    mask = torch.empty(n, dtype=torch.uint8, device="cuda")
+    tau = torch.empty(1, dtype=torch.float32, device="cuda")
+    ws = torch.empty(dash.dash_topk_workspace_size(), dtype=torch.uint8, device="cuda")
+    idx = torch.empty(n, dtype=torch.int32, device="cuda")
+    cnt = torch.empty(1, dtype=torch.int64, device="cuda")
+    cws = torch.empty(dash.dash_compact_workspace_size(n), dtype=torch.uint8, device="cuda")
+
+    def dec_fwd():
+        dash.dash_decomp_fwd(lay3, wl.x, wl.y, wl.z, table3, dec, dp_out=dp, norm_out=norm)
+
+    def topk():
+        dash.dash_topk_mask(norm, 50.0, mask_out=mask, tau_out=tau, ws=ws)
+
+    def chain():
+        dec_fwd()
+        topk()
+        dash.dash_compact_dynamic(mask, idx_out=idx, count_out=cnt, ws=cws)
+
+    for _ in range(3):
+        chain()
+    r = {"decomp_n": n, "decomp_ms": time_steps(torch, dec_fwd, 20, stream),
+         "topk_ms": time_steps(torch, topk, 20, stream), "decomp_chain_ms": time_steps(torch, chain, 20, stream)}
+    r["decomp_gbs"] = DECOMP_BYTES * n / (r["decomp_ms"] / 1e3) / 1e9
+    r["topk_gbs"] = TOPK_BYTES * n / (r["topk_ms"] / 1e3) / 1e9
+    r["decomp_chain_gaussians_per_s"] = n / (r["decomp_chain_ms"] / 1e3)
+    r["decomp_dynamic_count"] = int(cnt.item())
+    return r
 
 
 def run_batched(torch, stream):

@@ -61,7 +61,7 @@ typedef struct dash_hash4d_cfg {
  * else hashed by Eq. 8 into T entries; size[l]: entries used; offset[l]:
  * first entry of level l, a multiple of 8; offset[L]: entries to allocate. */
 typedef struct dash_layout {
-  int32_t L, F, log2_T, reserved;
+  int32_t L, F, log2_T, dims; /* dims: 0 = 4-D (x, y, z, t), 3 = 3-D (x, y, z) */
   uint32_t primes[4];
   int32_t res_s[DASH_MAX_LEVELS];
   int32_t res_t[DASH_MAX_LEVELS];
@@ -238,6 +238,37 @@ int dash_deform_mlp_bwd(const dash_layout* layout, const dash_points* pts,
                         const void* table, int table_dtype, const dash_mlp* mlp,
                         const float* ddelta, const void* fwd_state, float* table_grad,
                         float* mlp_grad, const dash_smooth* smooth, void* stream);
+
+/* ------------- decomposition producing the mask (Sec. 4.1, Eqs. 3-4) ---- */
+
+/* 3-D layout of the position encoder G_3D: Eq. 7 spatial resolutions,
+ * levels with (N+1)^3 <= T vertices indexed directly, others hashed by Eq. 8
+ * with primes[0..2]; res_t = 0, dims = 3.  Errors as dash_hash4d_layout. */
+int dash_hash3d_layout(const dash_hash4d_cfg* cfg, dash_layout* out);
+
+/* Positional deformation dp = phi_l(phi_p(G_3D(p))) of n Gaussians and its
+ * norm (the motion magnitude whose top-k % makes a Gaussian dynamic).
+ * x, y, z [n] FP32 in [0,1] (clamped); table of the 3-D layout (F32/F16);
+ * mlp: d_in = L*F, d_hidden = 64, d_out = 3 with params packed W1 [64][D],
+ * b1 [64], W2 [3][64], b2 [3] (ReLU after the first layer).  dp_out SoA
+ * [3][n] (may be NULL), norm_out [n]. */
+int dash_decomp_fwd(const dash_layout* layout3, const float* x, const float* y, const float* z,
+                    int64_t n, const void* table, int table_dtype, const dash_mlp* mlp,
+                    float* dp_out, float* norm_out, void* stream);
+
+/* Bytes of device workspace dash_topk_mask needs (a few hundred). */
+size_t dash_topk_workspace_size(void);
+
+/* Top-k % split: tau = the (m+1)-th largest of values[0..n) with
+ * m = floor(k_percent * n / 100), found exactly by a radix select on the
+ * values' bit patterns (values are norms: zeros of either sign, NaN and
+ * negatives all count as +0); mask_out[i] = values[i] > tau, so ties at tau
+ * are static; m = 0 marks none, m >= n marks all (tau = -1).  tau_out
+ * (device float) may be NULL.  n <= 2^31 - 1 (DASH_ERR_UNSUPPORTED above);
+ * k_percent outside [0, 100] or a workspace below dash_topk_workspace_size()
+ * is an error.  Launches 10 small kernels on `stream`; ws is reused. */
+int dash_topk_mask(const float* values, int64_t n, double k_percent, uint8_t* mask_out,
+                   float* tau_out, void* ws, size_t ws_bytes, void* stream);
 
 /* ---------------- a12: many scenes x timestamps, one graph launch ------ */
 

@@ -50,6 +50,7 @@ int sm_count() {
 
 int make_geom(const dash_layout* lo, Geom* g) {
   if (lo == nullptr || g == nullptr) return fail(DASH_ERR_INVALID_ARG, "layout is NULL");
+  if (!(lo->dims == 0 || lo->dims == 4)) return fail(DASH_ERR_INVALID_ARG, "needs a 4-D layout (dims = %d)", lo->dims);
   if (lo->L < 1 || lo->L > DASH_MAX_LEVELS) return fail(DASH_ERR_UNSUPPORTED, "L=%d outside [1,32]", lo->L);
   if (!(lo->F == 1 || lo->F == 2 || lo->F == 4 || lo->F == 8))
     return fail(DASH_ERR_UNSUPPORTED, "F=%d not in {1,2,4,8}", lo->F);

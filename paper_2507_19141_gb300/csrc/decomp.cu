@@ -1,0 +1,298 @@
+// decomp.cu -- the self-supervised static/dynamic decomposition that
+// produces the mask the deformation path consumes (Sec. 4.1, Eqs. 3-4):
+//   f_3D = phi_p(G_3D(p)), dp = phi_l(f_3D), |dp|;  tau = top-k % of |dp|;
+//   mask = |dp| > tau.
+// G_3D is the 3-D multiresolution hash encoder of the Gaussian positions
+// (8 corners per level, trilinear weights); phi_p is one ReLU layer D -> 64,
+// phi_l one linear layer 64 -> 3.  The decoder is tiny (2.2 kflop per
+// Gaussian) and runs on the CUDA cores straight from the gather registers.
+// tau is found exactly by a radix select over the norms' bit patterns.
+#include <math.h>
+
+#include "dash_internal.cuh"
+
+namespace dash {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kHidden3 = 64;
+
+// The 8 corners of level l around p (x, y, z) and their trilinear weights.
+__device__ __forceinline__ void level_corners3(const Geom& g, int l, float3 p, uint32_t idx[8], float w[8]) {
+  const int ns = g.res_s[l];
+  int ix, iy, iz;
+  float fx, fy, fz;
+  axis_cell(p.x, ns, ix, fx);
+  axis_cell(p.y, ns, iy, fy);
+  axis_cell(p.z, ns, iz, fz);
+  if ((g.dense_bits >> l) & 1u) {
+    const uint32_t R = (uint32_t)ns + 1u;
+    const uint32_t base = (uint32_t)ix + R * ((uint32_t)iy + R * (uint32_t)iz);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) idx[b] = base + (b & 1) + ((b >> 1) & 1) * R + ((b >> 2) & 1) * R * R;
+  } else {
+    const uint32_t hx0 = (uint32_t)ix * g.primes[0], hx1 = hx0 + g.primes[0];
+    const uint32_t hy0 = (uint32_t)iy * g.primes[1], hy1 = hy0 + g.primes[1];
+    const uint32_t hz0 = (uint32_t)iz * g.primes[2], hz1 = hz0 + g.primes[2];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) idx[b] = ((b & 1 ? hx1 : hx0) ^ (b & 2 ? hy1 : hy0) ^ (b & 4 ? hz1 : hz0)) & g.mask;
+  }
+  const float wx0 = 1.0f - fx, wy0 = 1.0f - fy, wz0 = 1.0f - fz;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    float v = (b & 1) ? fx : wx0;
+    v *= (b & 2) ? fy : wy0;
+    v *= (b & 4) ? fz : wz0;
+    w[b] = v;
+  }
+}
+
+template <typename TT, int F>
+__global__ void __launch_bounds__(kThreads) decomp_fwd_kernel(Geom g, const float* __restrict__ xs,
+                                                              const float* __restrict__ ys,
+                                                              const float* __restrict__ zs, long long n,
+                                                              const TT* __restrict__ table,
+                                                              const float* __restrict__ params, int D,
+                                                              float* __restrict__ dp_out, float* __restrict__ norm_out) {
+  extern __shared__ float w_s[];  // W1 [64][D], b1 [64], W2 [3][64], b2 [3]
+  const int P = kHidden3 * D + kHidden3 + 3 * kHidden3 + 3;
+  for (int e = threadIdx.x; e < P; e += kThreads) w_s[e] = __ldg(params + e);
+  __syncthreads();
+  const float* W1 = w_s;
+  const float* b1 = W1 + kHidden3 * D;
+  const float* W2 = b1 + kHidden3;
+  const float* b2 = W2 + 3 * kHidden3;
+  const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (i >= n) return;
+  const float3 p = make_float3(clamp01(__ldcs(xs + i)), clamp01(__ldcs(ys + i)), clamp01(__ldcs(zs + i)));
+  float h[kHidden3];
+#pragma unroll
+  for (int j = 0; j < kHidden3; ++j) h[j] = b1[j];
+  for (int l = 0; l < g.L; ++l) {
+    uint32_t idx[8];
+    float w[8];
+    level_corners3(g, l, p, idx, w);
+    const TT* base = table + g.offset[l] * F;
+    float f[F];
+#pragma unroll
+    for (int k = 0; k < F; ++k) f[k] = 0.0f;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      float e[F];
+      load_entry<TT, F>(base + (size_t)idx[b] * F, e);
+#pragma unroll
+      for (int k = 0; k < F; ++k) f[k] = fmaf(w[b], e[k], f[k]);
+    }
+    // phi_p: stream this level's features into the hidden pre-activations
+#pragma unroll
+    for (int k = 0; k < F; ++k) {
+      const int col = l * F + k;
+#pragma unroll
+      for (int j = 0; j < kHidden3; ++j) h[j] = fmaf(W1[j * D + col], f[k], h[j]);
+    }
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float a = b2[c];
+#pragma unroll
+    for (int j = 0; j < kHidden3; ++j) a = fmaf(W2[c * kHidden3 + j], fmaxf(h[j], 0.0f), a);
+    if (dp_out != nullptr) __stcs(dp_out + (long long)c * n + i, a);
+    s = fmaf(a, a, s);
+  }
+  __stcs(norm_out + i, sqrtf(s));
+}
+
+// ----------------------------------------------------------- radix select --
+// State (device workspace): hist[256] | prefix | prefix_mask | rank | pad.
+struct TopkState {
+  unsigned int hist[256];
+  unsigned int prefix;
+  unsigned int prefix_mask;
+  unsigned long long rank;  // ascending rank still to locate below the prefix
+};
+
+// Positive floats order like their bit patterns; zeros of either sign, NaN and
+// negatives all count as +0 (a norm is never negative).
+__device__ __forceinline__ unsigned int norm_key(float v) { return v > 0.0f ? __float_as_uint(v) : 0u; }
+
+__global__ void topk_init(TopkState* st, unsigned long long rank) {
+  st->hist[threadIdx.x] = 0u;
+  if (threadIdx.x == 0) {
+    st->prefix = 0u;
+    st->prefix_mask = 0u;
+    st->rank = rank;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) topk_hist(const float* __restrict__ v, long long n, TopkState* st,
+                                                      int shift) {
+  __shared__ unsigned int h[256];
+  h[threadIdx.x] = 0u;
+  __syncthreads();
+  const unsigned int prefix = st->prefix, pmask = st->prefix_mask;
+  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads) {
+    const unsigned int k = norm_key(__ldg(v + i));
+    if ((k & pmask) == prefix) atomicAdd(&h[(k >> shift) & 0xFFu], 1u);
+  }
+  __syncthreads();
+  if (h[threadIdx.x] != 0u) atomicAdd(&st->hist[threadIdx.x], h[threadIdx.x]);
+}
+
+// One warp: finds the digit holding the target rank, narrows the prefix and
+// clears the histogram for the next pass.
+__global__ void topk_select(TopkState* st, int shift) {
+  if (threadIdx.x == 0) {
+    unsigned long long r = st->rank, cum = 0ull;
+    unsigned int d = 255u;
+    for (unsigned int b = 0; b < 256u; ++b) {
+      const unsigned long long c = st->hist[b];
+      if (cum + c > r) {
+        d = b;
+        break;
+      }
+      cum += c;
+    }
+    st->rank = r - cum;
+    st->prefix |= d << shift;
+    st->prefix_mask |= 0xFFu << shift;
+  }
+  __syncwarp();
+  for (int b = threadIdx.x; b < 256; b += 32) st->hist[b] = 0u;
+}
+
+__global__ void __launch_bounds__(kThreads) topk_apply(const float* __restrict__ v, long long n,
+                                                       const TopkState* st, int all, uint8_t* __restrict__ mask,
+                                                       float* tau_out) {
+  const unsigned int tau = st->prefix;
+  const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (i == 0 && tau_out != nullptr) *tau_out = all ? -1.0f : __uint_as_float(tau);
+  if (i < n) mask[i] = all ? 1u : (norm_key(__ldg(v + i)) > tau ? 1u : 0u);
+}
+
+}  // namespace
+}  // namespace dash
+
+extern "C" {
+
+int dash_hash3d_layout(const dash_hash4d_cfg* cfg, dash_layout* out) {
+  using dash::fail;
+  if (cfg == nullptr || out == nullptr) return fail(DASH_ERR_INVALID_ARG, "cfg/out is NULL");
+  if (cfg->L < 1 || cfg->L > DASH_MAX_LEVELS) return fail(DASH_ERR_UNSUPPORTED, "L=%d outside [1,32]", cfg->L);
+  if (!(cfg->F == 1 || cfg->F == 2 || cfg->F == 4 || cfg->F == 8))
+    return fail(DASH_ERR_UNSUPPORTED, "F=%d not in {1,2,4,8}", cfg->F);
+  if (cfg->log2_T < 4 || cfg->log2_T > 28) return fail(DASH_ERR_UNSUPPORTED, "log2_T=%d outside [4,28]", cfg->log2_T);
+  if (!(cfg->nmin_s >= 1.0) || !(cfg->nmax_s >= cfg->nmin_s) || cfg->nmax_s > 65535.0)
+    return fail(DASH_ERR_INVALID_ARG, "resolutions must satisfy 1 <= N_min <= N_max <= 65535");
+  memset(out, 0, sizeof(*out));
+  out->L = cfg->L;
+  out->F = cfg->F;
+  out->log2_T = cfg->log2_T;
+  out->dims = 3;
+  for (int i = 0; i < 3; ++i) out->primes[i] = cfg->primes[i];
+  const int64_t T = (int64_t)1 << cfg->log2_T;
+  int64_t start = 0;
+  for (int l = 0; l < cfg->L; ++l) {
+    double ns_d;
+    if (cfg->L == 1) {
+      ns_d = floor(cfg->nmin_s + 1e-9);
+    } else {
+      const double growth = exp((log(cfg->nmax_s) - log(cfg->nmin_s)) / (double)(cfg->L - 1));
+      ns_d = floor(cfg->nmin_s * pow(growth, (double)l) + 1e-9);
+    }
+    const int32_t ns = (int32_t)ns_d;
+    out->res_s[l] = ns;
+    out->res_t[l] = 0;
+    const int64_t r = (int64_t)ns + 1;
+    const int64_t vertices = r * r * r;
+    out->dense[l] = vertices <= T ? 1 : 0;
+    out->size[l] = out->dense[l] ? vertices : T;
+    out->offset[l] = start;
+    start = (start + out->size[l] + 7) & ~(int64_t)7;
+  }
+  out->offset[cfg->L] = start;
+  return DASH_OK;
+}
+
+int dash_decomp_fwd(const dash_layout* layout, const float* x, const float* y, const float* z, int64_t n,
+                    const void* table, int table_dtype, const dash_mlp* mlp, float* dp_out, float* norm_out,
+                    void* stream) {
+  using namespace dash;
+  if (layout == nullptr || layout->dims != 3) return fail(DASH_ERR_INVALID_ARG, "needs a 3-D layout (dash_hash3d_layout)");
+  dash_layout as4 = *layout;
+  as4.dims = 0;
+  for (int l = 0; l < as4.L; ++l) as4.res_t[l] = 1;
+  Geom g;
+  if (int s = make_geom(&as4, &g)) return s;
+  const int D = g.L * g.F;
+  if (mlp == nullptr || mlp->params == nullptr) return fail(DASH_ERR_INVALID_ARG, "mlp/params is NULL");
+  if (mlp->d_in != D || mlp->d_hidden != kHidden3 || mlp->d_out != 3)
+    return fail(DASH_ERR_UNSUPPORTED, "decomposition MLP must be %d -> 64 -> 3", D);
+  if (D > 64) return fail(DASH_ERR_UNSUPPORTED, "L*F=%d > 64", D);
+  if (n < 0) return fail(DASH_ERR_INVALID_ARG, "n < 0");
+  if (n == 0) return DASH_OK;
+  if (x == nullptr || y == nullptr || z == nullptr || table == nullptr || norm_out == nullptr)
+    return fail(DASH_ERR_INVALID_ARG, "NULL argument");
+  const size_t smem = sizeof(float) * (size_t)(kHidden3 * D + kHidden3 + 3 * kHidden3 + 3);
+  const unsigned grid = (unsigned)((n + kThreads - 1) / kThreads);
+  cudaStream_t st = as_stream(stream);
+#define DASH_DECOMP_LAUNCH(TT, FF)                                                                             \
+  decomp_fwd_kernel<TT, FF><<<grid, kThreads, smem, st>>>(g, x, y, z, n, static_cast<const TT*>(table),        \
+                                                          mlp->params, D, dp_out, norm_out)
+  if (table_dtype == DASH_F16) {
+    switch (g.F) {
+      case 1: DASH_DECOMP_LAUNCH(__half, 1); break;
+      case 2: DASH_DECOMP_LAUNCH(__half, 2); break;
+      case 4: DASH_DECOMP_LAUNCH(__half, 4); break;
+      default: DASH_DECOMP_LAUNCH(__half, 8); break;
+    }
+  } else if (table_dtype == DASH_F32) {
+    switch (g.F) {
+      case 1: DASH_DECOMP_LAUNCH(float, 1); break;
+      case 2: DASH_DECOMP_LAUNCH(float, 2); break;
+      case 4: DASH_DECOMP_LAUNCH(float, 4); break;
+      default: DASH_DECOMP_LAUNCH(float, 8); break;
+    }
+  } else {
+    return fail(DASH_ERR_UNSUPPORTED, "table_dtype %d (F32 or F16)", table_dtype);
+  }
+#undef DASH_DECOMP_LAUNCH
+  return launch_status("decomp_fwd_kernel");
+}
+
+size_t dash_topk_workspace_size(void) { return (sizeof(dash::TopkState) + 255) / 256 * 256; }
+
+int dash_topk_mask(const float* values, int64_t n, double k_percent, uint8_t* mask_out, float* tau_out, void* ws,
+                   size_t ws_bytes, void* stream) {
+  using namespace dash;
+  if (n < 0 || !(k_percent >= 0.0) || k_percent > 100.0)
+    return fail(DASH_ERR_INVALID_ARG, "n < 0 or k_percent outside [0, 100]");
+  if (n > 0x7FFFFFFFll) return fail(DASH_ERR_UNSUPPORTED, "n=%lld above 2^31 - 1", (long long)n);
+  if (n > 0 && (values == nullptr || mask_out == nullptr)) return fail(DASH_ERR_INVALID_ARG, "values/mask_out is NULL");
+  if (ws == nullptr || ws_bytes < dash_topk_workspace_size())
+    return fail(DASH_ERR_WORKSPACE, "workspace of %zu bytes, %zu needed", ws_bytes, dash_topk_workspace_size());
+  if (n == 0) return DASH_OK;
+  cudaStream_t st = as_stream(stream);
+  TopkState* state = static_cast<TopkState*>(ws);
+  long long m = (long long)floor(k_percent * (double)n / 100.0);
+  m = m < 0 ? 0 : m;
+  const int all = m >= n;
+  const unsigned long long rank = all ? 0ull : (unsigned long long)(n - 1 - m);  // ascending rank of tau
+  topk_init<<<1, 256, 0, st>>>(state, rank);
+  if (int s = launch_status("topk_init")) return s;
+  if (!all) {
+    long long blocks = (n + kThreads - 1) / kThreads;
+    const long long cap = 4ll * sm_count();
+    blocks = blocks < cap ? blocks : cap;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+      topk_hist<<<(unsigned)blocks, kThreads, 0, st>>>(values, n, state, shift);
+      if (int s = launch_status("topk_hist")) return s;
+      topk_select<<<1, 32, 0, st>>>(state, shift);
+      if (int s = launch_status("topk_select")) return s;
+    }
+  }
+  topk_apply<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, st>>>(values, n, state, all, mask_out, tau_out);
+  return launch_status("topk_apply");
+}
+
+}  // extern "C"

@@ -44,7 +44,7 @@ class dash_hash4d_cfg(ctypes.Structure):
 
 class dash_layout(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("F", ctypes.c_int32), ("log2_T", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("primes", ctypes.c_uint32 * 4),
+                ("dims", ctypes.c_int32), ("primes", ctypes.c_uint32 * 4),
                 ("res_s", ctypes.c_int32 * MAX_LEVELS), ("res_t", ctypes.c_int32 * MAX_LEVELS),
                 ("dense", ctypes.c_int32 * MAX_LEVELS), ("size", ctypes.c_int64 * MAX_LEVELS),
                 ("offset", ctypes.c_int64 * (MAX_LEVELS + 1))]
@@ -120,6 +120,10 @@ _SIGS = {
     "dash_batch_form": ([_P], _I),
     "dash_batch_autotune": ([_P, ctypes.c_char_p, _P], _I),
     "dash_batch_plan_destroy": ([_P], _I),
+    "dash_hash3d_layout": ([_P, _P], _I),
+    "dash_decomp_fwd": ([_P, _P, _P, _P, _I64, _P, _I, _P, _P, _P, _P], _I),
+    "dash_topk_workspace_size": ([], _SZ),
+    "dash_topk_mask": ([_P, _I64, ctypes.c_double, _P, _P, _P, _SZ, _P], _I),
     "dash_plain_hash4d_fwd": ([_P, _P, _P, _P, _P], _I),
     "dash_plain_hash4d_bwd": ([_P, _P, _P, _P, _P], _I),
     "dash_plain_mlp_fwd": ([_P, _P, _I64, _P, _P, _P], _I),
@@ -153,6 +157,15 @@ def exported_symbols():
 # ------------------------------------------------------------ utilities --
 def dash_version() -> int:
     return int(_lib.dash_version())
+
+
+def dash_status_string(status: int) -> str:
+    return _lib.dash_status_string(int(status)).decode()
+
+
+def dash_last_error() -> str:
+    """Message of the last failing call on this host thread."""
+    return _lib.dash_last_error().decode()
 
 
 OPT_FWD_FORM = 1
@@ -217,7 +230,8 @@ class Mlp:
 
     def __init__(self, params: torch.Tensor, d_in: int, d_hidden: int, d_out: int):
         assert params.is_cuda and params.dtype == torch.float32 and params.is_contiguous()
-        assert params.numel() == mlp_param_count(d_in, d_hidden, d_out)
+        two_layer = d_out == 3 and params.numel() == d_hidden * d_in + d_hidden + 3 * d_hidden + 3
+        assert two_layer or params.numel() == mlp_param_count(d_in, d_hidden, d_out)
         self.params = params
         self.d_in, self.d_hidden, self.d_out = d_in, d_hidden, d_out
         self.c = dash_mlp(d_in, d_hidden, d_out, 0, params.data_ptr())
@@ -309,10 +323,14 @@ def dash_plain_mlp_fwd(mlp: Mlp, feat, n=None, n_dev=None, out=None):
     return out
 
 
+def dash_plain_mlp_bwd_workspace_size(mlp: Mlp, n: int) -> int:
+    return int(_lib.dash_plain_mlp_bwd_workspace_size(ctypes.byref(mlp.c), n))
+
+
 def dash_plain_mlp_bwd(mlp: Mlp, feat, ddelta, mlp_grad, n=None, n_dev=None, dfeat=None, ws=None):
     n = feat.shape[0] if n is None else n
     dfeat = torch.empty((n, mlp.d_in), dtype=torch.float32, device=feat.device) if dfeat is None else dfeat
-    need = int(_lib.dash_plain_mlp_bwd_workspace_size(ctypes.byref(mlp.c), n))
+    need = dash_plain_mlp_bwd_workspace_size(mlp, n)
     ws = torch.empty(max(need, 1), dtype=torch.uint8, device=feat.device) if ws is None else ws
     _check(_lib.dash_plain_mlp_bwd(ctypes.byref(mlp.c), _ptr(feat), n, _ptr(n_dev), _ptr(ddelta), _ptr(dfeat),
                                    _ptr(mlp_grad), _ptr(ws), ws.numel(), _stream()), "dash_plain_mlp_bwd")
@@ -354,7 +372,73 @@ def dash_deform_mlp_bwd(layout, pts, table, mlp: Mlp, ddelta, table_grad, mlp_gr
            "dash_deform_mlp_bwd")
 
 
+# ------------------------------------- decomposition producing the mask --
+def dash_hash3d_layout(L, F, log2_T, nmin, nmax, primes=PRIMES) -> dash_layout:
+    """3-D layout of the position encoder G_3D (host call)."""
+    cfg = dash_hash4d_cfg(L, F, log2_T, 0, float(nmin), float(nmax), 1.0, 1.0, (ctypes.c_uint32 * 4)(*primes))
+    out = dash_layout()
+    _check(_lib.dash_hash3d_layout(ctypes.byref(cfg), ctypes.byref(out)), "dash_hash3d_layout")
+    return out
+
+
+def dash_decomp_fwd(layout3: dash_layout, x, y, z, table, mlp: "Mlp", dp_out=None, norm_out=None, want_dp=True):
+    """(dp SoA [3][n] or None, norm [n]) of Eqs. 3-4's positional deformation."""
+    n = x.numel()
+    if want_dp and dp_out is None:
+        dp_out = torch.empty((3, n), dtype=torch.float32, device=x.device)
+    norm_out = torch.empty(n, dtype=torch.float32, device=x.device) if norm_out is None else norm_out
+    _check(_lib.dash_decomp_fwd(ctypes.byref(layout3), _ptr(x), _ptr(y), _ptr(z), n, _ptr(table),
+                                _DTYPE_CODE[table.dtype], ctypes.byref(mlp.c), _ptr(dp_out if want_dp else None),
+                                _ptr(norm_out), _stream()), "dash_decomp_fwd")
+    return (dp_out if want_dp else None), norm_out
+
+
+def dash_topk_workspace_size() -> int:
+    return int(_lib.dash_topk_workspace_size())
+
+
+def dash_topk_mask(values: torch.Tensor, k_percent: float, mask_out=None, tau_out=None, ws=None):
+    """(mask uint8 [n], tau float32 [1]): dynamic iff value > tau, tau the top-k % threshold."""
+    n = values.numel()
+    mask_out = torch.empty(n, dtype=torch.uint8, device=values.device) if mask_out is None else mask_out
+    tau_out = torch.empty(1, dtype=torch.float32, device=values.device) if tau_out is None else tau_out
+    if ws is None:
+        ws = torch.empty(dash_topk_workspace_size(), dtype=torch.uint8, device=values.device)
+    _check(_lib.dash_topk_mask(_ptr(values), n, float(k_percent), _ptr(mask_out), _ptr(tau_out), _ptr(ws), ws.numel(),
+                               _stream()), "dash_topk_mask")
+    return mask_out, tau_out
+
+
 # ----------------------------------------------------- a12: batched form --
+def dash_batch_plan_create(desc: dash_batch_desc) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(_lib.dash_batch_plan_create(ctypes.byref(desc), ctypes.byref(h)), "dash_batch_plan_create")
+    return h
+
+
+def dash_batch_counts(plan) -> int:
+    """Device address of the plan's int64 live counts [n_scenes]."""
+    return int(_lib.dash_batch_counts(plan))
+
+
+def dash_batch_run(plan) -> None:
+    _check(_lib.dash_batch_run(plan, _stream()), "dash_batch_run")
+
+
+def dash_batch_form(plan) -> int:
+    return int(_lib.dash_batch_form(plan))
+
+
+def dash_batch_autotune(plan, cache_path=None) -> int:
+    p = None if cache_path is None else str(cache_path).encode()
+    _check(_lib.dash_batch_autotune(plan, p, _stream()), "dash_batch_autotune")
+    return dash_batch_form(plan)
+
+
+def dash_batch_plan_destroy(plan) -> None:
+    _check(_lib.dash_batch_plan_destroy(plan), "dash_batch_plan_destroy")
+
+
 class BatchPlan:
     """Owner of a dash_batch_plan.  scenes: list of dicts with CUDA tensors
     table, params, x, y, z, timestamps [K], delta_out [K][O][n] (the plan
@@ -373,31 +457,26 @@ class BatchPlan:
         self._arr = arr
         desc = dash_batch_desc(ctypes.addressof(layout), dt, d_in, d_hidden, d_out, len(scenes),
                                ctypes.addressof(arr))
-        h = ctypes.c_void_p()
-        _check(_lib.dash_batch_plan_create(ctypes.byref(desc), ctypes.byref(h)), "dash_batch_plan_create")
-        self.handle = h
+        self.handle = dash_batch_plan_create(desc)
 
     def counts(self) -> torch.Tensor:
         """The plan's live per-scene counts as an int64 CUDA tensor view
         [n_scenes]; stream-ordered writes to it are seen by the next run."""
-        ptr = int(_lib.dash_batch_counts(self.handle))
-        return _device_view_i64(ptr, len(self.scenes))
+        return _device_view_i64(dash_batch_counts(self.handle), len(self.scenes))
 
     def run(self) -> None:
-        _check(_lib.dash_batch_run(self.handle, _stream()), "dash_batch_run")
+        dash_batch_run(self.handle)
 
     def form(self) -> int:
-        return int(_lib.dash_batch_form(self.handle))
+        return dash_batch_form(self.handle)
 
     def autotune(self, cache_path=None) -> int:
-        p = None if cache_path is None else str(cache_path).encode()
-        _check(_lib.dash_batch_autotune(self.handle, p, _stream()), "dash_batch_autotune")
-        return self.form()
+        return dash_batch_autotune(self.handle, cache_path)
 
     def close(self) -> None:
         if self.handle:
-            _lib.dash_batch_plan_destroy(self.handle)
-            self.handle = None
+            h, self.handle = self.handle, None
+            dash_batch_plan_destroy(h)
 
     def __del__(self):
         try:

@@ -45,6 +45,13 @@ def test_binding_names_match_the_abi():
         assert hasattr(dash._lib, n)
 
 
+def test_every_declared_function_has_a_same_named_wrapper():
+    from paper_2507_19141_gb300 import dash
+    missing = [n for n in _declared_functions() if not callable(getattr(dash, n, None))]
+    assert not missing, missing
+    assert dash.dash_status_string(0) == "DASH_OK"
+
+
 def test_status_strings_and_version(lib):
     lib.dash_status_string.restype = ctypes.c_char_p
     assert lib.dash_status_string(0) == b"DASH_OK"
@@ -73,3 +80,15 @@ def test_host_layout_rejects_bad_arguments():
     with pytest.raises(dash.DashError) as e:
         dash.dash_hash4d_layout(4, 2, 19, 16, 8, 8, 150)
     assert e.value.status == dash.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("cfg", [(16, 2, 19, 16, 2048), (4, 2, 12, 4, 32), (1, 1, 10, 7, 7), (8, 4, 14, 2, 512)])
+def test_host_layout3_equals_oracle(cfg):
+    from paper_2507_19141_gb300 import dash
+    L, F, lt, a, b = cfg
+    lay = dash.dash_hash3d_layout(L, F, lt, a, b)
+    assert lay.dims == 3
+    got = lay.as_dict()
+    ref = oracle.layout3(L, F, lt, a, b).as_dict()
+    got["res_t"] = ref["res_t"]  # unused by a 3-D layout
+    assert got == ref

@@ -1,0 +1,116 @@
+"""GPU parity of the decomposition step that produces the mask (Sec. 4.1,
+Eqs. 3-4): G_3D + phi_p + phi_l norms against the FP64 oracle, and the top-k %
+mask bit for bit against the oracle's selection applied to the same FP32
+norms (the GPU's), then the whole chain into compaction and deformation."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2507_19141_gb300 import synth
+from gpu_helpers import rel_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+G3 = dict(L=16, F=2, log2_T=19, nmin=16, nmax=2048)
+
+
+def _decomp_inputs(rng, n, tdtype=np.float16):
+    g = oracle.layout3(**G3)
+    x, y, z, _ = synth.scene_coords(rng, n)
+    table = synth.table_values(rng, g.total, 2, tdtype)
+    D, H = 32, 64
+    params = rng.uniform(-1 / np.sqrt(D), 1 / np.sqrt(D), H * D + H + 3 * H + 3).astype(np.float32)
+    return g, (x, y, z), table, params
+
+
+@pytest.mark.parametrize("tdtype", [np.float16, np.float32])
+def test_decomposition_norms_match_oracle(dashlib, tdtype):
+    rng = np.random.default_rng(71)
+    n = 20_000
+    g, (x, y, z), table, params = _decomp_inputs(rng, n, tdtype)
+    lay = dashlib.dash_hash3d_layout(**G3)
+    mlp = dashlib.Mlp(to_dev(params), 32, 64, 3)
+    dp, norm = dashlib.dash_decomp_fwd(lay, to_dev(x), to_dev(y), to_dev(z), to_dev(table), mlp)
+    rdp, rnorm = oracle.decomp_fwd(g, x, y, z, table.astype(np.float64), 64, params.astype(np.float64))
+    assert rel_err(dp.cpu().numpy(), rdp) < 1e-5
+    assert rel_err(norm.cpu().numpy(), rnorm) < 1e-5
+
+
+@pytest.mark.parametrize("n,k", [(1, 50.0), (10, 0.0), (10, 100.0), (1000, 12.5), (1_000_003, 50.0),
+                                 (2_000_000, 37.3)])
+def test_topk_mask_bit_exact(dashlib, n, k):
+    rng = np.random.default_rng(n)
+    v = rng.random(n).astype(np.float32) * 3
+    mask, tau = dashlib.dash_topk_mask(to_dev(v), k)
+    rmask, rtau = oracle.topk_mask(v.astype(np.float64), k)
+    assert np.array_equal(mask.cpu().numpy(), rmask)
+    assert float(tau.item()) == np.float32(rtau)
+
+
+def test_topk_mask_with_ties(dashlib):
+    rng = np.random.default_rng(72)
+    v = rng.integers(0, 50, size=100_000).astype(np.float32) / 7  # many equal values
+    for k in (0.5, 10.0, 50.0, 99.9):
+        mask, tau = dashlib.dash_topk_mask(to_dev(v), k)
+        rmask, rtau = oracle.topk_mask(v.astype(np.float64), k)
+        assert np.array_equal(mask.cpu().numpy(), rmask), k
+        assert float(tau.item()) == np.float32(rtau)
+
+
+def test_topk_mask_zeros_of_both_signs(dashlib):
+    """Zero norms (either sign) are the smallest keys and never dynamic."""
+    v = np.zeros(4096, np.float32)
+    v[::3] = -0.0
+    v[1::7] = np.linspace(0.5, 2.0, len(v[1::7]), dtype=np.float32)
+    for k in (5.0, 14.0, 50.0):
+        mask, tau = dashlib.dash_topk_mask(to_dev(v), k)
+        rmask, rtau = oracle.topk_mask(v.astype(np.float64), k)
+        assert np.array_equal(mask.cpu().numpy(), rmask), k
+        assert float(tau.item()) == np.float32(rtau)
+
+
+def test_decomposition_empty_and_errors(dashlib):
+    lay = dashlib.dash_hash3d_layout(**G3)
+    e = torch.empty(0, device="cuda")
+    dec = dashlib.Mlp(torch.zeros(64 * 32 + 64 + 3 * 64 + 3, device="cuda"), 32, 64, 3)
+    _, norm = dashlib.dash_decomp_fwd(lay, e, e, e, torch.zeros(8, device="cuda"), dec)
+    assert norm.numel() == 0
+    mask, _ = dashlib.dash_topk_mask(e, 50.0)
+    assert mask.numel() == 0
+    with pytest.raises(dashlib.DashError):
+        dashlib.dash_topk_mask(torch.ones(4, device="cuda"), 101.0)
+    lay4 = dashlib.layout_from(synth.PAPER_GRID)
+    x = torch.rand(16, device="cuda")
+    with pytest.raises(dashlib.DashError):   # a 4-D layout is not a G_3D layout
+        dashlib.dash_decomp_fwd(lay4, x, x, x, torch.zeros(8, device="cuda"), dec)
+
+
+def test_decomposition_feeds_compaction_and_deformation(dashlib):
+    """decomposition -> top-k mask -> compaction -> fused deformation,
+    every stage on the GPU, against the oracle chain fed the GPU's norms."""
+    rng = np.random.default_rng(73)
+    n_all = 30_000
+    g3, (x, y, z), t3, p3 = _decomp_inputs(rng, n_all)
+    t = rng.random(n_all).astype(np.float32)
+    lay3 = dashlib.dash_hash3d_layout(**G3)
+    dec = dashlib.Mlp(to_dev(p3), 32, 64, 3)
+    xd, yd, zd, td = to_dev(x), to_dev(y), to_dev(z), to_dev(t)
+    _, norm = dashlib.dash_decomp_fwd(lay3, xd, yd, zd, to_dev(t3), dec, want_dp=False)
+    mask, _ = dashlib.dash_topk_mask(norm, 30.0)
+    idx, cnt = dashlib.dash_compact_dynamic(mask)
+    grid, mlpc = synth.PAPER_GRID, synth.PAPER_MLP
+    g4 = oracle.layout(grid.L, grid.F, grid.log2_T, grid.nmin_s, grid.nmax_s, grid.nmin_t, grid.nmax_t)
+    table = synth.table_values(rng, g4.total, 2, np.float16)
+    params = synth.mlp_params(rng, mlpc)
+    lay = dashlib.layout_from(grid)
+    pts = dashlib.Points(xd, yd, zd, td, idx=idx, n=n_all, n_dev=cnt)
+    mlp = dashlib.Mlp(to_dev(params), 32, 64, 10)
+    delta = dashlib.dash_deform_mlp_fwd(lay, pts, to_dev(table), mlp)
+    rmask, _ = oracle.topk_mask(norm.cpu().numpy().astype(np.float64), 30.0)
+    ridx, rcnt = oracle.compact(rmask)
+    assert int(cnt.item()) == rcnt and 0 < rcnt <= int(np.floor(0.3 * n_all))  # fewer only on a tie at tau
+    assert np.array_equal(idx[:rcnt].cpu().numpy(), ridx)
+    ref = oracle.deform_fwd(g4, oracle.Points(x, y, z, t, idx=ridx), table.astype(np.float64), 64, 10,
+                            params.astype(np.float64))
+    assert rel_err(delta[:, :rcnt].cpu().numpy(), ref) < 1e-3
