@@ -134,6 +134,10 @@ def configure(lib):
     lib.orc_decomp_fwd.restype = i32
     lib.orc_topk_mask.argtypes = [P, i64, ctypes.c_double, P]
     lib.orc_topk_mask.restype = ctypes.c_double
+    lib.orc_linear_motion.argtypes = [P, P, P, P, i64, P, i64, P]
+    lib.orc_linear_motion.restype = None
+    lib.orc_static_loss.argtypes = [P, P, i64]
+    lib.orc_static_loss.restype = ctypes.c_double
     return lib
 
 
@@ -327,6 +331,25 @@ def decomp_fwd(g: Grid, x, y, z, table, H, params):
                               _ptr(norm)) != 0:
         raise ValueError("unsupported MLP shape")
     return dp, norm
+
+
+def linear_motion(x, y, z, t, dp):
+    """Eq. 4: p(t) = p + t dp, SoA [3][n]; t has n values or one."""
+    xs, ys, zs = (_c(v, np.float32) for v in (x, y, z))
+    ts = _c(np.atleast_1d(t), np.float32)
+    d = _c(dp, np.float64)
+    n = len(xs)
+    out = np.zeros((3, n), dtype=np.float64)
+    _load().orc_linear_motion(_ptr(xs), _ptr(ys), _ptr(zs), _ptr(ts), 0 if len(ts) == 1 and n != 1 else 1,
+                              _ptr(d), n, _ptr(out))
+    return out
+
+
+def static_loss(norm, mask) -> float:
+    """Eq. 5: mean |dp| over the static Gaussians (mask 0)."""
+    v = _c(norm, np.float64)
+    m = _c(mask, np.uint8)
+    return float(_load().orc_static_loss(_ptr(v), _ptr(m), len(v)))
 
 
 def topk_mask(values, k_percent):

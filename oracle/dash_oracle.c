@@ -563,6 +563,32 @@ int orc_decomp_fwd(const orc_grid* g, const float* x, const float* y, const floa
   return 0;
 }
 
+/* Eq. 4: linear motion p(t) = p + t * dp of each Gaussian; p the coordinates
+ * as given, t per Gaussian (t_stride 1) or one value for all (t_stride 0);
+ * out SoA [3][n]. */
+void orc_linear_motion(const float* x, const float* y, const float* z, const float* t, int64_t t_stride,
+                       const double* dp, int64_t n, double* out) {
+  for (int64_t i = 0; i < n; ++i) {
+    const double p[3] = {x[i], y[i], z[i]};
+    const double ti = t[i * t_stride];
+    for (int d = 0; d < 3; ++d) out[d * n + i] = p[d] + ti * dp[d * n + i];
+  }
+}
+
+/* Eq. 5: L_s = (1 / N_s) * sum of |dp| over the static Gaussians (mask 0),
+ * N_s their number; 0 when every Gaussian is dynamic. */
+double orc_static_loss(const double* norm, const uint8_t* mask, int64_t n) {
+  double sum = 0.0;
+  int64_t n_s = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (mask[i] == 0) {
+      sum += norm[i];
+      ++n_s;
+    }
+  }
+  return n_s > 0 ? sum / (double)n_s : 0.0;
+}
+
 static int orc_cmp_desc(const void* a, const void* b) {
   const double x = *(const double*)a, y = *(const double*)b;
   return x < y ? 1 : (x > y ? -1 : 0);

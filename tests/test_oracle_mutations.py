@@ -8,6 +8,7 @@ import pytest
 
 import oracle
 import test_oracle_pins as pins
+import test_oracle_pins_decomp as pins_decomp
 from paper_2507_19141_gb300 import synth
 
 MUTATIONS = [
@@ -72,11 +73,33 @@ MUTATIONS = [
      "const double scale = 2.0 * (double)lambda_r / (double)(n > 0 ? n : 1);",
      "const double scale = (double)lambda_r / (double)(n > 0 ? n : 1);",
      [("test_full_backward_finite_difference_with_smoothness", {})]),
+    ("Eq. 5 divides by all Gaussians instead of the static ones",
+     "return n_s > 0 ? sum / (double)n_s : 0.0;",
+     "return n_s > 0 ? sum / (double)n : 0.0;",
+     [("decomp:test_static_loss_special_cases", {})]),
+    ("Eq. 4 moves along dp by (1 - t)",
+     "out[d * n + i] = p[d] + ti * dp[d * n + i];",
+     "out[d * n + i] = p[d] + (1.0 - ti) * dp[d * n + i];",
+     [("decomp:test_linear_motion_speed_is_the_norm", {})]),
+    ("top-k threshold taken one rank too low",
+     "tau = s[m];",
+     "tau = s[m + 1 < n ? m + 1 : m];",
+     [("decomp:test_topk_mask_invariants", dict(n=1000, k=25.0)), ("decomp:test_topk_mask_ties_are_static", {})]),
+    ("G_3D dense stride N instead of N + 1",
+     "int64_t R = N + 1;",
+     "int64_t R = N;",
+     [("decomp:test_cell3_dense_bijection_and_partition_of_unity", {})]),
     ("Eq. 11 temporal perturbation applied to x",
      "const float e_t[4] = {0.f, 0.f, 0.f, eps_t};",
      "const float e_t[4] = {eps_t, 0.f, 0.f, 0.f};",
      [("test_smoothness_closed_form_on_affine_tables", {})]),
 ]
+
+
+def _pin(fname):
+    if fname.startswith("decomp:"):
+        return getattr(pins_decomp, fname[len("decomp:"):])
+    return getattr(pins, fname)
 
 
 @pytest.mark.parametrize("name,old,new,checks", MUTATIONS, ids=[m[0] for m in MUTATIONS])
@@ -90,7 +113,7 @@ def test_pins_catch_planted_mistake(tmp_path, monkeypatch, name, old, new, check
     caught = []
     for fname, kwargs in checks:
         try:
-            getattr(pins, fname)(**kwargs)
+            _pin(fname)(**kwargs)
         except (AssertionError, ValueError):
             caught.append(fname)
     assert caught, f"no pin caught: {name}"
@@ -104,4 +127,4 @@ def test_unmutated_copy_passes_the_same_checks(tmp_path, monkeypatch):
     monkeypatch.setattr(oracle, "_lib", lib)
     for _, _, _, checks in MUTATIONS:
         for fname, kwargs in checks:
-            getattr(pins, fname)(**kwargs)
+            _pin(fname)(**kwargs)

@@ -97,3 +97,41 @@ def test_topk_mask_ties_are_static():
     v = np.array([3.0, 2.0, 2.0, 2.0, 1.0, 0.5])
     mask, tau = oracle.topk_mask(v, 50)          # m = 3: tau = 2.0, only 3.0 is above it
     assert tau == 2.0 and list(mask) == [1, 0, 0, 0, 0, 0]
+
+
+def test_linear_motion_speed_is_the_norm():
+    """Eq. 4 makes |dp| the Gaussian's speed: the displacement between any
+    two times, divided by their distance, is dp itself, and p(0) = p."""
+    g = oracle.layout3(4, 2, 12, 4, 32)
+    rng = np.random.default_rng(6)
+    n, H = 300, 16
+    x, y, z = rng.random((3, n)).astype(np.float32)
+    table = rng.uniform(-1, 1, size=(g.total, 2))
+    params = rng.uniform(-0.5, 0.5, H * 8 + H + 3 * H + 3)
+    dp, norm = oracle.decomp_fwd(g, x, y, z, table, H, params)
+    t1 = rng.random(n).astype(np.float32)
+    p0 = oracle.linear_motion(x, y, z, np.float32(0.0), dp)
+    assert np.array_equal(p0, np.stack([x, y, z]).astype(np.float64))
+    p1 = oracle.linear_motion(x, y, z, t1, dp)
+    p2 = oracle.linear_motion(x, y, z, np.float32(1.0), dp)
+    speed = np.linalg.norm(p2 - p0, axis=0)
+    assert np.max(np.abs(speed - norm)) < 1e-12
+    assert np.max(np.abs((p1 - p0) - t1.astype(np.float64) * dp)) < 1e-12
+    # second difference of a linear trajectory vanishes
+    pm = oracle.linear_motion(x, y, z, np.float32(0.5), dp)
+    assert np.max(np.abs(p2 - 2 * pm + p0)) < 1e-12
+
+
+def test_static_loss_special_cases():
+    rng = np.random.default_rng(7)
+    n = 1000
+    mask = (rng.random(n) < 0.5).astype(np.uint8)
+    assert abs(oracle.static_loss(np.full(n, 0.75), mask) - 0.75) < 1e-15       # constant speed
+    v = rng.random(n)
+    assert abs(oracle.static_loss(v, np.zeros(n, np.uint8)) - v.mean()) < 1e-12  # nothing dynamic
+    assert oracle.static_loss(v, np.ones(n, np.uint8)) == 0.0                   # nothing static
+    for k in (10.0, 50.0, 90.0):                                                 # static speeds lie below tau
+        m, tau = oracle.topk_mask(v, k)
+        ls = oracle.static_loss(v, m)
+        assert v[m == 0].min() <= ls <= tau
+        assert abs(ls * (m == 0).sum() + v[m == 1].sum() - v.sum()) < 1e-9
