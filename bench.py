@@ -489,16 +489,18 @@ def run_extras(torch, wl, args, stream):
     return res
 
 
-# decomposition, algorithmic bytes per Gaussian: x, y, z (12) + 16 levels x 8
-# corners x one FP16 F=2 entry (512) + dp (12) + norm (4); top-k: norm (4) + mask (1)
-DECOMP_BYTES = 12 + 16 * 8 * 4 + 12 + 4
+# decomposition, algorithmic bytes per Gaussian: x, y, z, t (16) + 16 levels x 8
+# corners x one FP16 F=2 entry (512) + dp (12) + norm (4) + p(t) (12);
+# top-k: norm (4) + mask (1)
+DECOMP_BYTES = 16 + 16 * 8 * 4 + 12 + 4 + 12
 TOPK_BYTES = 4 + 1
 
 
 def run_decomp(torch, wl, stream):
     """Decomposition producing the mask, over all Gaussians of the workload:
     G_3D (16 levels 16..2048, T = 2^19, FP16) + phi_p/phi_l norms, the top-50 %
-    threshold and mask, and the chain decomposition -> mask -> compaction."""
+    threshold, mask and Eq. 5 static loss, and the chain decomposition (with
+    Eq. 4's p(t) at each Gaussian's timestamp) -> mask -> compaction."""
     import numpy as np
     from paper_2507_19141_gb300 import dash, synth
     rng = np.random.default_rng(11)
@@ -513,16 +515,18 @@ def run_decomp(torch, wl, stream):
     norm = torch.empty(n, dtype=torch.float32, device="cuda")
     mask = torch.empty(n, dtype=torch.uint8, device="cuda")
     tau = torch.empty(1, dtype=torch.float32, device="cuda")
+    ls = torch.empty(1, dtype=torch.float32, device="cuda")
+    pt = torch.empty((3, n), dtype=torch.float32, device="cuda")
     ws = torch.empty(dash.dash_topk_workspace_size(), dtype=torch.uint8, device="cuda")
     idx = torch.empty(n, dtype=torch.int32, device="cuda")
     cnt = torch.empty(1, dtype=torch.int64, device="cuda")
     cws = torch.empty(dash.dash_compact_workspace_size(n), dtype=torch.uint8, device="cuda")
 
     def dec_fwd():
-        dash.dash_decomp_fwd(lay3, wl.x, wl.y, wl.z, table3, dec, dp_out=dp, norm_out=norm)
+        dash.dash_decomp_fwd(lay3, wl.x, wl.y, wl.z, table3, dec, dp_out=dp, norm_out=norm, t=wl.t, pt_out=pt)
 
     def topk():
-        dash.dash_topk_mask(norm, 50.0, mask_out=mask, tau_out=tau, ws=ws)
+        dash.dash_topk_mask(norm, 50.0, mask_out=mask, tau_out=tau, ws=ws, static_loss_out=ls)
 
     def chain():
         dec_fwd()

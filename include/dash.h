@@ -251,10 +251,14 @@ int dash_hash3d_layout(const dash_hash4d_cfg* cfg, dash_layout* out);
  * x, y, z [n] FP32 in [0,1] (clamped); table of the 3-D layout (F32/F16);
  * mlp: d_in = L*F, d_hidden = 64, d_out = 3 with params packed W1 [64][D],
  * b1 [64], W2 [3][64], b2 [3] (ReLU after the first layer).  dp_out SoA
- * [3][n] (may be NULL), norm_out [n]. */
+ * [3][n] (may be NULL), norm_out [n].  With pt_out (SoA [3][n], may be NULL)
+ * also the Eq. 4 linear motion p(t) = p + t dp, p the unclamped x, y, z and
+ * t [n] (t_stride 1) or one value for all (t_stride 0).  n <= 2^31 - 1.
+ * One launch on `stream`; all pointers are device memory. */
 int dash_decomp_fwd(const dash_layout* layout3, const float* x, const float* y, const float* z,
                     int64_t n, const void* table, int table_dtype, const dash_mlp* mlp,
-                    float* dp_out, float* norm_out, void* stream);
+                    float* dp_out, float* norm_out, const float* t, int64_t t_stride,
+                    float* pt_out, void* stream);
 
 /* Bytes of device workspace dash_topk_mask needs (a few hundred). */
 size_t dash_topk_workspace_size(void);
@@ -264,11 +268,14 @@ size_t dash_topk_workspace_size(void);
  * values' bit patterns (values are norms: zeros of either sign, NaN and
  * negatives all count as +0); mask_out[i] = values[i] > tau, so ties at tau
  * are static; m = 0 marks none, m >= n marks all (tau = -1).  tau_out
- * (device float) may be NULL.  n <= 2^31 - 1 (DASH_ERR_UNSUPPORTED above);
- * k_percent outside [0, 100] or a workspace below dash_topk_workspace_size()
- * is an error.  Launches 10 small kernels on `stream`; ws is reused. */
+ * (device float) may be NULL.  static_loss_out (device float, may be NULL)
+ * receives Eq. 5's L_s = mean of the static values (0 if none is static),
+ * summed in FP64.  n <= 2^31 - 1 (DASH_ERR_UNSUPPORTED above); k_percent
+ * outside [0, 100] or a workspace below dash_topk_workspace_size() is an
+ * error.  Launches at most 11 small kernels on `stream`; ws is reused. */
 int dash_topk_mask(const float* values, int64_t n, double k_percent, uint8_t* mask_out,
-                   float* tau_out, void* ws, size_t ws_bytes, void* stream);
+                   float* tau_out, float* static_loss_out, void* ws, size_t ws_bytes,
+                   void* stream);
 
 /* ---------------- a12: many scenes x timestamps, one graph launch ------ */
 

@@ -217,15 +217,16 @@ __device__ __forceinline__ float2 entry_in16<float>(const uint4& v, uint32_t k) 
                   : make_float2(__uint_as_float(v.x), __uint_as_float(v.y));
 }
 
-// acc[0..2) = sum_b w[b] * table[base + idx[b]] for F = 2 (same summation
+// acc[0..2) = sum_b w[b] * table[base + idx[b]] for F = 2 over NC corners
+// (16 in 4-D, 8 in 3-D) whose x-neighbours come in pairs (same summation
 // order as corner by corner).
-template <typename TT>
-__device__ __forceinline__ void gather2_pairs(const TT* __restrict__ base, const uint32_t idx[16], const float w[16],
+template <typename TT, int NC = 16>
+__device__ __forceinline__ void gather2_pairs(const TT* __restrict__ base, const uint32_t* idx, const float* w,
                                               float acc[2]) {
   constexpr uint32_t kGroup = 16u / (2u * sizeof(TT));  // entries per 16 bytes: 4 (FP16) or 2 (FP32)
   float a0 = 0.0f, a1 = 0.0f;
 #pragma unroll
-  for (int p = 0; p < 8; ++p) {
+  for (int p = 0; p < NC / 2; ++p) {
     const uint32_t i0 = idx[2 * p], i1 = idx[2 * p + 1];
     const uint32_t g = i0 & ~(kGroup - 1u);
     const uint4 v = __ldg(reinterpret_cast<const uint4*>(base + (size_t)g * 2));

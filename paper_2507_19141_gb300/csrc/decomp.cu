@@ -53,18 +53,26 @@ __global__ void __launch_bounds__(kThreads) decomp_fwd_kernel(Geom g, const floa
                                                               const float* __restrict__ zs, long long n,
                                                               const TT* __restrict__ table,
                                                               const float* __restrict__ params, int D,
-                                                              float* __restrict__ dp_out, float* __restrict__ norm_out) {
-  extern __shared__ float w_s[];  // W1 [64][D], b1 [64], W2 [3][64], b2 [3]
+                                                              float* __restrict__ dp_out, float* __restrict__ norm_out,
+                                                              const float* __restrict__ ts, long long t_stride,
+                                                              float* __restrict__ pt_out) {
+  // shared: W1 transposed [D][64] (one input column's 64 weights contiguous),
+  // then b1 [64], W2 [3][64], b2 [3] as packed
+  extern __shared__ __align__(16) float w_s[];
   const int P = kHidden3 * D + kHidden3 + 3 * kHidden3 + 3;
-  for (int e = threadIdx.x; e < P; e += kThreads) w_s[e] = __ldg(params + e);
+  for (int e = threadIdx.x; e < P; e += kThreads) {
+    const int dst = e < kHidden3 * D ? (e % D) * kHidden3 + e / D : e;
+    w_s[dst] = __ldg(params + e);
+  }
   __syncthreads();
-  const float* W1 = w_s;
-  const float* b1 = W1 + kHidden3 * D;
+  const float* W1t = w_s;
+  const float* b1 = W1t + kHidden3 * D;
   const float* W2 = b1 + kHidden3;
   const float* b2 = W2 + 3 * kHidden3;
   const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (i >= n) return;
-  const float3 p = make_float3(clamp01(__ldcs(xs + i)), clamp01(__ldcs(ys + i)), clamp01(__ldcs(zs + i)));
+  const float3 praw = make_float3(__ldcs(xs + i), __ldcs(ys + i), __ldcs(zs + i));
+  const float3 p = make_float3(clamp01(praw.x), clamp01(praw.y), clamp01(praw.z));
   float h[kHidden3];
 #pragma unroll
   for (int j = 0; j < kHidden3; ++j) h[j] = b1[j];
@@ -74,33 +82,51 @@ __global__ void __launch_bounds__(kThreads) decomp_fwd_kernel(Geom g, const floa
     level_corners3(g, l, p, idx, w);
     const TT* base = table + g.offset[l] * F;
     float f[F];
+    if constexpr (F == 2) {
+      gather2_pairs<TT, 8>(base, idx, w, f);  // x-neighbours share a 16-byte group when aligned
+    } else {
 #pragma unroll
-    for (int k = 0; k < F; ++k) f[k] = 0.0f;
+      for (int k = 0; k < F; ++k) f[k] = 0.0f;
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      float e[F];
-      load_entry<TT, F>(base + (size_t)idx[b] * F, e);
+      for (int b = 0; b < 8; ++b) {
+        float e[F];
+        load_entry<TT, F>(base + (size_t)idx[b] * F, e);
 #pragma unroll
-      for (int k = 0; k < F; ++k) f[k] = fmaf(w[b], e[k], f[k]);
+        for (int k = 0; k < F; ++k) f[k] = fmaf(w[b], e[k], f[k]);
+      }
     }
     // phi_p: stream this level's features into the hidden pre-activations
 #pragma unroll
     for (int k = 0; k < F; ++k) {
-      const int col = l * F + k;
+      const float4* wc = reinterpret_cast<const float4*>(W1t + (l * F + k) * kHidden3);
 #pragma unroll
-      for (int j = 0; j < kHidden3; ++j) h[j] = fmaf(W1[j * D + col], f[k], h[j]);
+      for (int j4 = 0; j4 < kHidden3 / 4; ++j4) {
+        const float4 wv = wc[j4];
+        h[4 * j4 + 0] = fmaf(wv.x, f[k], h[4 * j4 + 0]);
+        h[4 * j4 + 1] = fmaf(wv.y, f[k], h[4 * j4 + 1]);
+        h[4 * j4 + 2] = fmaf(wv.z, f[k], h[4 * j4 + 2]);
+        h[4 * j4 + 3] = fmaf(wv.w, f[k], h[4 * j4 + 3]);
+      }
     }
   }
   float s = 0.0f;
+  float dp[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     float a = b2[c];
 #pragma unroll
     for (int j = 0; j < kHidden3; ++j) a = fmaf(W2[c * kHidden3 + j], fmaxf(h[j], 0.0f), a);
     if (dp_out != nullptr) __stcs(dp_out + (long long)c * n + i, a);
+    dp[c] = a;
     s = fmaf(a, a, s);
   }
   __stcs(norm_out + i, sqrtf(s));
+  if (pt_out != nullptr) {  // Eq. 4: p(t) = p + t dp, p as given
+    const float t = __ldg(ts + i * t_stride);
+    __stcs(pt_out + i, fmaf(t, dp[0], praw.x));
+    __stcs(pt_out + n + i, fmaf(t, dp[1], praw.y));
+    __stcs(pt_out + 2 * n + i, fmaf(t, dp[2], praw.z));
+  }
 }
 
 // ----------------------------------------------------------- radix select --
@@ -110,6 +136,8 @@ struct TopkState {
   unsigned int prefix;
   unsigned int prefix_mask;
   unsigned long long rank;  // ascending rank still to locate below the prefix
+  double static_sum;        // Eq. 5: sum of the static norms and their number
+  unsigned long long static_count;
 };
 
 // Positive floats order like their bit patterns; zeros of either sign, NaN and
@@ -122,6 +150,8 @@ __global__ void topk_init(TopkState* st, unsigned long long rank) {
     st->prefix = 0u;
     st->prefix_mask = 0u;
     st->rank = rank;
+    st->static_sum = 0.0;
+    st->static_count = 0ull;
   }
 }
 
@@ -161,13 +191,51 @@ __global__ void topk_select(TopkState* st, int shift) {
   for (int b = threadIdx.x; b < 256; b += 32) st->hist[b] = 0u;
 }
 
-__global__ void __launch_bounds__(kThreads) topk_apply(const float* __restrict__ v, long long n,
-                                                       const TopkState* st, int all, uint8_t* __restrict__ mask,
-                                                       float* tau_out) {
+// Writes the mask; with `sums` also accumulates Eq. 5's static sum and count
+// (a block reduction, then one FP64 atomic per block).
+__global__ void __launch_bounds__(kThreads) topk_apply(const float* __restrict__ v, long long n, TopkState* st,
+                                                       int all, uint8_t* __restrict__ mask, float* tau_out,
+                                                       int sums) {
   const unsigned int tau = st->prefix;
   const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (i == 0 && tau_out != nullptr) *tau_out = all ? -1.0f : __uint_as_float(tau);
-  if (i < n) mask[i] = all ? 1u : (norm_key(__ldg(v + i)) > tau ? 1u : 0u);
+  const unsigned int key = i < n ? norm_key(__ldg(v + i)) : 0u;
+  const bool dyn = all || key > tau;
+  if (i < n) mask[i] = dyn ? 1u : 0u;
+  if (!sums) return;
+  const bool stat = i < n && !dyn;
+  double x = stat ? (double)__uint_as_float(key) : 0.0;
+  unsigned int c = stat ? 1u : 0u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    x += __shfl_xor_sync(0xffffffffu, x, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  __shared__ double xs[kThreads / 32];
+  __shared__ unsigned int cs[kThreads / 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    xs[warp] = x;
+    cs[warp] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double bx = 0.0;
+    unsigned int bc = 0u;
+    for (int w = 0; w < kThreads / 32; ++w) {
+      bx += xs[w];
+      bc += cs[w];
+    }
+    if (bc != 0u) {
+      atomicAdd(&st->static_sum, bx);
+      atomicAdd(&st->static_count, (unsigned long long)bc);
+    }
+  }
+}
+
+__global__ void topk_static_loss(const TopkState* st, float* ls_out) {
+  const unsigned long long c = st->static_count;
+  *ls_out = c != 0ull ? (float)(st->static_sum / (double)c) : 0.0f;
 }
 
 }  // namespace
@@ -216,7 +284,7 @@ int dash_hash3d_layout(const dash_hash4d_cfg* cfg, dash_layout* out) {
 
 int dash_decomp_fwd(const dash_layout* layout, const float* x, const float* y, const float* z, int64_t n,
                     const void* table, int table_dtype, const dash_mlp* mlp, float* dp_out, float* norm_out,
-                    void* stream) {
+                    const float* t, int64_t t_stride, float* pt_out, void* stream) {
   using namespace dash;
   if (layout == nullptr || layout->dims != 3) return fail(DASH_ERR_INVALID_ARG, "needs a 3-D layout (dash_hash3d_layout)");
   dash_layout as4 = *layout;
@@ -233,12 +301,15 @@ int dash_decomp_fwd(const dash_layout* layout, const float* x, const float* y, c
   if (n == 0) return DASH_OK;
   if (x == nullptr || y == nullptr || z == nullptr || table == nullptr || norm_out == nullptr)
     return fail(DASH_ERR_INVALID_ARG, "NULL argument");
+  if (pt_out != nullptr && (t == nullptr || t_stride < 0 || t_stride > 1))
+    return fail(DASH_ERR_INVALID_ARG, "p(t) needs t with t_stride 0 or 1");
+  if (n > 0x7FFFFFFFll) return fail(DASH_ERR_UNSUPPORTED, "n=%lld above 2^31 - 1", (long long)n);
   const size_t smem = sizeof(float) * (size_t)(kHidden3 * D + kHidden3 + 3 * kHidden3 + 3);
   const unsigned grid = (unsigned)((n + kThreads - 1) / kThreads);
   cudaStream_t st = as_stream(stream);
 #define DASH_DECOMP_LAUNCH(TT, FF)                                                                             \
   decomp_fwd_kernel<TT, FF><<<grid, kThreads, smem, st>>>(g, x, y, z, n, static_cast<const TT*>(table),        \
-                                                          mlp->params, D, dp_out, norm_out)
+                                                          mlp->params, D, dp_out, norm_out, t, t_stride, pt_out)
   if (table_dtype == DASH_F16) {
     switch (g.F) {
       case 1: DASH_DECOMP_LAUNCH(__half, 1); break;
@@ -262,8 +333,8 @@ int dash_decomp_fwd(const dash_layout* layout, const float* x, const float* y, c
 
 size_t dash_topk_workspace_size(void) { return (sizeof(dash::TopkState) + 255) / 256 * 256; }
 
-int dash_topk_mask(const float* values, int64_t n, double k_percent, uint8_t* mask_out, float* tau_out, void* ws,
-                   size_t ws_bytes, void* stream) {
+int dash_topk_mask(const float* values, int64_t n, double k_percent, uint8_t* mask_out, float* tau_out,
+                   float* static_loss_out, void* ws, size_t ws_bytes, void* stream) {
   using namespace dash;
   if (n < 0 || !(k_percent >= 0.0) || k_percent > 100.0)
     return fail(DASH_ERR_INVALID_ARG, "n < 0 or k_percent outside [0, 100]");
@@ -271,8 +342,12 @@ int dash_topk_mask(const float* values, int64_t n, double k_percent, uint8_t* ma
   if (n > 0 && (values == nullptr || mask_out == nullptr)) return fail(DASH_ERR_INVALID_ARG, "values/mask_out is NULL");
   if (ws == nullptr || ws_bytes < dash_topk_workspace_size())
     return fail(DASH_ERR_WORKSPACE, "workspace of %zu bytes, %zu needed", ws_bytes, dash_topk_workspace_size());
-  if (n == 0) return DASH_OK;
   cudaStream_t st = as_stream(stream);
+  if (n == 0) {
+    if (static_loss_out != nullptr && cudaMemsetAsync(static_loss_out, 0, sizeof(float), st) != cudaSuccess)
+      return fail(DASH_ERR_CUDA, "cudaMemsetAsync failed");
+    return DASH_OK;
+  }
   TopkState* state = static_cast<TopkState*>(ws);
   long long m = (long long)floor(k_percent * (double)n / 100.0);
   m = m < 0 ? 0 : m;
@@ -291,8 +366,12 @@ int dash_topk_mask(const float* values, int64_t n, double k_percent, uint8_t* ma
       if (int s = launch_status("topk_select")) return s;
     }
   }
-  topk_apply<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, st>>>(values, n, state, all, mask_out, tau_out);
-  return launch_status("topk_apply");
+  topk_apply<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, st>>>(values, n, state, all, mask_out, tau_out,
+                                                                             static_loss_out != nullptr);
+  if (int s = launch_status("topk_apply")) return s;
+  if (static_loss_out == nullptr) return DASH_OK;
+  topk_static_loss<<<1, 1, 0, st>>>(state, static_loss_out);
+  return launch_status("topk_static_loss");
 }
 
 }  // extern "C"

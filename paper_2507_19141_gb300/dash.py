@@ -121,9 +121,9 @@ _SIGS = {
     "dash_batch_autotune": ([_P, ctypes.c_char_p, _P], _I),
     "dash_batch_plan_destroy": ([_P], _I),
     "dash_hash3d_layout": ([_P, _P], _I),
-    "dash_decomp_fwd": ([_P, _P, _P, _P, _I64, _P, _I, _P, _P, _P, _P], _I),
+    "dash_decomp_fwd": ([_P, _P, _P, _P, _I64, _P, _I, _P, _P, _P, _P, _I64, _P, _P], _I),
     "dash_topk_workspace_size": ([], _SZ),
-    "dash_topk_mask": ([_P, _I64, ctypes.c_double, _P, _P, _P, _SZ, _P], _I),
+    "dash_topk_mask": ([_P, _I64, ctypes.c_double, _P, _P, _P, _P, _SZ, _P], _I),
     "dash_plain_hash4d_fwd": ([_P, _P, _P, _P, _P], _I),
     "dash_plain_hash4d_bwd": ([_P, _P, _P, _P, _P], _I),
     "dash_plain_mlp_fwd": ([_P, _P, _I64, _P, _P, _P], _I),
@@ -381,31 +381,41 @@ def dash_hash3d_layout(L, F, log2_T, nmin, nmax, primes=PRIMES) -> dash_layout:
     return out
 
 
-def dash_decomp_fwd(layout3: dash_layout, x, y, z, table, mlp: "Mlp", dp_out=None, norm_out=None, want_dp=True):
-    """(dp SoA [3][n] or None, norm [n]) of Eqs. 3-4's positional deformation."""
+def dash_decomp_fwd(layout3: dash_layout, x, y, z, table, mlp: "Mlp", dp_out=None, norm_out=None, want_dp=True,
+                    t=None, pt_out=None):
+    """(dp SoA [3][n] or None, norm [n]) of Eq. 3's positional deformation;
+    with t (CUDA float32 [n] or [1]) returns (dp, norm, p(t) SoA [3][n]) of Eq. 4."""
     n = x.numel()
     if want_dp and dp_out is None:
         dp_out = torch.empty((3, n), dtype=torch.float32, device=x.device)
     norm_out = torch.empty(n, dtype=torch.float32, device=x.device) if norm_out is None else norm_out
+    t_stride = 0
+    if t is not None:
+        assert t.is_cuda and t.dtype == torch.float32 and t.numel() in (1, n)
+        t_stride = 0 if (t.numel() == 1 and n != 1) else 1
+        pt_out = torch.empty((3, n), dtype=torch.float32, device=x.device) if pt_out is None else pt_out
     _check(_lib.dash_decomp_fwd(ctypes.byref(layout3), _ptr(x), _ptr(y), _ptr(z), n, _ptr(table),
                                 _DTYPE_CODE[table.dtype], ctypes.byref(mlp.c), _ptr(dp_out if want_dp else None),
-                                _ptr(norm_out), _stream()), "dash_decomp_fwd")
-    return (dp_out if want_dp else None), norm_out
+                                _ptr(norm_out), _ptr(t), t_stride, _ptr(pt_out if t is not None else None),
+                                _stream()), "dash_decomp_fwd")
+    dp = dp_out if want_dp else None
+    return (dp, norm_out) if t is None else (dp, norm_out, pt_out)
 
 
 def dash_topk_workspace_size() -> int:
     return int(_lib.dash_topk_workspace_size())
 
 
-def dash_topk_mask(values: torch.Tensor, k_percent: float, mask_out=None, tau_out=None, ws=None):
-    """(mask uint8 [n], tau float32 [1]): dynamic iff value > tau, tau the top-k % threshold."""
+def dash_topk_mask(values: torch.Tensor, k_percent: float, mask_out=None, tau_out=None, ws=None, static_loss_out=None):
+    """(mask uint8 [n], tau float32 [1]): dynamic iff value > tau, tau the top-k % threshold.
+    With static_loss_out (CUDA float32 [1]) also Eq. 5's L_s there."""
     n = values.numel()
     mask_out = torch.empty(n, dtype=torch.uint8, device=values.device) if mask_out is None else mask_out
     tau_out = torch.empty(1, dtype=torch.float32, device=values.device) if tau_out is None else tau_out
     if ws is None:
         ws = torch.empty(dash_topk_workspace_size(), dtype=torch.uint8, device=values.device)
-    _check(_lib.dash_topk_mask(_ptr(values), n, float(k_percent), _ptr(mask_out), _ptr(tau_out), _ptr(ws), ws.numel(),
-                               _stream()), "dash_topk_mask")
+    _check(_lib.dash_topk_mask(_ptr(values), n, float(k_percent), _ptr(mask_out), _ptr(tau_out), _ptr(static_loss_out),
+                               _ptr(ws), ws.numel(), _stream()), "dash_topk_mask")
     return mask_out, tau_out
 
 

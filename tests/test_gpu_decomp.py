@@ -48,6 +48,43 @@ def test_topk_mask_bit_exact(dashlib, n, k):
     assert float(tau.item()) == np.float32(rtau)
 
 
+@pytest.mark.parametrize("per_gaussian_t", [True, False])
+def test_linear_motion_matches_oracle(dashlib, per_gaussian_t):
+    """Eq. 4 fused into the decomposition kernel: p(t) = p + t dp."""
+    rng = np.random.default_rng(74)
+    n = 5_000
+    g, (x, y, z), table, params = _decomp_inputs(rng, n)
+    x[:7] = [-0.25, 1.5, 0.0, 1.0, 0.5, 2.0, -1.0]        # p(t) uses p as given, the encoder the clamped p
+    t = rng.random(n).astype(np.float32) if per_gaussian_t else np.array([0.37], np.float32)
+    lay = dashlib.dash_hash3d_layout(**G3)
+    mlp = dashlib.Mlp(to_dev(params), 32, 64, 3)
+    dp, norm, pt = dashlib.dash_decomp_fwd(lay, to_dev(x), to_dev(y), to_dev(z), to_dev(table), mlp, t=to_dev(t))
+    rdp, _ = oracle.decomp_fwd(g, x, y, z, table.astype(np.float64), 64, params.astype(np.float64))
+    ref = oracle.linear_motion(x, y, z, t, rdp)
+    p = np.stack([x, y, z]).astype(np.float64)
+    assert rel_err(pt.cpu().numpy() - p, ref - p) < 1e-5
+    # and exactly one rounding of t * dp + p on the GPU's own dp
+    own = oracle.linear_motion(x, y, z, t, dp.cpu().numpy().astype(np.float64)).astype(np.float32)
+    assert np.max(np.abs(pt.cpu().numpy().view(np.int32).astype(np.int64) - own.view(np.int32))) <= 1
+
+
+@pytest.mark.parametrize("k", [0.0, 20.0, 50.0, 100.0])
+def test_static_loss_matches_oracle(dashlib, k):
+    """Eq. 5 accumulated while the mask is written (FP64 sums)."""
+    rng = np.random.default_rng(75)
+    v = (rng.random(300_001) * 2).astype(np.float32)
+    ls = torch.empty(1, device="cuda")
+    mask, _ = dashlib.dash_topk_mask(to_dev(v), k, static_loss_out=ls)
+    m = mask.cpu().numpy()
+    ref = oracle.static_loss(v.astype(np.float64), m)
+    assert np.array_equal(m, oracle.topk_mask(v.astype(np.float64), k)[0])
+    assert abs(float(ls.item()) - ref) <= 1e-6 * max(ref, 1e-30)
+    e = torch.empty(0, device="cuda")
+    ls.fill_(5.0)
+    dashlib.dash_topk_mask(e, k, static_loss_out=ls)
+    assert float(ls.item()) == 0.0
+
+
 def test_topk_mask_with_ties(dashlib):
     rng = np.random.default_rng(72)
     v = rng.integers(0, 50, size=100_000).astype(np.float32) / 7  # many equal values
