@@ -134,6 +134,8 @@ def configure(lib):
     lib.orc_decomp_fwd.restype = i32
     lib.orc_topk_mask.argtypes = [P, i64, ctypes.c_double, P]
     lib.orc_topk_mask.restype = ctypes.c_double
+    lib.orc_encode_coord_grad.argtypes = [G, P, P, P, P, i64, P, i64, P, P, P]
+    lib.orc_encode_coord_grad.restype = None
     lib.orc_linear_motion.argtypes = [P, P, P, P, i64, P, i64, P]
     lib.orc_linear_motion.restype = None
     lib.orc_static_loss.argtypes = [P, P, i64]
@@ -222,6 +224,15 @@ def encode_bwd(g: Grid, pts: Points, dfeat, table_grad=None) -> np.ndarray:
     assert tg.dtype == np.float64 and tg.flags.c_contiguous
     _load().orc_encode_bwd(ctypes.byref(g), *pts.args(), _ptr(d), _ptr(tg))
     return tg
+
+
+def encode_coord_grad(g: Grid, pts: Points, table, dfeat) -> np.ndarray:
+    """d(sum dfeat . G_4D(p)) / d(x, y, z, t) per compact point, SoA [4][n]."""
+    tab = _c(table, np.float64)
+    d = _c(dfeat, np.float64)
+    out = np.zeros((4, pts.n), dtype=np.float64)
+    _load().orc_encode_coord_grad(ctypes.byref(g), *pts.args(), _ptr(tab), _ptr(d), _ptr(out))
+    return out
 
 
 def mlp_param_count(D, H, O) -> int:

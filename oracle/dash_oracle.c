@@ -221,6 +221,59 @@ void orc_encode_bwd(const orc_grid* g, const float* x, const float* y, const flo
   }
 }
 
+/* Gradient of sum_i dfeat_i . G_4D(p_i) w.r.t. the coordinates (x, y, z, t)
+ * of each compact point, through the quadrilinear weights of Eq. 9.  Within
+ * a hypervoxel the encoding is multilinear in the continuous position
+ * x * N_l, whose derivative is N_l (N_s for x, y, z; N_t for t); the
+ * hypervoxel is the one orc_cell selects (lower corner min(floor, N - 1)), so
+ * at a vertex the derivative is taken from the cell above it, at x = 1 from
+ * the last cell.  The clamp to [0,1] passes the derivative for coordinates
+ * in [0,1] and blocks it outside (and for NaN).  dcoord: SoA [4][n]; with a
+ * broadcast t (t_stride 0) row 3 holds each point's share. */
+void orc_encode_coord_grad(const orc_grid* g, const float* x, const float* y, const float* z,
+                           const float* t, int64_t t_stride, const int32_t* pidx, int64_t n,
+                           const double* table, const double* dfeat, double* dcoord) {
+  const int F = g->F, LF = g->L * g->F;
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t j = pidx ? (int64_t)pidx[i] : i;
+    const float raw[4] = {x[j], y[j], z[j], t_stride ? t[j * t_stride] : t[0]};
+    float p[4];
+    orc_point(x, y, z, t, t_stride, pidx, i, p);
+    double grad[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int l = 0; l < g->L; ++l) {
+      const int64_t res[4] = {g->res_s[l], g->res_s[l], g->res_s[l], g->res_t[l]};
+      double frac[4];
+      for (int d = 0; d < 4; ++d) {
+        double pos = (double)(float)((double)p[d] * (double)res[d]);
+        int64_t c = (int64_t)floor(pos);
+        if (c > res[d] - 1) c = res[d] - 1;
+        frac[d] = pos - (double)c;
+      }
+      uint32_t idx[16];
+      double w[16];
+      orc_cell(g, l, p, idx, w);
+      for (int b = 0; b < 16; ++b) {
+        /* s_b = dfeat . (corner b's feature vector) */
+        double s_b = 0.0;
+        for (int f = 0; f < F; ++f) s_b += dfeat[i * LF + l * F + f] * table[(g->offset[l] + idx[b]) * F + f];
+        for (int d = 0; d < 4; ++d) {
+          /* d w_b / d pos_d: the factor of axis d becomes +1 (upper) or -1 */
+          double dw = ((b >> d) & 1) ? 1.0 : -1.0;
+          for (int e = 0; e < 4; ++e) {
+            if (e == d) continue;
+            dw *= ((b >> e) & 1) ? frac[e] : (1.0 - frac[e]);
+          }
+          grad[d] += s_b * dw * (double)res[d];
+        }
+      }
+    }
+    for (int d = 0; d < 4; ++d) {
+      const int inside = raw[d] >= 0.0f && raw[d] <= 1.0f;
+      dcoord[d * n + i] = inside ? grad[d] : 0.0;
+    }
+  }
+}
+
 /* ------------------------------------------------------ decoder MLP ------ */
 /* phi_d followed by the heads phi_x, phi_r, phi_s (Eq. 9, Sec. 4.2):
  *   z1 = W1 f + b1, h1 = relu(z1); z2 = W2 h1 + b2, h2 = relu(z2);

@@ -8,6 +8,7 @@ import pytest
 
 import oracle
 import test_oracle_pins as pins
+import test_oracle_pins_coord as pins_coord
 import test_oracle_pins_decomp as pins_decomp
 from paper_2507_19141_gb300 import synth
 
@@ -89,6 +90,26 @@ MUTATIONS = [
      "int64_t R = N + 1;",
      "int64_t R = N;",
      [("decomp:test_cell3_dense_bijection_and_partition_of_unity", {})]),
+    ("coordinate gradient: weight derivative with the wrong sign",
+     "double dw = ((b >> d) & 1) ? 1.0 : -1.0;",
+     "double dw = ((b >> d) & 1) ? -1.0 : 1.0;",
+     [("coord:test_affine_tables_give_the_closed_form", {})]),
+    ("coordinate gradient: chain factor N_l dropped",
+     "grad[d] += s_b * dw * (double)res[d];",
+     "grad[d] += s_b * dw;",
+     [("coord:test_affine_tables_give_the_closed_form", {})]),
+    ("coordinate gradient: t scaled by the spatial resolution",
+     "const int64_t res[4] = {g->res_s[l], g->res_s[l], g->res_s[l], g->res_t[l]};",
+     "const int64_t res[4] = {g->res_s[l], g->res_s[l], g->res_s[l], g->res_s[l]};",
+     [("coord:test_central_differences_are_exact_on_dyadic_inputs", dict(broadcast_t=False))]),
+    ("coordinate gradient: own axis weight kept in the product",
+     "if (e == d) continue;",
+     "if (e == d) dw *= 1.0;",
+     [("coord:test_affine_tables_give_the_closed_form", {})]),
+    ("coordinate gradient: clamp does not block",
+     "dcoord[d * n + i] = inside ? grad[d] : 0.0;",
+     "dcoord[d * n + i] = grad[d];",
+     [("coord:test_clamp_blocks_the_gradient_outside_the_unit_interval", {})]),
     ("Eq. 11 temporal perturbation applied to x",
      "const float e_t[4] = {0.f, 0.f, 0.f, eps_t};",
      "const float e_t[4] = {eps_t, 0.f, 0.f, 0.f};",
@@ -99,6 +120,8 @@ MUTATIONS = [
 def _pin(fname):
     if fname.startswith("decomp:"):
         return getattr(pins_decomp, fname[len("decomp:"):])
+    if fname.startswith("coord:"):
+        return getattr(pins_coord, fname[len("coord:"):])
     return getattr(pins, fname)
 
 
