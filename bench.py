@@ -429,6 +429,16 @@ def run_extras(torch, wl, args, stream):
     wl.backward(smooth)
     res["bwd_smooth_ms"] = time_steps(torch, lambda: wl.backward(smooth), reps, stream)
     res["fwd_bwd_smooth_gaussians_per_s"] = n / ((res["fwd_ms"] + res["bwd_smooth_ms"]) / 1e3)
+    # backward that also returns d loss / d(x, y, z, t) (gathers the corner entries as well)
+    cgrad = torch.empty((4, wl.n_all), dtype=torch.float32, device=wl.table.device)
+
+    def bwd_coord():
+        wl.dash.dash_deform_mlp_bwd(wl.layout, wl.pts, wl.table, wl.mlp, wl.ddelta, wl.table_grad, wl.mlp_grad,
+                                    fwd_state=wl.fsave, coord_grad=cgrad)
+
+    bwd_coord()
+    res["bwd_coord_grad_ms"] = time_steps(torch, bwd_coord, reps, stream)
+    del cgrad
     res["fwd_gaussians_per_s"] = n / (res["fwd_ms"] / 1e3)
     # plain FP32 GPU form (baseline to beat): FP32 tables, f_h in HBM, CUDA-core decoder, scalar atomics
     tab32 = wl.table.float()

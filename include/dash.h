@@ -204,6 +204,18 @@ int dash_hash4d_bwd(const dash_layout* layout, const dash_points* pts, const flo
 int dash_hash4d_bwd_half(const dash_layout* layout, const dash_points* pts, const float* dfeat,
                          void* table_grad, void* stream);
 
+/* Gradient of sum_i dfeat_i . G_4D(p_i) with respect to the coordinates
+ * (x, y, z, t) of each compact point (Eq. 9 differentiated through its
+ * quadrilinear weights; for canonical positions optimised through the
+ * field).  d(x * N_l)/dx = N_l; at a vertex the derivative of the hypervoxel
+ * above it is taken, at 1 that of the last one; the clamp passes the
+ * derivative on [0,1] and gives 0 outside and for NaN.  dfeat [n][L*F] FP32
+ * as dash_hash4d_bwd; dcoord SoA [4][pts->n] FP32 (rows x, y, z, t; with a
+ * broadcast t, row 3 holds each point's share; rows past the device count
+ * are not written).  table F32 or F16, 16-byte aligned.  One launch. */
+int dash_hash4d_coord_grad(const dash_layout* layout, const dash_points* pts, const void* table,
+                           int table_dtype, const float* dfeat, float* dcoord, void* stream);
+
 /* ------------------------- a2-a8: fused deformation forward (Eqs. 8-10) -- */
 
 /* Bytes of forward state per Gaussian that dash_deform_mlp_fwd keeps for
@@ -233,11 +245,16 @@ int dash_deform_mlp_fwd(const dash_layout* layout, const dash_points* pts,
  * accumulates mlp_grad (FP32, packed like params) and scatters dL/df_h into
  * table_grad (FP32 [offset[L]][F], 16-byte aligned) with vector atomics.
  * With smooth != NULL and lambda_r != 0 also adds the Eq. 11 term,
- * re-encoding p, p + e_s and p + e_t in the kernel.  Shapes as the forward. */
+ * re-encoding p, p + e_s and p + e_t in the kernel.  Shapes as the forward.
+ * coord_grad (may be NULL): SoA [4][pts->n] FP32 receives d loss / d(x, y,
+ * z, t) of each compact point as dash_hash4d_coord_grad defines it (the
+ * scatter step also gathers the corner entries); not available together with
+ * the Eq. 11 term (DASH_ERR_UNSUPPORTED). */
 int dash_deform_mlp_bwd(const dash_layout* layout, const dash_points* pts,
                         const void* table, int table_dtype, const dash_mlp* mlp,
                         const float* ddelta, const void* fwd_state, float* table_grad,
-                        float* mlp_grad, const dash_smooth* smooth, void* stream);
+                        float* mlp_grad, const dash_smooth* smooth, float* coord_grad,
+                        void* stream);
 
 /* ------------- decomposition producing the mask (Sec. 4.1, Eqs. 3-4) ---- */
 

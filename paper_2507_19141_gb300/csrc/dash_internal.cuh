@@ -248,6 +248,87 @@ __device__ __forceinline__ void gather2_pairs(const TT* __restrict__ base, const
   acc[1] = a1;
 }
 
+// ------------------------------------------- input-coordinate gradient ----
+// 1 where the raw coordinate lies in [0,1] (the clamp passes the derivative),
+// 0 outside and for NaN; one entry per axis x, y, z, t of compact point i.
+__device__ __forceinline__ float4 coord_inside(const Pts& p, long long i) {
+  const long long j = point_row(p, i);
+  const float v[4] = {__ldg(p.x + j), __ldg(p.y + j), __ldg(p.z + j),
+                      p.t_stride != 0 ? __ldg(p.t + j * p.t_stride) : __ldg(p.t)};
+  float m[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) m[a] = (v[a] >= 0.0f && v[a] <= 1.0f) ? 1.0f : 0.0f;
+  return make_float4(m[0], m[1], m[2], m[3]);
+}
+
+// acc += d(sum_f d[f] * f_l[f]) / d(x, y, z, t) at the clamped point p for
+// level l, whose corner indices idx come from level_corners.  With s_b the
+// dot product of d and corner b's entry, the derivative of the quadrilinear
+// interpolation along axis a is N_a times the sum over the corner pairs that
+// differ only in a of (s_upper - s_lower), each weighted by the other three
+// axes' weights; the hypervoxel is the one level_corners selected.
+template <typename TT, int F>
+__device__ __forceinline__ void level_coord_grad(const Geom& g, int l, float4 p, const TT* __restrict__ base,
+                                                 const uint32_t idx[16], const float d[F], float4& acc) {
+  float s[16];
+  if constexpr (F == 2) {
+    constexpr uint32_t kGroup = 16u / (2u * sizeof(TT));
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const uint32_t i0 = idx[2 * q], i1 = idx[2 * q + 1];
+      const uint32_t grp = i0 & ~(kGroup - 1u);
+      const uint4 v = __ldg(reinterpret_cast<const uint4*>(base + (size_t)grp * 2));
+      const float2 e0 = entry_in16<TT>(v, i0 & (kGroup - 1u));
+      float2 e1;
+      if ((i1 & ~(kGroup - 1u)) == grp) {
+        e1 = entry_in16<TT>(v, i1 & (kGroup - 1u));
+      } else {
+        float t[2];
+        load_entry<TT, 2>(base + (size_t)i1 * 2, t);
+        e1 = make_float2(t[0], t[1]);
+      }
+      s[2 * q] = fmaf(d[1], e0.y, d[0] * e0.x);
+      s[2 * q + 1] = fmaf(d[1], e1.y, d[0] * e1.x);
+    }
+  } else {
+#pragma unroll
+    for (int b = 0; b < 16; ++b) {
+      float e[F];
+      load_entry<TT, F>(base + (size_t)idx[b] * F, e);
+      float v = 0.0f;
+#pragma unroll
+      for (int f = 0; f < F; ++f) v = fmaf(d[f], e[f], v);
+      s[b] = v;
+    }
+  }
+  const int ns = g.res_s[l], nt = g.res_t[l];
+  int i0;
+  float fr[4];
+  axis_cell(p.x, ns, i0, fr[0]);
+  axis_cell(p.y, ns, i0, fr[1]);
+  axis_cell(p.z, ns, i0, fr[2]);
+  axis_cell(p.w, nt, i0, fr[3]);
+  float gr[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    float v = 0.0f;
+#pragma unroll
+    for (int b = 0; b < 16; ++b) {
+      if ((b >> a) & 1) continue;  // b is the lower corner of its pair along a
+      float w = 1.0f;
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (e != a) w *= ((b >> e) & 1) ? fr[e] : 1.0f - fr[e];
+      v = fmaf(s[b | (1 << a)] - s[b], w, v);
+    }
+    gr[a] = v;
+  }
+  acc.x = fmaf(gr[0], (float)ns, acc.x);
+  acc.y = fmaf(gr[1], (float)ns, acc.y);
+  acc.z = fmaf(gr[2], (float)ns, acc.z);
+  acc.w = fmaf(gr[3], (float)nt, acc.w);
+}
+
 // grad[base + idx[b]] += w[b] * d for F = 2 FP32 gradients: a 16-byte
 // reduction when a pair's two entries form one aligned 16-byte group.
 __device__ __forceinline__ void scatter2_pairs(float* __restrict__ base, const uint32_t idx[16], const float w[16],

@@ -51,6 +51,7 @@ struct BwdArgs {
   float eps_s[3];
   float eps_t;
   float* loss_out;
+  float* coord_grad;  // optional SoA [4][n_cap]: d loss / d(x, y, z, t)
   unsigned int* flags;
   uint32_t off_w2, off_w3, off_f, off_h1, off_x, off_g3, off_ring, off_bar;
 };
@@ -122,6 +123,16 @@ __device__ __forceinline__ void gather_level(const TT* __restrict__ table, long 
 #pragma unroll
     for (int f = 0; f < F; ++f) acc[f] = fmaf(w[b], e[f], acc[f]);
   }
+}
+
+// Writes compact point `row`'s coordinate gradient (zero on axes the clamp blocks).
+__device__ __forceinline__ void store_coord_grad(const BwdArgs& a, long long row, float4 cg) {
+  const float4 m = coord_inside(a.pts, row);
+  float* o = a.coord_grad;
+  __stcs(o + row, cg.x * m.x);
+  __stcs(o + a.n_cap + row, cg.y * m.y);
+  __stcs(o + 2 * a.n_cap + row, cg.z * m.z);
+  __stcs(o + 3 * a.n_cap + row, cg.w * m.w);
 }
 
 __device__ __forceinline__ float4 perturb(float4 p, float ex, float ey, float ez, float et) {
@@ -416,6 +427,7 @@ __global__ void __launch_bounds__(kRows, 1) deform_bwd_kernel(const __grid_const
     }
     tc::fence_before_sync();
     if (valid) {
+      float4 cg = make_float4(0.f, 0.f, 0.f, 0.f);
       for (int l = 0; l < a.g.L; ++l) {
         uint32_t idx[16];
         float w[16];
@@ -424,7 +436,9 @@ __global__ void __launch_bounds__(kRows, 1) deform_bwd_kernel(const __grid_const
 #pragma unroll
         for (int f = 0; f < F; ++f) d[f] = df[l * F + f] + (smooth ? dreg[l * F + f] : 0.0f);
         scatter_level<F>(a.table_grad, a.g.offset[l], idx, w, d);
+        if (a.coord_grad != nullptr) level_coord_grad<TT, F>(a.g, l, p, table + a.g.offset[l] * F, idx, d, cg);
       }
+      if (a.coord_grad != nullptr) store_coord_grad(a, row, cg);
     }
   }
 
@@ -779,6 +793,7 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_bwd_ws_kernel(const
       for (int k = 0; k < a.D; ++k) df[k] = stage[k * kRows + r];
       tc::mbar_arrive(tc::smem_addr(&empty[s]));
       if (row >= n) continue;
+      float4 cg = make_float4(0.f, 0.f, 0.f, 0.f);
       for (int l = 0; l < a.g.L; ++l) {
         uint32_t idx[16];
         float w[16];
@@ -786,6 +801,7 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_bwd_ws_kernel(const
         float d[F];
 #pragma unroll
         for (int f = 0; f < F; ++f) d[f] = df[l * F + f];
+        if (a.coord_grad != nullptr) level_coord_grad<TT, F>(a.g, l, p, table + a.g.offset[l] * F, idx, d, cg);
         if (smooth) {
           float fp[F];
           gather_level<TT, F>(table, a.g.offset[l], idx, w, fp);
@@ -810,6 +826,7 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_bwd_ws_kernel(const
         }
         scatter_level<F>(a.table_grad, a.g.offset[l], idx, w, d);
       }
+      if (a.coord_grad != nullptr) store_coord_grad(a, row, cg);
     }
   }
   if (smooth && a.loss_out != nullptr) {
@@ -934,7 +951,8 @@ unsigned int* bwd_flags_ptr() {
 
 extern "C" int dash_deform_mlp_bwd(const dash_layout* layout, const dash_points* pts, const void* table,
                                    int table_dtype, const dash_mlp* mlp, const float* ddelta, const void* fwd_state,
-                                   float* table_grad, float* mlp_grad, const dash_smooth* smooth, void* stream) {
+                                   float* table_grad, float* mlp_grad, const dash_smooth* smooth,
+                                   float* coord_grad, void* stream) {
   using namespace dash;
   using namespace dash::fused;
   BwdArgs a;
@@ -967,6 +985,9 @@ extern "C" int dash_deform_mlp_bwd(const dash_layout* layout, const dash_points*
     a.eps_t = smooth->eps_t;
     a.loss_out = smooth->loss_out;
   }
+  if (coord_grad != nullptr && a.lambda_r != 0.0f)
+    return fail(DASH_ERR_UNSUPPORTED, "coordinate gradients with the Eq. 11 term on are not supported");
+  a.coord_grad = coord_grad;
   a.flags = bwd_flags_ptr();
   if (a.flags == nullptr) return fail(DASH_ERR_CUDA, "cannot resolve the device flag word");
   cudaStream_t st = as_stream(stream);

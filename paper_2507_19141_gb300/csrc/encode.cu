@@ -80,6 +80,35 @@ __global__ void __launch_bounds__(kThreads) encode_bwd_kernel(Geom g, Pts pts, c
   }
 }
 
+// d(sum dfeat . G_4D(p)) / d(x, y, z, t) of each compact point, through the
+// interpolation weights; dcoord SoA [4][n_cap].
+template <typename TT, int F>
+__global__ void __launch_bounds__(kThreads) coord_grad_kernel(Geom g, Pts pts, const TT* __restrict__ table,
+                                                              const float* __restrict__ dfeat,
+                                                              float* __restrict__ dcoord) {
+  const long long n = point_count(pts);
+  const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if (i >= n) return;
+  const float4 p = load_point(pts, i);
+  const float* drow = dfeat + i * (long long)(g.L * F);
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int l = 0; l < g.L; ++l) {
+    uint32_t idx[16];
+    float w[16];
+    level_corners(g, l, p, idx, w);
+    float d[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) d[f] = __ldg(drow + l * F + f);
+    level_coord_grad<TT, F>(g, l, p, table + g.offset[l] * F, idx, d, acc);
+  }
+  const float4 m = coord_inside(pts, i);
+  const long long cap = pts.n;
+  __stcs(dcoord + i, acc.x * m.x);
+  __stcs(dcoord + cap + i, acc.y * m.y);
+  __stcs(dcoord + 2 * cap + i, acc.z * m.z);
+  __stcs(dcoord + 3 * cap + i, acc.w * m.w);
+}
+
 // Plain form of the transpose: one scalar FP32 atomicAdd per feature.
 template <int F>
 __global__ void __launch_bounds__(kThreads) plain_bwd_kernel(Geom g, Pts pts, const float* __restrict__ dfeat,
@@ -239,6 +268,36 @@ int dash_hash4d_bwd(const dash_layout* layout, const dash_points* pts, const flo
     default: encode_bwd_kernel<8><<<grid, kThreads, 0, st>>>(g, p, dfeat, table_grad); break;
   }
   return launch_status("encode_bwd_kernel");
+}
+
+int dash_hash4d_coord_grad(const dash_layout* layout, const dash_points* pts, const void* table, int table_dtype,
+                           const float* dfeat, float* dcoord, void* stream) {
+  using namespace dash;
+  Geom g;
+  Pts p;
+  if (int s = prepare(layout, pts, &g, &p)) return s;
+  if (p.n == 0) return DASH_OK;
+  if (table == nullptr || dfeat == nullptr || dcoord == nullptr)
+    return fail(DASH_ERR_INVALID_ARG, "table/dfeat/dcoord is NULL");
+  if ((reinterpret_cast<uintptr_t>(table) & 15u) != 0) return fail(DASH_ERR_INVALID_ARG, "table must be 16-byte aligned");
+  const unsigned grid = grid_for(p.n);
+  cudaStream_t st = as_stream(stream);
+#define DASH_COORD_LAUNCH(TT)                                                                                     \
+  switch (g.F) {                                                                                                 \
+    case 1: coord_grad_kernel<TT, 1><<<grid, kThreads, 0, st>>>(g, p, static_cast<const TT*>(table), dfeat, dcoord); break; \
+    case 2: coord_grad_kernel<TT, 2><<<grid, kThreads, 0, st>>>(g, p, static_cast<const TT*>(table), dfeat, dcoord); break; \
+    case 4: coord_grad_kernel<TT, 4><<<grid, kThreads, 0, st>>>(g, p, static_cast<const TT*>(table), dfeat, dcoord); break; \
+    default: coord_grad_kernel<TT, 8><<<grid, kThreads, 0, st>>>(g, p, static_cast<const TT*>(table), dfeat, dcoord); break; \
+  }
+  if (table_dtype == DASH_F32) {
+    DASH_COORD_LAUNCH(float)
+  } else if (table_dtype == DASH_F16) {
+    DASH_COORD_LAUNCH(__half)
+  } else {
+    return fail(DASH_ERR_UNSUPPORTED, "table_dtype %d (F32 or F16)", table_dtype);
+  }
+#undef DASH_COORD_LAUNCH
+  return launch_status("coord_grad_kernel");
 }
 
 int dash_hash4d_bwd_half(const dash_layout* layout, const dash_points* pts, const float* dfeat, void* table_grad,

@@ -111,9 +111,10 @@ _SIGS = {
     "dash_hash4d_fwd": ([_P, _P, _P, _I, _P, _I, _P], _I),
     "dash_hash4d_bwd": ([_P, _P, _P, _P, _P], _I),
     "dash_hash4d_bwd_half": ([_P, _P, _P, _P, _P], _I),
+    "dash_hash4d_coord_grad": ([_P, _P, _P, _I, _P, _P, _P], _I),
     "dash_deform_state_size": ([_P], _SZ),
     "dash_deform_mlp_fwd": ([_P, _P, _P, _I, _P, _P, _P, _P, _P], _I),
-    "dash_deform_mlp_bwd": ([_P, _P, _P, _I, _P, _P, _P, _P, _P, _P, _P], _I),
+    "dash_deform_mlp_bwd": ([_P, _P, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P], _I),
     "dash_batch_plan_create": ([_P, _P], _I),
     "dash_batch_counts": ([_P], ctypes.c_void_p),
     "dash_batch_run": ([_P, _P], _I),
@@ -301,6 +302,14 @@ def dash_hash4d_bwd_half(layout: dash_layout, pts: Points, dfeat: torch.Tensor, 
 
 
 # ------------------------------------------------------------ plain form --
+def dash_hash4d_coord_grad(layout: dash_layout, pts: Points, table: torch.Tensor, dfeat: torch.Tensor, out=None):
+    """d(sum dfeat . G_4D(p)) / d(x, y, z, t) per compact point, SoA [4][n] FP32."""
+    out = torch.zeros((4, pts.n), dtype=torch.float32, device=pts.device) if out is None else out
+    _check(_lib.dash_hash4d_coord_grad(ctypes.byref(layout), ctypes.byref(pts.c), _ptr(table), _DTYPE_CODE[table.dtype],
+                                       _ptr(dfeat), _ptr(out), _stream()), "dash_hash4d_coord_grad")
+    return out
+
+
 def dash_plain_hash4d_fwd(layout, pts, table, out=None):
     assert table.dtype == torch.float32
     out = torch.empty((pts.n, layout.L * layout.F), dtype=torch.float32, device=pts.device) if out is None else out
@@ -360,15 +369,18 @@ def dash_deform_mlp_fwd(layout, pts, table, mlp: Mlp, delta_out=None, fwd_state=
     return delta_out
 
 
-def dash_deform_mlp_bwd(layout, pts, table, mlp: Mlp, ddelta, table_grad, mlp_grad, fwd_state=None, smooth=None):
-    """smooth: optional (lambda_r, (eps_x, eps_y, eps_z), eps_t, loss_out float32 [1] tensor or None)."""
+def dash_deform_mlp_bwd(layout, pts, table, mlp: Mlp, ddelta, table_grad, mlp_grad, fwd_state=None, smooth=None,
+                        coord_grad=None):
+    """smooth: optional (lambda_r, (eps_x, eps_y, eps_z), eps_t, loss_out float32 [1] tensor or None).
+    coord_grad: optional float32 [4][n] CUDA tensor receiving d loss / d(x, y, z, t)."""
     sm = None
     if smooth is not None:
         lam, es, et, lo = smooth
         sm = dash_smooth(float(lam), (ctypes.c_float * 3)(*es), float(et), None if lo is None else lo.data_ptr())
     _check(_lib.dash_deform_mlp_bwd(ctypes.byref(layout), ctypes.byref(pts.c), _ptr(table), _DTYPE_CODE[table.dtype],
                                     ctypes.byref(mlp.c), _ptr(ddelta), _ptr(fwd_state), _ptr(table_grad),
-                                    _ptr(mlp_grad), None if sm is None else ctypes.byref(sm), _stream()),
+                                    _ptr(mlp_grad), None if sm is None else ctypes.byref(sm), _ptr(coord_grad),
+                                    _stream()),
            "dash_deform_mlp_bwd")
 
 
