@@ -136,6 +136,8 @@ def configure(lib):
     lib.orc_topk_mask.restype = ctypes.c_double
     lib.orc_encode_coord_grad.argtypes = [G, P, P, P, P, i64, P, i64, P, P, P]
     lib.orc_encode_coord_grad.restype = None
+    lib.orc_collision_stats.argtypes = [G, P, P, P, P, i64, P, i64, P]
+    lib.orc_collision_stats.restype = i32
     lib.orc_linear_motion.argtypes = [P, P, P, P, i64, P, i64, P]
     lib.orc_linear_motion.restype = None
     lib.orc_static_loss.argtypes = [P, P, i64]
@@ -232,6 +234,15 @@ def encode_coord_grad(g: Grid, pts: Points, table, dfeat) -> np.ndarray:
     d = _c(dfeat, np.float64)
     out = np.zeros((4, pts.n), dtype=np.float64)
     _load().orc_encode_coord_grad(ctypes.byref(g), *pts.args(), _ptr(tab), _ptr(d), _ptr(out))
+    return out
+
+
+def collision_stats(g: Grid, pts: Points) -> np.ndarray:
+    """Per level [V, E, C]: distinct touched vertices, distinct entries they
+    occupy, touched vertices sharing their entry with another (int64 [L][3])."""
+    out = np.zeros((g.L, 3), dtype=np.int64)
+    if _load().orc_collision_stats(ctypes.byref(g), *pts.args(), _ptr(out)) != 0:
+        raise MemoryError("collision statistics: out of host memory")
     return out
 
 

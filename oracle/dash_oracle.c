@@ -274,6 +274,85 @@ void orc_encode_coord_grad(const orc_grid* g, const float* x, const float* y, co
   }
 }
 
+/* ------------------------------------------------ hash collisions ------- */
+typedef struct {
+  int64_t vertex;  /* cx + R (cy + R (cz + R ct)), R = N_s + 1: one id per grid vertex */
+  uint32_t entry;  /* the level-local table entry the vertex maps to */
+} orc_touch;
+
+static int orc_cmp_touch(const void* a, const void* b) {
+  const orc_touch* u = (const orc_touch*)a;
+  const orc_touch* v = (const orc_touch*)b;
+  return u->vertex < v->vertex ? -1 : (u->vertex > v->vertex ? 1 : 0);
+}
+
+static int orc_cmp_u32(const void* a, const void* b) {
+  const uint32_t u = *(const uint32_t*)a, v = *(const uint32_t*)b;
+  return u < v ? -1 : (u > v ? 1 : 0);
+}
+
+/* Occupancy of each level by the n points (Sec. 4.2's collision argument):
+ * stats[l*3 + 0] = V, the distinct grid vertices touched by the points'
+ * hypervoxel corners; [1] = E, the distinct table entries those vertices map
+ * to; [2] = C, the touched vertices whose entry is shared with at least one
+ * other touched vertex (a collision).  Dense levels have E = V, C = 0.
+ * Returns 0, or -1 if the memory for the sort cannot be had. */
+int orc_collision_stats(const orc_grid* g, const float* x, const float* y, const float* z,
+                        const float* t, int64_t t_stride, const int32_t* pidx, int64_t n,
+                        int64_t* stats) {
+  orc_touch* tv = (orc_touch*)malloc(sizeof(orc_touch) * (size_t)(n > 0 ? n * 16 : 1));
+  uint32_t* ent = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n * 16 : 1));
+  if (tv == NULL || ent == NULL) {
+    free(tv);
+    free(ent);
+    return -1;
+  }
+  for (int l = 0; l < g->L; ++l) {
+    const int64_t res[4] = {g->res_s[l], g->res_s[l], g->res_s[l], g->res_t[l]};
+    const int64_t R = res[0] + 1;
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      float p[4];
+      orc_point(x, y, z, t, t_stride, pidx, i, p);
+      uint32_t idx[16];
+      double w[16];
+      orc_cell(g, l, p, idx, w);
+      int64_t i0[4];
+      for (int d = 0; d < 4; ++d) {
+        const double pos = (double)(float)((double)p[d] * (double)res[d]);
+        int64_t c = (int64_t)floor(pos);
+        i0[d] = c > res[d] - 1 ? res[d] - 1 : c;
+      }
+      for (int b = 0; b < 16; ++b) {
+        int64_t c[4];
+        for (int d = 0; d < 4; ++d) c[d] = i0[d] + ((b >> d) & 1);
+        tv[m].vertex = c[0] + R * (c[1] + R * (c[2] + R * c[3]));
+        tv[m].entry = idx[b];
+        ++m;
+      }
+    }
+    qsort(tv, (size_t)m, sizeof(orc_touch), orc_cmp_touch);
+    int64_t V = 0;
+    for (int64_t k = 0; k < m; ++k)
+      if (k == 0 || tv[k].vertex != tv[k - 1].vertex) ent[V++] = tv[k].entry;
+    qsort(ent, (size_t)V, sizeof(uint32_t), orc_cmp_u32);
+    int64_t E = 0, C = 0;
+    for (int64_t k = 0; k < V;) {
+      int64_t r = k;
+      while (r < V && ent[r] == ent[k]) ++r;
+      ++E;
+      if (r - k >= 2) C += r - k;
+      k = r;
+    }
+    stats[l * 3 + 0] = V;
+    stats[l * 3 + 1] = E;
+    stats[l * 3 + 2] = C;
+  }
+  free(tv);
+  free(ent);
+  return 0;
+}
+
 /* ------------------------------------------------------ decoder MLP ------ */
 /* phi_d followed by the heads phi_x, phi_r, phi_s (Eq. 9, Sec. 4.2):
  *   z1 = W1 f + b1, h1 = relu(z1); z2 = W2 h1 + b2, h2 = relu(z2);

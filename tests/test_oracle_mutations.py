@@ -8,6 +8,7 @@ import pytest
 
 import oracle
 import test_oracle_pins as pins
+import test_oracle_pins_collisions as pins_coll
 import test_oracle_pins_coord as pins_coord
 import test_oracle_pins_decomp as pins_decomp
 from paper_2507_19141_gb300 import synth
@@ -110,6 +111,18 @@ MUTATIONS = [
      "dcoord[d * n + i] = inside ? grad[d] : 0.0;",
      "dcoord[d * n + i] = grad[d];",
      [("coord:test_clamp_blocks_the_gradient_outside_the_unit_interval", {})]),
+    ("collisions: a shared entry counted once too few",
+     "if (r - k >= 2) C += r - k;",
+     "if (r - k >= 2) C += r - k - 1;",
+     [("coll:test_counts_equal_brute_force", dict(cfg=(4, 2, 8, 4, 64, 3, 20), n=300))]),
+    ("collisions: vertex id with stride N instead of N + 1",
+     "const int64_t R = res[0] + 1;",
+     "const int64_t R = res[0];",
+     [("coll:test_counts_equal_brute_force", dict(cfg=(3, 2, 6, 2, 9, 2, 5), n=500))]),
+    ("collisions: the temporal corner bit ignored",
+     "for (int d = 0; d < 4; ++d) c[d] = i0[d] + ((b >> d) & 1);",
+     "for (int d = 0; d < 4; ++d) c[d] = i0[d] + (d < 3 ? ((b >> d) & 1) : 0);",
+     [("coll:test_dense_levels_never_collide_and_one_point_touches_16_vertices", {})]),
     ("Eq. 11 temporal perturbation applied to x",
      "const float e_t[4] = {0.f, 0.f, 0.f, eps_t};",
      "const float e_t[4] = {eps_t, 0.f, 0.f, 0.f};",
@@ -122,6 +135,8 @@ def _pin(fname):
         return getattr(pins_decomp, fname[len("decomp:"):])
     if fname.startswith("coord:"):
         return getattr(pins_coord, fname[len("coord:"):])
+    if fname.startswith("coll:"):
+        return getattr(pins_coll, fname[len("coll:"):])
     return getattr(pins, fname)
 
 
