@@ -495,8 +495,69 @@ def run_extras(torch, wl, args, stream):
     res["scatter_fp16_rel_err_vs_fp32"] = float((g16.float() - g32).norm() / g32.norm())
     del g32, g16, dfeat
     res.update(run_decomp(torch, wl, stream))
+    res.update(run_wo_dec(torch, stream))
     res.update(run_batched(torch, stream))
     return res
+
+
+def run_wo_dec(torch, stream):
+    """The "w/o dec" comparison on the 600k-Gaussian scene shape (Bernoulli(0.5)
+    dynamic mask, scene coordinates, per-Gaussian t): fused forward + backward
+    over all Gaussians against compaction + the same over the dynamic ones,
+    and the tables' occupancy (touched vertices, occupied entries, colliding
+    vertices over the hashed levels) for both point sets."""
+    import numpy as np
+    from paper_2507_19141_gb300 import dash, synth
+    grid, mlpc = synth.PAPER_GRID, synth.PAPER_MLP
+    rng = np.random.default_rng(12)
+    n_all = 600_000
+    mask_h = synth.bernoulli_mask(rng, n_all)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    x, y, z, t = (dev(c) for c in synth.scene_coords(rng, n_all))
+    lay = dash.layout_from(grid)
+    table = dev(synth.table_values(rng, lay.total, grid.F, np.float16))
+    mlp = dash.Mlp(dev(synth.mlp_params(rng, mlpc)), mlpc.d_in, mlpc.d_hidden, mlpc.d_out)
+    mask = dev(mask_h)
+    idx = torch.empty(n_all, dtype=torch.int32, device="cuda")
+    cnt = torch.empty(1, dtype=torch.int64, device="cuda")
+    cws = torch.empty(dash.dash_compact_workspace_size(n_all), dtype=torch.uint8, device="cuda")
+    dd = dev(synth.upstream_grad(rng, mlpc.d_out, n_all))
+    delta = torch.empty((mlpc.d_out, n_all), dtype=torch.float32, device="cuda")
+    st = dash.deform_state(mlp, n_all, "cuda")
+    tg = torch.zeros((lay.total, grid.F), dtype=torch.float32, device="cuda")
+    pg = torch.zeros(mlpc.n_params, dtype=torch.float32, device="cuda")
+    pts_all = dash.Points(x, y, z, t)
+    pts_dyn = dash.Points(x, y, z, t, idx=idx, n=n_all, n_dev=cnt)
+
+    def step(pts, compact):
+        if compact:
+            dash.dash_compact_dynamic(mask, idx_out=idx, count_out=cnt, ws=cws)
+        dash.dash_deform_mlp_fwd(lay, pts, table, mlp, delta_out=delta, fwd_state=st)
+        dash.dash_deform_mlp_bwd(lay, pts, table, mlp, dd, tg, pg, fwd_state=st)
+
+    r = {"wo_dec_n_all": n_all}
+    for name, pts, compact in (("all", pts_all, False), ("dynamic", pts_dyn, True)):
+        for _ in range(3):
+            step(pts, compact)
+        r[f"wo_dec_{name}_step_ms"] = time_steps(torch, lambda: step(pts, compact), 20, stream)
+    r["wo_dec_dynamic_count"] = int(cnt.item())
+    hashed = [l for l in range(grid.L) if not lay.dense[l]]
+    cws2 = torch.empty(dash.dash_collision_workspace_size(lay, n_all), dtype=torch.uint8, device="cuda")
+    for name, pts in (("all", pts_all), ("dynamic", pts_dyn)):
+        stats = dash.dash_hash4d_collision_stats(lay, pts, ws=cws2)
+        r[f"wo_dec_{name}_occupancy_ms"] = time_steps(torch, lambda: dash.dash_hash4d_collision_stats(
+            lay, pts, out=stats, ws=cws2), 3, stream)
+        s = stats.cpu().numpy()[hashed]
+        V, E, C = (int(v) for v in s.sum(axis=0))
+        r[f"wo_dec_{name}_hashed_vertices"] = V
+        r[f"wo_dec_{name}_hashed_entries"] = E
+        r[f"wo_dec_{name}_colliding_vertices"] = C
+        r[f"wo_dec_{name}_collision_rate"] = C / V if V else 0.0
+        r[f"wo_dec_{name}_vertices_per_entry"] = V / E if E else 0.0
+        r[f"wo_dec_{name}_collision_rate_per_level"] = [round(float(c) / float(v), 4) if v else 0.0
+                                                       for v, _, c in s]
+    r["wo_dec_hashed_levels"] = hashed
+    return r
 
 
 # decomposition, algorithmic bytes per Gaussian: x, y, z, t (16) + 16 levels x 8

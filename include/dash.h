@@ -216,6 +216,26 @@ int dash_hash4d_bwd_half(const dash_layout* layout, const dash_points* pts, cons
 int dash_hash4d_coord_grad(const dash_layout* layout, const dash_points* pts, const void* table,
                            int table_dtype, const float* dfeat, float* dcoord, void* stream);
 
+/* ----------- table occupancy: the collision argument (Sec. 4.2, Sec. 5) -- */
+
+/* Bytes of device workspace dash_hash4d_collision_stats needs for up to n
+ * points: a set of 2^ceil(log2(32 n)) 64-bit vertex ids (at least 1024) plus
+ * one 32-bit counter per entry of the largest level.  0 for bad arguments. */
+size_t dash_collision_workspace_size(const dash_layout* layout, int64_t n);
+
+/* Per level l, into stats_out[3 l .. 3 l + 2] (device int64 [L][3]): V, the
+ * distinct grid vertices touched by the points' hypervoxel corners (Eq. 8's
+ * cells); E, the distinct table entries those vertices occupy; C, the touched
+ * vertices whose entry is shared with at least one other touched vertex.
+ * Dense levels give E = V, C = 0.  Exact integer counts (order independent).
+ * A level whose vertex set overflowed reports -1, -1, -1 (does not happen
+ * with the workspace size above).  ws: 256-byte aligned, at least
+ * dash_collision_workspace_size(layout, pts->n) bytes; stream-ordered memsets
+ * and 3 launches per level.  The paper has no such routine: it measures how
+ * crowded the tables are with and without the static/dynamic decomposition. */
+int dash_hash4d_collision_stats(const dash_layout* layout, const dash_points* pts,
+                                int64_t* stats_out, void* ws, size_t ws_bytes, void* stream);
+
 /* ------------------------- a2-a8: fused deformation forward (Eqs. 8-10) -- */
 
 /* Bytes of forward state per Gaussian that dash_deform_mlp_fwd keeps for

@@ -112,6 +112,8 @@ _SIGS = {
     "dash_hash4d_bwd": ([_P, _P, _P, _P, _P], _I),
     "dash_hash4d_bwd_half": ([_P, _P, _P, _P, _P], _I),
     "dash_hash4d_coord_grad": ([_P, _P, _P, _I, _P, _P, _P], _I),
+    "dash_collision_workspace_size": ([_P, _I64], _SZ),
+    "dash_hash4d_collision_stats": ([_P, _P, _P, _P, _SZ, _P], _I),
     "dash_deform_state_size": ([_P], _SZ),
     "dash_deform_mlp_fwd": ([_P, _P, _P, _I, _P, _P, _P, _P, _P], _I),
     "dash_deform_mlp_bwd": ([_P, _P, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P], _I),
@@ -307,6 +309,21 @@ def dash_hash4d_coord_grad(layout: dash_layout, pts: Points, table: torch.Tensor
     out = torch.zeros((4, pts.n), dtype=torch.float32, device=pts.device) if out is None else out
     _check(_lib.dash_hash4d_coord_grad(ctypes.byref(layout), ctypes.byref(pts.c), _ptr(table), _DTYPE_CODE[table.dtype],
                                        _ptr(dfeat), _ptr(out), _stream()), "dash_hash4d_coord_grad")
+    return out
+
+
+def dash_collision_workspace_size(layout: dash_layout, n: int) -> int:
+    return int(_lib.dash_collision_workspace_size(ctypes.byref(layout), n))
+
+
+def dash_hash4d_collision_stats(layout: dash_layout, pts: Points, out=None, ws=None):
+    """Per level (V, E, C): touched vertices, occupied entries, colliding
+    vertices, as a device int64 tensor [L][3]."""
+    out = torch.empty((layout.L, 3), dtype=torch.int64, device=pts.device) if out is None else out
+    if ws is None:
+        ws = torch.empty(dash_collision_workspace_size(layout, pts.n), dtype=torch.uint8, device=pts.device)
+    _check(_lib.dash_hash4d_collision_stats(ctypes.byref(layout), ctypes.byref(pts.c), _ptr(out), _ptr(ws), ws.numel(),
+                                            _stream()), "dash_hash4d_collision_stats")
     return out
 
 
