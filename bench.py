@@ -715,8 +715,9 @@ def run_reference(args):
 
 def profile_case(n):
     """Small case for ncu captures: n dynamic Gaussians (no compaction), about
-    0.6 GB on the device, two launches of the encoder forward/backward and of
-    the fused forward/backward."""
+    1 GB on the device, two launches each of the encoder forward/backward, the
+    fused forward/backward (the backward once more with the coordinate
+    gradient), the decomposition with its top-k mask, and one occupancy count."""
     import numpy as np
     import torch
     from paper_2507_19141_gb300 import dash, synth
@@ -735,11 +736,20 @@ def profile_case(n):
     pg = torch.zeros(mlpc.n_params, device="cuda")
     dd = dev(synth.upstream_grad(rng, mlpc.d_out, n))
     dfeat = dev(rng.standard_normal((n, mlpc.d_in)).astype(np.float32))
+    lay3 = dash.dash_hash3d_layout(16, 2, 19, 16, 2048)
+    table3 = dev(synth.table_values(rng, lay3.total, 2, np.float16))
+    k = 1 / np.sqrt(32)
+    dec = dash.Mlp(dev(rng.uniform(-k, k, 64 * 32 + 64 + 3 * 64 + 3).astype(np.float32)), 32, 64, 3)
+    cg = torch.empty((4, n), device="cuda")
     for _ in range(2):
         dash.dash_hash4d_fwd(lay, pts, table, torch.bfloat16, out=feat)
         dash.dash_hash4d_bwd(lay, pts, dfeat, tg)
         dash.dash_deform_mlp_fwd(lay, pts, table, mlp, delta_out=delta, fwd_state=state)
         dash.dash_deform_mlp_bwd(lay, pts, table, mlp, dd, tg, pg, fwd_state=state)
+        dash.dash_deform_mlp_bwd(lay, pts, table, mlp, dd, tg, pg, fwd_state=state, coord_grad=cg)
+        _, norm, _ = dash.dash_decomp_fwd(lay3, pts.x, pts.y, pts.z, table3, dec, t=pts.t)
+        dash.dash_topk_mask(norm, 50.0)
+    dash.dash_hash4d_collision_stats(lay, pts)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": n, "delta_abs_mean": float(delta.abs().mean()),
                       "grad_abs_sum": float(tg.abs().sum())}))
