@@ -40,6 +40,30 @@ N_DYN = 1_000_000
 FWD_BYTES = 16 + 4 + 1024 + 40 + 80 + 80
 BWD_BYTES = 16 + 4 + 80 + 40 + 2048
 STEP_BYTES = 2 + 4 + FWD_BYTES + BWD_BYTES
+
+# DRAM bytes read + written per launch at 1M Gaussians from one ncu capture
+# (profiles/warp_specialised_kernels_1M.md), valid while the kernel's sources
+# hash to the captured value; otherwise the benchmark reports no traffic.
+NCU_TRAFFIC = {
+    "bwd": {"bytes": (198.3 + 9.9) * 1e6, "n": 1_000_000, "sha256_16": "c2bfecf4271aadb0",
+            "sources": ("deform_bwd.cu", "deform_common.cuh", "dash_internal.cuh", "tc_ptx.cuh")},
+    "fwd": {"bytes": (45.5 + 73.0) * 1e6, "n": 1_000_000, "sha256_16": "b917b9f9192a5d4c",
+            "sources": ("deform_fwd.cu", "deform_common.cuh", "dash_internal.cuh", "tc_ptx.cuh")},
+}
+
+
+def captured_traffic(kernel, n):
+    """Per-launch DRAM traffic of `kernel` at n Gaussians, or None when the
+    capture was taken at another size or the kernel has changed since."""
+    import hashlib
+    rec = NCU_TRAFFIC[kernel]
+    if n != rec["n"]:
+        return None
+    m = hashlib.sha256()
+    for f in rec["sources"]:
+        with open(os.path.join(ROOT, "paper_2507_19141_gb300", "csrc", f), "rb") as fh:
+            m.update(fh.read())
+    return rec["bytes"] if m.hexdigest()[:16] == rec["sha256_16"] else None
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -306,7 +330,9 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": f"fused {dom}", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
                      "algorithmic_bytes_per_gaussian": FWD_BYTES if dom == "fwd" else BWD_BYTES,
-                     "traffic": None},
+                     "traffic": captured_traffic(dom, args.n_dyn),
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch at 1M "
+                                       "Gaussians without an index list (profile case)"},
         "clocks": clocks,
         "step_roofline": {"bytes_per_gaussian": STEP_BYTES, "achieved_gbs": STEP_BYTES * value / 1e9,
                           "frac": STEP_BYTES * value / 1e9 / peak,
