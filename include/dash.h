@@ -314,6 +314,73 @@ int dash_topk_mask(const float* values, int64_t n, double k_percent, uint8_t* ma
                    float* tau_out, float* static_loss_out, void* ws, size_t ws_bytes,
                    void* stream);
 
+/* ----------- the renderer the deformed Gaussians are drawn with --------
+ * 3D Gaussian splatting (Sec. 3): Eq. 1 with Sigma = R S S^T R^T projected
+ * to Sigma' = J W Sigma W^T J^T, spherical-harmonics colour, Eq. 2 alpha
+ * blending front to back in 16 x 16 pixel tiles, into a device image.
+ * Conventions: pinhole u = fx x/z + cx, v = fy y/z + cy (pixel (i, j) is
+ * evaluated at (i, j)); Gaussians with z <= near_plane or det(Sigma') <= 0
+ * are not drawn; `dilation` is added to Sigma''s diagonal; alpha =
+ * min(0.99, opacity exp(-d^T Sigma'^-1 d / 2)), contributions below 1/255
+ * are skipped and blending stops before T would fall below 1e-4; each
+ * Gaussian is considered in the tiles its square of half-side
+ * ceil(3 sqrt(lambda_max(Sigma'))) overlaps, in ascending depth (ties by
+ * index); colour = real orthonormal SH (degree <= 3, no Condon-Shortley
+ * phase) at the unit direction campos -> mean, + 0.5, clamped at 0. */
+
+typedef struct dash_camera {
+  float view[16];       /* world -> camera, row-major 4 x 4 acting on column vectors */
+  float fx, fy, cx, cy; /* pixels */
+  int32_t width, height;
+  float near_plane;
+  float dilation;       /* screen-space low-pass added to Sigma' (0.3 in 3DGS) */
+  float campos[3];      /* camera centre in world coordinates */
+  float bg[3];          /* background colour */
+} dash_camera;
+
+/* Device SoA attributes of n Gaussians (activations are the caller's). */
+typedef struct dash_gaussians {
+  const float* mean;    /* [3][n] world positions */
+  const float* scale;   /* [3][n] standard deviations along the local axes */
+  const float* rot;     /* [4][n] quaternion (w, x, y, z), any non-zero norm */
+  const float* opacity; /* [n] */
+  const float* sh;      /* [n][16][3] SH coefficients, the first (degree+1)^2 used */
+  int32_t sh_degree;    /* 0..3 */
+  int32_t reserved;
+  int64_t n;            /* < 2^31 */
+} dash_gaussians;
+
+/* Gradient buffers, same layouts as dash_gaussians; accumulated (+=). */
+typedef struct dash_gaussian_grads {
+  float* mean;
+  float* scale;
+  float* rot;
+  float* opacity;
+  float* sh;
+} dash_gaussian_grads;
+
+/* Bytes of device workspace for one view of n Gaussians with room for
+ * max_pairs (tile, Gaussian) pairs; 0 for bad arguments. */
+size_t dash_raster_workspace_size(const dash_camera* cam, int64_t n, int64_t max_pairs);
+
+/* Renders image [3][height][width] FP32 (device).  ws (256-byte aligned,
+ * dash_raster_workspace_size bytes) keeps the view's per-Gaussian, per-tile
+ * and per-pixel state for dash_raster_bwd.  pairs_needed (device int64, may
+ * be NULL) receives the number of pairs the view needs; when it exceeds
+ * max_pairs the image is NaN (grow the workspace and render again).  No host
+ * synchronisation; 5 launches.  Errors: INVALID_ARG (NULL), UNSUPPORTED
+ * (image > 16384, sh_degree > 3, n >= 2^31), WORKSPACE. */
+int dash_raster_fwd(const dash_camera* cam, const dash_gaussians* gaussians, float* image, void* ws,
+                    size_t ws_bytes, int64_t max_pairs, int64_t* pairs_needed, void* stream);
+
+/* Backward of the last dash_raster_fwd on this ws (same camera, Gaussians
+ * and max_pairs): accumulates dL/d(mean, scale, rot, opacity, sh) for
+ * dL/dimage [3][height][width].  Culled Gaussians get no gradient; the 0.99
+ * alpha clamp and the colour clamp pass none.  2 launches + 1 memset. */
+int dash_raster_bwd(const dash_camera* cam, const dash_gaussians* gaussians, const float* dimage,
+                    void* ws, size_t ws_bytes, int64_t max_pairs, const dash_gaussian_grads* grads,
+                    void* stream);
+
 /* ---------------- a12: many scenes x timestamps, one graph launch ------ */
 
 #define DASH_MAX_SCENES 64

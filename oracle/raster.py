@@ -147,12 +147,13 @@ def render(cam: dict, mean, scale, rot, opacity, sh, sh_degree: int):
     n = mean.shape[0]
     depth = p["depth"].detach()
     order = sorted((i for i in range(n) if bool(ok[i])), key=lambda i: (float(depth[i]), i))
+    rl = rect.tolist()
     final_T = torch.ones(H_, W_, dtype=torch.float64)
     count = torch.zeros(H_, W_, dtype=torch.int64)
     image = [[None] * ((W_ + TILE - 1) // TILE) for _ in range((H_ + TILE - 1) // TILE)]
     for ty in range((H_ + TILE - 1) // TILE):
         for tx in range((W_ + TILE - 1) // TILE):
-            ids = [i for i in order if rect[i, 0] <= tx < rect[i, 2] and rect[i, 1] <= ty < rect[i, 3]]
+            ids = [i for i in order if rl[i][0] <= tx < rl[i][2] and rl[i][1] <= ty < rl[i][3]]
             px = torch.arange(tx * TILE, min(tx * TILE + TILE, W_), dtype=torch.float64)
             py = torch.arange(ty * TILE, min(ty * TILE + TILE, H_), dtype=torch.float64)
             gy, gx = torch.meshgrid(py, px, indexing="ij")

@@ -80,6 +80,24 @@ class dash_smooth(ctypes.Structure):
                 ("loss_out", ctypes.c_void_p)]
 
 
+class dash_camera(ctypes.Structure):
+    _fields_ = [("view", ctypes.c_float * 16), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("near_plane", ctypes.c_float), ("dilation", ctypes.c_float),
+                ("campos", ctypes.c_float * 3), ("bg", ctypes.c_float * 3)]
+
+
+class dash_gaussians(ctypes.Structure):
+    _fields_ = [("mean", ctypes.c_void_p), ("scale", ctypes.c_void_p), ("rot", ctypes.c_void_p),
+                ("opacity", ctypes.c_void_p), ("sh", ctypes.c_void_p), ("sh_degree", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("n", ctypes.c_int64)]
+
+
+class dash_gaussian_grads(ctypes.Structure):
+    _fields_ = [("mean", ctypes.c_void_p), ("scale", ctypes.c_void_p), ("rot", ctypes.c_void_p),
+                ("opacity", ctypes.c_void_p), ("sh", ctypes.c_void_p)]
+
+
 class dash_batch_scene(ctypes.Structure):
     _fields_ = [("table", ctypes.c_void_p), ("params", ctypes.c_void_p), ("x", ctypes.c_void_p),
                 ("y", ctypes.c_void_p), ("z", ctypes.c_void_p), ("timestamps", ctypes.c_void_p),
@@ -113,6 +131,9 @@ _SIGS = {
     "dash_hash4d_bwd_half": ([_P, _P, _P, _P, _P], _I),
     "dash_hash4d_coord_grad": ([_P, _P, _P, _I, _P, _P, _P], _I),
     "dash_collision_workspace_size": ([_P, _I64], _SZ),
+    "dash_raster_workspace_size": ([_P, _I64, _I64], _SZ),
+    "dash_raster_fwd": ([_P, _P, _P, _P, _SZ, _I64, _P, _P], _I),
+    "dash_raster_bwd": ([_P, _P, _P, _P, _SZ, _I64, _P, _P], _I),
     "dash_hash4d_collision_stats": ([_P, _P, _P, _P, _SZ, _P], _I),
     "dash_deform_state_size": ([_P], _SZ),
     "dash_deform_mlp_fwd": ([_P, _P, _P, _I, _P, _P, _P, _P, _P], _I),
@@ -446,6 +467,66 @@ def dash_topk_mask(values: torch.Tensor, k_percent: float, mask_out=None, tau_ou
     _check(_lib.dash_topk_mask(_ptr(values), n, float(k_percent), _ptr(mask_out), _ptr(tau_out), _ptr(static_loss_out),
                                _ptr(ws), ws.numel(), _stream()), "dash_topk_mask")
     return mask_out, tau_out
+
+
+# ----------------------------------------------- splatting renderer ------
+def camera(view, fx, fy, cx, cy, width, height, near=0.2, dilation=0.3, campos=(0.0, 0.0, 0.0),
+           bg=(0.0, 0.0, 0.0)) -> dash_camera:
+    """view: 16 floats, row-major world -> camera matrix."""
+    v = [float(a) for a in view]
+    assert len(v) == 16
+    return dash_camera((ctypes.c_float * 16)(*v), fx, fy, cx, cy, int(width), int(height), near, dilation,
+                       (ctypes.c_float * 3)(*campos), (ctypes.c_float * 3)(*bg))
+
+
+class Gaussians:
+    """Device SoA attributes (float32 CUDA tensors): mean [3][n], scale [3][n],
+    rot [4][n] (w, x, y, z), opacity [n], sh [n][16][3]; kept alive here."""
+
+    def __init__(self, mean, scale, rot, opacity, sh, sh_degree=3):
+        n = mean.shape[1]
+        for t_, shape in ((mean, (3, n)), (scale, (3, n)), (rot, (4, n)), (opacity, (n,)), (sh, (n, 16, 3))):
+            assert t_.is_cuda and t_.dtype == torch.float32 and t_.is_contiguous() and tuple(t_.shape) == shape
+        self.mean, self.scale, self.rot, self.opacity, self.sh = mean, scale, rot, opacity, sh
+        self.n = n
+        self.c = dash_gaussians(mean.data_ptr(), scale.data_ptr(), rot.data_ptr(), opacity.data_ptr(), sh.data_ptr(),
+                                int(sh_degree), 0, n)
+
+
+def dash_raster_workspace_size(cam: dash_camera, n: int, max_pairs: int) -> int:
+    return int(_lib.dash_raster_workspace_size(ctypes.byref(cam), n, max_pairs))
+
+
+def dash_raster_fwd(cam: dash_camera, g: Gaussians, image=None, ws=None, max_pairs=None, pairs_needed=None):
+    """Renders [3][H][W]; returns (image, ws, max_pairs, pairs_needed).  Without
+    max_pairs the capacity starts at 64 n + 4096 and the call is repeated with
+    the needed capacity if the view exceeds it (one host synchronisation)."""
+    dev = g.mean.device
+    image = torch.empty((3, cam.height, cam.width), dtype=torch.float32, device=dev) if image is None else image
+    pairs_needed = torch.zeros(1, dtype=torch.int64, device=dev) if pairs_needed is None else pairs_needed
+    grow = max_pairs is None
+    max_pairs = 64 * g.n + 4096 if max_pairs is None else int(max_pairs)
+    while True:
+        need = dash_raster_workspace_size(cam, g.n, max_pairs)
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(need, dtype=torch.uint8, device=dev)
+        _check(_lib.dash_raster_fwd(ctypes.byref(cam), ctypes.byref(g.c), _ptr(image), _ptr(ws), ws.numel(),
+                                    max_pairs, _ptr(pairs_needed), _stream()), "dash_raster_fwd")
+        if not grow:
+            return image, ws, max_pairs, pairs_needed
+        p = int(pairs_needed.item())
+        if p <= max_pairs:
+            return image, ws, max_pairs, pairs_needed
+        max_pairs = p
+
+
+def dash_raster_bwd(cam: dash_camera, g: Gaussians, dimage, ws, max_pairs: int, grads: dict):
+    """Accumulates into grads (dict of float32 CUDA tensors mean, scale, rot,
+    opacity, sh shaped like the attributes)."""
+    gr = dash_gaussian_grads(*(grads[k].data_ptr() for k in ("mean", "scale", "rot", "opacity", "sh")))
+    _check(_lib.dash_raster_bwd(ctypes.byref(cam), ctypes.byref(g.c), _ptr(dimage), _ptr(ws), ws.numel(), int(max_pairs),
+                                ctypes.byref(gr), _stream()), "dash_raster_bwd")
+    return grads
 
 
 # ----------------------------------------------------- a12: batched form --

@@ -166,3 +166,35 @@ def batched(seed=4, scenes=8, timestamps=64, n_lo=50_000, n_hi=2_000_000, frames
         f = np.sort(rng.choice(frames, size=timestamps, replace=False))
         ts.append((f / (frames - 1)).astype(np.float32))
     return counts, ts, rng
+
+
+def raster_scene(rng, n, width, height, sh_degree=3, depth=(2.0, 8.0), spread=0.6, scale=(0.004, 0.04)):
+    """Gaussians in front of a camera (float32 arrays): means with depth
+    z ~ U[depth] and x, y ~ U[-spread z, spread z]; scales log-uniform in
+    [scale] times z; random quaternions (w, x, y, z); opacity ~ U[0.05, 0.95];
+    SH coefficients [n][16][3] ~ N(0, 0.25) beyond degree 0 and a degree-0
+    term giving colours ~ U[0, 1].  The camera (dict) sits at campos with a
+    small rotation about y; fx = fy = 0.8 width."""
+    z = rng.uniform(*depth, n)
+    x = rng.uniform(-spread, spread, n) * z
+    y = rng.uniform(-spread, spread, n) * z * height / width
+    mean_cam = np.stack([x, y, z])
+    theta = 0.1
+    Rv = np.array([[math.cos(theta), 0.0, math.sin(theta)], [0.0, 1.0, 0.0], [-math.sin(theta), 0.0, math.cos(theta)]])
+    tv = np.array([0.05, -0.03, 0.2])
+    mean = Rv.T @ (mean_cam - tv[:, None])          # world positions whose camera coordinates are mean_cam
+    sc = np.exp(rng.uniform(np.log(scale[0]), np.log(scale[1]), (3, n))) * z[None, :]
+    q = rng.standard_normal((4, n))
+    opacity = rng.uniform(0.05, 0.95, n)
+    sh = rng.standard_normal((n, 16, 3)) * 0.25
+    sh[:, 0, :] = (rng.uniform(0.0, 1.0, (n, 3)) - 0.5) * 2.0 * math.sqrt(math.pi)
+    if sh_degree < 3:
+        sh[:, (sh_degree + 1) ** 2:, :] = 0.0
+    view = np.eye(4)
+    view[:3, :3] = Rv
+    view[:3, 3] = tv
+    cam = {"view": view.reshape(-1).tolist(), "fx": 0.8 * width, "fy": 0.8 * width, "cx": width / 2,
+           "cy": height / 2, "width": width, "height": height, "near": 0.2, "dilation": 0.3,
+           "campos": (-Rv.T @ tv).tolist(), "bg": [0.1, 0.15, 0.2]}
+    f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
+    return cam, {"mean": f32(mean), "scale": f32(sc), "rot": f32(q), "opacity": f32(opacity), "sh": f32(sh)}
