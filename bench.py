@@ -522,8 +522,84 @@ def run_extras(torch, wl, args, stream):
     del g32, g16, dfeat
     res.update(run_decomp(torch, wl, stream))
     res.update(run_wo_dec(torch, stream))
+    res.update(run_render(torch, stream))
     res.update(run_batched(torch, stream))
     return res
+
+
+def render_frame_setup(torch, n=106_600, width=1352, height=1014, seed=13, scale=(0.001, 0.01)):
+    """Inference frame at the paper's FPS shape (1352 x 1014, ~106.6k Gaussians,
+    half of them dynamic): canonical attributes SoA [10][n] (position,
+    quaternion, scale), normalised canonical coordinates for the encoder, FP16
+    tables and a BF16 decoder whose last layer is scaled by 1e-2 (small
+    offsets), opacities and degree-3 SH colours."""
+    import numpy as np
+    from paper_2507_19141_gb300 import dash, synth
+    rng = np.random.default_rng(seed)
+    cam, g = synth.raster_scene(rng, n, width, height, scale=scale)
+    grid, mlpc = synth.PAPER_GRID, synth.PAPER_MLP
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    lo = g["mean"].min(axis=1, keepdims=True)
+    hi = g["mean"].max(axis=1, keepdims=True)
+    ncoord = ((g["mean"] - lo) / (hi - lo)).astype(np.float32)
+    lay = dash.layout_from(grid)
+    params = synth.mlp_params(rng, mlpc)
+    D, H, O = mlpc.d_in, mlpc.d_hidden, mlpc.d_out
+    params[H * D + H + H * H + H:] *= 1e-2
+    f = {"cam": dash.camera(cam["view"], cam["fx"], cam["fy"], cam["cx"], cam["cy"], width, height, cam["near"],
+                            cam["dilation"], cam["campos"], cam["bg"]),
+         "n": n, "lay": lay, "mask": dev(synth.bernoulli_mask(rng, n)),
+         "x": dev(ncoord[0]), "y": dev(ncoord[1]), "z": dev(ncoord[2]), "t": dev(np.array([0.37], np.float32)),
+         "table": dev(synth.table_values(rng, lay.total, grid.F, np.float16)),
+         "mlp": dash.Mlp(dev(params), D, H, O),
+         "attrs_in": dev(np.concatenate([g["mean"], g["rot"], g["scale"]], 0)),
+         "opacity": dev(g["opacity"]), "sh": dev(g["sh"])}
+    f["attrs_out"] = f["attrs_in"].clone()
+    f["idx"] = torch.empty(n, dtype=torch.int32, device="cuda")
+    f["cnt"] = torch.empty(1, dtype=torch.int64, device="cuda")
+    f["cws"] = torch.empty(dash.dash_compact_workspace_size(n), dtype=torch.uint8, device="cuda")
+    f["delta"] = torch.empty((O, n), dtype=torch.float32, device="cuda")
+    f["pts"] = dash.Points(f["x"], f["y"], f["z"], f["t"], idx=f["idx"], n=n, n_dev=f["cnt"])
+    ao = f["attrs_out"]
+    # the renderer reads the Eq. 10 output rows in place: x (0-2), r (3-6), s (7-9)
+    f["G"] = dash.Gaussians(ao[0:3], ao[7:10], ao[3:7], f["opacity"], f["sh"], 3)
+    f["image"] = torch.empty((3, height, width), dtype=torch.float32, device="cuda")
+    return f
+
+
+def render_frame(f, ws, cap, pairs):
+    from paper_2507_19141_gb300 import dash
+    dash.dash_compact_dynamic(f["mask"], idx_out=f["idx"], count_out=f["cnt"], ws=f["cws"])
+    dash.dash_deform_mlp_fwd(f["lay"], f["pts"], f["table"], f["mlp"], delta_out=f["delta"],
+                             apply=(f["attrs_in"], f["attrs_out"]))
+    dash.dash_raster_fwd(f["cam"], f["G"], image=f["image"], ws=ws, max_pairs=cap, pairs_needed=pairs)
+
+
+def run_render(torch, stream):
+    """Inference frames at the paper's FPS shape: compaction + deformation
+    forward (Eq. 10 applied) + splatting of all Gaussians; and the renderer's
+    forward and backward alone."""
+    from paper_2507_19141_gb300 import dash
+    f = render_frame_setup(torch)
+    dash.dash_compact_dynamic(f["mask"], idx_out=f["idx"], count_out=f["cnt"], ws=f["cws"])
+    dash.dash_deform_mlp_fwd(f["lay"], f["pts"], f["table"], f["mlp"], delta_out=f["delta"],
+                             apply=(f["attrs_in"], f["attrs_out"]))
+    _, ws, cap, pairs = dash.dash_raster_fwd(f["cam"], f["G"], image=f["image"])   # sizes the pair buffer
+    for _ in range(3):
+        render_frame(f, ws, cap, pairs)
+    r = {"render_n": f["n"], "render_size": [f["cam"].width, f["cam"].height], "render_pairs": int(pairs.item()),
+         "render_pairs_per_gaussian": int(pairs.item()) / f["n"]}
+    r["render_frame_ms"] = time_steps(torch, lambda: render_frame(f, ws, cap, pairs), 50, stream)
+    r["render_fps"] = 1e3 / r["render_frame_ms"]
+    r["render_raster_fwd_ms"] = time_steps(torch, lambda: dash.dash_raster_fwd(
+        f["cam"], f["G"], image=f["image"], ws=ws, max_pairs=cap, pairs_needed=pairs), 50, stream)
+    grads = {k: torch.zeros_like(getattr(f["G"], k)) for k in ("mean", "scale", "rot", "opacity", "sh")}
+    dimg = torch.randn_like(f["image"])
+    dash.dash_raster_bwd(f["cam"], f["G"], dimg, ws, cap, grads)
+    r["render_raster_bwd_ms"] = time_steps(torch, lambda: dash.dash_raster_bwd(f["cam"], f["G"], dimg, ws, cap, grads),
+                                           20, stream)
+    r["render_nan_free"] = bool(torch.isfinite(f["image"]).all().item())
+    return r
 
 
 def run_wo_dec(torch, stream):

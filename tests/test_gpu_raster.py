@@ -111,3 +111,43 @@ def test_backward_matches_oracle_autograd(dashlib, n, w, h, degree):
             got, ref_k = got[:, :K], ref_k[:, :K]
             assert np.all(grads[k].cpu().numpy()[:, K:] == 0)
         assert rel_err(got, ref_k) < 2e-3, (k, rel_err(got, ref_k))
+
+
+def test_deformed_gaussians_render_matches_oracle_chain(dashlib):
+    """compaction -> fused deformation with Eq. 10 applied in place -> the
+    renderer reading the deformed rows, against oracle deformation (FP64) ->
+    oracle renderer."""
+    import oracle
+    from gpu_helpers import oracle_grid
+    rng = np.random.default_rng(105)
+    n, w, h = 1500, 128, 96
+    cam, g = synth.raster_scene(rng, n, w, h)
+    mask = synth.bernoulli_mask(rng, n)
+    lo, hi = g["mean"].min(1, keepdims=True), g["mean"].max(1, keepdims=True)
+    nc = ((g["mean"] - lo) / (hi - lo)).astype(np.float32)
+    t = np.array([0.37], np.float32)
+    grid, mlpc = synth.PAPER_GRID, synth.PAPER_MLP
+    gg = oracle_grid(grid)
+    table = synth.table_values(rng, gg.total, 2, np.float16)
+    params = synth.mlp_params(rng, mlpc)
+    params[64 * 32 + 64 + 64 * 64 + 64:] *= 1e-2          # small offsets
+    attrs = np.concatenate([g["mean"], g["rot"], g["scale"]], 0).astype(np.float32)
+    lay = dashlib.layout_from(grid)
+    idx, cnt = dashlib.dash_compact_dynamic(to_dev(mask))
+    pts = dashlib.Points(to_dev(nc[0]), to_dev(nc[1]), to_dev(nc[2]), to_dev(t), idx=idx, n=n, n_dev=cnt)
+    a_in = to_dev(attrs)
+    a_out = a_in.clone()
+    dashlib.dash_deform_mlp_fwd(lay, pts, to_dev(table), dashlib.Mlp(to_dev(params), 32, 64, 10),
+                                apply=(a_in, a_out))
+    G = dashlib.Gaussians(a_out[0:3], a_out[7:10], a_out[3:7], to_dev(g["opacity"]), to_dev(g["sh"]), 3)
+    img, _, _, _ = dashlib.dash_raster_fwd(_gpu_cam(dashlib, cam), G)
+    ridx, _ = oracle.compact(mask)
+    _, ref_attrs = oracle.deform_fwd(gg, oracle.Points(nc[0], nc[1], nc[2], t, idx=ridx, t_stride=0),
+                                     table.astype(np.float64), 64, 10, params.astype(np.float64), attrs)
+    ra = torch.tensor(ref_attrs)
+    ref, _, _ = oraster.render(cam, ra[0:3].T.contiguous(), ra[7:10].T.contiguous(), ra[3:7].T.contiguous(),
+                               torch.tensor(g["opacity"].astype(np.float64)), torch.tensor(g["sh"].astype(np.float64)),
+                               3)
+    _image_close(img.cpu().numpy(), ref.numpy())
+    moved = np.abs(ref_attrs[0:3] - attrs[0:3]).max()
+    assert moved > 1e-4                                   # the deformation did move the dynamic Gaussians
