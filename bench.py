@@ -819,7 +819,9 @@ def profile_case(n):
     """Small case for ncu captures: n dynamic Gaussians (no compaction), about
     1 GB on the device, two launches each of the encoder forward/backward, the
     fused forward/backward (the backward once more with the coordinate
-    gradient), the decomposition with its top-k mask, and one occupancy count."""
+    gradient), the decomposition with its top-k mask, one occupancy count, and
+    two render frames (1352 x 1014, 106.6k Gaussians) with the renderer's
+    backward."""
     import numpy as np
     import torch
     from paper_2507_19141_gb300 import dash, synth
@@ -852,6 +854,14 @@ def profile_case(n):
         _, norm, _ = dash.dash_decomp_fwd(lay3, pts.x, pts.y, pts.z, table3, dec, t=pts.t)
         dash.dash_topk_mask(norm, 50.0)
     dash.dash_hash4d_collision_stats(lay, pts)
+    # render frames at 1352 x 1014 with 106.6k Gaussians, and the renderer's backward
+    f = render_frame_setup(torch)
+    _, rws, cap, pairs = dash.dash_raster_fwd(f["cam"], f["G"], image=f["image"])
+    grads = {k: torch.zeros_like(getattr(f["G"], k)) for k in ("mean", "scale", "rot", "opacity", "sh")}
+    dimg = torch.randn_like(f["image"])
+    for _ in range(2):
+        render_frame(f, rws, cap, pairs)
+        dash.dash_raster_bwd(f["cam"], f["G"], dimg, rws, cap, grads)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": n, "delta_abs_mean": float(delta.abs().mean()),
                       "grad_abs_sum": float(tg.abs().sum())}))
