@@ -10,8 +10,9 @@
 //      Eq. 1 (alpha = sigma exp(power), power = -d^T Q d / 2, d = mean' -
 //      pixel) these become gradients of the screen mean, the conic Q and the
 //      opacity; the 0.99 clamp passes no gradient.  All lanes of a warp visit
-//      the same Gaussian together, so each value is summed over the warp
-//      before one atomic per warp.
+//      the same Gaussian together: warps none of whose pixels blended it
+//      skip it, the others sum the nine values over the warp with a
+//      reduce-scatter and add them with one atomic instruction.
 //   2. preprocess_bwd (thread per Gaussian): conic -> Sigma' -> (J, Sigma) ->
 //      camera-space mean -> world mean; Sigma = R S S^T R^T -> scale and the
 //      (normalised) quaternion; colour -> SH coefficients and, through the
@@ -24,10 +25,51 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ float warp_sum(float v) {
+// One halving step of a warp reduce-scatter: lanes whose `off` bit is clear
+// keep the first H of the M values (summed with their partner's), the others
+// the last M - H (padded with zero to H).  One shuffle per kept value.
+template <int M, int H>
+__device__ __forceinline__ void halve(float* a, unsigned lane, int off) {
+  const bool up = (lane & (unsigned)off) != 0u;
+  float b[H];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+  for (int i = 0; i < H; ++i) {
+    const float lo = a[i];
+    const float hi = i + H < M ? a[i + H] : 0.f;
+    b[i] = (up ? hi : lo) + __shfl_xor_sync(0xffffffffu, up ? lo : hi, off);
+  }
+#pragma unroll
+  for (int i = 0; i < H; ++i) a[i] = b[i];
+}
+
+// Sums 9 values over the warp with 12 shuffles (instead of 45 for nine
+// butterflies): afterwards an even lane l with scatter_index(l) >= 0 holds
+// the warp total of that value in v[0] (its odd neighbour holds a copy).
+__device__ __forceinline__ void warp_reduce_scatter9(float v[9], unsigned lane) {
+  halve<9, 5>(v, lane, 16);
+  halve<5, 3>(v, lane, 8);
+  halve<3, 2>(v, lane, 4);
+  halve<2, 1>(v, lane, 2);
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+// Which value lane `lane` ends up with: the halving steps' (size, half, bit)
+// replayed on the index range [start, start + size) this lane keeps; an upper
+// half may hold fewer real values than its padded width.  -1: padding only.
+__device__ __forceinline__ int scatter_index(unsigned lane) {
+  const int half[4] = {5, 3, 2, 1};
+  const unsigned bit[4] = {16u, 8u, 4u, 2u};
+  int start = 0, size = 9;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    if (lane & bit[s]) {
+      start += half[s];
+      size = size > half[s] ? size - half[s] : 0;
+    } else {
+      size = size < half[s] ? size : half[s];
+    }
+  }
+  return size >= 1 ? start : -1;
 }
 
 __global__ void __launch_bounds__(kTilePix) render_bwd_kernel(Cam c, long long n, const float* __restrict__ opacity,
@@ -62,6 +104,23 @@ __global__ void __launch_bounds__(kTilePix) render_bwd_kernel(Cam c, long long n
     g2 = dimage[2 * plane + pix];
   }
   const float bg_dot = c.bg[0] * g0 + c.bg[1] * g1 + c.bg[2] * g2;
+  // the gradient array this lane adds into after the warp's reduce-scatter
+  const unsigned lane = threadIdx.x & 31u;
+  const int red_k = scatter_index(lane);
+  const bool red_lane = (lane & 1u) == 0u && red_k >= 0;
+  float* red_ptr = nullptr;
+  switch (red_k) {
+    case 0: red_ptr = w.dmean2d; break;
+    case 1: red_ptr = w.dmean2d + n; break;
+    case 2: red_ptr = w.dconic; break;
+    case 3: red_ptr = w.dconic + n; break;
+    case 4: red_ptr = w.dconic + 2 * n; break;
+    case 5: red_ptr = dopacity; break;
+    case 6: red_ptr = w.dcolor; break;
+    case 7: red_ptr = w.dcolor + n; break;
+    case 8: red_ptr = w.dcolor + 2 * n; break;
+    default: break;
+  }
   float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;  // colour behind the current Gaussian
   float last_alpha = 0.f, lc0 = 0.f, lc1 = 0.f, lc2 = 0.f;
   for (int end = (int)todo; end > 0; end -= kTilePix) {
@@ -87,6 +146,7 @@ __global__ void __launch_bounds__(kTilePix) render_bwd_kernel(Cam c, long long n
       const uint32_t position = (uint32_t)(end - j);  // 1-based list position of this Gaussian
       float d_mx = 0.f, d_my = 0.f, d_ca = 0.f, d_cb = 0.f, d_cc = 0.f, d_op = 0.f, d_c0 = 0.f, d_c1 = 0.f,
             d_c2 = 0.f;
+      bool hit = false;
       if (position <= last) {
         const float dx = s_xy[j][0] - fx, dy = s_xy[j][1] - fy;
         const float ca = s_con[j][0], cb = s_con[j][1], cc = s_con[j][2];
@@ -95,6 +155,7 @@ __global__ void __launch_bounds__(kTilePix) render_bwd_kernel(Cam c, long long n
         const float raw = s_op[j] * G;
         const float alpha = fminf(kAlphaMax, raw);
         if (power <= 0.f && alpha >= kAlphaMin) {
+          hit = true;
           T = T / (1.f - alpha);  // transmittance in front of this Gaussian
           const float wgt = alpha * T;
           d_c0 = wgt * g0, d_c1 = wgt * g1, d_c2 = wgt * g2;
@@ -116,23 +177,12 @@ __global__ void __launch_bounds__(kTilePix) render_bwd_kernel(Cam c, long long n
           }
         }
       }
-      d_mx = warp_sum(d_mx), d_my = warp_sum(d_my);
-      d_ca = warp_sum(d_ca), d_cb = warp_sum(d_cb), d_cc = warp_sum(d_cc);
-      d_op = warp_sum(d_op);
-      d_c0 = warp_sum(d_c0), d_c1 = warp_sum(d_c1), d_c2 = warp_sum(d_c2);
-      if ((threadIdx.x & 31) == 0 && (d_mx != 0.f || d_my != 0.f || d_op != 0.f || d_c0 != 0.f || d_c1 != 0.f ||
-                                      d_c2 != 0.f || d_ca != 0.f || d_cb != 0.f || d_cc != 0.f)) {
-        const long long gid = s_gid[j];
-        atomicAdd(w.dmean2d + gid, d_mx);
-        atomicAdd(w.dmean2d + n + gid, d_my);
-        atomicAdd(w.dconic + gid, d_ca);
-        atomicAdd(w.dconic + n + gid, d_cb);
-        atomicAdd(w.dconic + 2 * n + gid, d_cc);
-        atomicAdd(dopacity + gid, d_op);
-        atomicAdd(w.dcolor + gid, d_c0);
-        atomicAdd(w.dcolor + n + gid, d_c1);
-        atomicAdd(w.dcolor + 2 * n + gid, d_c2);
-      }
+      // most warps see only part of a Gaussian's footprint: skip the
+      // reduction when no lane of this warp blended it
+      if (!__any_sync(0xffffffffu, hit)) continue;
+      float v[9] = {d_mx, d_my, d_ca, d_cb, d_cc, d_op, d_c0, d_c1, d_c2};
+      warp_reduce_scatter9(v, lane);
+      if (red_lane && v[0] != 0.f) atomicAdd(red_ptr + s_gid[j], v[0]);  // nine lanes, one instruction
     }
   }
 }
