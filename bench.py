@@ -599,6 +599,33 @@ def run_render(torch, stream):
     r["render_raster_bwd_ms"] = time_steps(torch, lambda: dash.dash_raster_bwd(f["cam"], f["G"], dimg, ws, cap, grads),
                                            20, stream)
     r["render_nan_free"] = bool(torch.isfinite(f["image"]).all().item())
+    # a training frame: the frame above + splatting backward + Eq. 10 backward
+    # + fused deformation backward with the Eq. 11 term (loss gradient stands
+    # in as N(0,1) per pixel; no optimiser step)
+    n = f["n"]
+    st = dash.deform_state(f["mlp"], n, "cuda")
+    d10 = torch.zeros((10, n), dtype=torch.float32, device="cuda")
+    tg = {"mean": d10[0:3], "rot": d10[3:7], "scale": d10[7:10], "opacity": grads["opacity"], "sh": grads["sh"]}
+    ddelta = torch.zeros((10, n), dtype=torch.float32, device="cuda")
+    table_grad = torch.zeros((f["lay"].total, 2), dtype=torch.float32, device="cuda")
+    mlp_grad = torch.zeros(f["mlp"].params.numel(), dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    smooth = (1.0, (1 / 2048, 1 / 2048, 1 / 2048), 1 / 300, loss)
+
+    def train_frame():
+        dash.dash_compact_dynamic(f["mask"], idx_out=f["idx"], count_out=f["cnt"], ws=f["cws"])
+        dash.dash_deform_mlp_fwd(f["lay"], f["pts"], f["table"], f["mlp"], delta_out=f["delta"], fwd_state=st,
+                                 apply=(f["attrs_in"], f["attrs_out"]))
+        dash.dash_raster_fwd(f["cam"], f["G"], image=f["image"], ws=ws, max_pairs=cap, pairs_needed=pairs)
+        dash.dash_raster_bwd(f["cam"], f["G"], dimg, ws, cap, tg)
+        dash.dash_deform_apply_bwd(f["pts"], d10, ddelta=ddelta)
+        dash.dash_deform_mlp_bwd(f["lay"], f["pts"], f["table"], f["mlp"], ddelta, table_grad, mlp_grad,
+                                 fwd_state=st, smooth=smooth)
+
+    for _ in range(3):
+        train_frame()
+    r["train_frame_ms"] = time_steps(torch, train_frame, 30, stream)
+    r["train_frames_per_s"] = 1e3 / r["train_frame_ms"]
     return r
 
 

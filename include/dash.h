@@ -256,6 +256,15 @@ int dash_deform_mlp_fwd(const dash_layout* layout, const dash_points* pts,
                         float* delta_out, void* fwd_state, const dash_apply* apply,
                         void* stream);
 
+/* Backward of the Eq. 10 update: for each compact point k (row
+ * i = idx[k], or k without a list) ddelta[j][k] = dattrs[j][i] for the
+ * d_out attribute rows (x, r, s for O = 10).  dattrs SoA [d_out][n_all]
+ * (e.g. the renderer's gradients at the deformed attributes), ddelta SoA
+ * [d_out][pts->n] as dash_deform_mlp_bwd takes it; rows past the device
+ * count are not written.  One launch. */
+int dash_deform_apply_bwd(const dash_points* pts, int d_out, const float* dattrs, int64_t n_all,
+                          float* ddelta, void* stream);
+
 /* ---------------------- a9-a11: fused deformation backward (+ Eq. 11) -- */
 
 /* Backward of dash_deform_mlp_fwd for upstream ddelta SoA [O][n] FP32:

@@ -136,6 +136,7 @@ _SIGS = {
     "dash_raster_bwd": ([_P, _P, _P, _P, _SZ, _I64, _P, _P], _I),
     "dash_hash4d_collision_stats": ([_P, _P, _P, _P, _SZ, _P], _I),
     "dash_deform_state_size": ([_P], _SZ),
+    "dash_deform_apply_bwd": ([_P, _I, _P, _I64, _P, _P], _I),
     "dash_deform_mlp_fwd": ([_P, _P, _P, _I, _P, _P, _P, _P, _P], _I),
     "dash_deform_mlp_bwd": ([_P, _P, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P], _I),
     "dash_batch_plan_create": ([_P, _P], _I),
@@ -405,6 +406,15 @@ def dash_deform_mlp_fwd(layout, pts, table, mlp: Mlp, delta_out=None, fwd_state=
                                     ctypes.byref(mlp.c), _ptr(delta_out), _ptr(fwd_state),
                                     None if ap is None else ctypes.byref(ap), _stream()), "dash_deform_mlp_fwd")
     return delta_out
+
+
+def dash_deform_apply_bwd(pts: Points, dattrs: torch.Tensor, ddelta=None):
+    """Gathers the dynamic rows of dattrs SoA [O][n_all] into ddelta SoA [O][pts.n]."""
+    O, n_all = dattrs.shape
+    ddelta = torch.zeros((O, pts.n), dtype=torch.float32, device=dattrs.device) if ddelta is None else ddelta
+    _check(_lib.dash_deform_apply_bwd(ctypes.byref(pts.c), O, _ptr(dattrs), n_all, _ptr(ddelta), _stream()),
+           "dash_deform_apply_bwd")
+    return ddelta
 
 
 def dash_deform_mlp_bwd(layout, pts, table, mlp: Mlp, ddelta, table_grad, mlp_grad, fwd_state=None, smooth=None,
