@@ -626,6 +626,12 @@ def run_render(torch, stream):
         train_frame()
     r["train_frame_ms"] = time_steps(torch, train_frame, 30, stream)
     r["train_frames_per_s"] = 1e3 / r["train_frame_ms"]
+    # the same frame captured once into a CUDA graph and replayed
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):          # captured on a side stream, replayed on this one
+        train_frame()
+    graph.replay()
+    r["train_frame_graph_ms"] = time_steps(torch, graph.replay, 30, stream)
     return r
 
 
