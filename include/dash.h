@@ -1,11 +1,23 @@
 /*
  * dash.h -- C ABI of libdash, the GB300 (sm_103a) implementation of the DASH
- * 4D-hash deformation path (arXiv 2507.19141, Sec. 4.2-4.3, Eqs. 7-11).
+ * 4D-hash deformation path (arXiv 2507.19141, Sec. 4.2-4.3, Eqs. 7-11) and
+ * of the steps on either side of it: the static/dynamic decomposition that
+ * produces the mask (Sec. 4.1, Eqs. 3-5), the hash-table occupancy behind
+ * the collision argument (Sec. 4.2, Sec. 5 "w/o dec"), and the 3D Gaussian
+ * splatting renderer the deformed Gaussians are drawn with (Sec. 3, Eqs. 1-2).
+ *
+ * Sections below, in order: status and layouts; utilities; compaction (a1);
+ * the 4-D encoder alone (a2-a6, a10); table occupancy; the fused
+ * deformation forward (a2-a8) and backward (a9-a11) with the Eq. 10
+ * backward; the decomposition (Eqs. 3-5); the renderer; the batched
+ * persistent form (a12); the plain FP32 baseline forms.
  *
  * Conventions shared by every entry point
  *   - All pointers are DEVICE pointers unless a comment says "host".
  *   - The caller owns all memory.  Nothing here allocates device memory
- *     except dash_batch_plan_create (the plan's descriptors and graph).
+ *     except dash_batch_plan_create (the plan's descriptors and graph);
+ *     scratch comes from caller workspaces sized by the *_workspace_size
+ *     calls.
  *   - Every call is asynchronous on the CUDA stream passed as `void* stream`
  *     (a cudaStream_t; NULL = the legacy default stream).  Nothing
  *     synchronises; a kernel fault surfaces at the caller's next sync.
@@ -285,7 +297,7 @@ int dash_deform_mlp_bwd(const dash_layout* layout, const dash_points* pts,
                         float* mlp_grad, const dash_smooth* smooth, float* coord_grad,
                         void* stream);
 
-/* ------------- decomposition producing the mask (Sec. 4.1, Eqs. 3-4) ---- */
+/* ------------- decomposition producing the mask (Sec. 4.1, Eqs. 3-5) ---- */
 
 /* 3-D layout of the position encoder G_3D: Eq. 7 spatial resolutions,
  * levels with (N+1)^3 <= T vertices indexed directly, others hashed by Eq. 8
