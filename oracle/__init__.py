@@ -138,6 +138,8 @@ def configure(lib):
     lib.orc_encode_coord_grad.restype = None
     lib.orc_collision_stats.argtypes = [G, P, P, P, P, i64, P, i64, P]
     lib.orc_collision_stats.restype = i32
+    lib.orc_decomp_bwd.argtypes = [G, P, P, P, i64, P, i32, P, P, P, ctypes.c_double, P, P]
+    lib.orc_decomp_bwd.restype = i32
     lib.orc_linear_motion.argtypes = [P, P, P, P, i64, P, i64, P]
     lib.orc_linear_motion.restype = None
     lib.orc_static_loss.argtypes = [P, P, i64]
@@ -353,6 +355,21 @@ def decomp_fwd(g: Grid, x, y, z, table, H, params):
                               _ptr(norm)) != 0:
         raise ValueError("unsupported MLP shape")
     return dp, norm
+
+
+def decomp_bwd(g: Grid, x, y, z, table, H, params, d_dp=None, mask=None, lambda_s=0.0):
+    """(table_grad [total][F], param_grad) of sum d_dp . dp + lambda_s L_s."""
+    xs, ys, zs = (_c(v, np.float32) for v in (x, y, z))
+    tab = _c(table, np.float64)
+    p = _c(params, np.float64)
+    dd = _c(d_dp, np.float64)
+    m = _c(mask, np.uint8)
+    tg = np.zeros((g.total, g.F), dtype=np.float64)
+    pg = np.zeros(len(p), dtype=np.float64)
+    if _load().orc_decomp_bwd(ctypes.byref(g), _ptr(xs), _ptr(ys), _ptr(zs), len(xs), _ptr(tab), H, _ptr(p), _ptr(dd),
+                              _ptr(m), float(lambda_s), _ptr(tg), _ptr(pg)) != 0:
+        raise ValueError("unsupported MLP shape")
+    return tg, pg
 
 
 def linear_motion(x, y, z, t, dp):

@@ -695,6 +695,79 @@ int orc_decomp_fwd(const orc_grid* g, const float* x, const float* y, const floa
   return 0;
 }
 
+/* Backward of the decomposition (Eqs. 3-5): for the loss
+ *   sum_i d_dp_i . dp_i + lambda_s * L_s,  L_s = (1/N_s) sum_{mask_i = 0} |dp_i|
+ * accumulates the gradients of the G_3D tables (table_grad [offset[L]][F])
+ * and of the packed W1, b1, W2, b2 (param_grad).  d_dp SoA [3][n] may be
+ * NULL (no upstream term); mask may be NULL (no L_s term).  The L_s term is
+ * lambda_s dp_i / (N_s |dp_i|) for static i with |dp_i| > 0.  Returns 0, or
+ * -1 for unsupported widths. */
+int orc_decomp_bwd(const orc_grid* g, const float* x, const float* y, const float* z, int64_t n,
+                   const double* table, int H, const double* params, const double* d_dp, const uint8_t* mask,
+                   double lambda_s, double* table_grad, double* param_grad) {
+  const int D = g->L * g->F, F = g->F;
+  if (D > 256 || H > 256) return -1;
+  const double* W1 = params;
+  const double* b1 = W1 + (size_t)H * D;
+  const double* W2 = b1 + H;
+  const double* b2 = W2 + (size_t)3 * H;
+  double* gW1 = param_grad;
+  double* gb1 = gW1 + (size_t)H * D;
+  double* gW2 = gb1 + H;
+  double* gb2 = gW2 + (size_t)3 * H;
+  int64_t n_s = 0;
+  if (mask != NULL)
+    for (int64_t i = 0; i < n; ++i) n_s += mask[i] == 0;
+  double f[256], z1[256], h[256], dz1[256], df[256];
+  for (int64_t i = 0; i < n; ++i) {
+    orc_encode3(g, x + i, y + i, z + i, 1, table, f);
+    for (int j = 0; j < H; ++j) {
+      double a = b1[j];
+      for (int k = 0; k < D; ++k) a += W1[(size_t)j * D + k] * f[k];
+      z1[j] = a;
+      h[j] = a > 0.0 ? a : 0.0;
+    }
+    double dp[3], s = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      double a = b2[c];
+      for (int k = 0; k < H; ++k) a += W2[(size_t)c * H + k] * h[k];
+      dp[c] = a;
+      s += a * a;
+    }
+    const double norm = sqrt(s);
+    double g_dp[3];
+    for (int c = 0; c < 3; ++c) {
+      g_dp[c] = d_dp != NULL ? d_dp[c * n + i] : 0.0;
+      if (mask != NULL && mask[i] == 0 && norm > 0.0) g_dp[c] += lambda_s * dp[c] / ((double)n_s * norm);
+    }
+    for (int c = 0; c < 3; ++c) {
+      gb2[c] += g_dp[c];
+      for (int k = 0; k < H; ++k) gW2[(size_t)c * H + k] += g_dp[c] * h[k];
+    }
+    for (int j = 0; j < H; ++j) {
+      double a = 0.0;
+      for (int c = 0; c < 3; ++c) a += W2[(size_t)c * H + j] * g_dp[c];
+      dz1[j] = z1[j] > 0.0 ? a : 0.0;
+      gb1[j] += dz1[j];
+      for (int k = 0; k < D; ++k) gW1[(size_t)j * D + k] += dz1[j] * f[k];
+    }
+    for (int k = 0; k < D; ++k) {
+      double a = 0.0;
+      for (int j = 0; j < H; ++j) a += W1[(size_t)j * D + k] * dz1[j];
+      df[k] = a;
+    }
+    const float p[3] = {orc_clamp01(x[i]), orc_clamp01(y[i]), orc_clamp01(z[i])};
+    for (int l = 0; l < g->L; ++l) {
+      uint32_t idx[8];
+      double w[8];
+      orc_cell3(g, l, p, idx, w);
+      for (int b = 0; b < 8; ++b)
+        for (int ff = 0; ff < F; ++ff) table_grad[(g->offset[l] + idx[b]) * F + ff] += w[b] * df[l * F + ff];
+    }
+  }
+  return 0;
+}
+
 /* Eq. 4: linear motion p(t) = p + t * dp of each Gaussian; p the coordinates
  * as given, t per Gaussian (t_stride 1) or one value for all (t_stride 0);
  * out SoA [3][n]. */

@@ -87,6 +87,18 @@ MUTATIONS = [
      "tau = s[m];",
      "tau = s[m + 1 < n ? m + 1 : m];",
      [("decomp:test_topk_mask_invariants", dict(n=1000, k=25.0)), ("decomp:test_topk_mask_ties_are_static", {})]),
+    ("decomposition backward: L_s term divided by n instead of N_s",
+     "g_dp[c] += lambda_s * dp[c] / ((double)n_s * norm);",
+     "g_dp[c] += lambda_s * dp[c] / ((double)n * norm);",
+     [("decomp:test_decomposition_backward_matches_finite_differences", {})]),
+    ("decomposition backward: ReLU mask dropped",
+     "dz1[j] = z1[j] > 0.0 ? a : 0.0;",
+     "dz1[j] = a;",
+     [("decomp:test_decomposition_backward_matches_finite_differences", {})]),
+    ("decomposition backward: W1 transposed for the feature gradient",
+     "for (int j = 0; j < H; ++j) a += W1[(size_t)j * D + k] * dz1[j];",
+     "for (int j = 0; j < H; ++j) a += W1[(size_t)(j % D) * D + (k % D)] * dz1[j];",
+     [("decomp:test_decomposition_backward_matches_finite_differences", {})]),
     ("G_3D dense stride N instead of N + 1",
      "int64_t R = N + 1;",
      "int64_t R = N;",

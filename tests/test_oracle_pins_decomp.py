@@ -135,3 +135,43 @@ def test_static_loss_special_cases():
         ls = oracle.static_loss(v, m)
         assert v[m == 0].min() <= ls <= tau
         assert abs(ls * (m == 0).sum() + v[m == 1].sum() - v.sum()) < 1e-9
+
+
+def _decomp_loss(g, x, y, z, table, H, params, d_dp, mask, lam):
+    dp, norm = oracle.decomp_fwd(g, x, y, z, table, H, params)
+    return float(np.sum(d_dp * dp)) + lam * oracle.static_loss(norm, mask)
+
+
+def test_decomposition_backward_matches_finite_differences():
+    g = oracle.layout3(4, 2, 12, 4, 32)
+    rng = np.random.default_rng(8)
+    n, D, H = 150, 8, 16
+    x, y, z = rng.random((3, n)).astype(np.float32)
+    table = rng.uniform(-1, 1, size=(g.total, 2))
+    params = rng.uniform(-0.5, 0.5, H * D + H + 3 * H + 3)
+    d_dp = rng.standard_normal((3, n))
+    _, norm = oracle.decomp_fwd(g, x, y, z, table, H, params)
+    mask, _ = oracle.topk_mask(norm, 50.0)
+    lam = 0.7
+    tg, pg = oracle.decomp_bwd(g, x, y, z, table, H, params, d_dp, mask, lam)
+    h = 1e-6
+    for j in rng.choice(len(params), size=25, replace=False):
+        pp, pm = params.copy(), params.copy()
+        pp[j] += h
+        pm[j] -= h
+        fd = (_decomp_loss(g, x, y, z, table, H, pp, d_dp, mask, lam) -
+              _decomp_loss(g, x, y, z, table, H, pm, d_dp, mask, lam)) / (2 * h)
+        assert abs(fd - pg[j]) <= 1e-6 * max(1.0, abs(fd)), (j, fd, pg[j])
+    touched = np.flatnonzero(np.abs(tg).sum(1) > 0)
+    for e in rng.choice(touched, size=20, replace=False):
+        for f in range(2):
+            tp, tm = table.copy(), table.copy()
+            tp[e, f] += h
+            tm[e, f] -= h
+            fd = (_decomp_loss(g, x, y, z, tp, H, params, d_dp, mask, lam) -
+                  _decomp_loss(g, x, y, z, tm, H, params, d_dp, mask, lam)) / (2 * h)
+            assert abs(fd - tg[e, f]) <= 1e-6 * max(1.0, abs(fd)), (e, f, fd, tg[e, f])
+    # the two terms add up
+    tg1, pg1 = oracle.decomp_bwd(g, x, y, z, table, H, params, d_dp, None, 0.0)
+    tg2, pg2 = oracle.decomp_bwd(g, x, y, z, table, H, params, None, mask, lam)
+    assert np.max(np.abs(tg1 + tg2 - tg)) < 1e-12 and np.max(np.abs(pg1 + pg2 - pg)) < 1e-12
