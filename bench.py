@@ -747,6 +747,17 @@ def run_decomp(torch, wl, stream):
     r["topk_gbs"] = TOPK_BYTES * n / (r["topk_ms"] / 1e3) / 1e9
     r["decomp_chain_gaussians_per_s"] = n / (r["decomp_chain_ms"] / 1e3)
     r["decomp_dynamic_count"] = int(cnt.item())
+    # training the decomposition: backward of an upstream dp gradient plus lambda_s L_s
+    tg3 = torch.zeros((lay3.total, 2), dtype=torch.float32, device="cuda")
+    pg3 = torch.zeros(dec.params.numel(), dtype=torch.float32, device="cuda")
+    d_dp = torch.randn((3, n), dtype=torch.float32, device="cuda")
+    bws = torch.empty(dash.dash_decomp_bwd_workspace_size(), dtype=torch.uint8, device="cuda")
+
+    def dec_bwd():
+        dash.dash_decomp_bwd(lay3, wl.x, wl.y, wl.z, table3, dec, tg3, pg3, d_dp=d_dp, mask=mask, lambda_s=1.0, ws=bws)
+
+    dec_bwd()
+    r["decomp_bwd_ms"] = time_steps(torch, dec_bwd, 20, stream)
     return r
 
 

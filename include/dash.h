@@ -318,6 +318,23 @@ int dash_decomp_fwd(const dash_layout* layout3, const float* x, const float* y, 
                     float* dp_out, float* norm_out, const float* t, int64_t t_stride,
                     float* pt_out, void* stream);
 
+/* Backward of the decomposition (Eqs. 3-5) for the loss
+ *   sum_i d_dp_i . dp_i + lambda_s * L_s,  L_s = (1/N_s) sum_{mask_i = 0} |dp_i|
+ * (Eq. 5 over the static Gaussians of `mask`, N_s their number):
+ * recomputes G_3D, phi_p and phi_l per Gaussian and ACCUMULATES the
+ * gradients of the G_3D tables (table_grad FP32 [offset[L]][F], 16-byte
+ * aligned, as the table) and of the packed W1, b1, W2, b2 (mlp_grad).
+ * d_dp SoA [3][n] may be NULL (no upstream term, e.g. from p(t) through
+ * Eq. 4: d_dp = t dL/dp(t)); mask may be NULL or lambda_s 0 (no L_s term);
+ * static Gaussians with |dp| = 0 contribute nothing.  Shapes as
+ * dash_decomp_fwd.  ws: dash_decomp_bwd_workspace_size() bytes.  2-3
+ * launches. */
+size_t dash_decomp_bwd_workspace_size(void);
+int dash_decomp_bwd(const dash_layout* layout3, const float* x, const float* y, const float* z,
+                    int64_t n, const void* table, int table_dtype, const dash_mlp* mlp,
+                    const float* d_dp, const uint8_t* mask, float lambda_s, float* table_grad,
+                    float* mlp_grad, void* ws, size_t ws_bytes, void* stream);
+
 /* Bytes of device workspace dash_topk_mask needs (a few hundred). */
 size_t dash_topk_workspace_size(void);
 

@@ -329,12 +329,14 @@ __device__ __forceinline__ void level_coord_grad(const Geom& g, int l, float4 p,
   acc.w = fmaf(gr[3], (float)nt, acc.w);
 }
 
-// grad[base + idx[b]] += w[b] * d for F = 2 FP32 gradients: a 16-byte
-// reduction when a pair's two entries form one aligned 16-byte group.
-__device__ __forceinline__ void scatter2_pairs(float* __restrict__ base, const uint32_t idx[16], const float w[16],
-                                               float d0, float d1) {
+// grad[base + idx[b]] += w[b] * d for F = 2 FP32 gradients over NC corners
+// (16 in 4-D, 8 in 3-D): a 16-byte reduction when a pair's two entries form
+// one aligned 16-byte group.
+template <int NC = 16>
+__device__ __forceinline__ void scatter2_pairs(float* __restrict__ base, const uint32_t* idx, const float* w, float d0,
+                                               float d1) {
 #pragma unroll
-  for (int p = 0; p < 8; ++p) {
+  for (int p = 0; p < NC / 2; ++p) {
     const uint32_t i0 = idx[2 * p], i1 = idx[2 * p + 1];
     const float u0 = w[2 * p] * d0, u1 = w[2 * p] * d1;
     const float v0 = w[2 * p + 1] * d0, v1 = w[2 * p + 1] * d1;

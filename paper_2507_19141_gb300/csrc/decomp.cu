@@ -129,6 +129,226 @@ __global__ void __launch_bounds__(kThreads) decomp_fwd_kernel(Geom g, const floa
   }
 }
 
+// ---------------------------------------------------------- backward ------
+// Gradients of  sum_i d_dp_i . dp_i + lambda_s L_s  (Eq. 5 over the static
+// Gaussians of `mask`) w.r.t. the G_3D tables and the packed W1, b1, W2, b2.
+// CTA of kBwdRows threads, one Gaussian each, persistent over tiles.  Per
+// tile every thread recomputes its encoding and decoder, back-propagates to
+// dL/df and scatters it into the tables; it leaves f, h, dz1 and the dp
+// gradient in shared memory, from which the CTA contracts the weight
+// gradients over the tile's Gaussians into per-thread register accumulators,
+// flushed with one atomic per weight and CTA at the end.
+constexpr int kBwdRows = 128;
+
+struct DecompBwdArgs {
+  Geom g;
+  const float* x;
+  const float* y;
+  const float* z;
+  long long n;
+  const void* table;
+  const float* params;
+  int D;
+  const float* d_dp;
+  const uint8_t* mask;
+  float lambda_s;
+  const unsigned long long* n_static;
+  float* table_grad;
+  float* mlp_grad;
+};
+
+__global__ void __launch_bounds__(kThreads) count_static_kernel(const uint8_t* __restrict__ mask, long long n,
+                                                                unsigned long long* out) {
+  unsigned int c = 0;
+  for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < n; i += (long long)gridDim.x * kThreads)
+    c += mask[i] == 0 ? 1u : 0u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c != 0u) atomicAdd(out, (unsigned long long)c);
+}
+
+template <typename TT, int F>
+__global__ void __launch_bounds__(kBwdRows) decomp_bwd_kernel(const __grid_constant__ DecompBwdArgs a) {
+  extern __shared__ __align__(16) float sm[];
+  const int D = a.D, r = threadIdx.x;
+  // weights: W1 transposed [D][64], b1 [64], W2 [3][64], b2 [3]; per tile:
+  // f [kBwdRows][D], h [kBwdRows][64], dz1 [kBwdRows][64], gdp [kBwdRows][4]
+  float* W1t = sm;
+  float* b1 = W1t + kHidden3 * D;
+  float* W2 = b1 + kHidden3;
+  float* b2 = W2 + 3 * kHidden3;
+  float* s_f = b2 + 4;
+  float* s_h = s_f + kBwdRows * D;
+  float* s_dz = s_h + kBwdRows * kHidden3;
+  float* s_g = s_dz + kBwdRows * kHidden3;
+  const int P = kHidden3 * D + kHidden3 + 3 * kHidden3 + 3;
+  for (int e = r; e < P; e += kBwdRows) {
+    const int dst = e < kHidden3 * D ? (e % D) * kHidden3 + e / D : e;
+    W1t[dst] = __ldg(a.params + e);
+  }
+  const TT* table = static_cast<const TT*>(a.table);
+  const float inv_ns = (a.mask != nullptr && *a.n_static > 0ull) ? 1.0f / (float)*a.n_static : 0.0f;
+  // this thread's weight-gradient outputs: dW1 rows j = r / 2, columns of one half
+  const int j1 = r >> 1;
+  const int kh = (D + 1) / 2, k0 = (r & 1) * kh;
+  const int nk = (k0 + kh <= D) ? kh : D - k0;
+  float acc1[32];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) acc1[q] = 0.f;
+  float acc_b1 = 0.f;         // b1[r] for r < 64
+  float acc2[2] = {0.f, 0.f}; // W2 entries r and r + 128 (of 192)
+  float acc_b2 = 0.f;         // b2[r] for r < 3
+  __syncthreads();
+  const long long ntiles = (a.n + kBwdRows - 1) / kBwdRows;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long i = tile * kBwdRows + r;
+    const bool valid = i < a.n;
+    float h[kHidden3];
+#pragma unroll
+    for (int j = 0; j < kHidden3; ++j) h[j] = b1[j];
+    float3 p = make_float3(0.f, 0.f, 0.f);
+    if (valid) p = make_float3(clamp01(__ldg(a.x + i)), clamp01(__ldg(a.y + i)), clamp01(__ldg(a.z + i)));
+    for (int l = 0; l < a.g.L; ++l) {
+      float f[F];
+#pragma unroll
+      for (int k = 0; k < F; ++k) f[k] = 0.f;
+      if (valid) {
+        uint32_t idx[8];
+        float w[8];
+        level_corners3(a.g, l, p, idx, w);
+        const TT* base = table + a.g.offset[l] * F;
+        if constexpr (F == 2) {
+          gather2_pairs<TT, 8>(base, idx, w, f);
+        } else {
+#pragma unroll
+          for (int b = 0; b < 8; ++b) {
+            float e[F];
+            load_entry<TT, F>(base + (size_t)idx[b] * F, e);
+#pragma unroll
+            for (int k = 0; k < F; ++k) f[k] = fmaf(w[b], e[k], f[k]);
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < F; ++k) {
+        const int col = l * F + k;
+        s_f[r * D + col] = f[k];
+        const float4* wc = reinterpret_cast<const float4*>(W1t + col * kHidden3);
+#pragma unroll
+        for (int j4 = 0; j4 < kHidden3 / 4; ++j4) {
+          const float4 wv = wc[j4];
+          h[4 * j4 + 0] = fmaf(wv.x, f[k], h[4 * j4 + 0]);
+          h[4 * j4 + 1] = fmaf(wv.y, f[k], h[4 * j4 + 1]);
+          h[4 * j4 + 2] = fmaf(wv.z, f[k], h[4 * j4 + 2]);
+          h[4 * j4 + 3] = fmaf(wv.w, f[k], h[4 * j4 + 3]);
+        }
+      }
+    }
+    // phi_l, the dp gradient (upstream + Eq. 5), and back through phi_l
+    float dp[3], s = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float v = b2[c];
+#pragma unroll
+      for (int j = 0; j < kHidden3; ++j) v = fmaf(W2[c * kHidden3 + j], fmaxf(h[j], 0.f), v);
+      dp[c] = v;
+      s = fmaf(v, v, s);
+    }
+    const float norm = sqrtf(s);
+    float gd[3] = {0.f, 0.f, 0.f};
+    if (valid) {
+      const bool stat = a.mask != nullptr && a.mask[i] == 0 && norm > 0.f;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        gd[c] = a.d_dp != nullptr ? __ldg(a.d_dp + (long long)c * a.n + i) : 0.f;
+        if (stat) gd[c] = fmaf(a.lambda_s * inv_ns, dp[c] / norm, gd[c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) s_g[r * 4 + c] = gd[c];
+    // h -> relu(h) kept for dW2; dz1 = (W2^T gd) * [z1 > 0] kept for dW1, db1
+#pragma unroll
+    for (int j = 0; j < kHidden3; ++j) {
+      const float dh = W2[j] * gd[0] + W2[kHidden3 + j] * gd[1] + W2[2 * kHidden3 + j] * gd[2];
+      const float dz = h[j] > 0.f ? dh : 0.f;
+      s_h[r * kHidden3 + j] = fmaxf(h[j], 0.f);
+      s_dz[r * kHidden3 + j] = dz;
+      h[j] = dz;  // h now holds dz1
+    }
+    // dL/df = W1^T dz1, scattered into the tables level by level
+    if (valid) {
+      for (int l = 0; l < a.g.L; ++l) {
+        float df[F];
+#pragma unroll
+        for (int k = 0; k < F; ++k) {
+          const float4* wc = reinterpret_cast<const float4*>(W1t + (l * F + k) * kHidden3);
+          float v = 0.f;
+#pragma unroll
+          for (int j4 = 0; j4 < kHidden3 / 4; ++j4) {
+            const float4 wv = wc[j4];
+            v = fmaf(wv.x, h[4 * j4], v);
+            v = fmaf(wv.y, h[4 * j4 + 1], v);
+            v = fmaf(wv.z, h[4 * j4 + 2], v);
+            v = fmaf(wv.w, h[4 * j4 + 3], v);
+          }
+          df[k] = v;
+        }
+        uint32_t idx[8];
+        float w[8];
+        level_corners3(a.g, l, p, idx, w);
+        float* gbase = a.table_grad + a.g.offset[l] * F;
+        if constexpr (F == 2) {
+          scatter2_pairs<8>(gbase, idx, w, df[0], df[1]);
+        } else {
+#pragma unroll
+          for (int b = 0; b < 8; ++b) {
+            float* e = gbase + (size_t)idx[b] * F;
+            if constexpr (F == 1) {
+              atomicAdd(e, w[b] * df[0]);
+            } else {
+#pragma unroll
+              for (int k = 0; k < F; k += 4)
+                red_add_v4(e + k, w[b] * df[k], w[b] * df[k + 1], w[b] * df[k + 2], w[b] * df[k + 3]);
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // weight gradients of this tile (rows of invalid threads are zero)
+    for (int g_ = 0; g_ < kBwdRows; ++g_) {
+      const float dz = s_dz[g_ * kHidden3 + j1];
+      const float* fr = s_f + g_ * D + k0;
+#pragma unroll
+      for (int q = 0; q < 32; ++q)
+        if (q < nk) acc1[q] = fmaf(dz, fr[q], acc1[q]);
+      if (r < kHidden3) acc_b1 += s_dz[g_ * kHidden3 + r];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int e = r + u * kBwdRows;  // W2 entry e = c * 64 + j
+        if (e < 3 * kHidden3) acc2[u] = fmaf(s_g[g_ * 4 + e / kHidden3], s_h[g_ * kHidden3 + (e % kHidden3)], acc2[u]);
+      }
+      if (r < 3) acc_b2 += s_g[g_ * 4 + r];
+    }
+    __syncthreads();
+  }
+  // flush: W1 [64][D], b1 [64], W2 [3][64], b2 [3]
+  float* gW1 = a.mlp_grad;
+  float* gb1 = gW1 + kHidden3 * D;
+  float* gW2 = gb1 + kHidden3;
+  float* gb2 = gW2 + 3 * kHidden3;
+#pragma unroll
+  for (int q = 0; q < 32; ++q)
+    if (q < nk && acc1[q] != 0.f) atomicAdd(gW1 + j1 * D + k0 + q, acc1[q]);
+  if (r < kHidden3 && acc_b1 != 0.f) atomicAdd(gb1 + r, acc_b1);
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int e = r + u * kBwdRows;
+    if (e < 3 * kHidden3 && acc2[u] != 0.f) atomicAdd(gW2 + e, acc2[u]);
+  }
+  if (r < 3 && acc_b2 != 0.f) atomicAdd(gb2 + r, acc_b2);
+}
+
 // ----------------------------------------------------------- radix select --
 // State (device workspace): hist[256] | prefix | prefix_mask | rank | pad.
 struct TopkState {
@@ -329,6 +549,84 @@ int dash_decomp_fwd(const dash_layout* layout, const float* x, const float* y, c
   }
 #undef DASH_DECOMP_LAUNCH
   return launch_status("decomp_fwd_kernel");
+}
+
+size_t dash_decomp_bwd_workspace_size(void) { return 256; }
+
+int dash_decomp_bwd(const dash_layout* layout, const float* x, const float* y, const float* z, int64_t n,
+                    const void* table, int table_dtype, const dash_mlp* mlp, const float* d_dp, const uint8_t* mask,
+                    float lambda_s, float* table_grad, float* mlp_grad, void* ws, size_t ws_bytes, void* stream) {
+  using namespace dash;
+  if (layout == nullptr || layout->dims != 3) return fail(DASH_ERR_INVALID_ARG, "needs a 3-D layout (dash_hash3d_layout)");
+  dash_layout as4 = *layout;
+  as4.dims = 0;
+  for (int l = 0; l < as4.L; ++l) as4.res_t[l] = 1;
+  DecompBwdArgs a;
+  if (int s = make_geom(&as4, &a.g)) return s;
+  const int D = a.g.L * a.g.F;
+  if (mlp == nullptr || mlp->params == nullptr) return fail(DASH_ERR_INVALID_ARG, "mlp/params is NULL");
+  if (mlp->d_in != D || mlp->d_hidden != kHidden3 || mlp->d_out != 3)
+    return fail(DASH_ERR_UNSUPPORTED, "decomposition MLP must be %d -> 64 -> 3", D);
+  if (D > 64) return fail(DASH_ERR_UNSUPPORTED, "L*F=%d > 64", D);
+  if (n < 0 || n > 0x7FFFFFFFll) return fail(DASH_ERR_UNSUPPORTED, "n outside [0, 2^31)");
+  if (ws == nullptr || ws_bytes < dash_decomp_bwd_workspace_size())
+    return fail(DASH_ERR_WORKSPACE, "workspace of %zu bytes, %zu needed", ws_bytes, dash_decomp_bwd_workspace_size());
+  if (n == 0) return DASH_OK;
+  if (x == nullptr || y == nullptr || z == nullptr || table == nullptr || table_grad == nullptr || mlp_grad == nullptr)
+    return fail(DASH_ERR_INVALID_ARG, "NULL argument");
+  if ((reinterpret_cast<uintptr_t>(table) & 15u) != 0 || (reinterpret_cast<uintptr_t>(table_grad) & 15u) != 0)
+    return fail(DASH_ERR_INVALID_ARG, "table and table_grad must be 16-byte aligned");
+  cudaStream_t st = as_stream(stream);
+  a.x = x, a.y = y, a.z = z, a.n = n;
+  a.table = table;
+  a.params = mlp->params;
+  a.D = D;
+  a.d_dp = d_dp;
+  a.mask = lambda_s != 0.0f ? mask : nullptr;
+  a.lambda_s = lambda_s;
+  a.n_static = static_cast<const unsigned long long*>(ws);
+  a.table_grad = table_grad;
+  a.mlp_grad = mlp_grad;
+  if (a.mask != nullptr) {
+    if (int s = cuda_status(cudaMemsetAsync(ws, 0, 8, st), "cudaMemsetAsync")) return s;
+    long long blocks = (n + kThreads - 1) / kThreads;
+    const long long cap = 4ll * sm_count();
+    blocks = blocks < cap ? blocks : cap;
+    count_static_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(a.mask, n, static_cast<unsigned long long*>(ws));
+    if (int s = launch_status("count_static_kernel")) return s;
+  }
+  const size_t smem = sizeof(float) * ((size_t)kHidden3 * D + kHidden3 + 3 * kHidden3 + 4 +
+                                       (size_t)kBwdRows * (D + 2 * kHidden3 + 4));
+  const long long ntiles = (n + kBwdRows - 1) / kBwdRows;
+  long long grid = 2ll * sm_count();
+  grid = ntiles < grid ? ntiles : grid;
+#define DASH_DECOMP_BWD(TT, FF)                                                                                     \
+  {                                                                                                                 \
+    auto kern = decomp_bwd_kernel<TT, FF>;                                                                          \
+    if (int s = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),     \
+                            "cudaFuncSetAttribute(decomp_bwd)"))                                                     \
+      return s;                                                                                                     \
+    kern<<<(unsigned)grid, kBwdRows, smem, st>>>(a);                                                                \
+  }
+  if (table_dtype == DASH_F16) {
+    switch (a.g.F) {
+      case 1: DASH_DECOMP_BWD(__half, 1) break;
+      case 2: DASH_DECOMP_BWD(__half, 2) break;
+      case 4: DASH_DECOMP_BWD(__half, 4) break;
+      default: DASH_DECOMP_BWD(__half, 8) break;
+    }
+  } else if (table_dtype == DASH_F32) {
+    switch (a.g.F) {
+      case 1: DASH_DECOMP_BWD(float, 1) break;
+      case 2: DASH_DECOMP_BWD(float, 2) break;
+      case 4: DASH_DECOMP_BWD(float, 4) break;
+      default: DASH_DECOMP_BWD(float, 8) break;
+    }
+  } else {
+    return fail(DASH_ERR_UNSUPPORTED, "table_dtype %d (F32 or F16)", table_dtype);
+  }
+#undef DASH_DECOMP_BWD
+  return launch_status("decomp_bwd_kernel");
 }
 
 size_t dash_topk_workspace_size(void) { return (sizeof(dash::TopkState) + 255) / 256 * 256; }

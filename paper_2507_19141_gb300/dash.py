@@ -148,6 +148,8 @@ _SIGS = {
     "dash_hash3d_layout": ([_P, _P], _I),
     "dash_decomp_fwd": ([_P, _P, _P, _P, _I64, _P, _I, _P, _P, _P, _P, _I64, _P, _P], _I),
     "dash_topk_workspace_size": ([], _SZ),
+    "dash_decomp_bwd_workspace_size": ([], _SZ),
+    "dash_decomp_bwd": ([_P, _P, _P, _P, _I64, _P, _I, _P, _P, _P, ctypes.c_float, _P, _P, _P, _SZ, _P], _I),
     "dash_topk_mask": ([_P, _I64, ctypes.c_double, _P, _P, _P, _P, _SZ, _P], _I),
     "dash_plain_hash4d_fwd": ([_P, _P, _P, _P, _P], _I),
     "dash_plain_hash4d_bwd": ([_P, _P, _P, _P, _P], _I),
@@ -460,6 +462,20 @@ def dash_decomp_fwd(layout3: dash_layout, x, y, z, table, mlp: "Mlp", dp_out=Non
                                 _stream()), "dash_decomp_fwd")
     dp = dp_out if want_dp else None
     return (dp, norm_out) if t is None else (dp, norm_out, pt_out)
+
+
+def dash_decomp_bwd_workspace_size() -> int:
+    return int(_lib.dash_decomp_bwd_workspace_size())
+
+
+def dash_decomp_bwd(layout3: dash_layout, x, y, z, table, mlp: "Mlp", table_grad, mlp_grad, d_dp=None, mask=None,
+                    lambda_s=0.0, ws=None):
+    """Accumulates the G_3D table and decoder gradients of sum d_dp . dp + lambda_s L_s."""
+    ws = torch.empty(dash_decomp_bwd_workspace_size(), dtype=torch.uint8, device=x.device) if ws is None else ws
+    _check(_lib.dash_decomp_bwd(ctypes.byref(layout3), _ptr(x), _ptr(y), _ptr(z), x.numel(), _ptr(table),
+                                _DTYPE_CODE[table.dtype], ctypes.byref(mlp.c), _ptr(d_dp), _ptr(mask), float(lambda_s),
+                                _ptr(table_grad), _ptr(mlp_grad), _ptr(ws), ws.numel(), _stream()), "dash_decomp_bwd")
+    return table_grad, mlp_grad
 
 
 def dash_topk_workspace_size() -> int:

@@ -151,3 +151,29 @@ def test_decomposition_feeds_compaction_and_deformation(dashlib):
     ref = oracle.deform_fwd(g4, oracle.Points(x, y, z, t, idx=ridx), table.astype(np.float64), 64, 10,
                             params.astype(np.float64))
     assert rel_err(delta[:, :rcnt].cpu().numpy(), ref) < 1e-3
+
+
+@pytest.mark.parametrize("tdtype,with_up,with_ls", [(np.float16, True, True), (np.float32, True, False),
+                                                    (np.float16, False, True)])
+def test_decomposition_backward_matches_oracle(dashlib, tdtype, with_up, with_ls):
+    rng = np.random.default_rng(76)
+    n = 9_999
+    g, (x, y, z), table, params = _decomp_inputs(rng, n, tdtype)
+    lay = dashlib.dash_hash3d_layout(**G3)
+    mlp = dashlib.Mlp(to_dev(params), 32, 64, 3)
+    xd, yd, zd, td = to_dev(x), to_dev(y), to_dev(z), to_dev(table)
+    _, norm = dashlib.dash_decomp_fwd(lay, xd, yd, zd, td, mlp)
+    mask, _ = dashlib.dash_topk_mask(norm, 40.0)
+    d_dp = rng.standard_normal((3, n)).astype(np.float32)
+    tg = torch.zeros((g.total, 2), device="cuda")
+    pg = torch.zeros(params.size, device="cuda")
+    dashlib.dash_decomp_bwd(lay, xd, yd, zd, td, mlp, tg, pg, d_dp=to_dev(d_dp) if with_up else None,
+                            mask=mask if with_ls else None, lambda_s=0.8 if with_ls else 0.0)
+    rtg, rpg = oracle.decomp_bwd(g, x, y, z, table.astype(np.float64), 64, params.astype(np.float64),
+                                 d_dp.astype(np.float64) if with_up else None,
+                                 mask.cpu().numpy() if with_ls else None, 0.8 if with_ls else 0.0)
+    assert rel_err(tg.cpu().numpy(), rtg) < 1e-4
+    bounds = np.cumsum([0, 64 * 32, 64, 3 * 64, 3])
+    pgn = pg.cpu().numpy()
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        assert rel_err(pgn[a:b], rpg[a:b]) < 1e-4, (a, b, rel_err(pgn[a:b], rpg[a:b]))
