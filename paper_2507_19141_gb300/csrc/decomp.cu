@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(kBwdRows) decomp_bwd_kernel(const __grid_const
   float* b1 = W1t + kHidden3 * D;
   float* W2 = b1 + kHidden3;
   float* b2 = W2 + 3 * kHidden3;
-  float* s_f = b2 + 4;
+  float* s_f = b2 + 4;  // 64 D + 64 + 192 + 4 floats: a multiple of 4 (16-byte aligned rows for D % 4 == 0)
   float* s_h = s_f + kBwdRows * D;
   float* s_dz = s_h + kBwdRows * kHidden3;
   float* s_g = s_dz + kBwdRows * kHidden3;
@@ -316,12 +316,26 @@ __global__ void __launch_bounds__(kBwdRows) decomp_bwd_kernel(const __grid_const
     }
     __syncthreads();
     // weight gradients of this tile (rows of invalid threads are zero)
+    const bool vec4 = (D & 7) == 0;  // f rows and this thread's half start on 16-byte boundaries
     for (int g_ = 0; g_ < kBwdRows; ++g_) {
       const float dz = s_dz[g_ * kHidden3 + j1];
       const float* fr = s_f + g_ * D + k0;
+      if (vec4) {
 #pragma unroll
-      for (int q = 0; q < 32; ++q)
-        if (q < nk) acc1[q] = fmaf(dz, fr[q], acc1[q]);
+        for (int q4 = 0; q4 < 8; ++q4) {
+          if (4 * q4 < nk) {
+            const float4 fv = *reinterpret_cast<const float4*>(fr + 4 * q4);
+            acc1[4 * q4 + 0] = fmaf(dz, fv.x, acc1[4 * q4 + 0]);
+            acc1[4 * q4 + 1] = fmaf(dz, fv.y, acc1[4 * q4 + 1]);
+            acc1[4 * q4 + 2] = fmaf(dz, fv.z, acc1[4 * q4 + 2]);
+            acc1[4 * q4 + 3] = fmaf(dz, fv.w, acc1[4 * q4 + 3]);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 32; ++q)
+          if (q < nk) acc1[q] = fmaf(dz, fr[q], acc1[q]);
+      }
       if (r < kHidden3) acc_b1 += s_dz[g_ * kHidden3 + r];
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
