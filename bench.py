@@ -863,7 +863,8 @@ def profile_case(n):
     """Small case for ncu captures: n dynamic Gaussians (no compaction), about
     1 GB on the device, two launches each of the encoder forward/backward, the
     fused forward/backward (the backward once more with the coordinate
-    gradient), the decomposition with its top-k mask, one occupancy count, and
+    gradient), the decomposition with its top-k mask and its backward, one
+    occupancy count, and
     two render frames (1352 x 1014, 106.6k Gaussians) with the renderer's
     backward."""
     import numpy as np
@@ -889,6 +890,9 @@ def profile_case(n):
     k = 1 / np.sqrt(32)
     dec = dash.Mlp(dev(rng.uniform(-k, k, 64 * 32 + 64 + 3 * 64 + 3).astype(np.float32)), 32, 64, 3)
     cg = torch.empty((4, n), device="cuda")
+    tg3 = torch.zeros((lay3.total, 2), dtype=torch.float32, device="cuda")
+    pg3 = torch.zeros(dec.params.numel(), dtype=torch.float32, device="cuda")
+    d_dp = torch.randn((3, n), dtype=torch.float32, device="cuda")
     for _ in range(2):
         dash.dash_hash4d_fwd(lay, pts, table, torch.bfloat16, out=feat)
         dash.dash_hash4d_bwd(lay, pts, dfeat, tg)
@@ -896,7 +900,8 @@ def profile_case(n):
         dash.dash_deform_mlp_bwd(lay, pts, table, mlp, dd, tg, pg, fwd_state=state)
         dash.dash_deform_mlp_bwd(lay, pts, table, mlp, dd, tg, pg, fwd_state=state, coord_grad=cg)
         _, norm, _ = dash.dash_decomp_fwd(lay3, pts.x, pts.y, pts.z, table3, dec, t=pts.t)
-        dash.dash_topk_mask(norm, 50.0)
+        mask, _ = dash.dash_topk_mask(norm, 50.0)
+        dash.dash_decomp_bwd(lay3, pts.x, pts.y, pts.z, table3, dec, tg3, pg3, d_dp=d_dp, mask=mask, lambda_s=1.0)
     dash.dash_hash4d_collision_stats(lay, pts)
     # render frames at 1352 x 1014 with 106.6k Gaussians, and the renderer's backward
     f = render_frame_setup(torch)
