@@ -28,6 +28,7 @@ int sm_count();
 // Kernel-form options (dash_set_option).
 extern int g_opt_fwd_form;
 extern int g_opt_bwd_form;
+extern int g_opt_scatter_form;
 
 // ------------------------------------------------ kernel-side geometry ----
 // Level layout in the form the kernels read it (by-value kernel argument).
@@ -137,6 +138,45 @@ __device__ __forceinline__ void level_corners(const Geom& g, int l, float4 p, ui
     v *= (b & 4) ? fz : wz0;
     v *= (b & 8) ? ft : wt0;
     w[b] = v;
+  }
+}
+
+// The 8 corners of level l around p whose x bit is xb (corner b = xb | 2q,
+// q = 0..7 over the y, z, t bits), with the index and weight arithmetic of
+// level_corners, so that idx[q], w[q] equal its idx[xb | 2q], w[xb | 2q] bit
+// for bit.
+__device__ __forceinline__ void level_corners_x(const Geom& g, int l, float4 p, uint32_t xb, uint32_t idx[8],
+                                                float w[8]) {
+  const int ns = g.res_s[l], nt = g.res_t[l];
+  int ix, iy, iz, it;
+  float fx, fy, fz, ft;
+  axis_cell(p.x, ns, ix, fx);
+  axis_cell(p.y, ns, iy, fy);
+  axis_cell(p.z, ns, iz, fz);
+  axis_cell(p.w, nt, it, ft);
+  if ((g.dense_bits >> l) & 1u) {
+    const uint32_t R = (uint32_t)ns + 1u;
+    const uint32_t base = (uint32_t)ix + R * ((uint32_t)iy + R * ((uint32_t)iz + R * (uint32_t)it)) + xb;
+    const uint32_t sy = R, sz = R * R, st = R * R * R;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) idx[q] = base + (q & 1) * sy + ((q >> 1) & 1) * sz + ((q >> 2) & 1) * st;
+  } else {
+    const uint32_t hx = (uint32_t)ix * g.primes[0] + (xb ? g.primes[0] : 0u);
+    const uint32_t hy0 = (uint32_t)iy * g.primes[1], hy1 = hy0 + g.primes[1];
+    const uint32_t hz0 = (uint32_t)iz * g.primes[2], hz1 = hz0 + g.primes[2];
+    const uint32_t ht0 = (uint32_t)it * g.primes[3], ht1 = ht0 + g.primes[3];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      idx[q] = (hx ^ (q & 1 ? hy1 : hy0) ^ (q & 2 ? hz1 : hz0) ^ (q & 4 ? ht1 : ht0)) & g.mask;
+  }
+  const float wx = xb ? fx : 1.0f - fx, wy0 = 1.0f - fy, wz0 = 1.0f - fz, wt0 = 1.0f - ft;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    float v = wx;
+    v *= (q & 1) ? fy : wy0;
+    v *= (q & 2) ? fz : wz0;
+    v *= (q & 4) ? ft : wt0;
+    w[q] = v;
   }
 }
 

@@ -53,6 +53,7 @@ struct BwdArgs {
   float* loss_out;
   float* coord_grad;  // optional SoA [4][n_cap]: d loss / d(x, y, z, t)
   unsigned int* flags;
+  int paired;  // F = 2 scatter by lane pairs (no Eq. 11 term, no coordinate gradient)
   uint32_t off_w2, off_w3, off_f, off_h1, off_x, off_g3, off_ring, off_bar;
 };
 
@@ -102,6 +103,42 @@ __device__ __forceinline__ void scatter_level(float* __restrict__ grad, long lon
     } else {
 #pragma unroll
       for (int f = 0; f < F; f += 4) red_add_v4(e + f, w[b] * d[f], w[b] * d[f + 1], w[b] * d[f + 2], w[b] * d[f + 3]);
+    }
+  }
+}
+
+// F = 2 table-gradient scatter of two Gaussians by a lane pair.  Lane xb of
+// the pair (xb = lane & 1) issues, for both Gaussians A (the even lane's) and
+// B (the odd lane's), the reductions of the corners whose x bit is xb, so an
+// x-neighbour pair's two reductions leave in the same warp instruction; the
+// L2 then serves them as one operation when they share a 32-byte sector
+// (three pairs in four: always when the lower x coordinate is even, half the
+// time otherwise), where one lane issuing both would cost two whenever they
+// do not form one aligned 16-byte group.  p and df are this lane's own
+// Gaussian's; va / vb say whether A / B exist; pm names the pair's lanes.
+__device__ __forceinline__ void scatter_levels_paired(const Geom& g, float* __restrict__ grad, float4 p,
+                                                      const float* df, uint32_t xb, bool va, bool vb,
+                                                      unsigned int pm) {
+  float4 q;
+  q.x = __shfl_xor_sync(pm, p.x, 1);
+  q.y = __shfl_xor_sync(pm, p.y, 1);
+  q.z = __shfl_xor_sync(pm, p.z, 1);
+  q.w = __shfl_xor_sync(pm, p.w, 1);
+  const float4 pa = xb ? q : p, pb = xb ? p : q;
+  for (int l = 0; l < g.L; ++l) {
+    const float d0 = df[2 * l], d1 = df[2 * l + 1];
+    const float e0 = __shfl_xor_sync(pm, d0, 1), e1 = __shfl_xor_sync(pm, d1, 1);
+    const float a0 = xb ? e0 : d0, a1 = xb ? e1 : d1;
+    const float b0 = xb ? d0 : e0, b1 = xb ? d1 : e1;
+    uint32_t ia[8], ib[8];
+    float wa[8], wb[8];
+    level_corners_x(g, l, pa, xb, ia, wa);
+    level_corners_x(g, l, pb, xb, ib, wb);
+    float* base = grad + g.offset[l] * 2;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      if (va) red_add_v2(base + (size_t)ia[c] * 2, wa[c] * a0, wa[c] * a1);
+      if (vb) red_add_v2(base + (size_t)ib[c] * 2, wb[c] * b0, wb[c] * b1);
     }
   }
 }
@@ -792,6 +829,15 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_bwd_ws_kernel(const
       const float* stage = ring + (size_t)s * stage_floats;
       for (int k = 0; k < a.D; ++k) df[k] = stage[k * kRows + r];
       tc::mbar_arrive(tc::smem_addr(&empty[s]));
+      if constexpr (F == 2) {
+        if (a.paired) {
+          const long long row_a = row - (r & 1);  // the pair's even row
+          if (row_a >= n) continue;                // both lanes of the pair leave together
+          scatter_levels_paired(a.g, a.table_grad, p, df, (uint32_t)(r & 1), true, row_a + 1 < n,
+                                3u << (r & 30));
+          continue;
+        }
+      }
       if (row >= n) continue;
       float4 cg = make_float4(0.f, 0.f, 0.f, 0.f);
       for (int l = 0; l < a.g.L; ++l) {
@@ -988,6 +1034,7 @@ extern "C" int dash_deform_mlp_bwd(const dash_layout* layout, const dash_points*
   if (coord_grad != nullptr && a.lambda_r != 0.0f)
     return fail(DASH_ERR_UNSUPPORTED, "coordinate gradients with the Eq. 11 term on are not supported");
   a.coord_grad = coord_grad;
+  a.paired = (g_opt_scatter_form == 0 && a.g.F == 2 && a.lambda_r == 0.0f && coord_grad == nullptr) ? 1 : 0;
   a.flags = bwd_flags_ptr();
   if (a.flags == nullptr) return fail(DASH_ERR_CUDA, "cannot resolve the device flag word");
   cudaStream_t st = as_stream(stream);

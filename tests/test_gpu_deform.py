@@ -291,3 +291,44 @@ def test_backward_kernel_forms_agree(dashlib, smooth):
                                          params.astype(np.float64), dd.astype(np.float64), lam, es, et)
         for tg_, pg_, l_ in res:
             assert rel_err(tg_, rtg) < 1e-2 and rel_err(pg_, rpg) < 1e-2 and abs(l_ - rl) < 1e-2 * abs(rl)
+
+
+@pytest.mark.parametrize("n_all,n,tdtype,grid", [
+    (50_000, 20_001, np.float16, synth.PAPER_GRID),   # odd count: the last lane pair has one Gaussian
+    (4_000, 1_283, np.float32, synth.PAPER_GRID),
+    (2_000, 129, np.float16, synth.TINY_GRID),        # all levels hashed, tail of one row past a tile
+    (10, 1, np.float16, synth.PAPER_GRID),
+])
+def test_backward_scatter_forms_agree_with_oracle(dashlib, n_all, n, tdtype, grid):
+    """The lane-paired and the per-lane table-gradient scatter of the
+    warp-specialised backward: same sums up to the order of the additions,
+    both against the oracle (index list, device count, ragged tails)."""
+    mlpc = synth.PAPER_MLP if grid is synth.PAPER_GRID else synth.TINY_MLP
+    g, coords, idx, table, params, dd = _case(grid, mlpc, n, tdtype, seed=61 + n, n_all=n_all)
+    lay = dashlib.layout_from(grid)
+    x, y, z, t = (to_dev(c) for c in coords)
+    cnt = torch.tensor([n], dtype=torch.int64, device="cuda")
+    pts = dashlib.Points(x, y, z, t, idx=to_dev(idx), n=n, n_dev=cnt)
+    mlp = dashlib.Mlp(to_dev(params), mlpc.d_in, mlpc.d_hidden, mlpc.d_out)
+    tab = to_dev(table)
+    st = dashlib.deform_state(mlp, n, "cuda")
+    dashlib.dash_deform_mlp_fwd(lay, pts, tab, mlp, fwd_state=st)
+    res = []
+    old = dashlib.dash_get_option(dashlib.OPT_SCATTER_FORM)
+    try:
+        for form in (0, 1):
+            dashlib.dash_set_option(dashlib.OPT_SCATTER_FORM, form)
+            tg = torch.zeros((g.total, grid.F), dtype=torch.float32, device="cuda")
+            pg = torch.zeros(mlpc.n_params, dtype=torch.float32, device="cuda")
+            dashlib.dash_deform_mlp_bwd(lay, pts, tab, mlp, to_dev(dd), tg, pg, fwd_state=st)
+            res.append((tg.cpu().numpy(), pg.cpu().numpy()))
+    finally:
+        dashlib.dash_set_option(dashlib.OPT_SCATTER_FORM, old)
+    assert rel_err(res[0][0], res[1][0]) < 1e-6
+    assert np.array_equal(res[0][0] != 0, res[1][0] != 0)  # the same entries touched
+    assert rel_err(res[0][1], res[1][1]) < 1e-6
+    ref_pts = oracle.Points(*coords, idx=idx)
+    rtg, rpg, _ = oracle.deform_bwd(g, ref_pts, table.astype(np.float64), mlpc.d_hidden, mlpc.d_out,
+                                    params.astype(np.float64), dd.astype(np.float64))
+    for tg_, pg_ in res:
+        assert rel_err(tg_, rtg) < 1e-2 and rel_err(pg_, rpg) < 1e-2
