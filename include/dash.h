@@ -147,17 +147,21 @@ int dash_version(void);
  * three groups, or four with the Eq. 11 term; used when a forward state is
  * given), 1 = one combined group per CTA, 10..13 = the shapes (3, 6), (4, 4),
  * (2, 4), (5, 5).  Forward forms agree bit for bit, backward forms up to the
- * order of the atomic additions.  DASH_OPT_SCATTER_FORM selects how the
- * warp-specialised backward issues its F = 2 table-gradient reductions when
- * neither the Eq. 11 term nor the coordinate gradient is on: 0 = lane pairs
- * (default: lanes 2j and 2j+1 take the lower and upper x corner of both
- * their Gaussians, so the two reductions of an x-neighbour pair leave in one
- * warp instruction and the L2 merges them when they share a 32-byte
- * sector), 1 = one Gaussian per lane (a pair is one 16-byte reduction when
- * both entries share an aligned 16 bytes, else two).  Both give the same
- * sums up to the order of the additions.  dash_get_option returns the
- * current value (negative status for an unknown option). */
-enum dash_option { DASH_OPT_FWD_FORM = 1, DASH_OPT_BWD_FORM = 2, DASH_OPT_SCATTER_FORM = 3 };
+ * order of the atomic additions.  DASH_OPT_ACCESS_FORM selects how the
+ * warp-specialised forward and backward kernels issue their F = 2 table
+ * accesses: 0 = lane pairs (default; lanes 2j and 2j+1 take the lower and
+ * upper x corner of both their Gaussians, so the two accesses of an
+ * x-neighbour pair leave in one warp instruction: L1 serves two loads in
+ * one 128-byte line with one lookup and L2 two reductions in one 32-byte
+ * sector as one operation), 1 = one Gaussian per lane (a pair is one
+ * 16-byte access when both entries share an aligned 16 bytes, else two).
+ * The forward's features agree bit for bit; the backward's table gradients
+ * up to the order of the additions.  The backward pairs its scatter only
+ * when neither the Eq. 11 term nor the coordinate gradient is on; a batched
+ * plan keeps the value current when it was created.
+ * dash_get_option returns the current value (negative status for an
+ * unknown option). */
+enum dash_option { DASH_OPT_FWD_FORM = 1, DASH_OPT_BWD_FORM = 2, DASH_OPT_ACCESS_FORM = 3 };
 int dash_set_option(int option, int value);
 int dash_get_option(int option);
 

@@ -47,6 +47,7 @@ struct BatchArgs {
   const SceneDev* scenes;
   const long long* counts;
   unsigned int* flags;
+  int paired;  // F = 2 gathers by lane pairs (fixed when the plan is created)
   uint32_t off_w2, off_w3, off_ring, off_a2, off_bar, off_tab, stage_bytes;
 };
 
@@ -219,7 +220,7 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) batch_fwd_kernel(const __g
         p.w = clamp01(__ldg(sc.ts + it.k));
       }
       encode_operand_row<TT, F>(a.g, static_cast<const TT*>(sc.table), p, valid, a.D, a.Dp,
-                                ring + s * a.stage_bytes, r, nullptr);
+                                ring + s * a.stage_bytes, r, nullptr, a.paired != 0);
       tc::fence_async_smem();
       tc::mbar_arrive(tc::smem_addr(&full[s]));
     }
@@ -362,6 +363,7 @@ int dash_batch_plan_create(const dash_batch_desc* desc, dash_batch_plan** out) {
   a.Dp = fused::pad16(D);
   a.O = desc->d_out;
   a.n_scenes = desc->n_scenes;
+  a.paired = (g_opt_access_form == 0 && a.g.F == 2) ? 1 : 0;
   a.flags = fused::batch_flags_ptr();
   if (a.flags == nullptr) return fail(DASH_ERR_CUDA, "cannot resolve the device flag word");
   fused::SceneDev host[DASH_MAX_SCENES];

@@ -13,7 +13,7 @@ static thread_local char g_last_error[512] = "";
 
 int g_opt_fwd_form = 0;
 int g_opt_bwd_form = 0;
-int g_opt_scatter_form = 0;
+int g_opt_access_form = 0;
 
 void set_error(const char* fmt, ...) {
   va_list ap;
@@ -129,10 +129,10 @@ int dash_set_option(int option, int value) {
         return dash::fail(DASH_ERR_INVALID_ARG, "backward form %d not in {0, 1, 10..13}", value);
       dash::g_opt_bwd_form = value;
       return DASH_OK;
-    case DASH_OPT_SCATTER_FORM:
+    case DASH_OPT_ACCESS_FORM:
       if (!(value == 0 || value == 1))
-        return dash::fail(DASH_ERR_INVALID_ARG, "scatter form %d not in {0, 1}", value);
-      dash::g_opt_scatter_form = value;
+        return dash::fail(DASH_ERR_INVALID_ARG, "access form %d not in {0, 1}", value);
+      dash::g_opt_access_form = value;
       return DASH_OK;
     default: return dash::fail(DASH_ERR_INVALID_ARG, "unknown option %d", option);
   }
@@ -142,7 +142,7 @@ int dash_get_option(int option) {
   switch (option) {
     case DASH_OPT_FWD_FORM: return dash::g_opt_fwd_form;
     case DASH_OPT_BWD_FORM: return dash::g_opt_bwd_form;
-    case DASH_OPT_SCATTER_FORM: return dash::g_opt_scatter_form;
+    case DASH_OPT_ACCESS_FORM: return dash::g_opt_access_form;
     default: return dash::fail(DASH_ERR_INVALID_ARG, "unknown option %d", option);
   }
 }

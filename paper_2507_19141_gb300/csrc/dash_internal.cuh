@@ -28,7 +28,7 @@ int sm_count();
 // Kernel-form options (dash_set_option).
 extern int g_opt_fwd_form;
 extern int g_opt_bwd_form;
-extern int g_opt_scatter_form;
+extern int g_opt_access_form;
 
 // ------------------------------------------------ kernel-side geometry ----
 // Level layout in the form the kernels read it (by-value kernel argument).
@@ -141,19 +141,17 @@ __device__ __forceinline__ void level_corners(const Geom& g, int l, float4 p, ui
   }
 }
 
-// The 8 corners of level l around p whose x bit is xb (corner b = xb | 2q,
-// q = 0..7 over the y, z, t bits), with the index and weight arithmetic of
-// level_corners, so that idx[q], w[q] equal its idx[xb | 2q], w[xb | 2q] bit
-// for bit.
-__device__ __forceinline__ void level_corners_x(const Geom& g, int l, float4 p, uint32_t xb, uint32_t idx[8],
-                                                float w[8]) {
+// The indices of the 8 corners of level l around p whose x bit is xb
+// (corner b = xb | 2q, q = 0..7 over the y, z, t bits) and the fractional
+// offsets fr = (fx, fy, fz, ft), with the arithmetic of level_corners.
+__device__ __forceinline__ void level_index_x(const Geom& g, int l, float4 p, uint32_t xb, uint32_t idx[8],
+                                              float fr[4]) {
   const int ns = g.res_s[l], nt = g.res_t[l];
   int ix, iy, iz, it;
-  float fx, fy, fz, ft;
-  axis_cell(p.x, ns, ix, fx);
-  axis_cell(p.y, ns, iy, fy);
-  axis_cell(p.z, ns, iz, fz);
-  axis_cell(p.w, nt, it, ft);
+  axis_cell(p.x, ns, ix, fr[0]);
+  axis_cell(p.y, ns, iy, fr[1]);
+  axis_cell(p.z, ns, iz, fr[2]);
+  axis_cell(p.w, nt, it, fr[3]);
   if ((g.dense_bits >> l) & 1u) {
     const uint32_t R = (uint32_t)ns + 1u;
     const uint32_t base = (uint32_t)ix + R * ((uint32_t)iy + R * ((uint32_t)iz + R * (uint32_t)it)) + xb;
@@ -169,15 +167,29 @@ __device__ __forceinline__ void level_corners_x(const Geom& g, int l, float4 p, 
     for (int q = 0; q < 8; ++q)
       idx[q] = (hx ^ (q & 1 ? hy1 : hy0) ^ (q & 2 ? hz1 : hz0) ^ (q & 4 ? ht1 : ht0)) & g.mask;
   }
-  const float wx = xb ? fx : 1.0f - fx, wy0 = 1.0f - fy, wz0 = 1.0f - fz, wt0 = 1.0f - ft;
+}
+
+// Weights of the corners with x bit xb from the fractional offsets, as
+// level_corners forms them: w[q] equals its w[xb | 2q] bit for bit.
+__device__ __forceinline__ void level_weights_x(const float fr[4], uint32_t xb, float w[8]) {
+  const float wx = xb ? fr[0] : 1.0f - fr[0], wy0 = 1.0f - fr[1], wz0 = 1.0f - fr[2], wt0 = 1.0f - fr[3];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     float v = wx;
-    v *= (q & 1) ? fy : wy0;
-    v *= (q & 2) ? fz : wz0;
-    v *= (q & 4) ? ft : wt0;
+    v *= (q & 1) ? fr[1] : wy0;
+    v *= (q & 2) ? fr[2] : wz0;
+    v *= (q & 4) ? fr[3] : wt0;
     w[q] = v;
   }
+}
+
+// level_index_x and level_weights_x together: the 8 corners with x bit xb
+// and their weights (idx[q], w[q] = level_corners' idx[xb | 2q], w[xb | 2q]).
+__device__ __forceinline__ void level_corners_x(const Geom& g, int l, float4 p, uint32_t xb, uint32_t idx[8],
+                                                float w[8]) {
+  float fr[4];
+  level_index_x(g, l, p, xb, idx, fr);
+  level_weights_x(fr, xb, w);
 }
 
 // ------------------------------------------------------ value helpers ----
@@ -283,6 +295,70 @@ __device__ __forceinline__ void gather2_pairs(const TT* __restrict__ base, const
     a1 = fmaf(w[2 * p], e0.y, a1);
     a0 = fmaf(w[2 * p + 1], e1.x, a0);
     a1 = fmaf(w[2 * p + 1], e1.y, a1);
+  }
+  acc[0] = a0;
+  acc[1] = a1;
+}
+
+// acc[0..2) for F = 2 exactly as gather2_pairs forms it for this lane's own
+// Gaussian (the same products in the same order, so the same value bit for
+// bit), with the loads issued by lane pairs: lane xb of the pair loads the
+// entries of the corners whose x bit is xb for both Gaussians A (the even
+// lane's, at pa) and B (the odd lane's, at pb), so an x-neighbour pair's two
+// loads leave in one warp instruction and L1 serves them with one lookup
+// when they share a 128-byte line (31 pairs in 32 for FP16 entries); the two
+// lanes then swap the halves they loaded for each other.  pm names the
+// pair's lanes.  Both lanes must call it with the same level.
+template <typename TT>
+__device__ __forceinline__ void gather2_level_paired(const Geom& g, int l, float4 pa, float4 pb, uint32_t xb,
+                                                     const TT* __restrict__ base, unsigned int pm, float acc[2]) {
+  uint32_t ia[8], ib[8];
+  float fa[4], fb[4], fr[4];
+  level_index_x(g, l, pa, xb, ia, fa);
+  level_index_x(g, l, pb, xb, ib, fb);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) fr[k] = xb ? fb[k] : fa[k];
+  float w0[8], w1[8];  // the own Gaussian's weights of its x = 0 and x = 1 corners
+  level_weights_x(fr, 0u, w0);
+  level_weights_x(fr, 1u, w1);
+  float a0 = 0.0f, a1 = 0.0f;
+  if constexpr (sizeof(TT) == 2) {
+    uint32_t ea[8], eb[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      ea[q] = __ldg(reinterpret_cast<const unsigned int*>(base + (size_t)ia[q] * 2));
+      eb[q] = __ldg(reinterpret_cast<const unsigned int*>(base + (size_t)ib[q] * 2));
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const uint32_t own = xb ? eb[q] : ea[q];
+      const uint32_t other = __shfl_xor_sync(pm, xb ? ea[q] : eb[q], 1);
+      const uint32_t u0 = xb ? other : own, u1 = xb ? own : other;
+      const float2 e0 = __half22float2(*reinterpret_cast<const __half2*>(&u0));
+      const float2 e1 = __half22float2(*reinterpret_cast<const __half2*>(&u1));
+      a0 = fmaf(w0[q], e0.x, a0);
+      a1 = fmaf(w0[q], e0.y, a1);
+      a0 = fmaf(w1[q], e1.x, a0);
+      a1 = fmaf(w1[q], e1.y, a1);
+    }
+  } else {
+    float2 ea[8], eb[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      ea[q] = __ldg(reinterpret_cast<const float2*>(base + (size_t)ia[q] * 2));
+      eb[q] = __ldg(reinterpret_cast<const float2*>(base + (size_t)ib[q] * 2));
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float2 own = xb ? eb[q] : ea[q];
+      const float2 snd = xb ? ea[q] : eb[q];
+      const float2 other = make_float2(__shfl_xor_sync(pm, snd.x, 1), __shfl_xor_sync(pm, snd.y, 1));
+      const float2 e0 = xb ? other : own, e1 = xb ? own : other;
+      a0 = fmaf(w0[q], e0.x, a0);
+      a1 = fmaf(w0[q], e0.y, a1);
+      a0 = fmaf(w1[q], e1.x, a0);
+      a1 = fmaf(w1[q], e1.y, a1);
+    }
   }
   acc[0] = a0;
   acc[1] = a1;

@@ -1034,7 +1034,7 @@ extern "C" int dash_deform_mlp_bwd(const dash_layout* layout, const dash_points*
   if (coord_grad != nullptr && a.lambda_r != 0.0f)
     return fail(DASH_ERR_UNSUPPORTED, "coordinate gradients with the Eq. 11 term on are not supported");
   a.coord_grad = coord_grad;
-  a.paired = (g_opt_scatter_form == 0 && a.g.F == 2 && a.lambda_r == 0.0f && coord_grad == nullptr) ? 1 : 0;
+  a.paired = (g_opt_access_form == 0 && a.g.F == 2 && a.lambda_r == 0.0f && coord_grad == nullptr) ? 1 : 0;
   a.flags = bwd_flags_ptr();
   if (a.flags == nullptr) return fail(DASH_ERR_CUDA, "cannot resolve the device flag word");
   cudaStream_t st = as_stream(stream);

@@ -105,13 +105,30 @@ constexpr uint32_t kATileBytes = kRows * kKH * 2;  // 36,864 B
 
 // Eqs. 8-9 for one point p into operand row r (K = [hi | 1 | lo], FP32
 // interpolation split into BF16 hi + lo); with state_row, also the BF16 copy
-// of f_h for the backward.  Invalid rows are zero features.
+// of f_h for the backward.  Invalid rows are zero features.  With `paired`
+// (F = 2; uniform over the warp) the gathers are issued by lane pairs
+// (gather2_level_paired) and give the same features bit for bit; both lanes
+// of every pair must then call this.
 template <typename TT, int F>
 __device__ __forceinline__ void encode_operand_row(const Geom& g, const TT* __restrict__ table, float4 p, bool valid,
-                                                   int D, int Dp, uint8_t* A, int r, uint8_t* state_row) {
+                                                   int D, int Dp, uint8_t* A, int r, uint8_t* state_row,
+                                                   bool paired = false) {
   const int KA = 2 * Dp + 16;
   constexpr int kLevelsPerChunk = 8 / F;
   const int nchunks = Dp / 8;
+  const uint32_t lane = threadIdx.x & 31u, xb = lane & 1u;
+  const unsigned int pm = 3u << (lane & 30u);
+  float4 pa = p, pb = p;
+  bool live = valid;
+  if constexpr (F == 2) {
+    if (paired) {
+      const float4 q = make_float4(__shfl_xor_sync(pm, p.x, 1), __shfl_xor_sync(pm, p.y, 1),
+                                   __shfl_xor_sync(pm, p.z, 1), __shfl_xor_sync(pm, p.w, 1));
+      pa = xb ? q : p;
+      pb = xb ? p : q;
+      live = __shfl_xor_sync(pm, valid ? 1 : 0, 1) != 0 || valid;  // either Gaussian of the pair exists
+    }
+  }
   for (int c = 0; c < nchunks; ++c) {
     float v[8];
 #pragma unroll
@@ -120,6 +137,17 @@ __device__ __forceinline__ void encode_operand_row(const Geom& g, const TT* __re
       float acc[F];
 #pragma unroll
       for (int f = 0; f < F; ++f) acc[f] = 0.0f;
+      if constexpr (F == 2) {
+        if (paired) {
+          if (live && l < g.L) {
+            gather2_level_paired<TT>(g, l, pa, pb, xb, table + g.offset[l] * 2, pm, acc);
+            if (!valid) acc[0] = acc[1] = 0.0f;
+          }
+#pragma unroll
+          for (int f = 0; f < F; ++f) v[j * F + f] = acc[f];
+          continue;
+        }
+      }
       if (valid && l < g.L) {
         uint32_t idx[16];
         float w[16];

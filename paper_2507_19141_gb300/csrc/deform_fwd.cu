@@ -31,6 +31,7 @@ struct FwdArgs {
   float* attrs_out;
   long long n_all;
   unsigned int* flags;
+  int paired;  // F = 2 gathers of the warp-specialised form by lane pairs
   uint32_t off_w2, off_w3, off_a, off_bar;
 };
 
@@ -312,7 +313,7 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_fwd_ws_kernel(const
       if (*abort_flag) break;
       uint8_t* srow = (valid && a.state != nullptr) ? a.state + row * state_stride(a.D) : nullptr;
       encode_operand_row<TT, F>(a.g, static_cast<const TT*>(a.table), p, valid, a.D, a.Dp, ring + s * stage_bytes, r,
-                                srow);
+                                srow, a.paired != 0);
       tc::fence_async_smem();
       tc::mbar_arrive(tc::smem_addr(&full[s]));
     }
@@ -480,6 +481,7 @@ extern "C" int dash_deform_mlp_fwd(const dash_layout* layout, const dash_points*
     a.attrs_out = apply->attrs_out;
     a.n_all = apply->n_all;
   }
+  a.paired = (g_opt_access_form == 0 && a.g.F == 2) ? 1 : 0;
   a.flags = fwd_flags_ptr();
   if (a.flags == nullptr) return fail(DASH_ERR_CUDA, "cannot resolve the device flag word");
   cudaStream_t st = as_stream(stream);

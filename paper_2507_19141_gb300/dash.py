@@ -197,7 +197,7 @@ def dash_last_error() -> str:
 
 OPT_FWD_FORM = 1
 OPT_BWD_FORM = 2
-OPT_SCATTER_FORM = 3
+OPT_ACCESS_FORM = 3
 
 
 def dash_set_option(option: int, value: int) -> None:

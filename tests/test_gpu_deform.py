@@ -314,16 +314,16 @@ def test_backward_scatter_forms_agree_with_oracle(dashlib, n_all, n, tdtype, gri
     st = dashlib.deform_state(mlp, n, "cuda")
     dashlib.dash_deform_mlp_fwd(lay, pts, tab, mlp, fwd_state=st)
     res = []
-    old = dashlib.dash_get_option(dashlib.OPT_SCATTER_FORM)
+    old = dashlib.dash_get_option(dashlib.OPT_ACCESS_FORM)
     try:
         for form in (0, 1):
-            dashlib.dash_set_option(dashlib.OPT_SCATTER_FORM, form)
+            dashlib.dash_set_option(dashlib.OPT_ACCESS_FORM, form)
             tg = torch.zeros((g.total, grid.F), dtype=torch.float32, device="cuda")
             pg = torch.zeros(mlpc.n_params, dtype=torch.float32, device="cuda")
             dashlib.dash_deform_mlp_bwd(lay, pts, tab, mlp, to_dev(dd), tg, pg, fwd_state=st)
             res.append((tg.cpu().numpy(), pg.cpu().numpy()))
     finally:
-        dashlib.dash_set_option(dashlib.OPT_SCATTER_FORM, old)
+        dashlib.dash_set_option(dashlib.OPT_ACCESS_FORM, old)
     assert rel_err(res[0][0], res[1][0]) < 1e-6
     assert np.array_equal(res[0][0] != 0, res[1][0] != 0)  # the same entries touched
     assert rel_err(res[0][1], res[1][1]) < 1e-6
@@ -332,3 +332,40 @@ def test_backward_scatter_forms_agree_with_oracle(dashlib, n_all, n, tdtype, gri
                                     params.astype(np.float64), dd.astype(np.float64))
     for tg_, pg_ in res:
         assert rel_err(tg_, rtg) < 1e-2 and rel_err(pg_, rpg) < 1e-2
+
+
+@pytest.mark.parametrize("n_all,n,tdtype,grid", [
+    (50_000, 20_001, np.float16, synth.PAPER_GRID),
+    (4_000, 1_283, np.float32, synth.PAPER_GRID),
+    (2_000, 129, np.float32, synth.TINY_GRID),
+    (10, 1, np.float16, synth.PAPER_GRID),
+])
+def test_forward_access_forms_bit_identical(dashlib, n_all, n, tdtype, grid):
+    """Lane-paired and per-lane gathers of the warp-specialised forward give
+    the same offsets, Eq. 10 update and state bit for bit (index list,
+    device count, odd counts), and meet the oracle."""
+    mlpc = synth.PAPER_MLP if grid is synth.PAPER_GRID else synth.TINY_MLP
+    g, coords, idx, table, params, _ = _case(grid, mlpc, n, tdtype, seed=71 + n, n_all=n_all)
+    lay = dashlib.layout_from(grid)
+    x, y, z, t = (to_dev(c) for c in coords)
+    cnt = torch.tensor([n], dtype=torch.int64, device="cuda")
+    pts = dashlib.Points(x, y, z, t, idx=to_dev(idx), n=n, n_dev=cnt)
+    mlp = dashlib.Mlp(to_dev(params), mlpc.d_in, mlpc.d_hidden, mlpc.d_out)
+    tab = to_dev(table)
+    attrs = torch.randn((mlpc.d_out, n_all), dtype=torch.float32, device="cuda")
+    outs = []
+    old = dashlib.dash_get_option(dashlib.OPT_ACCESS_FORM)
+    try:
+        for form in (0, 1):
+            dashlib.dash_set_option(dashlib.OPT_ACCESS_FORM, form)
+            st = dashlib.deform_state(mlp, n, "cuda")
+            out = attrs.clone()
+            d = dashlib.dash_deform_mlp_fwd(lay, pts, tab, mlp, fwd_state=st, apply=(attrs, out))
+            outs.append((d.cpu(), st.cpu(), out.cpu()))
+    finally:
+        dashlib.dash_set_option(dashlib.OPT_ACCESS_FORM, old)
+    for a, b in zip(outs[0], outs[1]):
+        assert torch.equal(a, b)
+    ref = oracle.deform_fwd(g, oracle.Points(*coords, idx=idx), table.astype(np.float64), mlpc.d_hidden,
+                            mlpc.d_out, params.astype(np.float64))
+    assert rel_err(outs[0][0].numpy()[:, :n], ref) < 1e-3
