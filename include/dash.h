@@ -144,8 +144,8 @@ int dash_version(void);
  * the warp-specialised shapes (gather groups, ring stages) 10 = (3, 6),
  * 11 = (3, 3), 12 = (2, 4), 13 = (5, 5).  DASH_OPT_BWD_FORM selects the fused
  * backward: 0 = warp-specialised (a decoder group feeding scatter groups;
- * three groups, or four with the Eq. 11 term; used when a forward state is
- * given), 1 = one combined group per CTA, 10..13 = the shapes (3, 6), (4, 4),
+ * three groups, with six ring stages when the Eq. 11 term is on; used when a
+ * forward state is given), 1 = one combined group per CTA, 10..13 = the shapes (3, 6), (4, 4),
  * (2, 4), (5, 5).  Forward forms agree bit for bit, backward forms up to the
  * order of the atomic additions.  DASH_OPT_ACCESS_FORM selects how the
  * warp-specialised forward and backward kernels issue their F = 2 table

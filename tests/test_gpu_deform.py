@@ -120,8 +120,8 @@ def test_fused_forward_rejects_unsupported(dashlib):
     assert e.value.status == dashlib.ERR_UNSUPPORTED
 
 
-def _grad_errors(dashlib, grid, mlpc, n, tdtype, seed, use_saved, smooth=None, n_all=None):
-    g, coords, idx, table, params, dd = _case(grid, mlpc, n, tdtype, seed, n_all=n_all)
+def _grad_errors(dashlib, grid, mlpc, n, tdtype, seed, use_saved, smooth=None, n_all=None, coords=None):
+    g, coords, idx, table, params, dd = _case(grid, mlpc, n, tdtype, seed, coords=coords, n_all=n_all)
     lay = dashlib.layout_from(grid)
     pts = _dev_points(dashlib, coords, idx, n)
     mlp = dashlib.Mlp(to_dev(params), mlpc.d_in, mlpc.d_hidden, mlpc.d_out)
@@ -170,6 +170,25 @@ def test_fused_backward_smoothness_term(dashlib, grid, mlpc, tdtype):
     """Eq. 11 with the paper-shaped perturbations dx = 1/2048, dt = 1/300."""
     smooth = (1.0, (1 / 2048, 1 / 2048, 1 / 2048), 1 / 300)
     errs = _grad_errors(dashlib, grid, mlpc, 8000, tdtype, 43, True, smooth=smooth)
+    assert all(v < 1e-2 for v in errs.values()), errs
+
+
+@pytest.mark.parametrize("case", ["index_list", "edge_coords", "coarse_eps"])
+def test_fused_backward_smoothness_term_cases(dashlib, case):
+    """Eq. 11 where the perturbed points share the hypervoxel of p on some
+    levels and not on others: scene points through an index list, the
+    degenerate coordinates (0, 1, NaN, out of range, vertices; clamped
+    perturbations), and perturbations wide enough to leave the hypervoxel
+    on the coarse levels too."""
+    smooth = (0.7, (1 / 2048, 1 / 2048, 1 / 2048), 1 / 300)
+    kw = {}
+    if case == "index_list":
+        kw = dict(n_all=9_000)
+    elif case == "edge_coords":
+        kw = dict(coords=edge_coords(3000, np.random.default_rng(48)))
+    else:
+        smooth = (0.7, (1 / 20, -1 / 30, 1 / 40), -1 / 10)
+    errs = _grad_errors(dashlib, synth.PAPER_GRID, synth.PAPER_MLP, 3000, np.float16, 49, True, smooth=smooth, **kw)
     assert all(v < 1e-2 for v in errs.values()), errs
 
 
