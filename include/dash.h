@@ -216,7 +216,8 @@ int dash_hash4d_fwd(const dash_layout* layout, const dash_points* pts, const voi
 
 /* Transpose of the encoder: table_grad[offset[l] + idx][f] += w * dfeat[i][l*F+f]
  * over the 16 corners of every level.  dfeat [n][L*F] FP32, table_grad FP32
- * [offset[L]][F].  Vector FP32 atomics; summation order is not deterministic. */
+ * [offset[L]][F].  Vector FP32 atomics; summation order is not deterministic.
+ * For F = 2 the reductions are issued by lane pairs (see DASH_OPT_ACCESS_FORM). */
 int dash_hash4d_bwd(const dash_layout* layout, const dash_points* pts, const float* dfeat,
                     float* table_grad, void* stream);
 

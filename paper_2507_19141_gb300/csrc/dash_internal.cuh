@@ -364,6 +364,38 @@ __device__ __forceinline__ void gather2_level_paired(const Geom& g, int l, float
   acc[1] = a1;
 }
 
+// F = 2 table-gradient scatter of one level for two Gaussians by a lane
+// pair.  Lane xb of the pair (xb = lane & 1) issues, for both Gaussians A
+// (the even lane's, at pa, gradient (a0, a1)) and B (the odd lane's, at pb,
+// gradient (b0, b1)), the reductions of the corners whose x bit is xb, so an
+// x-neighbour pair's two reductions leave in the same warp instruction; the
+// L2 then serves them as one operation when they share a 32-byte sector
+// (three pairs in four: always when the lower x coordinate is even, half the
+// time otherwise), where one lane issuing both costs two whenever they do
+// not form one aligned 16-byte group.  va / vb say whether A / B exist.
+__device__ __forceinline__ void scatter2_level_paired(const Geom& g, int l, float4 pa, float4 pb, uint32_t xb,
+                                                      bool va, bool vb, float* __restrict__ base, float a0,
+                                                      float a1, float b0, float b1) {
+  uint32_t ia[8], ib[8];
+  float wa[8], wb[8];
+  level_corners_x(g, l, pa, xb, ia, wa);
+  level_corners_x(g, l, pb, xb, ib, wb);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    if (va) red_add_v2(base + (size_t)ia[c] * 2, wa[c] * a0, wa[c] * a1);
+    if (vb) red_add_v2(base + (size_t)ib[c] * 2, wb[c] * b0, wb[c] * b1);
+  }
+}
+
+// The lane pair's two points: this lane's p and its partner's, as (A, B) =
+// (even lane's, odd lane's).  pm names the pair's lanes.
+__device__ __forceinline__ void pair_points(float4 p, uint32_t xb, unsigned int pm, float4& pa, float4& pb) {
+  const float4 q = make_float4(__shfl_xor_sync(pm, p.x, 1), __shfl_xor_sync(pm, p.y, 1),
+                               __shfl_xor_sync(pm, p.z, 1), __shfl_xor_sync(pm, p.w, 1));
+  pa = xb ? q : p;
+  pb = xb ? p : q;
+}
+
 // One F = 2 table entry as loaded (FP16: the packed pair; FP32: two floats).
 template <typename TT>
 struct Entry2;

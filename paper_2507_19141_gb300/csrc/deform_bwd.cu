@@ -108,40 +108,19 @@ __device__ __forceinline__ void scatter_level(float* __restrict__ grad, long lon
   }
 }
 
-// F = 2 table-gradient scatter of two Gaussians by a lane pair.  Lane xb of
-// the pair (xb = lane & 1) issues, for both Gaussians A (the even lane's) and
-// B (the odd lane's), the reductions of the corners whose x bit is xb, so an
-// x-neighbour pair's two reductions leave in the same warp instruction; the
-// L2 then serves them as one operation when they share a 32-byte sector
-// (three pairs in four: always when the lower x coordinate is even, half the
-// time otherwise), where one lane issuing both would cost two whenever they
-// do not form one aligned 16-byte group.  p is this lane's own Gaussian;
-// dfp points at A's column of the transposed [D][kRows] dL/df_h stage (B's
-// is the next one); va / vb say whether A / B exist; pm names the pair's
-// lanes.
+// The F = 2 table-gradient scatter of a lane pair's two Gaussians over all
+// levels (scatter2_level_paired).  p is this lane's own Gaussian; dfp points
+// at A's column of the transposed [D][kRows] dL/df_h stage (B's is the next
+// one); va / vb say whether A / B exist; pm names the pair's lanes.
 __device__ __forceinline__ void scatter_levels_paired(const Geom& g, float* __restrict__ grad, float4 p,
                                                       const float* dfp, uint32_t xb, bool va, bool vb,
                                                       unsigned int pm) {
-  float4 q;
-  q.x = __shfl_xor_sync(pm, p.x, 1);
-  q.y = __shfl_xor_sync(pm, p.y, 1);
-  q.z = __shfl_xor_sync(pm, p.z, 1);
-  q.w = __shfl_xor_sync(pm, p.w, 1);
-  const float4 pa = xb ? q : p, pb = xb ? p : q;
+  float4 pa, pb;
+  pair_points(p, xb, pm, pa, pb);
   for (int l = 0; l < g.L; ++l) {
     const float2 f0 = *reinterpret_cast<const float2*>(dfp + (2 * l) * kRows);      // (A, B) feature 0
     const float2 f1 = *reinterpret_cast<const float2*>(dfp + (2 * l + 1) * kRows);  // (A, B) feature 1
-    const float a0 = f0.x, a1 = f1.x, b0 = f0.y, b1 = f1.y;
-    uint32_t ia[8], ib[8];
-    float wa[8], wb[8];
-    level_corners_x(g, l, pa, xb, ia, wa);
-    level_corners_x(g, l, pb, xb, ib, wb);
-    float* base = grad + g.offset[l] * 2;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      if (va) red_add_v2(base + (size_t)ia[c] * 2, wa[c] * a0, wa[c] * a1);
-      if (vb) red_add_v2(base + (size_t)ib[c] * 2, wb[c] * b0, wb[c] * b1);
-    }
+    scatter2_level_paired(g, l, pa, pb, xb, va, vb, grad + g.offset[l] * 2, f0.x, f1.x, f0.y, f1.y);
   }
 }
 

@@ -122,10 +122,7 @@ __device__ __forceinline__ void encode_operand_row(const Geom& g, const TT* __re
   bool live = valid;
   if constexpr (F == 2) {
     if (paired) {
-      const float4 q = make_float4(__shfl_xor_sync(pm, p.x, 1), __shfl_xor_sync(pm, p.y, 1),
-                                   __shfl_xor_sync(pm, p.z, 1), __shfl_xor_sync(pm, p.w, 1));
-      pa = xb ? q : p;
-      pb = xb ? p : q;
+      pair_points(p, xb, pm, pa, pb);
       live = __shfl_xor_sync(pm, valid ? 1 : 0, 1) != 0 || valid;  // either Gaussian of the pair exists
     }
   }

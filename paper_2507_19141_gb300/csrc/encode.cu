@@ -18,6 +18,27 @@ __global__ void __launch_bounds__(kThreads) encode_fwd_kernel(Geom g, Pts pts, c
                                                               OT* __restrict__ out) {
   const long long n = point_count(pts);
   const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
+  if constexpr (kPairs && F == 2) {
+    // lane pairs (gather2_level_paired): both lanes of a pair stay while
+    // either of their points exists
+    if ((i & ~1ll) >= n) return;
+    const bool valid = i < n;
+    const uint32_t xb = threadIdx.x & 1u;
+    const unsigned int pm = 3u << (threadIdx.x & 30u);
+    const float4 p = valid ? load_point(pts, i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 pa, pb;
+    pair_points(p, xb, pm, pa, pb);
+    OT* row = out + i * (long long)(g.L * F);
+    for (int l = 0; l < g.L; ++l) {
+      float acc[2];
+      gather2_level_paired<TT>(g, l, pa, pb, xb, table + g.offset[l] * 2, pm, acc);
+      if (valid) {
+        row[2 * l] = from_f32<OT>(acc[0]);
+        row[2 * l + 1] = from_f32<OT>(acc[1]);
+      }
+    }
+    return;
+  }
   if (i >= n) return;
   const float4 p = load_point(pts, i);
   OT* row = out + i * (long long)(g.L * F);
@@ -52,29 +73,45 @@ __global__ void __launch_bounds__(kThreads) encode_bwd_kernel(Geom g, Pts pts, c
                                                               float* __restrict__ grad) {
   const long long n = point_count(pts);
   const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
-  if (i >= n) return;
-  const float4 p = load_point(pts, i);
-  const float* drow = dfeat + i * (long long)(g.L * F);
-  for (int l = 0; l < g.L; ++l) {
-    uint32_t idx[16];
-    float w[16];
-    level_corners(g, l, p, idx, w);
-    float d[F];
-#pragma unroll
-    for (int f = 0; f < F; ++f) d[f] = __ldg(drow + l * F + f);
-    float* base = grad + g.offset[l] * F;
-    if constexpr (F == 2) {
-      scatter2_pairs(base, idx, w, d[0], d[1]);
-      continue;
+  if constexpr (F == 2) {
+    // lane pairs (scatter2_level_paired): point A = row i_a, B = row i_a + 1
+    const long long ia = i & ~1ll;
+    if (ia >= n) return;  // both lanes of the pair
+    const bool vb = ia + 1 < n;
+    const uint32_t xb = threadIdx.x & 1u;
+    const unsigned int pm = 3u << (threadIdx.x & 30u);
+    const float4 p = i < n ? load_point(pts, i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 pa, pb;
+    pair_points(p, xb, pm, pa, pb);
+    const float* da = dfeat + ia * (long long)(g.L * 2);
+    const float* db = da + g.L * 2;
+    for (int l = 0; l < g.L; ++l) {
+      const float a0 = __ldg(da + 2 * l), a1 = __ldg(da + 2 * l + 1);
+      const float b0 = vb ? __ldg(db + 2 * l) : 0.f, b1 = vb ? __ldg(db + 2 * l + 1) : 0.f;
+      scatter2_level_paired(g, l, pa, pb, xb, true, vb, grad + g.offset[l] * 2, a0, a1, b0, b1);
     }
+  } else {
+    if (i >= n) return;
+    const float4 p = load_point(pts, i);
+    const float* drow = dfeat + i * (long long)(g.L * F);
+    for (int l = 0; l < g.L; ++l) {
+      uint32_t idx[16];
+      float w[16];
+      level_corners(g, l, p, idx, w);
+      float d[F];
 #pragma unroll
-    for (int b = 0; b < 16; ++b) {
-      float* e = base + (size_t)idx[b] * F;
-      if constexpr (F == 1) {
-        atomicAdd(e, w[b] * d[0]);
-      } else {
+      for (int f = 0; f < F; ++f) d[f] = __ldg(drow + l * F + f);
+      float* base = grad + g.offset[l] * F;
 #pragma unroll
-        for (int f = 0; f < F; f += 4) red_add_v4(e + f, w[b] * d[f], w[b] * d[f + 1], w[b] * d[f + 2], w[b] * d[f + 3]);
+      for (int b = 0; b < 16; ++b) {
+        float* e = base + (size_t)idx[b] * F;
+        if constexpr (F == 1) {
+          atomicAdd(e, w[b] * d[0]);
+        } else {
+#pragma unroll
+          for (int f = 0; f < F; f += 4)
+            red_add_v4(e + f, w[b] * d[f], w[b] * d[f + 1], w[b] * d[f + 2], w[b] * d[f + 3]);
+        }
       }
     }
   }
