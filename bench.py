@@ -45,9 +45,9 @@ STEP_BYTES = 2 + 4 + FWD_BYTES + BWD_BYTES
 # (profiles/warp_specialised_kernels_1M.md), valid while the kernel's sources
 # hash to the captured value; otherwise the benchmark reports no traffic.
 NCU_TRAFFIC = {
-    "bwd": {"bytes": (198.3 + 9.9) * 1e6, "n": 1_000_000, "sha256_16": "c2bfecf4271aadb0",
+    "bwd": {"bytes": (196.9 + 4.0) * 1e6, "n": 1_000_000, "sha256_16": "fd2b775637185288",
             "sources": ("deform_bwd.cu", "deform_common.cuh", "dash_internal.cuh", "tc_ptx.cuh")},
-    "fwd": {"bytes": (45.5 + 73.0) * 1e6, "n": 1_000_000, "sha256_16": "b917b9f9192a5d4c",
+    "fwd": {"bytes": (45.8 + 71.7) * 1e6, "n": 1_000_000, "sha256_16": "9b5a1c705694f0ac",
             "sources": ("deform_fwd.cu", "deform_common.cuh", "dash_internal.cuh", "tc_ptx.cuh")},
 }
 

@@ -699,15 +699,21 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_bwd_ws_kernel(const
       // f_h [hi | 1 | 0] from the state, masks from the forward
       const __nv_bfloat16* fs = reinterpret_cast<const __nv_bfloat16*>(srow);
       for (int c = 0; c < a.Dp / 8; ++c) {
-        uint32_t h[4];
+        uint4 hv;
+        if (srow != nullptr && 8 * c + 8 <= a.D) {
+          hv = __ldcs(reinterpret_cast<const uint4*>(fs + 8 * c));  // rows are 16-byte aligned
+        } else {
+          uint32_t h[4];
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-          const int k = 8 * c + 2 * jj;
-          const float v0 = (srow != nullptr && k < a.D) ? __bfloat162float(__ldcs(fs + k)) : 0.0f;
-          const float v1 = (srow != nullptr && k + 1 < a.D) ? __bfloat162float(__ldcs(fs + k + 1)) : 0.0f;
-          h[jj] = pack_bf16x2(v0, v1);
+          for (int jj = 0; jj < 4; ++jj) {
+            const int k = 8 * c + 2 * jj;
+            const float v0 = (srow != nullptr && k < a.D) ? __bfloat162float(__ldcs(fs + k)) : 0.0f;
+            const float v1 = (srow != nullptr && k + 1 < a.D) ? __bfloat162float(__ldcs(fs + k + 1)) : 0.0f;
+            h[jj] = pack_bf16x2(v0, v1);
+          }
+          hv = make_uint4(h[0], h[1], h[2], h[3]);
         }
-        *reinterpret_cast<uint4*>(Ft + tile_off(r, 8 * c, KF)) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4*>(Ft + tile_off(r, 8 * c, KF)) = hv;
         *reinterpret_cast<uint4*>(Ft + tile_off(r, a.Dp + 16 + 8 * c, KF)) = make_uint4(0u, 0u, 0u, 0u);
       }
       write_ones(Ft, r, a.Dp, KF);
