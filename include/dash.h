@@ -118,7 +118,7 @@ typedef struct dash_apply {
  * L_r = (1/n) sum_i |f(p_i) - f(p_i + e_s)|^2 + |f(p_i) - f(p_i + e_t)|^2,
  * e_s = (eps_s[0], eps_s[1], eps_s[2], 0), e_t = (0, 0, 0, eps_t); perturbed
  * coordinates are clamp(fl32(clamp(p) + e)).  The perturbed encodings are
- * recomputed inside the backward kernel, never stored.  loss_out (device
+ * recomputed by the backward, never stored.  loss_out (device
  * float, may be NULL) accumulates lambda_r * L_r. */
 typedef struct dash_smooth {
   float lambda_r;
@@ -144,8 +144,7 @@ int dash_version(void);
  * the warp-specialised shapes (gather groups, ring stages) 10 = (3, 6),
  * 11 = (3, 3), 12 = (2, 4), 13 = (5, 5).  DASH_OPT_BWD_FORM selects the fused
  * backward: 0 = warp-specialised (a decoder group feeding scatter groups;
- * three groups, with six ring stages when the Eq. 11 term is on; used when a
- * forward state is given), 1 = one combined group per CTA, 10..13 = the shapes (3, 6), (4, 4),
+ * three groups; used when a forward state is given), 1 = one combined group per CTA, 10..13 = the shapes (3, 6), (4, 4),
  * (2, 4), (5, 5).  Forward forms agree bit for bit, backward forms up to the
  * order of the atomic additions.  DASH_OPT_ACCESS_FORM selects how the
  * warp-specialised forward and backward kernels issue their F = 2 table
@@ -156,9 +155,10 @@ int dash_version(void);
  * sector as one operation), 1 = one Gaussian per lane (a pair is one
  * 16-byte access when both entries share an aligned 16 bytes, else two).
  * The forward's features agree bit for bit; the backward's table gradients
- * up to the order of the additions.  The backward pairs its scatter only
- * when neither the Eq. 11 term nor the coordinate gradient is on; a batched
- * plan keeps the value current when it was created.
+ * up to the order of the additions.  The backward pairs its scatter unless
+ * the coordinate gradient is requested; a batched plan keeps the value
+ * current when it was created.  (The F = 2 Eq. 11 kernel and the encoder-only
+ * kernels always use lane pairs.)
  * dash_get_option returns the current value (negative status for an
  * unknown option). */
 enum dash_option { DASH_OPT_FWD_FORM = 1, DASH_OPT_BWD_FORM = 2, DASH_OPT_ACCESS_FORM = 3 };
@@ -299,7 +299,9 @@ int dash_deform_apply_bwd(const dash_points* pts, int d_out, const float* dattrs
  * accumulates mlp_grad (FP32, packed like params) and scatters dL/df_h into
  * table_grad (FP32 [offset[L]][F], 16-byte aligned) with vector atomics.
  * With smooth != NULL and lambda_r != 0 also adds the Eq. 11 term,
- * re-encoding p, p + e_s and p + e_t in the kernel.  Shapes as the forward.
+ * re-encoding p, p + e_s and p + e_t (for F = 2 with a forward state in a
+ * second kernel launched right after, on the same stream; otherwise inside
+ * the backward kernel).  Shapes as the forward.
  * coord_grad (may be NULL): SoA [4][pts->n] FP32 receives d loss / d(x, y,
  * z, t) of each compact point as dash_hash4d_coord_grad defines it (the
  * scatter step also gathers the corner entries); not available together with

@@ -141,32 +141,45 @@ __device__ __forceinline__ void level_corners(const Geom& g, int l, float4 p, ui
   }
 }
 
-// The indices of the 8 corners of level l around p whose x bit is xb
-// (corner b = xb | 2q, q = 0..7 over the y, z, t bits) and the fractional
-// offsets fr = (fx, fy, fz, ft), with the arithmetic of level_corners.
-__device__ __forceinline__ void level_index_x(const Geom& g, int l, float4 p, uint32_t xb, uint32_t idx[8],
-                                              float fr[4]) {
-  const int ns = g.res_s[l], nt = g.res_t[l];
-  int ix, iy, iz, it;
-  axis_cell(p.x, ns, ix, fr[0]);
-  axis_cell(p.y, ns, iy, fr[1]);
-  axis_cell(p.z, ns, iz, fr[2]);
-  axis_cell(p.w, nt, it, fr[3]);
+// The indices of the 8 corners with x bit xb (corner b = xb | 2q, q = 0..7
+// over the y, z, t bits) of the level-l hypervoxel whose lower corner is
+// ci, with the arithmetic of level_corners.
+__device__ __forceinline__ void cell_index_x(const Geom& g, int l, const int ci[4], uint32_t xb, uint32_t idx[8]) {
   if ((g.dense_bits >> l) & 1u) {
-    const uint32_t R = (uint32_t)ns + 1u;
-    const uint32_t base = (uint32_t)ix + R * ((uint32_t)iy + R * ((uint32_t)iz + R * (uint32_t)it)) + xb;
+    const uint32_t R = (uint32_t)g.res_s[l] + 1u;
+    const uint32_t base =
+        (uint32_t)ci[0] + R * ((uint32_t)ci[1] + R * ((uint32_t)ci[2] + R * (uint32_t)ci[3])) + xb;
     const uint32_t sy = R, sz = R * R, st = R * R * R;
 #pragma unroll
     for (int q = 0; q < 8; ++q) idx[q] = base + (q & 1) * sy + ((q >> 1) & 1) * sz + ((q >> 2) & 1) * st;
   } else {
-    const uint32_t hx = (uint32_t)ix * g.primes[0] + (xb ? g.primes[0] : 0u);
-    const uint32_t hy0 = (uint32_t)iy * g.primes[1], hy1 = hy0 + g.primes[1];
-    const uint32_t hz0 = (uint32_t)iz * g.primes[2], hz1 = hz0 + g.primes[2];
-    const uint32_t ht0 = (uint32_t)it * g.primes[3], ht1 = ht0 + g.primes[3];
+    const uint32_t hx = (uint32_t)ci[0] * g.primes[0] + (xb ? g.primes[0] : 0u);
+    const uint32_t hy0 = (uint32_t)ci[1] * g.primes[1], hy1 = hy0 + g.primes[1];
+    const uint32_t hz0 = (uint32_t)ci[2] * g.primes[2], hz1 = hz0 + g.primes[2];
+    const uint32_t ht0 = (uint32_t)ci[3] * g.primes[3], ht1 = ht0 + g.primes[3];
 #pragma unroll
     for (int q = 0; q < 8; ++q)
       idx[q] = (hx ^ (q & 1 ? hy1 : hy0) ^ (q & 2 ? hz1 : hz0) ^ (q & 4 ? ht1 : ht0)) & g.mask;
   }
+}
+
+// The hypervoxel of level l around p: lower corners i[4] and fractional
+// offsets fr[4] (axis_cell on x, y, z with N_s and t with N_t).
+__device__ __forceinline__ void level_cell(const Geom& g, int l, float4 p, int i[4], float fr[4]) {
+  const int ns = g.res_s[l], nt = g.res_t[l];
+  axis_cell(p.x, ns, i[0], fr[0]);
+  axis_cell(p.y, ns, i[1], fr[1]);
+  axis_cell(p.z, ns, i[2], fr[2]);
+  axis_cell(p.w, nt, i[3], fr[3]);
+}
+
+// The indices of the 8 corners of level l around p whose x bit is xb
+// and the fractional offsets fr = (fx, fy, fz, ft).
+__device__ __forceinline__ void level_index_x(const Geom& g, int l, float4 p, uint32_t xb, uint32_t idx[8],
+                                              float fr[4]) {
+  int ci[4];
+  level_cell(g, l, p, ci, fr);
+  cell_index_x(g, l, ci, xb, idx);
 }
 
 // Weights of the corners with x bit xb from the fractional offsets, as
@@ -442,16 +455,6 @@ __device__ __forceinline__ void load_corners2(const TT* __restrict__ base, const
   }
 }
 
-// The hypervoxel of level l around p: lower corners i[4] and fractional
-// offsets fr[4] (axis_cell on x, y, z with N_s and t with N_t).
-__device__ __forceinline__ void level_cell(const Geom& g, int l, float4 p, int i[4], float fr[4]) {
-  const int ns = g.res_s[l], nt = g.res_t[l];
-  axis_cell(p.x, ns, i[0], fr[0]);
-  axis_cell(p.y, ns, i[1], fr[1]);
-  axis_cell(p.z, ns, i[2], fr[2]);
-  axis_cell(p.w, nt, i[3], fr[3]);
-}
-
 // Weight of corner b as (w_x w_y)(w_z w_t): the same value as corner_weight
 // up to rounding, for uses that need not match level_corners bit for bit.
 __device__ __forceinline__ float corner_weight_xy_zt(const float fr[4], int b) {
@@ -570,5 +573,10 @@ __device__ __forceinline__ void scatter2_pairs(float* __restrict__ base, const u
     }
   }
 }
+
+// Backward of the Eq. 11 smoothness term for F = 2 (smooth.cu): adds its
+// table gradient into table_grad and lambda_r L_r into sm->loss_out.
+int launch_smooth2(const Geom& g, const Pts& pts, const void* table, int table_dtype, float* table_grad,
+                   const dash_smooth* sm, cudaStream_t st);
 
 }  // namespace dash

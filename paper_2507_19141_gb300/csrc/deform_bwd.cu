@@ -158,116 +158,6 @@ __device__ __forceinline__ float4 perturb(float4 p, float ex, float ey, float ez
                      clamp01(__fadd_rn(p.w, et)));
 }
 
-// Eq. 11 at level l for F = 2, for the Gaussian at p: f(p) and, for
-// e = e_s and e_t, f(p + e); the gradient of
-// lambda_r ||f(p) - f(p + e)||^2 / n (scale = 2 lambda_r / n) is added to d
-// (p's corners) and scattered into the corners of p + e.  Where p + e lies in
-// p's hypervoxel (the same 16 corners), the entries loaded for f(p) serve
-// f(p + e) as well (the same products in the same order as a fresh gather)
-// and its gradient joins p's, corner by corner, in one reduction per corner
-// pair; otherwise p + e is gathered and scattered on its own.  It also
-// scatters d (df_h plus this term) into p's corners.  p's weights are
-// recomputed from its fractional offsets where needed, not kept, to hold
-// the registers of the scatter threads down.
-template <typename TT>
-__device__ __forceinline__ void smooth_level2(const BwdArgs& a, int l, float4 p, float d[2], float scale,
-                                              float& loss) {
-  const TT* base = static_cast<const TT*>(a.table) + a.g.offset[l] * 2;
-  float* gbase = a.table_grad + a.g.offset[l] * 2;
-  // hypervoxels of p and of the two perturbed points
-  int ci[4];
-  float cf[4];
-  level_cell(a.g, l, p, ci, cf);
-  float4 pq[2];
-  pq[0] = perturb(p, a.eps_s[0], a.eps_s[1], a.eps_s[2], 0.0f);
-  pq[1] = perturb(p, 0.0f, 0.0f, 0.0f, a.eps_t);
-  bool same[2];
-  float qf[2][4];
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    int qc[4];
-    level_cell(a.g, l, pq[k], qc, qf[k]);
-    same[k] = qc[0] == ci[0] && qc[1] == ci[1] && qc[2] == ci[2] && qc[3] == ci[3];
-  }
-  // f(p), and f(p + e) from the same entries where p + e shares p's corners
-  uint32_t idx[16];
-  float fp0 = 0.0f, fp1 = 0.0f, fq[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
-  {
-    float w[16];
-    level_corners(a.g, l, p, idx, w);
-    Entry2<TT> e[16];
-    load_corners2<TT>(base, idx, e);
-#pragma unroll
-    for (int b = 0; b < 16; ++b) {
-      const float2 v = e[b].f();
-      fp0 = fmaf(w[b], v.x, fp0);
-      fp1 = fmaf(w[b], v.y, fp1);
-    }
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      if (same[k]) {
-#pragma unroll
-        for (int b = 0; b < 16; ++b) {
-          const float wq = corner_weight(qf[k], b);
-          const float2 v = e[b].f();
-          fq[k][0] = fmaf(wq, v.x, fq[k][0]);
-          fq[k][1] = fmaf(wq, v.y, fq[k][1]);
-        }
-      }
-    }
-  }
-  // the other perturbed points: own gather, gradient and scatter
-  float dq[2][2];
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    uint32_t qi[16];
-    float qw[16];
-    if (!same[k]) {
-      level_corners(a.g, l, pq[k], qi, qw);
-      gather2_pairs<TT>(base, qi, qw, fq[k]);
-    }
-    const float diff0 = fp0 - fq[k][0], diff1 = fp1 - fq[k][1];
-    loss = fmaf(diff0, diff0, loss);
-    loss = fmaf(diff1, diff1, loss);
-    d[0] = fmaf(scale, diff0, d[0]);
-    d[1] = fmaf(scale, diff1, d[1]);
-    dq[k][0] = -scale * diff0;
-    dq[k][1] = -scale * diff1;
-    if (!same[k]) scatter2_pairs(gbase, qi, qw, dq[k][0], dq[k][1]);
-  }
-  // p's corners, joined by the gradients of the perturbed points that share
-  // them (weights re-formed as (w_x w_y)(w_z w_t) rather than kept live)
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    float c[2][2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int b = 2 * q + h;
-      const float wb = corner_weight_xy_zt(cf, b);
-      float c0 = wb * d[0], c1 = wb * d[1];
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        if (same[k]) {
-          const float wq = corner_weight_xy_zt(qf[k], b);
-          c0 = fmaf(wq, dq[k][0], c0);
-          c1 = fmaf(wq, dq[k][1], c1);
-        }
-      }
-      c[h][0] = c0;
-      c[h][1] = c1;
-    }
-    const uint32_t i0 = idx[2 * q], i1 = idx[2 * q + 1];
-    if ((i0 ^ i1) == 1u) {
-      if (i0 < i1) red_add_v4(gbase + (size_t)i0 * 2, c[0][0], c[0][1], c[1][0], c[1][1]);
-      else red_add_v4(gbase + (size_t)i1 * 2, c[1][0], c[1][1], c[0][0], c[0][1]);
-    } else {
-      red_add_v2(gbase + (size_t)i0 * 2, c[0][0], c[0][1]);
-      red_add_v2(gbase + (size_t)i1 * 2, c[1][0], c[1][1]);
-    }
-  }
-}
-
-
 template <typename TT, int F>
 __global__ void __launch_bounds__(kRows, 1) deform_bwd_kernel(const __grid_constant__ BwdArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -626,7 +516,7 @@ __global__ void __launch_bounds__(kRows, 1) deform_bwd_kernel(const __grid_const
 // smoothness term on they also encode p, p + e_s, p + e_t and scatter the
 // perturbed points' gradients.  Requires the forward state.
 // ---------------------------------------------------------------------------
-template <typename TT, int F, int P, int S, bool SM>
+template <typename TT, int F, int P, int S>
 __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_bwd_ws_kernel(const __grid_constant__ BwdArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tid = threadIdx.x;
@@ -676,7 +566,7 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_bwd_ws_kernel(const
   const long long n = point_count(a.pts);
   const long long ntiles = (n + kRows - 1) / kRows;
   const long long my_tiles = ntiles > blockIdx.x ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
-  const bool smooth = SM && a.lambda_r != 0.0f;  // SM: compiled with the Eq. 11 path
+  const bool smooth = F != 2 && a.lambda_r != 0.0f;  // F = 2: the Eq. 11 term runs in smooth.cu
   const float scale = n > 0 ? 2.0f * a.lambda_r / (float)n : 0.0f;
   float loss = 0.0f;
 
@@ -941,17 +831,11 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_bwd_ws_kernel(const
           float d[F];
 #pragma unroll
           for (int f = 0; f < F; ++f) d[f] = stage[(l * F + f) * kRows + r];
-          if constexpr (F == 2) {
-            if (smooth) {
-              smooth_level2<TT>(a, l, p, d, scale, loss);  // scatters p's corners too
-              continue;
-            }
-          }
           uint32_t idx[16];
           float w[16];
           level_corners(a.g, l, p, idx, w);
           if (a.coord_grad != nullptr) level_coord_grad<TT, F>(a.g, l, p, table + a.g.offset[l] * F, idx, d, cg);
-          if constexpr (F != 2) if (smooth) {  // F = 2 took smooth_level2 above
+          if constexpr (F != 2) if (smooth) {
             float fp[F];
             gather_level<TT, F>(table, a.g.offset[l], idx, w, fp);
 #pragma unroll
@@ -991,8 +875,8 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_bwd_ws_kernel(const
   if (tid < 32) tc::tmem_dealloc(tbase, kTmemCols);
 }
 
-template <typename TT, int F, int P, int S, bool SM>
-int launch_ws_impl(BwdArgs a, cudaStream_t st) {
+template <typename TT, int F, int P, int S>
+int launch_ws(BwdArgs a, cudaStream_t st) {
   const int KF = 2 * a.Dp + 16;
   uint32_t off = (uint32_t)kHidden * KF * 2;
   a.off_w2 = (off + 127) & ~127u;
@@ -1006,7 +890,7 @@ int launch_ws_impl(BwdArgs a, cudaStream_t st) {
   a.off_bar = a.off_ring + (uint32_t)S * a.Dp * kRows * 4;
   const size_t smem = a.off_bar + 8 * (2 * S + 1) + 16;
   if (smem > 227 * 1024) return fail(DASH_ERR_UNSUPPORTED, "backward form needs %zu B of shared memory", smem);
-  auto kern = deform_bwd_ws_kernel<TT, F, P, S, SM>;
+  auto kern = deform_bwd_ws_kernel<TT, F, P, S>;
   if (int s = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                           "cudaFuncSetAttribute(deform_bwd_ws)"))
     return s;
@@ -1015,17 +899,6 @@ int launch_ws_impl(BwdArgs a, cudaStream_t st) {
   grid = ntiles < grid ? (ntiles > 0 ? ntiles : 1) : grid;
   kern<<<(unsigned)grid, (P + 1) * kRows, smem, st>>>(a);
   return launch_status("deform_bwd_ws_kernel");
-}
-
-// For F = 2 the Eq. 11 path is compiled into kernels of its own so that it
-// does not raise the register count of the plain backward; the other F keep
-// one kernel for both.
-template <typename TT, int F, int P, int S>
-int launch_ws(BwdArgs a, cudaStream_t st) {
-  if constexpr (F == 2) {
-    if (a.lambda_r == 0.0f) return launch_ws_impl<TT, F, P, S, false>(a, st);
-  }
-  return launch_ws_impl<TT, F, P, S, true>(a, st);
 }
 
 template <typename TT, int F>
@@ -1063,10 +936,9 @@ int launch(BwdArgs a, cudaStream_t st) {
 template <typename TT>
 int dispatch(int F, bool ws, BwdArgs& a, cudaStream_t st) {
   if (ws && F == 2 && a.Dp <= 32) {
-    // warp-specialised shapes (scatter groups, ring stages); 0 = the measured best:
-    // three groups, with six stages for the smoothness term's longer tiles
+    // warp-specialised shapes (scatter groups, ring stages); 0 = the measured best
     switch (g_opt_bwd_form) {
-      case 0: return a.lambda_r != 0.0f ? launch_ws<TT, 2, 3, 6>(a, st) : launch_ws<TT, 2, 3, 3>(a, st);
+      case 0: return launch_ws<TT, 2, 3, 3>(a, st);
       case 10: return launch_ws<TT, 2, 3, 6>(a, st);
       case 11: return launch_ws<TT, 2, 4, 4>(a, st);
       case 12: return launch_ws<TT, 2, 2, 4>(a, st);
@@ -1157,9 +1029,18 @@ extern "C" int dash_deform_mlp_bwd(const dash_layout* layout, const dash_points*
   // the warp-specialised form needs the forward state; without it the
   // single-group form re-encodes f_h itself
   const bool ws = g_opt_bwd_form != 1 && a.state != nullptr;
-  switch (table_dtype) {
-    case DASH_F32: return dispatch<float>(a.g.F, ws, a, st);
-    case DASH_F16: return dispatch<__half>(a.g.F, ws, a, st);
-    default: return fail(DASH_ERR_UNSUPPORTED, "table_dtype %d (F32 or F16)", table_dtype);
+  if (table_dtype != DASH_F32 && table_dtype != DASH_F16)
+    return fail(DASH_ERR_UNSUPPORTED, "table_dtype %d (F32 or F16)", table_dtype);
+  // F = 2 with the warp-specialised form: the Eq. 11 term runs in its own
+  // kernel after the df_h scatter (both add into table_grad)
+  const bool smooth_apart = ws && a.g.F == 2 && a.lambda_r != 0.0f;
+  BwdArgs b = a;
+  if (smooth_apart) {
+    b.lambda_r = 0.0f;
+    b.loss_out = nullptr;
+    b.paired = g_opt_access_form == 0 ? 1 : 0;
   }
+  const int s = table_dtype == DASH_F32 ? dispatch<float>(a.g.F, ws, b, st) : dispatch<__half>(a.g.F, ws, b, st);
+  if (s != DASH_OK || !smooth_apart) return s;
+  return launch_smooth2(a.g, a.pts, table, table_dtype, table_grad, smooth, st);
 }
