@@ -155,10 +155,10 @@ int dash_version(void);
  * sector as one operation), 1 = one Gaussian per lane (a pair is one
  * 16-byte access when both entries share an aligned 16 bytes, else two).
  * The forward's features agree bit for bit; the backward's table gradients
- * up to the order of the additions.  The backward pairs its scatter unless
- * the coordinate gradient is requested; a batched plan keeps the value
- * current when it was created.  (The F = 2 Eq. 11 kernel and the encoder-only
- * kernels always use lane pairs.)
+ * up to the order of the additions (as are the coordinate gradients, whose
+ * gathers are paired too).  A batched plan keeps the value current when it
+ * was created.  (The F = 2 Eq. 11 kernel and the encoder-only kernels always
+ * use lane pairs.)
  * dash_get_option returns the current value (negative status for an
  * unknown option). */
 enum dash_option { DASH_OPT_FWD_FORM = 1, DASH_OPT_BWD_FORM = 2, DASH_OPT_ACCESS_FORM = 3 };

@@ -400,6 +400,13 @@ __device__ __forceinline__ void scatter2_level_paired(const Geom& g, int l, floa
   }
 }
 
+// The sum of a value over the lane pair, the x = 0 lane's term first on both
+// lanes (so both hold the same bits).
+__device__ __forceinline__ float pair_sum(float v, uint32_t xb, unsigned int pm) {
+  const float o = __shfl_xor_sync(pm, v, 1);
+  return xb ? o + v : v + o;
+}
+
 // The lane pair's two points: this lane's p and its partner's, as (A, B) =
 // (even lane's, odd lane's).  pm names the pair's lanes.
 __device__ __forceinline__ void pair_points(float4 p, uint32_t xb, unsigned int pm, float4& pa, float4& pb) {

@@ -124,6 +124,69 @@ __device__ __forceinline__ void scatter_levels_paired(const Geom& g, float* __re
   }
 }
 
+// scatter_levels_paired plus the input-coordinate gradient (the quantity
+// level_coord_grad computes, summed over the levels and scaled by N_l):
+// lane xb gathers its x half of each Gaussian's corners, forms s = d . entry
+// for them and its share of the four axis derivatives, and the lanes add
+// their shares; returns the gradient of this lane's own Gaussian (before
+// the clamp mask).  Matches level_coord_grad up to the order of additions.
+template <typename TT>
+__device__ __forceinline__ float4 scatter_coord_levels_paired(const Geom& g, const TT* __restrict__ table,
+                                                              float* __restrict__ grad, float4 p, const float* dfp,
+                                                              uint32_t xb, bool vb, unsigned int pm) {
+  float4 pa, pb;
+  pair_points(p, xb, pm, pa, pb);
+  float4 cg = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int l = 0; l < g.L; ++l) {
+    const float2 f0 = *reinterpret_cast<const float2*>(dfp + (2 * l) * kRows);
+    const float2 f1 = *reinterpret_cast<const float2*>(dfp + (2 * l + 1) * kRows);
+    const TT* base = table + g.offset[l] * 2;
+    float* gbase = grad + g.offset[l] * 2;
+    const float ns = (float)g.res_s[l], nt = (float)g.res_t[l];
+#pragma unroll 1
+    for (int G = 0; G < 2; ++G) {
+      if (G == 1 && !vb) break;  // the same on both lanes
+      const float4 pp = G == 0 ? pa : pb;
+      const float d0 = G == 0 ? f0.x : f0.y, d1 = G == 0 ? f1.x : f1.y;
+      uint32_t idx[8];
+      float fr[4], w[8], sv[8];
+      level_index_x(g, l, pp, xb, idx, fr);
+      level_weights_x(fr, xb, w);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float2 e = Entry2<TT>::load(base + (size_t)idx[q] * 2).f();
+        sv[q] = fmaf(d1, e.y, d0 * e.x);
+      }
+      const float wx = xb ? fr[0] : 1.0f - fr[0];
+      float gx = 0.f, gy = 0.f, gz = 0.f, gt = 0.f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float wy = (q & 1) ? fr[1] : 1.0f - fr[1];
+        const float wz = (q & 2) ? fr[2] : 1.0f - fr[2];
+        const float wt = (q & 4) ? fr[3] : 1.0f - fr[3];
+        gx = fmaf(sv[q], wy * wz * wt, gx);
+        if (!(q & 1)) gy = fmaf(sv[q | 1] - sv[q], wx * wz * wt, gy);
+        if (!(q & 2)) gz = fmaf(sv[q | 2] - sv[q], wx * wy * wt, gz);
+        if (!(q & 4)) gt = fmaf(sv[q | 4] - sv[q], wx * wy * wz, gt);
+      }
+      if (!xb) gx = -gx;  // the lower x corners enter the x derivative with a minus sign
+      gx = pair_sum(gx, xb, pm);
+      gy = pair_sum(gy, xb, pm);
+      gz = pair_sum(gz, xb, pm);
+      gt = pair_sum(gt, xb, pm);
+      if ((uint32_t)G == xb) {
+        cg.x = fmaf(gx, ns, cg.x);
+        cg.y = fmaf(gy, ns, cg.y);
+        cg.z = fmaf(gz, ns, cg.z);
+        cg.w = fmaf(gt, nt, cg.w);
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) red_add_v2(gbase + (size_t)idx[q] * 2, w[q] * d0, w[q] * d1);
+    }
+  }
+  return cg;
+}
+
 template <typename TT, int F>
 __device__ __forceinline__ void gather_level(const TT* __restrict__ table, long long off, const uint32_t idx[16],
                                              const float w[16], float acc[F]) {
@@ -819,9 +882,17 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_bwd_ws_kernel(const
       if constexpr (F == 2) {
         if (a.paired) {
           const long long row_a = row - (r & 1);  // the pair's even row; both lanes agree on row_a < n
-          if (row_a < n)
-            scatter_levels_paired(a.g, a.table_grad, p, stage + (r & ~1), (uint32_t)(r & 1), true, row_a + 1 < n,
-                                  3u << (r & 30));
+          const uint32_t xb = (uint32_t)(r & 1);
+          const unsigned int pm = 3u << (r & 30);
+          if (row_a < n) {
+            if (a.coord_grad == nullptr) {
+              scatter_levels_paired(a.g, a.table_grad, p, stage + (r & ~1), xb, true, row_a + 1 < n, pm);
+            } else {
+              const float4 cg = scatter_coord_levels_paired<TT>(a.g, table, a.table_grad, p, stage + (r & ~1), xb,
+                                                                row_a + 1 < n, pm);
+              if (row < n) store_coord_grad(a, row, cg);
+            }
+          }
           done = true;
         }
       }
@@ -1022,7 +1093,7 @@ extern "C" int dash_deform_mlp_bwd(const dash_layout* layout, const dash_points*
   if (coord_grad != nullptr && a.lambda_r != 0.0f)
     return fail(DASH_ERR_UNSUPPORTED, "coordinate gradients with the Eq. 11 term on are not supported");
   a.coord_grad = coord_grad;
-  a.paired = (g_opt_access_form == 0 && a.g.F == 2 && a.lambda_r == 0.0f && coord_grad == nullptr) ? 1 : 0;
+  a.paired = (g_opt_access_form == 0 && a.g.F == 2 && a.lambda_r == 0.0f) ? 1 : 0;
   a.flags = bwd_flags_ptr();
   if (a.flags == nullptr) return fail(DASH_ERR_CUDA, "cannot resolve the device flag word");
   cudaStream_t st = as_stream(stream);

@@ -42,12 +42,6 @@ __device__ __forceinline__ bool same_cell(const int a[4], const int b[4]) {
   return a[0] == b[0] && a[1] == b[1] && a[2] == b[2] && a[3] == b[3];
 }
 
-// The sum of the pair's two halves, the x = 0 half first on both lanes.
-__device__ __forceinline__ float pair_sum(float v, uint32_t xb, unsigned int pm) {
-  const float o = __shfl_xor_sync(pm, v, 1);
-  return xb ? o + v : v + o;
-}
-
 // sum over this lane's 8 corners of w[q] * entry[q]
 template <typename TT>
 __device__ __forceinline__ float2 half_sum(const float w[8], const Entry2<TT> e[8]) {
