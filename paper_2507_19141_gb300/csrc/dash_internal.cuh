@@ -492,6 +492,42 @@ __device__ __forceinline__ float4 coord_inside(const Pts& p, long long i) {
   return make_float4(m[0], m[1], m[2], m[3]);
 }
 
+// The four axis derivatives of d . f_l (F = 2, d = (d0, d1)) at the point pp
+// of a lane pair's Gaussian -- level_coord_grad's quantity before the N_l
+// factor -- with the gathers issued by the lane pair: lane xb loads the
+// corners whose x bit is xb, forms s = d . entry and its share of each
+// derivative, and the two lanes add their shares (both end with the same
+// sums).  Both lanes call it with the same pp, d0, d1.  idx / w receive this
+// lane's corners and weights.  Equal to level_coord_grad up to the order of
+// the additions.
+template <typename TT>
+__device__ __forceinline__ float4 coord_level_paired(const Geom& g, int l, float4 pp, uint32_t xb, unsigned int pm,
+                                                     const TT* __restrict__ base, float d0, float d1,
+                                                     uint32_t idx[8], float w[8]) {
+  float fr[4], sv[8];
+  level_index_x(g, l, pp, xb, idx, fr);
+  level_weights_x(fr, xb, w);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float2 e = Entry2<TT>::load(base + (size_t)idx[q] * 2).f();
+    sv[q] = fmaf(d1, e.y, d0 * e.x);
+  }
+  const float wx = xb ? fr[0] : 1.0f - fr[0];
+  float gx = 0.f, gy = 0.f, gz = 0.f, gt = 0.f;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float wy = (q & 1) ? fr[1] : 1.0f - fr[1];
+    const float wz = (q & 2) ? fr[2] : 1.0f - fr[2];
+    const float wt = (q & 4) ? fr[3] : 1.0f - fr[3];
+    gx = fmaf(sv[q], wy * wz * wt, gx);
+    if (!(q & 1)) gy = fmaf(sv[q | 1] - sv[q], wx * wz * wt, gy);
+    if (!(q & 2)) gz = fmaf(sv[q | 2] - sv[q], wx * wy * wt, gz);
+    if (!(q & 4)) gt = fmaf(sv[q | 4] - sv[q], wx * wy * wz, gt);
+  }
+  if (!xb) gx = -gx;  // the lower x corners enter the x derivative with a minus sign
+  return make_float4(pair_sum(gx, xb, pm), pair_sum(gy, xb, pm), pair_sum(gz, xb, pm), pair_sum(gt, xb, pm));
+}
+
 // acc += d(sum_f d[f] * f_l[f]) / d(x, y, z, t) at the clamped point p for
 // level l, whose corner indices idx come from level_corners.  With s_b the
 // dot product of d and corner b's entry, the derivative of the quadrilinear

@@ -149,31 +149,9 @@ __device__ __forceinline__ float4 scatter_coord_levels_paired(const Geom& g, con
       const float4 pp = G == 0 ? pa : pb;
       const float d0 = G == 0 ? f0.x : f0.y, d1 = G == 0 ? f1.x : f1.y;
       uint32_t idx[8];
-      float fr[4], w[8], sv[8];
-      level_index_x(g, l, pp, xb, idx, fr);
-      level_weights_x(fr, xb, w);
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float2 e = Entry2<TT>::load(base + (size_t)idx[q] * 2).f();
-        sv[q] = fmaf(d1, e.y, d0 * e.x);
-      }
-      const float wx = xb ? fr[0] : 1.0f - fr[0];
-      float gx = 0.f, gy = 0.f, gz = 0.f, gt = 0.f;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float wy = (q & 1) ? fr[1] : 1.0f - fr[1];
-        const float wz = (q & 2) ? fr[2] : 1.0f - fr[2];
-        const float wt = (q & 4) ? fr[3] : 1.0f - fr[3];
-        gx = fmaf(sv[q], wy * wz * wt, gx);
-        if (!(q & 1)) gy = fmaf(sv[q | 1] - sv[q], wx * wz * wt, gy);
-        if (!(q & 2)) gz = fmaf(sv[q | 2] - sv[q], wx * wy * wt, gz);
-        if (!(q & 4)) gt = fmaf(sv[q | 4] - sv[q], wx * wy * wz, gt);
-      }
-      if (!xb) gx = -gx;  // the lower x corners enter the x derivative with a minus sign
-      gx = pair_sum(gx, xb, pm);
-      gy = pair_sum(gy, xb, pm);
-      gz = pair_sum(gz, xb, pm);
-      gt = pair_sum(gt, xb, pm);
+      float w[8];
+      const float4 gr = coord_level_paired<TT>(g, l, pp, xb, pm, base, d0, d1, idx, w);
+      const float gx = gr.x, gy = gr.y, gz = gr.z, gt = gr.w;
       if ((uint32_t)G == xb) {
         cg.x = fmaf(gx, ns, cg.x);
         cg.y = fmaf(gy, ns, cg.y);

@@ -125,18 +125,49 @@ __global__ void __launch_bounds__(kThreads) coord_grad_kernel(Geom g, Pts pts, c
                                                               float* __restrict__ dcoord) {
   const long long n = point_count(pts);
   const long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
-  if (i >= n) return;
-  const float4 p = load_point(pts, i);
-  const float* drow = dfeat + i * (long long)(g.L * F);
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int l = 0; l < g.L; ++l) {
-    uint32_t idx[16];
-    float w[16];
-    level_corners(g, l, p, idx, w);
-    float d[F];
+  if constexpr (F == 2) {
+    // lane pairs (coord_level_paired): point A = row i_a, B = row i_a + 1
+    const long long i_a = i & ~1ll;
+    if (i_a >= n) return;  // both lanes of the pair
+    const bool vb = i_a + 1 < n;
+    const uint32_t xb = threadIdx.x & 1u;
+    const unsigned int pm = 3u << (threadIdx.x & 30u);
+    const float4 p = i < n ? load_point(pts, i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 pa, pb;
+    pair_points(p, xb, pm, pa, pb);
+    for (int l = 0; l < g.L; ++l) {
+      const float ns = (float)g.res_s[l], nt = (float)g.res_t[l];
+#pragma unroll 1
+      for (int G = 0; G < 2; ++G) {
+        if (G == 1 && !vb) break;  // the same on both lanes
+        const float* drow = dfeat + (i_a + G) * (long long)(g.L * 2) + 2 * l;
+        uint32_t idx[8];
+        float w[8];
+        const float4 gr = coord_level_paired<TT>(g, l, G == 0 ? pa : pb, xb, pm, table + g.offset[l] * 2,
+                                                 __ldg(drow), __ldg(drow + 1), idx, w);
+        if ((uint32_t)G == xb) {
+          acc.x = fmaf(gr.x, ns, acc.x);
+          acc.y = fmaf(gr.y, ns, acc.y);
+          acc.z = fmaf(gr.z, ns, acc.z);
+          acc.w = fmaf(gr.w, nt, acc.w);
+        }
+      }
+    }
+    if (i >= n) return;
+  } else {
+    if (i >= n) return;
+    const float4 p = load_point(pts, i);
+    const float* drow = dfeat + i * (long long)(g.L * F);
+    for (int l = 0; l < g.L; ++l) {
+      uint32_t idx[16];
+      float w[16];
+      level_corners(g, l, p, idx, w);
+      float d[F];
 #pragma unroll
-    for (int f = 0; f < F; ++f) d[f] = __ldg(drow + l * F + f);
-    level_coord_grad<TT, F>(g, l, p, table + g.offset[l] * F, idx, d, acc);
+      for (int f = 0; f < F; ++f) d[f] = __ldg(drow + l * F + f);
+      level_coord_grad<TT, F>(g, l, p, table + g.offset[l] * F, idx, d, acc);
+    }
   }
   const float4 m = coord_inside(pts, i);
   const long long cap = pts.n;
