@@ -47,6 +47,81 @@ __device__ __forceinline__ void level_corners3(const Geom& g, int l, float3 p, u
   }
 }
 
+// The indices of the 4 corners with x bit xb (corner b = xb | 2q, q over
+// the y, z bits) of level l around p, and the fractional offsets, with the
+// arithmetic of level_corners3.
+__device__ __forceinline__ void level_index3_x(const Geom& g, int l, float3 p, uint32_t xb, uint32_t idx[4],
+                                               float fr[3]) {
+  const int ns = g.res_s[l];
+  int ix, iy, iz;
+  axis_cell(p.x, ns, ix, fr[0]);
+  axis_cell(p.y, ns, iy, fr[1]);
+  axis_cell(p.z, ns, iz, fr[2]);
+  if ((g.dense_bits >> l) & 1u) {
+    const uint32_t R = (uint32_t)ns + 1u;
+    const uint32_t base = (uint32_t)ix + R * ((uint32_t)iy + R * (uint32_t)iz) + xb;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) idx[q] = base + (q & 1) * R + ((q >> 1) & 1) * R * R;
+  } else {
+    const uint32_t hx = (uint32_t)ix * g.primes[0] + (xb ? g.primes[0] : 0u);
+    const uint32_t hy0 = (uint32_t)iy * g.primes[1], hy1 = hy0 + g.primes[1];
+    const uint32_t hz0 = (uint32_t)iz * g.primes[2], hz1 = hz0 + g.primes[2];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) idx[q] = (hx ^ (q & 1 ? hy1 : hy0) ^ (q & 2 ? hz1 : hz0)) & g.mask;
+  }
+}
+
+// Weights of the corners with x bit xb, as level_corners3 forms them.
+__device__ __forceinline__ void level_weights3_x(const float fr[3], uint32_t xb, float w[4]) {
+  const float wx = xb ? fr[0] : 1.0f - fr[0], wy0 = 1.0f - fr[1], wz0 = 1.0f - fr[2];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float v = wx;
+    v *= (q & 1) ? fr[1] : wy0;
+    v *= (q & 2) ? fr[2] : wz0;
+    w[q] = v;
+  }
+}
+
+// G_3D level l (F = 2) of this lane's own Gaussian, the value gather2_pairs
+// forms bit for bit, with the loads issued by the lane pair: lane xb loads
+// the corners with x bit xb of both Gaussians A (pa) and B (pb), and the
+// lanes swap the halves they loaded for each other (as gather2_level_paired
+// does in 4-D).
+template <typename TT>
+__device__ __forceinline__ void gather2_level3_paired(const Geom& g, int l, float3 pa, float3 pb, uint32_t xb,
+                                                      const TT* __restrict__ base, unsigned int pm, float acc[2]) {
+  uint32_t ia[4], ib[4];
+  float fa[3], fb[3], fr[3];
+  level_index3_x(g, l, pa, xb, ia, fa);
+  level_index3_x(g, l, pb, xb, ib, fb);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) fr[k] = xb ? fb[k] : fa[k];
+  float w0[4], w1[4];
+  level_weights3_x(fr, 0u, w0);
+  level_weights3_x(fr, 1u, w1);
+  Entry2<TT> ea[4], eb[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    ea[q] = Entry2<TT>::load(base + (size_t)ia[q] * 2);
+    eb[q] = Entry2<TT>::load(base + (size_t)ib[q] * 2);
+  }
+  float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float2 own = (xb ? eb[q] : ea[q]).f();
+    const float2 snd = (xb ? ea[q] : eb[q]).f();
+    const float2 other = make_float2(__shfl_xor_sync(pm, snd.x, 1), __shfl_xor_sync(pm, snd.y, 1));
+    const float2 e0 = xb ? other : own, e1 = xb ? own : other;
+    a0 = fmaf(w0[q], e0.x, a0);
+    a1 = fmaf(w0[q], e0.y, a1);
+    a0 = fmaf(w1[q], e1.x, a0);
+    a1 = fmaf(w1[q], e1.y, a1);
+  }
+  acc[0] = a0;
+  acc[1] = a1;
+}
+
 template <typename TT, int F>
 __global__ void __launch_bounds__(kThreads) decomp_fwd_kernel(Geom g, const float* __restrict__ xs,
                                                               const float* __restrict__ ys,
@@ -76,6 +151,8 @@ __global__ void __launch_bounds__(kThreads) decomp_fwd_kernel(Geom g, const floa
   float h[kHidden3];
 #pragma unroll
   for (int j = 0; j < kHidden3; ++j) h[j] = b1[j];
+  // the gathers here are one Gaussian per lane: with lane pairs (as in the
+  // backward) this ALU-heavy kernel measured slower
   for (int l = 0; l < g.L; ++l) {
     uint32_t idx[8];
     float w[8];
@@ -208,18 +285,32 @@ __global__ void __launch_bounds__(kBwdRows) decomp_bwd_kernel(const __grid_const
     for (int j = 0; j < kHidden3; ++j) h[j] = b1[j];
     float3 p = make_float3(0.f, 0.f, 0.f);
     if (valid) p = make_float3(clamp01(__ldg(a.x + i)), clamp01(__ldg(a.y + i)), clamp01(__ldg(a.z + i)));
+    // F = 2: lane pairs -- Gaussian A is the even lane's, B the odd lane's
+    const uint32_t xb = (uint32_t)(r & 1);
+    const unsigned int pm = 3u << (r & 30);
+    const bool va = i - (long long)xb < a.n, vb = i - (long long)xb + 1 < a.n;  // the same on both lanes
+    float3 pa = p, pb = p;
+    if constexpr (F == 2) {
+      const float3 q =
+          make_float3(__shfl_xor_sync(pm, p.x, 1), __shfl_xor_sync(pm, p.y, 1), __shfl_xor_sync(pm, p.z, 1));
+      pa = xb ? q : p;
+      pb = xb ? p : q;
+    }
     for (int l = 0; l < a.g.L; ++l) {
       float f[F];
 #pragma unroll
       for (int k = 0; k < F; ++k) f[k] = 0.f;
-      if (valid) {
+      if constexpr (F == 2) {
+        if (va) {
+          gather2_level3_paired<TT>(a.g, l, pa, pb, xb, table + a.g.offset[l] * 2, pm, f);
+          if (!valid) f[0] = f[1] = 0.f;
+        }
+      } else if (valid) {
         uint32_t idx[8];
         float w[8];
         level_corners3(a.g, l, p, idx, w);
         const TT* base = table + a.g.offset[l] * F;
-        if constexpr (F == 2) {
-          gather2_pairs<TT, 8>(base, idx, w, f);
-        } else {
+        {
 #pragma unroll
           for (int b = 0; b < 8; ++b) {
             float e[F];
@@ -276,7 +367,7 @@ __global__ void __launch_bounds__(kBwdRows) decomp_bwd_kernel(const __grid_const
       h[j] = dz;  // h now holds dz1
     }
     // dL/df = W1^T dz1, scattered into the tables level by level
-    if (valid) {
+    if (F == 2 ? va : valid) {
       for (int l = 0; l < a.g.L; ++l) {
         float df[F];
 #pragma unroll
@@ -293,13 +384,26 @@ __global__ void __launch_bounds__(kBwdRows) decomp_bwd_kernel(const __grid_const
           }
           df[k] = v;
         }
-        uint32_t idx[8];
-        float w[8];
-        level_corners3(a.g, l, p, idx, w);
         float* gbase = a.table_grad + a.g.offset[l] * F;
         if constexpr (F == 2) {
-          scatter2_pairs<8>(gbase, idx, w, df[0], df[1]);
+          // the pair's two Gaussians, lane xb issuing the corners with x bit xb
+          const float e0 = __shfl_xor_sync(pm, df[0], 1), e1 = __shfl_xor_sync(pm, df[1], 1);
+          const float a0 = xb ? e0 : df[0], a1 = xb ? e1 : df[1], b0 = xb ? df[0] : e0, b1 = xb ? df[1] : e1;
+          uint32_t ia[4], ib[4];
+          float fa[3], fb[3], wa[4], wb[4];
+          level_index3_x(a.g, l, pa, xb, ia, fa);
+          level_index3_x(a.g, l, pb, xb, ib, fb);
+          level_weights3_x(fa, xb, wa);
+          level_weights3_x(fb, xb, wb);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            red_add_v2(gbase + (size_t)ia[q] * 2, wa[q] * a0, wa[q] * a1);
+            if (vb) red_add_v2(gbase + (size_t)ib[q] * 2, wb[q] * b0, wb[q] * b1);
+          }
         } else {
+          uint32_t idx[8];
+          float w[8];
+          level_corners3(a.g, l, p, idx, w);
 #pragma unroll
           for (int b = 0; b < 8; ++b) {
             float* e = gbase + (size_t)idx[b] * F;

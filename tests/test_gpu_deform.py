@@ -388,3 +388,52 @@ def test_forward_access_forms_bit_identical(dashlib, n_all, n, tdtype, grid):
     ref = oracle.deform_fwd(g, oracle.Points(*coords, idx=idx), table.astype(np.float64), mlpc.d_hidden,
                             mlpc.d_out, params.astype(np.float64))
     assert rel_err(outs[0][0].numpy()[:, :n], ref) < 1e-3
+
+
+@pytest.mark.parametrize("coord", [False, True])
+def test_backward_device_count_broadcast_t(dashlib, coord):
+    """Fused forward + backward through an index list whose live length is
+    an odd device count below the capacity, with one broadcast timestamp:
+    the lane-paired gathers, scatter, coordinate gradient and (without the
+    coordinate gradient) the Eq. 11 kernel against the oracle."""
+    grid, mlpc = synth.PAPER_GRID, synth.PAPER_MLP
+    rng = np.random.default_rng(81)
+    n_all, cap, live = 9000, 4001, 2999
+    g = oracle_grid(grid)
+    x, y, z, _ = synth.scene_coords(rng, n_all)
+    t = np.array([0.37], dtype=np.float32)
+    idx = np.sort(rng.choice(n_all, size=cap, replace=False)).astype(np.int32)
+    table = synth.table_values(rng, g.total, grid.F, np.float16)
+    params = synth.mlp_params(rng, mlpc)
+    dd = synth.upstream_grad(rng, mlpc.d_out, cap)
+    lay = dashlib.layout_from(grid)
+    cnt = torch.tensor([live], dtype=torch.int64, device="cuda")
+    pts = dashlib.Points(to_dev(x), to_dev(y), to_dev(z), to_dev(t), idx=to_dev(idx), n=cap, n_dev=cnt)
+    assert pts.t_stride == 0
+    mlp = dashlib.Mlp(to_dev(params), mlpc.d_in, mlpc.d_hidden, mlpc.d_out)
+    tab = to_dev(table)
+    st = dashlib.deform_state(mlp, cap, "cuda")
+    delta = dashlib.dash_deform_mlp_fwd(lay, pts, tab, mlp, fwd_state=st).cpu().numpy()
+    tg = torch.zeros((g.total, 2), dtype=torch.float32, device="cuda")
+    pg = torch.zeros(mlpc.n_params, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    lam, es, et = (0.0, (0.0,) * 3, 0.0) if coord else (0.6, (1 / 2048, 1 / 2048, 1 / 2048), 1 / 300)
+    cg = torch.full((4, cap), 7.0, dtype=torch.float32, device="cuda") if coord else None
+    dashlib.dash_deform_mlp_bwd(lay, pts, tab, mlp, to_dev(dd), tg, pg, fwd_state=st,
+                                smooth=None if coord else (lam, es, et, loss), coord_grad=cg)
+    opts = oracle.Points(x, y, z, t, idx=idx[:live], t_stride=0)
+    ref = oracle.deform_fwd(g, opts, table.astype(np.float64), 64, 10, params.astype(np.float64))
+    assert rel_err(delta[:, :live], ref) < 1e-3
+    rtg, rpg, rl = oracle.deform_bwd(g, opts, table.astype(np.float64), 64, 10, params.astype(np.float64),
+                                     dd[:, :live].astype(np.float64), lam, es, et)
+    assert rel_err(tg.cpu().numpy(), rtg) < 1e-2 and rel_err(pg.cpu().numpy(), rpg) < 1e-2
+    if coord:
+        fh = oracle.encode(g, opts, table.astype(np.float64))
+        dfh, _ = oracle.mlp_bwd(32, 64, 10, params.astype(np.float64), fh, dd[:, :live].astype(np.float64))
+        rcg = oracle.encode_coord_grad(g, opts, table.astype(np.float64), dfh)
+        c = cg.cpu().numpy()
+        for ax in range(4):
+            assert rel_err(c[ax, :live], rcg[ax]) < 1e-2, ax
+        assert np.all(c[:, live:] == 7.0)
+    else:
+        assert abs(float(loss.item()) - rl) <= 1e-2 * abs(rl)
