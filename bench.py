@@ -45,9 +45,9 @@ STEP_BYTES = 2 + 4 + FWD_BYTES + BWD_BYTES
 # (profiles/warp_specialised_kernels_1M.md), valid while the kernel's sources
 # hash to the captured value; otherwise the benchmark reports no traffic.
 NCU_TRAFFIC = {
-    "bwd": {"bytes": (196.9 + 4.0) * 1e6, "n": 1_000_000, "sha256_16": "fd2b775637185288",
+    "bwd": {"bytes": (196.6 + 4.1) * 1e6, "n": 1_000_000, "sha256_16": "1fc3eed2c906ae59",
             "sources": ("deform_bwd.cu", "deform_common.cuh", "dash_internal.cuh", "tc_ptx.cuh")},
-    "fwd": {"bytes": (45.8 + 71.7) * 1e6, "n": 1_000_000, "sha256_16": "9b5a1c705694f0ac",
+    "fwd": {"bytes": (45.7 + 71.8) * 1e6, "n": 1_000_000, "sha256_16": "fee0a2fbcb4a4568",
             "sources": ("deform_fwd.cu", "deform_common.cuh", "dash_internal.cuh", "tc_ptx.cuh")},
 }
 
@@ -870,7 +870,7 @@ def profile_case(n):
     """Small case for ncu captures: n dynamic Gaussians (no compaction), about
     1 GB on the device, two launches each of the encoder forward/backward, the
     fused forward/backward (the backward once more with the coordinate
-    gradient), the decomposition with its top-k mask and its backward, one
+    gradient and once with the Eq. 11 term), the decomposition with its top-k mask and its backward, one
     occupancy count, and
     two render frames (1352 x 1014, 106.6k Gaussians) with the renderer's
     backward."""
@@ -906,6 +906,8 @@ def profile_case(n):
         dash.dash_deform_mlp_fwd(lay, pts, table, mlp, delta_out=delta, fwd_state=state)
         dash.dash_deform_mlp_bwd(lay, pts, table, mlp, dd, tg, pg, fwd_state=state)
         dash.dash_deform_mlp_bwd(lay, pts, table, mlp, dd, tg, pg, fwd_state=state, coord_grad=cg)
+        dash.dash_deform_mlp_bwd(lay, pts, table, mlp, dd, tg, pg, fwd_state=state,
+                                 smooth=(1.0, (1 / 2048, 1 / 2048, 1 / 2048), 1 / 300, None))
         _, norm, _ = dash.dash_decomp_fwd(lay3, pts.x, pts.y, pts.z, table3, dec, t=pts.t)
         mask, _ = dash.dash_topk_mask(norm, 50.0)
         dash.dash_decomp_bwd(lay3, pts.x, pts.y, pts.z, table3, dec, tg3, pg3, d_dp=d_dp, mask=mask, lambda_s=1.0)
