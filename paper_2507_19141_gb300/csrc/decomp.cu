@@ -209,13 +209,20 @@ __global__ void __launch_bounds__(kThreads) decomp_fwd_kernel(Geom g, const floa
 // ---------------------------------------------------------- backward ------
 // Gradients of  sum_i d_dp_i . dp_i + lambda_s L_s  (Eq. 5 over the static
 // Gaussians of `mask`) w.r.t. the G_3D tables and the packed W1, b1, W2, b2.
-// CTA of kBwdRows threads, one Gaussian each, persistent over tiles.  Per
-// tile every thread recomputes its encoding and decoder, back-propagates to
-// dL/df and scatters it into the tables; it leaves f, h, dz1 and the dp
-// gradient in shared memory, from which the CTA contracts the weight
-// gradients over the tile's Gaussians into per-thread register accumulators,
-// flushed with one atomic per weight and CTA at the end.
+// Persistent CTAs over tiles of kBwdRows Gaussians, two threads per
+// Gaussian (lanes 2r and 2r + 1 of the CTA take tile row r): thread half hb
+// gathers and scatters the corners whose x bit is hb (so an x-neighbour
+// pair's two accesses leave in one warp instruction) and owns half of the
+// hidden units of phi_p (groups of four, interleaved between the two); the two halves add their shares of the
+// encoding, of phi_l and of dL/df with one shuffle each.  Per tile the CTA
+// leaves f, relu(h), dz1 and the dp gradient in shared memory and contracts
+// the weight gradients over the tile's Gaussians into per-thread register
+// accumulators, flushed with one atomic per weight and CTA at the end.
+// Splitting each Gaussian over two threads halves the per-thread registers,
+// which doubles the warps an SM holds for this latency-bound work.
 constexpr int kBwdRows = 128;
+constexpr int kBwdThreads = 2 * kBwdRows;
+constexpr int kHalfHidden = kHidden3 / 2;
 
 struct DecompBwdArgs {
   Geom g;
@@ -244,104 +251,106 @@ __global__ void __launch_bounds__(kThreads) count_static_kernel(const uint8_t* _
   if ((threadIdx.x & 31) == 0 && c != 0u) atomicAdd(out, (unsigned long long)c);
 }
 
+// The sum over a thread pair, the hb = 0 thread's term first on both.
+__device__ __forceinline__ float half_pair_sum(float v, uint32_t hb, unsigned int pm) {
+  const float o = __shfl_xor_sync(pm, v, 1);
+  return hb ? o + v : v + o;
+}
+
 template <typename TT, int F>
-__global__ void __launch_bounds__(kBwdRows) decomp_bwd_kernel(const __grid_constant__ DecompBwdArgs a) {
+__global__ void __launch_bounds__(kBwdThreads, 2) decomp_bwd_kernel(const __grid_constant__ DecompBwdArgs a) {
   extern __shared__ __align__(16) float sm[];
-  const int D = a.D, r = threadIdx.x;
+  const int D = a.D, t = threadIdx.x;
+  const int r = t >> 1;                       // tile row of this thread pair
+  const uint32_t hb = (uint32_t)(t & 1);      // x half of the corners, half of the hidden units
+  // this thread's hidden units: j(u) = 8 (u / 4) + 4 hb + u % 4, so the two
+  // threads of a pair read neighbouring 16-byte groups of a weight row
+  // (different shared-memory banks, one wavefront)
+  const int u0 = 4 * (int)hb;
+  const unsigned int pm = 3u << (t & 30);
   // weights: W1 transposed [D][64], b1 [64], W2 [3][64], b2 [3]; per tile:
-  // f [kBwdRows][D], h [kBwdRows][64], dz1 [kBwdRows][64], gdp [kBwdRows][4]
+  // f [kBwdRows][D + 4], relu(h) [kBwdRows][65], dz1 [kBwdRows][65], gdp [kBwdRows][4]
   float* W1t = sm;
   float* b1 = W1t + kHidden3 * D;
   float* W2 = b1 + kHidden3;
   float* b2 = W2 + 3 * kHidden3;
   float* s_f = b2 + 4;  // 64 D + 64 + 192 + 4 floats: a multiple of 4 (16-byte aligned rows for D % 4 == 0)
-  float* s_h = s_f + kBwdRows * D;
-  float* s_dz = s_h + kBwdRows * kHidden3;
-  float* s_g = s_dz + kBwdRows * kHidden3;
+  // padded row strides: a warp's threads write 16 different rows at once,
+  // which with strides of 64 or D floats would all fall in one bank
+  const int SF = D + 4;            // keeps f rows 16-byte aligned for D % 4 == 0
+  constexpr int SH = kHidden3 + 1;
+  float* s_h = s_f + kBwdRows * SF;
+  float* s_dz = s_h + kBwdRows * SH;
+  float* s_g = s_dz + kBwdRows * SH;
   const int P = kHidden3 * D + kHidden3 + 3 * kHidden3 + 3;
-  for (int e = r; e < P; e += kBwdRows) {
+  for (int e = t; e < P; e += kBwdThreads) {
     const int dst = e < kHidden3 * D ? (e % D) * kHidden3 + e / D : e;
     W1t[dst] = __ldg(a.params + e);
   }
   const TT* table = static_cast<const TT*>(a.table);
   const float inv_ns = (a.mask != nullptr && *a.n_static > 0ull) ? 1.0f / (float)*a.n_static : 0.0f;
-  // this thread's weight-gradient outputs: dW1 rows j = r / 2, columns of one half
-  const int j1 = r >> 1;
-  const int kh = (D + 1) / 2, k0 = (r & 1) * kh;
-  const int nk = (k0 + kh <= D) ? kh : D - k0;
-  float acc1[32];
+  // this thread's weight-gradient outputs: dW1 row j1 = t / 4, a quarter of its columns;
+  // db1[t] (t < 64) or dW2 entry t - 64 (64 <= t < 256); db2[t] (t < 3)
+  const int j1 = t >> 2;
+  const int kq = (D + 3) / 4, k0 = (t & 3) * kq;
+  const int nk = k0 + kq <= D ? kq : (D > k0 ? D - k0 : 0);
+  float acc1[16];
 #pragma unroll
-  for (int q = 0; q < 32; ++q) acc1[q] = 0.f;
-  float acc_b1 = 0.f;         // b1[r] for r < 64
-  float acc2[2] = {0.f, 0.f}; // W2 entries r and r + 128 (of 192)
-  float acc_b2 = 0.f;         // b2[r] for r < 3
+  for (int q = 0; q < 16; ++q) acc1[q] = 0.f;
+  float acc_x = 0.f, acc_b2 = 0.f;
   __syncthreads();
   const long long ntiles = (a.n + kBwdRows - 1) / kBwdRows;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long i = tile * kBwdRows + r;
-    const bool valid = i < a.n;
-    float h[kHidden3];
+    const bool valid = i < a.n;  // the same for both threads of the pair
+    float h[kHalfHidden];
 #pragma unroll
-    for (int j = 0; j < kHidden3; ++j) h[j] = b1[j];
+    for (int u = 0; u < kHalfHidden; ++u) h[u] = b1[8 * (u >> 2) + u0 + (u & 3)];
     float3 p = make_float3(0.f, 0.f, 0.f);
     if (valid) p = make_float3(clamp01(__ldg(a.x + i)), clamp01(__ldg(a.y + i)), clamp01(__ldg(a.z + i)));
-    // F = 2: lane pairs -- Gaussian A is the even lane's, B the odd lane's
-    const uint32_t xb = (uint32_t)(r & 1);
-    const unsigned int pm = 3u << (r & 30);
-    const bool va = i - (long long)xb < a.n, vb = i - (long long)xb + 1 < a.n;  // the same on both lanes
-    float3 pa = p, pb = p;
-    if constexpr (F == 2) {
-      const float3 q =
-          make_float3(__shfl_xor_sync(pm, p.x, 1), __shfl_xor_sync(pm, p.y, 1), __shfl_xor_sync(pm, p.z, 1));
-      pa = xb ? q : p;
-      pb = xb ? p : q;
-    }
     for (int l = 0; l < a.g.L; ++l) {
       float f[F];
 #pragma unroll
       for (int k = 0; k < F; ++k) f[k] = 0.f;
-      if constexpr (F == 2) {
-        if (va) {
-          gather2_level3_paired<TT>(a.g, l, pa, pb, xb, table + a.g.offset[l] * 2, pm, f);
-          if (!valid) f[0] = f[1] = 0.f;
-        }
-      } else if (valid) {
-        uint32_t idx[8];
-        float w[8];
-        level_corners3(a.g, l, p, idx, w);
+      if (valid) {
+        uint32_t idx[4];
+        float fr[3], w[4];
+        level_index3_x(a.g, l, p, hb, idx, fr);
+        level_weights3_x(fr, hb, w);
         const TT* base = table + a.g.offset[l] * F;
-        {
 #pragma unroll
-          for (int b = 0; b < 8; ++b) {
-            float e[F];
-            load_entry<TT, F>(base + (size_t)idx[b] * F, e);
+        for (int q = 0; q < 4; ++q) {
+          float e[F];
+          load_entry<TT, F>(base + (size_t)idx[q] * F, e);
 #pragma unroll
-            for (int k = 0; k < F; ++k) f[k] = fmaf(w[b], e[k], f[k]);
-          }
+          for (int k = 0; k < F; ++k) f[k] = fmaf(w[q], e[k], f[k]);
         }
+#pragma unroll
+        for (int k = 0; k < F; ++k) f[k] = half_pair_sum(f[k], hb, pm);
       }
 #pragma unroll
       for (int k = 0; k < F; ++k) {
         const int col = l * F + k;
-        s_f[r * D + col] = f[k];
-        const float4* wc = reinterpret_cast<const float4*>(W1t + col * kHidden3);
+        if (hb == 0u) s_f[r * SF + col] = f[k];
+        const float* wc = W1t + col * kHidden3 + u0;
 #pragma unroll
-        for (int j4 = 0; j4 < kHidden3 / 4; ++j4) {
-          const float4 wv = wc[j4];
-          h[4 * j4 + 0] = fmaf(wv.x, f[k], h[4 * j4 + 0]);
-          h[4 * j4 + 1] = fmaf(wv.y, f[k], h[4 * j4 + 1]);
-          h[4 * j4 + 2] = fmaf(wv.z, f[k], h[4 * j4 + 2]);
-          h[4 * j4 + 3] = fmaf(wv.w, f[k], h[4 * j4 + 3]);
+        for (int u4 = 0; u4 < kHalfHidden / 4; ++u4) {
+          const float4 wv = *reinterpret_cast<const float4*>(wc + 8 * u4);
+          h[4 * u4 + 0] = fmaf(wv.x, f[k], h[4 * u4 + 0]);
+          h[4 * u4 + 1] = fmaf(wv.y, f[k], h[4 * u4 + 1]);
+          h[4 * u4 + 2] = fmaf(wv.z, f[k], h[4 * u4 + 2]);
+          h[4 * u4 + 3] = fmaf(wv.w, f[k], h[4 * u4 + 3]);
         }
       }
     }
-    // phi_l, the dp gradient (upstream + Eq. 5), and back through phi_l
+    // phi_l (the two halves' shares added), the dp gradient (upstream + Eq. 5), and back through phi_l
     float dp[3], s = 0.f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      float v = b2[c];
+      float v = 0.f;
 #pragma unroll
-      for (int j = 0; j < kHidden3; ++j) v = fmaf(W2[c * kHidden3 + j], fmaxf(h[j], 0.f), v);
+      for (int u = 0; u < kHalfHidden; ++u) v = fmaf(W2[c * kHidden3 + 8 * (u >> 2) + u0 + (u & 3)], fmaxf(h[u], 0.f), v);
+      v = b2[c] + half_pair_sum(v, hb, pm);
       dp[c] = v;
       s = fmaf(v, v, s);
     }
@@ -355,78 +364,67 @@ __global__ void __launch_bounds__(kBwdRows) decomp_bwd_kernel(const __grid_const
         if (stat) gd[c] = fmaf(a.lambda_s * inv_ns, dp[c] / norm, gd[c]);
       }
     }
+    if (hb == 0u) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) s_g[r * 4 + c] = gd[c];
+      for (int c = 0; c < 3; ++c) s_g[r * 4 + c] = gd[c];
+    }
     // h -> relu(h) kept for dW2; dz1 = (W2^T gd) * [z1 > 0] kept for dW1, db1
 #pragma unroll
-    for (int j = 0; j < kHidden3; ++j) {
+    for (int u = 0; u < kHalfHidden; ++u) {
+      const int j = 8 * (u >> 2) + u0 + (u & 3);
       const float dh = W2[j] * gd[0] + W2[kHidden3 + j] * gd[1] + W2[2 * kHidden3 + j] * gd[2];
-      const float dz = h[j] > 0.f ? dh : 0.f;
-      s_h[r * kHidden3 + j] = fmaxf(h[j], 0.f);
-      s_dz[r * kHidden3 + j] = dz;
-      h[j] = dz;  // h now holds dz1
+      const float dz = h[u] > 0.f ? dh : 0.f;
+      s_h[r * SH + j] = fmaxf(h[u], 0.f);
+      s_dz[r * SH + j] = dz;
+      h[u] = dz;  // h now holds this thread's half of dz1
     }
-    // dL/df = W1^T dz1, scattered into the tables level by level
-    if (F == 2 ? va : valid) {
+    // dL/df = W1^T dz1 (the halves' shares added), scattered into the tables level by level
+    if (valid) {
       for (int l = 0; l < a.g.L; ++l) {
         float df[F];
 #pragma unroll
         for (int k = 0; k < F; ++k) {
-          const float4* wc = reinterpret_cast<const float4*>(W1t + (l * F + k) * kHidden3);
+          const float* wc = W1t + (l * F + k) * kHidden3 + u0;
           float v = 0.f;
 #pragma unroll
-          for (int j4 = 0; j4 < kHidden3 / 4; ++j4) {
-            const float4 wv = wc[j4];
-            v = fmaf(wv.x, h[4 * j4], v);
-            v = fmaf(wv.y, h[4 * j4 + 1], v);
-            v = fmaf(wv.z, h[4 * j4 + 2], v);
-            v = fmaf(wv.w, h[4 * j4 + 3], v);
+          for (int u4 = 0; u4 < kHalfHidden / 4; ++u4) {
+            const float4 wv = *reinterpret_cast<const float4*>(wc + 8 * u4);
+            v = fmaf(wv.x, h[4 * u4], v);
+            v = fmaf(wv.y, h[4 * u4 + 1], v);
+            v = fmaf(wv.z, h[4 * u4 + 2], v);
+            v = fmaf(wv.w, h[4 * u4 + 3], v);
           }
-          df[k] = v;
+          df[k] = half_pair_sum(v, hb, pm);
         }
+        uint32_t idx[4];
+        float fr[3], w[4];
+        level_index3_x(a.g, l, p, hb, idx, fr);
+        level_weights3_x(fr, hb, w);
         float* gbase = a.table_grad + a.g.offset[l] * F;
-        if constexpr (F == 2) {
-          // the pair's two Gaussians, lane xb issuing the corners with x bit xb
-          const float e0 = __shfl_xor_sync(pm, df[0], 1), e1 = __shfl_xor_sync(pm, df[1], 1);
-          const float a0 = xb ? e0 : df[0], a1 = xb ? e1 : df[1], b0 = xb ? df[0] : e0, b1 = xb ? df[1] : e1;
-          uint32_t ia[4], ib[4];
-          float fa[3], fb[3], wa[4], wb[4];
-          level_index3_x(a.g, l, pa, xb, ia, fa);
-          level_index3_x(a.g, l, pb, xb, ib, fb);
-          level_weights3_x(fa, xb, wa);
-          level_weights3_x(fb, xb, wb);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            red_add_v2(gbase + (size_t)ia[q] * 2, wa[q] * a0, wa[q] * a1);
-            if (vb) red_add_v2(gbase + (size_t)ib[q] * 2, wb[q] * b0, wb[q] * b1);
-          }
-        } else {
-          uint32_t idx[8];
-          float w[8];
-          level_corners3(a.g, l, p, idx, w);
+        for (int q = 0; q < 4; ++q) {
+          float* e = gbase + (size_t)idx[q] * F;
+          if constexpr (F == 1) {
+            atomicAdd(e, w[q] * df[0]);
+          } else if constexpr (F == 2) {
+            red_add_v2(e, w[q] * df[0], w[q] * df[1]);
+          } else {
 #pragma unroll
-          for (int b = 0; b < 8; ++b) {
-            float* e = gbase + (size_t)idx[b] * F;
-            if constexpr (F == 1) {
-              atomicAdd(e, w[b] * df[0]);
-            } else {
-#pragma unroll
-              for (int k = 0; k < F; k += 4)
-                red_add_v4(e + k, w[b] * df[k], w[b] * df[k + 1], w[b] * df[k + 2], w[b] * df[k + 3]);
-            }
+            for (int k = 0; k < F; k += 4)
+              red_add_v4(e + k, w[q] * df[k], w[q] * df[k + 1], w[q] * df[k + 2], w[q] * df[k + 3]);
           }
         }
       }
     }
     __syncthreads();
-    // weight gradients of this tile (rows of invalid threads are zero)
-    const bool vec4 = (D & 7) == 0;  // f rows and this thread's half start on 16-byte boundaries
+    // weight gradients of this tile (rows of invalid Gaussians are zero)
+    const bool vec4 = (kq & 3) == 0 && (D & 3) == 0;  // this thread's columns start on 16-byte boundaries
     for (int g_ = 0; g_ < kBwdRows; ++g_) {
-      const float dz = s_dz[g_ * kHidden3 + j1];
-      const float* fr = s_f + g_ * D + k0;
+      const float dz = s_dz[g_ * SH + j1];
+      const float* fr = s_f + g_ * SF + k0;
       if (vec4) {
 #pragma unroll
-        for (int q4 = 0; q4 < 8; ++q4) {
+        for (int q4 = 0; q4 < 4; ++q4) {
           if (4 * q4 < nk) {
             const float4 fv = *reinterpret_cast<const float4*>(fr + 4 * q4);
             acc1[4 * q4 + 0] = fmaf(dz, fv.x, acc1[4 * q4 + 0]);
@@ -437,16 +435,16 @@ __global__ void __launch_bounds__(kBwdRows) decomp_bwd_kernel(const __grid_const
         }
       } else {
 #pragma unroll
-        for (int q = 0; q < 32; ++q)
+        for (int q = 0; q < 16; ++q)
           if (q < nk) acc1[q] = fmaf(dz, fr[q], acc1[q]);
       }
-      if (r < kHidden3) acc_b1 += s_dz[g_ * kHidden3 + r];
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int e = r + u * kBwdRows;  // W2 entry e = c * 64 + j
-        if (e < 3 * kHidden3) acc2[u] = fmaf(s_g[g_ * 4 + e / kHidden3], s_h[g_ * kHidden3 + (e % kHidden3)], acc2[u]);
+      if (t < kHidden3) {
+        acc_x += s_dz[g_ * SH + t];
+      } else {
+        const int e = t - kHidden3;  // W2 entry e = c * 64 + j
+        acc_x = fmaf(s_g[g_ * 4 + e / kHidden3], s_h[g_ * SH + (e % kHidden3)], acc_x);
       }
-      if (r < 3) acc_b2 += s_g[g_ * 4 + r];
+      if (t < 3) acc_b2 += s_g[g_ * 4 + t];
     }
     __syncthreads();
   }
@@ -456,15 +454,10 @@ __global__ void __launch_bounds__(kBwdRows) decomp_bwd_kernel(const __grid_const
   float* gW2 = gb1 + kHidden3;
   float* gb2 = gW2 + 3 * kHidden3;
 #pragma unroll
-  for (int q = 0; q < 32; ++q)
+  for (int q = 0; q < 16; ++q)
     if (q < nk && acc1[q] != 0.f) atomicAdd(gW1 + j1 * D + k0 + q, acc1[q]);
-  if (r < kHidden3 && acc_b1 != 0.f) atomicAdd(gb1 + r, acc_b1);
-#pragma unroll
-  for (int u = 0; u < 2; ++u) {
-    const int e = r + u * kBwdRows;
-    if (e < 3 * kHidden3 && acc2[u] != 0.f) atomicAdd(gW2 + e, acc2[u]);
-  }
-  if (r < 3 && acc_b2 != 0.f) atomicAdd(gb2 + r, acc_b2);
+  if (acc_x != 0.f) atomicAdd(t < kHidden3 ? gb1 + t : gW2 + (t - kHidden3), acc_x);
+  if (t < 3 && acc_b2 != 0.f) atomicAdd(gb2 + t, acc_b2);
 }
 
 // ----------------------------------------------------------- radix select --
@@ -714,7 +707,7 @@ int dash_decomp_bwd(const dash_layout* layout, const float* x, const float* y, c
     if (int s = launch_status("count_static_kernel")) return s;
   }
   const size_t smem = sizeof(float) * ((size_t)kHidden3 * D + kHidden3 + 3 * kHidden3 + 4 +
-                                       (size_t)kBwdRows * (D + 2 * kHidden3 + 4));
+                                       (size_t)kBwdRows * ((D + 4) + 2 * (kHidden3 + 1) + 4));
   const long long ntiles = (n + kBwdRows - 1) / kBwdRows;
   long long grid = 2ll * sm_count();
   grid = ntiles < grid ? ntiles : grid;
@@ -724,7 +717,7 @@ int dash_decomp_bwd(const dash_layout* layout, const float* x, const float* y, c
     if (int s = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),     \
                             "cudaFuncSetAttribute(decomp_bwd)"))                                                     \
       return s;                                                                                                     \
-    kern<<<(unsigned)grid, kBwdRows, smem, st>>>(a);                                                                \
+    kern<<<(unsigned)grid, kBwdThreads, smem, st>>>(a);                                                             \
   }
   if (table_dtype == DASH_F16) {
     switch (a.g.F) {
