@@ -27,6 +27,9 @@ def test_reference_arm_prints_contract_line():
     assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "Gaussians/s"
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+    sys.path.insert(0, ROOT)
+    import bench
+    assert line["config"] == bench.step_config(bench.parse_args([]), 1)  # the same workload as our arm
 
 
 def _rank_main(rank, world, port, q):

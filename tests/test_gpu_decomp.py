@@ -177,3 +177,33 @@ def test_decomposition_backward_matches_oracle(dashlib, tdtype, with_up, with_ls
     pgn = pg.cpu().numpy()
     for a, b in zip(bounds[:-1], bounds[1:]):
         assert rel_err(pgn[a:b], rpg[a:b]) < 1e-4, (a, b, rel_err(pgn[a:b], rpg[a:b]))
+
+
+@pytest.mark.parametrize("L,F,tdtype,n", [(16, 1, np.float32, 5_001), (8, 4, np.float16, 3_333),
+                                          (4, 8, np.float32, 257), (16, 2, np.float16, 1)])
+def test_decomposition_backward_feature_widths(dashlib, L, F, tdtype, n):
+    """The two-threads-per-Gaussian backward for F = 1, 4, 8 (and F = 2 with a
+    single Gaussian): tile tails, L*F of 16..32, FP16 and FP32 tables."""
+    rng = np.random.default_rng(90 + F)
+    cfg = dict(L=L, F=F, log2_T=14, nmin=16, nmax=512)
+    g = oracle.layout3(**cfg)
+    x, y, z, _ = synth.scene_coords(rng, n)
+    table = synth.table_values(rng, g.total, F, tdtype)
+    D, H = L * F, 64
+    params = rng.uniform(-1 / np.sqrt(D), 1 / np.sqrt(D), H * D + H + 3 * H + 3).astype(np.float32)
+    lay = dashlib.dash_hash3d_layout(**cfg)
+    mlp = dashlib.Mlp(to_dev(params), D, 64, 3)
+    xd, yd, zd, td = to_dev(x), to_dev(y), to_dev(z), to_dev(table)
+    _, norm = dashlib.dash_decomp_fwd(lay, xd, yd, zd, td, mlp)
+    mask, _ = dashlib.dash_topk_mask(norm, 30.0)
+    d_dp = rng.standard_normal((3, n)).astype(np.float32)
+    tg = torch.zeros((g.total, F), device="cuda")
+    pg = torch.zeros(params.size, device="cuda")
+    dashlib.dash_decomp_bwd(lay, xd, yd, zd, td, mlp, tg, pg, d_dp=to_dev(d_dp), mask=mask, lambda_s=0.5)
+    rtg, rpg = oracle.decomp_bwd(g, x, y, z, table.astype(np.float64), 64, params.astype(np.float64),
+                                 d_dp.astype(np.float64), mask.cpu().numpy(), 0.5)
+    assert rel_err(tg.cpu().numpy(), rtg) < 1e-4
+    bounds = np.cumsum([0, 64 * D, 64, 3 * 64, 3])
+    pgn = pg.cpu().numpy()
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        assert rel_err(pgn[a:b], rpg[a:b]) < 1e-4, (a, b, rel_err(pgn[a:b], rpg[a:b]))
