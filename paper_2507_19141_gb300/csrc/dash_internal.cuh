@@ -423,11 +423,6 @@ template <>
 struct Entry2<__half> {
   uint32_t v;
   __device__ __forceinline__ float2 f() const { return __half22float2(*reinterpret_cast<const __half2*>(&v)); }
-  __device__ __forceinline__ static Entry2 in16(const uint4& q, uint32_t k) {
-    const uint32_t lo = (k & 1u) ? q.y : q.x;
-    const uint32_t hi = (k & 1u) ? q.w : q.z;
-    return Entry2{(k & 2u) ? hi : lo};
-  }
   __device__ __forceinline__ static Entry2 load(const __half* p) {
     return Entry2{__ldg(reinterpret_cast<const unsigned int*>(p))};
   }
@@ -436,48 +431,10 @@ template <>
 struct Entry2<float> {
   float2 v;
   __device__ __forceinline__ float2 f() const { return v; }
-  __device__ __forceinline__ static Entry2 in16(const uint4& q, uint32_t k) {
-    return Entry2{(k & 1u) ? make_float2(__uint_as_float(q.z), __uint_as_float(q.w))
-                           : make_float2(__uint_as_float(q.x), __uint_as_float(q.y))};
-  }
   __device__ __forceinline__ static Entry2 load(const float* p) {
     return Entry2{__ldg(reinterpret_cast<const float2*>(p))};
   }
 };
-
-// The F = 2 entries of the 16 corners idx, loaded as gather2_pairs loads
-// them (an x-neighbour pair through one aligned 16-byte load when they share
-// it), kept so that other weights can be applied to the same corners.
-template <typename TT>
-__device__ __forceinline__ void load_corners2(const TT* __restrict__ base, const uint32_t idx[16], Entry2<TT> e[16]) {
-  constexpr uint32_t kGroup = 16u / (2u * sizeof(TT));
-#pragma unroll
-  for (int p = 0; p < 8; ++p) {
-    const uint32_t i0 = idx[2 * p], i1 = idx[2 * p + 1];
-    const uint32_t g = i0 & ~(kGroup - 1u);
-    const uint4 v = __ldg(reinterpret_cast<const uint4*>(base + (size_t)g * 2));
-    e[2 * p] = Entry2<TT>::in16(v, i0 & (kGroup - 1u));
-    e[2 * p + 1] = ((i1 & ~(kGroup - 1u)) == g) ? Entry2<TT>::in16(v, i1 & (kGroup - 1u))
-                                                 : Entry2<TT>::load(base + (size_t)i1 * 2);
-  }
-}
-
-// Weight of corner b as (w_x w_y)(w_z w_t): the same value as corner_weight
-// up to rounding, for uses that need not match level_corners bit for bit.
-__device__ __forceinline__ float corner_weight_xy_zt(const float fr[4], int b) {
-  const float wx = (b & 1) ? fr[0] : 1.0f - fr[0], wy = (b & 2) ? fr[1] : 1.0f - fr[1];
-  const float wz = (b & 4) ? fr[2] : 1.0f - fr[2], wt = (b & 8) ? fr[3] : 1.0f - fr[3];
-  return (wx * wy) * (wz * wt);
-}
-
-// Weight of corner b from the fractional offsets, as level_corners forms it.
-__device__ __forceinline__ float corner_weight(const float fr[4], int b) {
-  float v = (b & 1) ? fr[0] : 1.0f - fr[0];
-  v *= (b & 2) ? fr[1] : 1.0f - fr[1];
-  v *= (b & 4) ? fr[2] : 1.0f - fr[2];
-  v *= (b & 8) ? fr[3] : 1.0f - fr[3];
-  return v;
-}
 
 // ------------------------------------------- input-coordinate gradient ----
 // 1 where the raw coordinate lies in [0,1] (the clamp passes the derivative),
