@@ -219,10 +219,11 @@ __global__ void __launch_bounds__(kThreads) tile_sort_kernel(Ws w) {
 
 __global__ void __launch_bounds__(kTilePix) render_kernel(Cam c, long long n, const float* __restrict__ opacity, Ws w,
                                                           float* __restrict__ image) {
-  __shared__ float s_xy[kTilePix][2];
-  __shared__ float s_con[kTilePix][3];
-  __shared__ float s_op[kTilePix];
-  __shared__ float s_col[kTilePix][3];
+  // one Gaussian's screen data per slot, packed so a pixel reads it with
+  // two 16-byte and one 4-byte shared-memory loads (all lanes read the same slot)
+  __shared__ float4 s_a[kTilePix];  // mean x, mean y, conic a, conic b
+  __shared__ float4 s_b[kTilePix];  // conic c, opacity, colour r, colour g
+  __shared__ float s_c[kTilePix];   // colour b
   const int t = blockIdx.x;
   const int tx_ = t % w.tiles_x, ty_ = t / w.tiles_x;
   const int px = tx_ * kTile + (int)(threadIdx.x % kTile), py = ty_ * kTile + (int)(threadIdx.x / kTile);
@@ -239,24 +240,20 @@ __global__ void __launch_bounds__(kTilePix) render_kernel(Cam c, long long n, co
     const long long k = base + threadIdx.x;
     if (k < s1) {
       const long long gid = (long long)(w.keys[k] & 0xffffffffull);
-      s_xy[threadIdx.x][0] = w.mean2d[gid];
-      s_xy[threadIdx.x][1] = w.mean2d[n + gid];
-      s_con[threadIdx.x][0] = w.conic[gid];
-      s_con[threadIdx.x][1] = w.conic[n + gid];
-      s_con[threadIdx.x][2] = w.conic[2 * n + gid];
-      s_op[threadIdx.x] = opacity[gid];
-      s_col[threadIdx.x][0] = w.color[gid];
-      s_col[threadIdx.x][1] = w.color[n + gid];
-      s_col[threadIdx.x][2] = w.color[2 * n + gid];
+      s_a[threadIdx.x] = make_float4(w.mean2d[gid], w.mean2d[n + gid], w.conic[gid], w.conic[n + gid]);
+      s_b[threadIdx.x] = make_float4(w.conic[2 * n + gid], opacity[gid], w.color[gid], w.color[n + gid]);
+      s_c[threadIdx.x] = w.color[2 * n + gid];
     }
     __syncthreads();
     const int cnt = (int)((s1 - base) < kTilePix ? (s1 - base) : kTilePix);
     for (int j = 0; j < cnt && !done; ++j) {
       ++pos;
-      const float dx = s_xy[j][0] - fx, dy = s_xy[j][1] - fy;
-      const float power = -0.5f * (s_con[j][0] * dx * dx + s_con[j][2] * dy * dy) - s_con[j][1] * dx * dy;
+      const float4 A = s_a[j];
+      const float dx = A.x - fx, dy = A.y - fy;
+      const float4 B = s_b[j];
+      const float power = -0.5f * (A.z * dx * dx + B.x * dy * dy) - A.w * dx * dy;
       if (power > 0.f) continue;
-      const float alpha = fminf(kAlphaMax, s_op[j] * expf(power));
+      const float alpha = fminf(kAlphaMax, B.y * expf(power));
       if (alpha < kAlphaMin) continue;
       const float tt = T * (1.f - alpha);
       if (tt < kTMin) {
@@ -264,9 +261,9 @@ __global__ void __launch_bounds__(kTilePix) render_kernel(Cam c, long long n, co
         break;
       }
       const float wgt = alpha * T;
-      C0 = fmaf(s_col[j][0], wgt, C0);
-      C1 = fmaf(s_col[j][1], wgt, C1);
-      C2 = fmaf(s_col[j][2], wgt, C2);
+      C0 = fmaf(B.z, wgt, C0);
+      C1 = fmaf(B.w, wgt, C1);
+      C2 = fmaf(s_c[j], wgt, C2);
       T = tt;
       last = pos;
     }

@@ -75,10 +75,10 @@ __device__ __forceinline__ int scatter_index(unsigned lane) {
 __global__ void __launch_bounds__(kTilePix) render_bwd_kernel(Cam c, long long n, const float* __restrict__ opacity,
                                                               Ws w, const float* __restrict__ dimage,
                                                               float* __restrict__ dopacity) {
-  __shared__ float s_xy[kTilePix][2];
-  __shared__ float s_con[kTilePix][3];
-  __shared__ float s_op[kTilePix];
-  __shared__ float s_col[kTilePix][3];
+  // one Gaussian's screen data per slot, packed as in render_kernel
+  __shared__ float4 s_a[kTilePix];  // mean x, mean y, conic a, conic b
+  __shared__ float4 s_b[kTilePix];  // conic c, opacity, colour r, colour g
+  __shared__ float s_c[kTilePix];   // colour b
   __shared__ int s_gid[kTilePix];
   __shared__ uint32_t s_max;
   const int t = blockIdx.x;
@@ -131,15 +131,9 @@ __global__ void __launch_bounds__(kTilePix) render_bwd_kernel(Cam c, long long n
       const int k = end - 1 - (int)threadIdx.x;  // back to front
       const long long gid = (long long)(w.keys[s0 + k] & 0xffffffffull);
       s_gid[threadIdx.x] = (int)gid;
-      s_xy[threadIdx.x][0] = w.mean2d[gid];
-      s_xy[threadIdx.x][1] = w.mean2d[n + gid];
-      s_con[threadIdx.x][0] = w.conic[gid];
-      s_con[threadIdx.x][1] = w.conic[n + gid];
-      s_con[threadIdx.x][2] = w.conic[2 * n + gid];
-      s_op[threadIdx.x] = opacity[gid];
-      s_col[threadIdx.x][0] = w.color[gid];
-      s_col[threadIdx.x][1] = w.color[n + gid];
-      s_col[threadIdx.x][2] = w.color[2 * n + gid];
+      s_a[threadIdx.x] = make_float4(w.mean2d[gid], w.mean2d[n + gid], w.conic[gid], w.conic[n + gid]);
+      s_b[threadIdx.x] = make_float4(w.conic[2 * n + gid], opacity[gid], w.color[gid], w.color[n + gid]);
+      s_c[threadIdx.x] = w.color[2 * n + gid];
     }
     __syncthreads();
     for (int j = 0; j < cnt; ++j) {
@@ -148,11 +142,13 @@ __global__ void __launch_bounds__(kTilePix) render_bwd_kernel(Cam c, long long n
             d_c2 = 0.f;
       bool hit = false;
       if (position <= last) {
-        const float dx = s_xy[j][0] - fx, dy = s_xy[j][1] - fy;
-        const float ca = s_con[j][0], cb = s_con[j][1], cc = s_con[j][2];
+        const float4 A = s_a[j];
+        const float4 B = s_b[j];
+        const float dx = A.x - fx, dy = A.y - fy;
+        const float ca = A.z, cb = A.w, cc = B.x;
         const float power = -0.5f * (ca * dx * dx + cc * dy * dy) - cb * dx * dy;
         const float G = expf(power);
-        const float raw = s_op[j] * G;
+        const float raw = B.y * G;
         const float alpha = fminf(kAlphaMax, raw);
         if (power <= 0.f && alpha >= kAlphaMin) {
           hit = true;
@@ -162,7 +158,7 @@ __global__ void __launch_bounds__(kTilePix) render_bwd_kernel(Cam c, long long n
           acc0 = last_alpha * lc0 + (1.f - last_alpha) * acc0;
           acc1 = last_alpha * lc1 + (1.f - last_alpha) * acc1;
           acc2 = last_alpha * lc2 + (1.f - last_alpha) * acc2;
-          const float c0 = s_col[j][0], c1 = s_col[j][1], c2 = s_col[j][2];
+          const float c0 = B.z, c1 = B.w, c2 = s_c[j];
           float dL_da = ((c0 - acc0) * g0 + (c1 - acc1) * g1 + (c2 - acc2) * g2) * T;
           dL_da -= T_final / (1.f - alpha) * bg_dot;
           last_alpha = alpha, lc0 = c0, lc1 = c1, lc2 = c2;
