@@ -45,9 +45,9 @@ STEP_BYTES = 2 + 4 + FWD_BYTES + BWD_BYTES
 # (profiles/warp_specialised_kernels_1M.md), valid while the kernel's sources
 # hash to the captured value; otherwise the benchmark reports no traffic.
 NCU_TRAFFIC = {
-    "bwd": {"bytes": (196.6 + 4.1) * 1e6, "n": 1_000_000, "sha256_16": "1fc3eed2c906ae59",
+    "bwd": {"bytes": (196.5 + 3.9) * 1e6, "n": 1_000_000, "sha256_16": "85065c5ed4ba26e0",
             "sources": ("deform_bwd.cu", "deform_common.cuh", "dash_internal.cuh", "tc_ptx.cuh")},
-    "fwd": {"bytes": (45.7 + 71.8) * 1e6, "n": 1_000_000, "sha256_16": "fee0a2fbcb4a4568",
+    "fwd": {"bytes": (45.8 + 71.9) * 1e6, "n": 1_000_000, "sha256_16": "75960e6b790fadf3",
             "sources": ("deform_fwd.cu", "deform_common.cuh", "dash_internal.cuh", "tc_ptx.cuh")},
 }
 
