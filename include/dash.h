@@ -139,13 +139,15 @@ int dash_version(void);
 /* Process-wide kernel-form options (host; take effect at the next launch).
  * DASH_OPT_FWD_FORM selects the fused forward kernel: 0 = warp-specialised
  * (one decoder group fed by gather groups through a shared-memory ring;
- * default, four groups x four stages for F = 2, L*F <= 32), 1 / 2 / 4 = that
- * many independent gather+decoder groups per CTA, and for F = 2, L*F <= 32
- * the warp-specialised shapes (gather groups, ring stages) 10 = (3, 6),
- * 11 = (3, 3), 12 = (2, 4), 13 = (5, 5).  DASH_OPT_BWD_FORM selects the fused
- * backward: 0 = warp-specialised (a decoder group feeding scatter groups;
- * three groups; used when a forward state is given), 1 = one combined group per CTA, 10..13 = the shapes (3, 6), (4, 4),
- * (2, 4), (5, 5).  Forward forms agree bit for bit, backward forms up to the
+ * default, two groups x two stages for F = 2, L*F <= 32: the small ring
+ * leaves the L1 more room for the gathers), 1 / 2 / 4 = that many
+ * independent gather+decoder groups per CTA, and for F = 2, L*F <= 32 the
+ * warp-specialised shapes (gather groups, ring stages) 10 = (3, 6),
+ * 11 = (3, 3), 12 = (2, 4), 13 = (5, 5), 14 = (4, 4).  DASH_OPT_BWD_FORM
+ * selects the fused backward: 0 = warp-specialised (a decoder group feeding
+ * scatter groups; three groups; used when a forward state is given),
+ * 1 = one combined group per CTA, 10..13 = the shapes (3, 6), (4, 4),
+ * (2, 4), (5, 5).  Every shape has at least one ring stage per group.  Forward forms agree bit for bit, backward forms up to the
  * order of the atomic additions.  DASH_OPT_ACCESS_FORM selects how the
  * warp-specialised forward and backward kernels issue their F = 2 table
  * accesses: 0 = lane pairs (default; lanes 2j and 2j+1 take the lower and

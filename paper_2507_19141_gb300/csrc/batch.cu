@@ -70,6 +70,9 @@ __device__ __forceinline__ Item decode_item(long long item, const long long* ite
 
 template <typename TT, int F, int P, int S>
 __global__ void __launch_bounds__((P + 1) * kRows, 1) batch_fwd_kernel(const __grid_constant__ BatchArgs a) {
+  // tile j uses stage j % S and group j % P; the mbarrier waits tell phases
+  // apart only by parity, so no two groups may wait on one stage at once
+  static_assert(S >= P, "the ring needs at least one stage per gather group");
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tid = threadIdx.x;
   const int KB1 = 2 * a.Dp + 16;
@@ -235,7 +238,7 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) batch_fwd_kernel(const __g
 struct Form {
   int P, S;
 };
-constexpr Form kForms[] = {{4, 4}, {3, 6}, {3, 3}, {2, 4}};
+constexpr Form kForms[] = {{4, 4}, {3, 6}, {3, 3}, {2, 4}, {2, 2}};
 constexpr int kNumForms = sizeof(kForms) / sizeof(kForms[0]);
 
 size_t smem_for(int P, int S, int Dp, BatchArgs* a) {
@@ -269,7 +272,8 @@ int launch_tt_f(int form, BatchArgs& a, cudaStream_t st) {
     case 0: return launch_form<TT, F, 4, 4>(a, st);
     case 1: return launch_form<TT, F, 3, 6>(a, st);
     case 2: return launch_form<TT, F, 3, 3>(a, st);
-    default: return launch_form<TT, F, 2, 4>(a, st);
+    case 3: return launch_form<TT, F, 2, 4>(a, st);
+    default: return launch_form<TT, F, 2, 2>(a, st);
   }
 }
 

@@ -559,6 +559,9 @@ __global__ void __launch_bounds__(kRows, 1) deform_bwd_kernel(const __grid_const
 // ---------------------------------------------------------------------------
 template <typename TT, int F, int P, int S>
 __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_bwd_ws_kernel(const __grid_constant__ BwdArgs a) {
+  // tile j uses stage j % S and group j % P; the mbarrier waits tell phases
+  // apart only by parity, so no two groups may wait on one stage at once
+  static_assert(S >= P, "the ring needs at least one stage per scatter group");
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tid = threadIdx.x;
   const int KF = 2 * a.Dp + 16;

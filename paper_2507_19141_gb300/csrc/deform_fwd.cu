@@ -184,6 +184,9 @@ WsPlan ws_plan(int Dp) {
 
 template <typename TT, int F, int P, int S>
 __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_fwd_ws_kernel(const __grid_constant__ FwdArgs a) {
+  // tile j uses stage j % S and group j % P; the mbarrier waits tell phases
+  // apart only by parity, so no two groups may wait on one stage at once
+  static_assert(S >= P, "the ring needs at least one stage per gather group");
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tid = threadIdx.x;
   const int KB1 = 2 * a.Dp + 16;
@@ -391,11 +394,12 @@ int dispatch_f(int F, int Dp, int variant, FwdArgs& a, cudaStream_t st) {
   if (F == 2 && Dp <= 32) {
     // warp-specialised shapes (gather groups, ring stages); 0 = the measured best
     switch (variant) {
-      case 0: return launch_ws<TT, 2, 4, 4>(a, st);
+      case 0: return launch_ws<TT, 2, 2, 2>(a, st);
       case 10: return launch_ws<TT, 2, 3, 6>(a, st);
       case 11: return launch_ws<TT, 2, 3, 3>(a, st);
       case 12: return launch_ws<TT, 2, 2, 4>(a, st);
       case 13: return launch_ws<TT, 2, 5, 5>(a, st);
+      case 14: return launch_ws<TT, 2, 4, 4>(a, st);
       default: break;
     }
   }
