@@ -45,9 +45,9 @@ STEP_BYTES = 2 + 4 + FWD_BYTES + BWD_BYTES
 # (profiles/warp_specialised_kernels_1M.md), valid while the kernel's sources
 # hash to the captured value; otherwise the benchmark reports no traffic.
 NCU_TRAFFIC = {
-    "bwd": {"bytes": (196.5 + 3.9) * 1e6, "n": 1_000_000, "sha256_16": "85065c5ed4ba26e0",
+    "bwd": {"bytes": (196.7 + 3.7) * 1e6, "n": 1_000_000, "sha256_16": "f6868470811792cc",
             "sources": ("deform_bwd.cu", "deform_common.cuh", "dash_internal.cuh", "tc_ptx.cuh")},
-    "fwd": {"bytes": (45.8 + 71.9) * 1e6, "n": 1_000_000, "sha256_16": "75960e6b790fadf3",
+    "fwd": {"bytes": (45.5 + 72.0) * 1e6, "n": 1_000_000, "sha256_16": "758ded77607693f1",
             "sources": ("deform_fwd.cu", "deform_common.cuh", "dash_internal.cuh", "tc_ptx.cuh")},
 }
 
