@@ -196,7 +196,7 @@ class Workload:
     Gaussians, exactly 1M dynamic, scene-like coordinates, FP16 tables, BF16
     decoder weights, N(0,1) upstream gradients; resident on the device."""
 
-    def __init__(self, seed, n_all, n_dyn, device):
+    def __init__(self, seed, n_all, n_dyn, device, morton=False):
         import numpy as np
         import torch
         from paper_2507_19141_gb300 import dash, synth
@@ -210,6 +210,11 @@ class Workload:
         self.table_h = synth.table_values(rng, self.layout.total, self.grid.F, np.float16)
         self.params_h = synth.mlp_params(rng, self.mlpc)
         self.attrs_h = synth.gaussian_attrs(rng, n_all)
+        if morton:  # the same Gaussians stored in the Z order of their positions
+            order = np.argsort(morton3(*self.coords_h[:3]), kind="stable")
+            self.mask_h = self.mask_h[order]
+            self.coords_h = tuple(c[order] for c in self.coords_h)
+            self.attrs_h = np.ascontiguousarray(self.attrs_h[:, order])
         dd = synth.upstream_grad(rng, self.mlpc.d_out, n_dyn)
         self.ddelta_h = dd
         dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
@@ -252,6 +257,22 @@ class Workload:
 
 
 LAUNCHES_PER_STEP = 5  # compaction count/scan/write, fused forward, fused backward
+
+
+def morton3(x, y, z, bits=10):
+    """Z-order (Morton) keys of points in [0,1]^3: each coordinate quantised
+    to `bits` bits and the bits interleaved (x lowest)."""
+    import numpy as np
+
+    def spread(v):  # bit i of v moves to bit 3 i
+        v = v.astype(np.uint64)
+        out = np.zeros_like(v)
+        for i in range(bits):
+            out |= ((v >> np.uint64(i)) & np.uint64(1)) << np.uint64(3 * i)
+        return out
+
+    q = lambda c: np.minimum((np.clip(c, 0.0, 1.0) * (1 << bits)).astype(np.int64), (1 << bits) - 1)
+    return spread(q(x)) | (spread(q(y)) << np.uint64(1)) | (spread(q(z)) << np.uint64(2))
 
 
 def time_steps(torch, fn, steps, stream):
@@ -526,10 +547,29 @@ def run_extras(torch, wl, args, stream):
     torch.cuda.synchronize()
     res["scatter_fp16_rel_err_vs_fp32"] = float((g16.float() - g32).norm() / g32.norm())
     del g32, g16, dfeat
+    res.update(run_morton(torch, args, stream))
     res.update(run_decomp(torch, wl, stream))
     res.update(run_wo_dec(torch, stream))
     res.update(run_render(torch, stream))
     res.update(run_batched(torch, stream))
+    return res
+
+
+def run_morton(torch, args, stream):
+    """The benchmark step on the same kind of scene with the Gaussians stored
+    in the Z order of their positions (so consecutive dynamic Gaussians are
+    spatial neighbours)."""
+    wl = Workload(seed=2, n_all=args.n_all, n_dyn=args.n_dyn, device=torch.device("cuda"), morton=True)
+    for _ in range(3):
+        wl.step()
+    res = {"morton_step_ms": time_steps(torch, wl.step, 50, stream)}
+    for _ in range(3):
+        wl.forward()
+    res["morton_fwd_ms"] = time_steps(torch, wl.forward, 50, stream)
+    res["morton_bwd_ms"] = time_steps(torch, wl.backward, 50, stream)
+    res["morton_gaussians_per_s"] = args.n_dyn / (res["morton_step_ms"] / 1e3)
+    del wl
+    torch.cuda.empty_cache()
     return res
 
 
