@@ -46,7 +46,8 @@ STEP_BYTES = 2 + 4 + FWD_BYTES + BWD_BYTES
 # hash to the captured value; otherwise the benchmark reports no traffic.
 NCU_TRAFFIC = {
     "bwd": {"bytes": (196.7 + 3.7) * 1e6, "n": 1_000_000, "sha256_16": "f6868470811792cc",
-            "sources": ("deform_bwd.cu", "deform_common.cuh", "dash_internal.cuh", "tc_ptx.cuh")},
+            "sources": ("deform_bwd.cu", "deform_bwd_common.cuh", "deform_common.cuh", "dash_internal.cuh",
+                        "tc_ptx.cuh")},
     "fwd": {"bytes": (45.5 + 72.0) * 1e6, "n": 1_000_000, "sha256_16": "758ded77607693f1",
             "sources": ("deform_fwd.cu", "deform_common.cuh", "dash_internal.cuh", "tc_ptx.cuh")},
 }
@@ -810,7 +811,8 @@ def run_decomp(torch, wl, stream):
 def run_batched(torch, stream):
     """Batched form: 8 scenes with dynamic counts log-uniform in 50k..2M, 64
     timestamps each, FP16 tables and BF16 decoders per scene, one persistent
-    graph-captured launch with the autotuned kernel form."""
+    graph-captured launch with the autotuned kernel form; then the same
+    work list forward + backward in one graph."""
     import numpy as np
     from paper_2507_19141_gb300 import dash, synth
     counts, tss, rng = synth.batched()
@@ -832,9 +834,24 @@ def run_batched(torch, stream):
     ms = time_steps(torch, plan.run, 3, stream)
     evals = sum(counts) * len(tss[0])
     plan.close()
+    # forward + backward in one graph: upstream gradients N(0, 1) drawn on the
+    # device (14 GB), FP32 table and decoder gradients per scene
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5)
+    for sc in scenes:
+        sc["ddelta"] = torch.randn(sc["delta_out"].shape, generator=gen, device="cuda")
+        sc["table_grad"] = torch.zeros((lay.total, grid.F), dtype=torch.float32, device="cuda")
+        sc["mlp_grad"] = torch.zeros(mlpc.n_params, dtype=torch.float32, device="cuda")
+    plan = dash.BatchPlan(lay, scenes, backward=True)
+    plan.autotune(cache)
+    plan.run()
+    torch.cuda.synchronize()
+    ms_b = time_steps(torch, plan.run, 3, stream)
+    plan.close()
     return {"batched_scenes": len(counts), "batched_counts": counts, "batched_timestamps": len(tss[0]),
             "batched_evaluations": evals, "batched_launch_ms": ms, "batched_form": form,
-            "batched_evaluations_per_s": evals / (ms / 1e3)}
+            "batched_evaluations_per_s": evals / (ms / 1e3),
+            "batched_fwd_bwd_launch_ms": ms_b, "batched_fwd_bwd_evaluations_per_s": evals / (ms_b / 1e3)}
 
 
 # ------------------------------------------------------------ CPU oracle --

@@ -444,7 +444,13 @@ int dash_raster_bwd(const dash_camera* cam, const dash_gaussians* gaussians, con
  * Gaussians' FP32 coordinates x, y, z [n], K normalised timestamps (device
  * [K]; one broadcast t per frame), and delta_out SoA [K][O][n] FP32.  n is the
  * capacity and initial count; the live count can be changed on the device
- * through dash_batch_counts() without rebuilding the plan. */
+ * through dash_batch_counts() without rebuilding the plan.
+ * With a backward (dash_batch_desc.with_backward): ddelta SoA [K][O][n] FP32
+ * is the upstream gradient of each (timestamp, Gaussian); fwd_state
+ * [K][n][dash_deform_state_size] (16-byte aligned) receives the forward's
+ * per-Gaussian state; table_grad (FP32 [offset[L]][F], 16-byte aligned) and
+ * mlp_grad (FP32, packed like params) ACCUMULATE the scene's gradients over
+ * its K timestamps. */
 typedef struct dash_batch_scene {
   const void* table;
   const float* params;
@@ -455,15 +461,24 @@ typedef struct dash_batch_scene {
   float* delta_out;
   int64_t n;
   int32_t K, reserved;
+  const float* ddelta;
+  void* fwd_state;
+  float* table_grad;
+  float* mlp_grad;
 } dash_batch_scene;
 
-/* All scenes share the grid layout, table dtype and decoder widths. */
+/* All scenes share the grid layout, table dtype and decoder widths.
+ * with_backward = 1 adds, after the forward, the fused backward (a9-a10:
+ * decoder gradients, lane-paired table-gradient scatter) of every (scene,
+ * timestamp, tile) in a second persistent kernel of the same graph; F = 2
+ * and L*F <= 32 only. */
 typedef struct dash_batch_desc {
   const dash_layout* layout;
   int32_t table_dtype;
   int32_t d_in, d_hidden, d_out;
   int32_t n_scenes;
   const dash_batch_scene* scenes; /* host array of n_scenes */
+  int32_t with_backward, reserved;
 } dash_batch_desc;
 
 typedef struct dash_batch_plan dash_batch_plan;

@@ -11,13 +11,16 @@
 // Each CTA (one per SM) is warp-specialised as in the single-scene forward:
 // P gather groups fill an S-stage ring; the decoder group drains it on the
 // tensor cores and rebuilds its BF16 weight tiles when the scene changes.
+// With a backward the forward also writes each item's per-Gaussian state,
+// and a second persistent kernel in the same graph runs the fused backward
+// (a9-a10) over the same work list.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
 
 #include <string>
 
-#include "deform_common.cuh"
+#include "deform_bwd_common.cuh"
 
 struct dash_batch_plan;
 
@@ -39,6 +42,12 @@ struct SceneDev {
   float* delta;
   long long n_cap;
   int K, pad;
+  // backward (NULL without one): upstream gradient [K][O][n_cap], forward
+  // state [K][n_cap][state_stride], FP32 table and decoder gradients
+  const float* ddelta;
+  uint8_t* state;
+  float* table_grad;
+  float* mlp_grad;
 };
 
 struct BatchArgs {
@@ -68,6 +77,23 @@ __device__ __forceinline__ Item decode_item(long long item, const long long* ite
   return it;
 }
 
+// The work list: item_off[s] = first item of scene s, tiles[s] = its tiles
+// per timestamp (at least one, for decoding), item_off[n_scenes] = the total.
+__device__ __forceinline__ void build_item_table(const SceneDev* scenes, const long long* counts, int n_scenes,
+                                                 long long* item_off, long long* tiles) {
+  long long acc = 0;
+  for (int s = 0; s < n_scenes; ++s) {
+    long long c = counts[s];
+    const long long cap = scenes[s].n_cap;
+    c = c < 0 ? 0 : (c > cap ? cap : c);
+    const long long t = (c + kRows - 1) / kRows;
+    tiles[s] = t > 0 ? t : 1;
+    item_off[s] = acc;
+    acc += t * (long long)scenes[s].K;  // an empty scene has no items
+  }
+  item_off[n_scenes] = acc;
+}
+
 template <typename TT, int F, int P, int S>
 __global__ void __launch_bounds__((P + 1) * kRows, 1) batch_fwd_kernel(const __grid_constant__ BatchArgs a) {
   // tile j uses stage j % S and group j % P; the mbarrier waits tell phases
@@ -90,17 +116,7 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) batch_fwd_kernel(const __g
   long long* tiles = item_off + kMaxScenes + 1;                           // [n_scenes]
 
   if (tid == 0) {
-    long long acc = 0;
-    for (int s = 0; s < a.n_scenes; ++s) {
-      long long c = a.counts[s];
-      const long long cap = a.scenes[s].n_cap;
-      c = c < 0 ? 0 : (c > cap ? cap : c);
-      const long long t = (c + kRows - 1) / kRows;
-      tiles[s] = t > 0 ? t : 1;
-      item_off[s] = acc;
-      acc += t * (long long)a.scenes[s].K;
-    }
-    item_off[a.n_scenes] = acc;
+    build_item_table(a.scenes, a.counts, a.n_scenes, item_off, tiles);
     for (int s = 0; s < S; ++s) {
       tc::mbar_init(tc::smem_addr(&full[s]), kRows);
       tc::mbar_init(tc::smem_addr(&empty[s]), 1);
@@ -155,8 +171,8 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) batch_fwd_kernel(const __g
       }
       phase ^= 1u;
       tc::fence_after_sync();
-      uint32_t m[2];
-      hidden_epilogue(trow, A2, r, m);
+      uint32_t m1[2], m2[2];
+      hidden_epilogue(trow, A2, r, m1);
       tc::fence_before_sync();
       tc::fence_async_smem();
       tc::named_sync(1, kRows);
@@ -172,7 +188,12 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) batch_fwd_kernel(const __g
       }
       phase ^= 1u;
       tc::fence_after_sync();
-      hidden_epilogue(trow, A2, r, m);
+      hidden_epilogue(trow, A2, r, m2);
+      const long long row = it.tile * kRows + r;
+      if (row < cnt && sc.state != nullptr)  // the ReLU masks of the state (f_h comes from the gather groups)
+        __stcs(reinterpret_cast<uint4*>(sc.state + ((long long)it.k * sc.n_cap + row) * state_stride(a.D) +
+                                        state_mask_off(a.D)),
+               make_uint4(m1[0], m1[1], m2[0], m2[1]));
       tc::fence_before_sync();
       tc::fence_async_smem();
       tc::named_sync(1, kRows);
@@ -190,7 +211,6 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) batch_fwd_kernel(const __g
       tc::fence_after_sync();
       float o[16];
       tc::tmem_ld16(trow, o);
-      const long long row = it.tile * kRows + r;
       if (row < cnt) {
         float* out = sc.delta + (long long)it.k * a.O * sc.n_cap + row;
         for (int c = 0; c < a.O; ++c) __stcs(out + (long long)c * sc.n_cap, o[c]);
@@ -222,8 +242,11 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) batch_fwd_kernel(const __g
         p.z = clamp01(__ldg(sc.z + row));
         p.w = clamp01(__ldg(sc.ts + it.k));
       }
+      uint8_t* srow = (valid && sc.state != nullptr)
+                          ? sc.state + ((long long)it.k * sc.n_cap + row) * state_stride(a.D)
+                          : nullptr;
       encode_operand_row<TT, F>(a.g, static_cast<const TT*>(sc.table), p, valid, a.D, a.Dp,
-                                ring + s * a.stage_bytes, r, nullptr, a.paired != 0);
+                                ring + s * a.stage_bytes, r, srow, a.paired != 0);
       tc::fence_async_smem();
       tc::mbar_arrive(tc::smem_addr(&full[s]));
     }
@@ -232,6 +255,143 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) batch_fwd_kernel(const __g
   __syncthreads();
   tc::fence_after_sync();
   if (tid < 32) tc::tmem_dealloc(tbase, 64);
+}
+
+// ---------------------------------------------------------------------------
+// The batched backward: the warp-specialised backward of deform_bwd.cu for
+// every (scene, timestamp, tile) item.  The decoder group (deform_bwd_common
+// .cuh) recomputes the decoder from the item's forward state and back-
+// propagates its upstream gradient; when the scene changes it adds its TMEM
+// weight-gradient accumulators into the finished scene's mlp_grad and
+// rebuilds its weight tiles.  The scatter groups add each tile's lane-paired
+// table-gradient reductions into the item's scene.  F = 2, L*F <= 32.
+// ---------------------------------------------------------------------------
+struct BatchBwdArgs {
+  Geom g;
+  int D, Dp, O, n_scenes;
+  const SceneDev* scenes;
+  const long long* counts;
+  unsigned int* flags;
+  uint32_t off_w2, off_w3, off_f, off_h1, off_x, off_g3, off_ring, off_bar, off_tab;
+};
+
+template <typename TT, int P, int S>
+__global__ void __launch_bounds__((P + 1) * kRows, 1) batch_bwd_kernel(const __grid_constant__ BatchBwdArgs a) {
+  // tile j uses stage j % S and group j % P; the mbarrier waits tell phases
+  // apart only by parity, so no two groups may wait on one stage at once
+  static_assert(S >= P, "the ring needs at least one stage per scatter group");
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int tid = threadIdx.x;
+  const int KF = 2 * a.Dp + 16;
+  const bwdk::Tiles tl{smem,           smem + a.off_w2, smem + a.off_w3, smem + a.off_f, smem + a.off_h1,
+                       smem + a.off_x, smem + a.off_g3, KF,              a.D,            a.Dp,
+                       a.O};
+  float* ring = reinterpret_cast<float*>(smem + a.off_ring);  // S stages of [Dp][kRows]
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + a.off_bar);
+  uint64_t* empty = full + S;
+  uint64_t* mma_bar = empty + S;
+  volatile uint32_t* holder = reinterpret_cast<volatile uint32_t*>(mma_bar + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(mma_bar + 1) + 1;
+  long long* item_off = reinterpret_cast<long long*>(smem + a.off_tab);  // [n_scenes + 1]
+  long long* tiles = item_off + kMaxScenes + 1;                           // [n_scenes]
+  const int stage_floats = a.Dp * kRows;
+  if (tid == 0) {
+    build_item_table(a.scenes, a.counts, a.n_scenes, item_off, tiles);
+    for (int s = 0; s < S; ++s) {
+      tc::mbar_init(tc::smem_addr(&full[s]), kRows);
+      tc::mbar_init(tc::smem_addr(&empty[s]), kRows);
+    }
+    tc::mbar_init(tc::smem_addr(mma_bar), 1);
+    tc::mbar_init_fence();
+    *abort_flag = 0;
+  }
+  if (tid < 32) tc::tmem_alloc(tc::smem_addr(const_cast<uint32_t*>(holder)), bwdk::kTmemCols);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *holder;
+  const long long total = item_off[a.n_scenes];
+  const long long my_items = total > blockIdx.x ? (total - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+
+  if (tid < kRows) {
+    // ----------------------------------------------------- decoder group
+    const int r = tid, q = tid >> 5;
+    const uint32_t trow = tbase + ((uint32_t)(q * 32) << 16);
+    const uint32_t bar = tc::smem_addr(mma_bar);
+    uint32_t phase = 0;
+    bool had_tile = false;
+    int cur_scene = -1;
+    const bwdk::Ids ids = bwdk::make_ids(a.Dp);
+    for (long long j = 0; j < my_items; ++j) {
+      const Item it = decode_item(blockIdx.x + j * gridDim.x, item_off, tiles, a.n_scenes);
+      const SceneDev& sc = a.scenes[it.s];
+      long long cnt = a.counts[it.s];
+      cnt = cnt < 0 ? 0 : (cnt > sc.n_cap ? sc.n_cap : cnt);
+      if (it.s != cur_scene) {
+        // the previous tile's MMAs have completed: its scene's weight
+        // gradients are final in TMEM and the weight tiles are free
+        if (had_tile && !*abort_flag) bwdk::flush_dw(trow, r, a.D, a.Dp, a.O, a.scenes[cur_scene].mlp_grad);
+        tc::named_sync(1, kRows);
+        bwdk::build_weights(tl, sc.params, r, kRows);
+        cur_scene = it.s;
+        had_tile = false;
+      }
+      const long long row = it.tile * kRows + r;
+      const bool valid = row < cnt;
+      const uint8_t* srow = valid ? sc.state + ((long long)it.k * sc.n_cap + row) * state_stride(a.D) : nullptr;
+      const float* dd = sc.ddelta + (long long)it.k * a.O * sc.n_cap + row;
+      if (!bwdk::decoder_tile(tl, ids, tbase, trow, r, bar, phase, a.flags, abort_flag, srow, dd, sc.n_cap, valid,
+                              had_tile))
+        break;
+      had_tile = true;
+      // publish dL/df_h of this tile to the scatter groups
+      const int s = (int)(j % S);
+      const uint32_t round = (uint32_t)(j / S);
+      if (!tc::mbar_wait(tc::smem_addr(&empty[s]), (round & 1u) ^ 1u, kWaitIters)) {
+        atomicOr(a.flags, 1u);
+        *abort_flag = 1;
+      }
+      bwdk::publish(ring + (size_t)s * stage_floats, trow, r, a.Dp);
+      tc::fence_before_sync();
+      tc::mbar_arrive(tc::smem_addr(&full[s]));
+    }
+    tc::named_sync(1, kRows);
+    tc::fence_after_sync();
+    if (had_tile && !*abort_flag) bwdk::flush_dw(trow, r, a.D, a.Dp, a.O, a.scenes[cur_scene].mlp_grad);
+  } else {
+    // ------------------------------------------------------ scatter groups
+    const int pg = tid / kRows - 1, r = tid % kRows;
+    for (long long j = pg; j < my_items; j += P) {
+      const int s = (int)(j % S);
+      const uint32_t round = (uint32_t)(j / S);
+      const Item it = decode_item(blockIdx.x + j * gridDim.x, item_off, tiles, a.n_scenes);
+      const SceneDev& sc = a.scenes[it.s];
+      long long cnt = a.counts[it.s];
+      cnt = cnt < 0 ? 0 : (cnt > sc.n_cap ? sc.n_cap : cnt);
+      const long long row = it.tile * kRows + r;
+      float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (row < cnt) {
+        p.x = clamp01(__ldg(sc.x + row));
+        p.y = clamp01(__ldg(sc.y + row));
+        p.z = clamp01(__ldg(sc.z + row));
+        p.w = clamp01(__ldg(sc.ts + it.k));
+      }
+      if (!tc::mbar_wait(tc::smem_addr(&full[s]), round & 1u, kWaitIters)) {
+        atomicOr(a.flags, 1u);
+        *abort_flag = 1;
+      }
+      if (*abort_flag) break;
+      const long long row_a = row - (r & 1);  // the pair's even row; both lanes agree on row_a < cnt
+      if (row_a < cnt)
+        bwdk::scatter_levels_paired(a.g, sc.table_grad, p, ring + (size_t)s * stage_floats + (r & ~1),
+                                    (uint32_t)(r & 1), true, row_a + 1 < cnt, 3u << (r & 30));
+      tc::mbar_arrive(tc::smem_addr(&empty[s]));
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (tid < 32) tc::tmem_dealloc(tbase, bwdk::kTmemCols);
 }
 
 // Compiled forms the autotuner chooses from: (gather groups P, ring stages S).
@@ -294,6 +454,43 @@ int launch_batch(int form, int table_dtype, BatchArgs& a, cudaStream_t st) {
   }
 }
 
+// The batched backward in the single-scene default shape: three scatter
+// groups, three ring stages.
+template <typename TT>
+int launch_bwd_tt(BatchBwdArgs a, cudaStream_t st) {
+  using bwdk::kKG;
+  using bwdk::kKH;
+  using bwdk::kKH2;
+  using bwdk::kKO;
+  constexpr int P = 3, S = 3;
+  const int KF = 2 * a.Dp + 16;
+  uint32_t off = (uint32_t)kHidden * KF * 2;
+  a.off_w2 = (off + 127) & ~127u;
+  a.off_w3 = a.off_w2 + (uint32_t)kHidden * kKH2 * 2;
+  off = a.off_w3 + (uint32_t)kOutPad * kKH * 2;
+  // f_h, h1 and h2 tiles are read transposed with M = 128 rows past their
+  // own end into the next region; G3 comes last and is read within bounds
+  a.off_f = (off + 127) & ~127u;
+  a.off_h1 = a.off_f + (uint32_t)kRows * KF * 2;
+  a.off_x = a.off_h1 + (uint32_t)kRows * kKH2 * 2;
+  a.off_g3 = a.off_x + (uint32_t)kRows * kKH * 2;
+  a.off_ring = a.off_g3 + (uint32_t)kRows * kKO * 2;
+  a.off_bar = a.off_ring + (uint32_t)S * a.Dp * kRows * 4;
+  a.off_tab = (a.off_bar + 8 * (2 * S + 1) + 16 + 15) & ~15u;
+  const size_t smem = a.off_tab + sizeof(long long) * (2 * kMaxScenes + 1);
+  if (smem > 227 * 1024) return fail(DASH_ERR_UNSUPPORTED, "batched backward needs %zu B of shared memory", smem);
+  auto kern = batch_bwd_kernel<TT, P, S>;
+  if (int s = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                          "cudaFuncSetAttribute(batch_bwd)"))
+    return s;
+  kern<<<(unsigned)sm_count(), (P + 1) * kRows, smem, st>>>(a);
+  return launch_status("batch_bwd_kernel");
+}
+
+int launch_batch_bwd(int table_dtype, const BatchBwdArgs& a, cudaStream_t st) {
+  return table_dtype == DASH_F16 ? launch_bwd_tt<__half>(a, st) : launch_bwd_tt<float>(a, st);
+}
+
 unsigned int* batch_flags_ptr() {
   void* p = nullptr;
   if (cudaGetSymbolAddress(&p, g_batch_flags) != cudaSuccess) return nullptr;
@@ -309,7 +506,9 @@ struct dash_batch_plan {
   int device;
   int table_dtype;
   int form;
+  int with_bwd;
   dash::fused::BatchArgs args;
+  dash::fused::BatchBwdArgs bargs;
   dash::fused::SceneDev* d_scenes;
   long long* d_counts;
   cudaGraph_t graph;
@@ -334,7 +533,8 @@ int capture(dash_batch_plan* p) {
   if (int s = cuda_status(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "cudaStreamCreate")) return s;
   int rc = cuda_status(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
   if (rc == DASH_OK) {
-    const int lr = fused::launch_batch(p->form, p->table_dtype, p->args, cs);
+    int lr = fused::launch_batch(p->form, p->table_dtype, p->args, cs);
+    if (lr == DASH_OK && p->with_bwd) lr = fused::launch_batch_bwd(p->table_dtype, p->bargs, cs);
     const int er = cuda_status(cudaStreamEndCapture(cs, &p->graph), "cudaStreamEndCapture");
     rc = lr != DASH_OK ? lr : er;
   }
@@ -370,6 +570,9 @@ int dash_batch_plan_create(const dash_batch_desc* desc, dash_batch_plan** out) {
   a.paired = (g_opt_access_form == 0 && a.g.F == 2) ? 1 : 0;
   a.flags = fused::batch_flags_ptr();
   if (a.flags == nullptr) return fail(DASH_ERR_CUDA, "cannot resolve the device flag word");
+  const bool with_bwd = desc->with_backward != 0;
+  if (with_bwd && (a.g.F != 2 || D > 32))
+    return fail(DASH_ERR_UNSUPPORTED, "the batched backward supports F = 2 and L*F <= 32");
   fused::SceneDev host[DASH_MAX_SCENES];
   long long counts[DASH_MAX_SCENES];
   long long total_n = 0, total_k = 0;
@@ -381,7 +584,18 @@ int dash_batch_plan_create(const dash_batch_desc* desc, dash_batch_plan** out) {
       return fail(DASH_ERR_INVALID_ARG, "scene %d: NULL pointer", s);
     if ((reinterpret_cast<uintptr_t>(sc.table) & 15u) != 0)
       return fail(DASH_ERR_INVALID_ARG, "scene %d: table must be 16-byte aligned", s);
-    host[s] = fused::SceneDev{sc.table, sc.params, sc.x, sc.y, sc.z, sc.timestamps, sc.delta_out, sc.n, sc.K, 0};
+    host[s] = fused::SceneDev{sc.table, sc.params, sc.x, sc.y, sc.z, sc.timestamps, sc.delta_out, sc.n, sc.K, 0,
+                              nullptr, nullptr, nullptr, nullptr};
+    if (with_bwd) {
+      if (sc.ddelta == nullptr || sc.fwd_state == nullptr || sc.table_grad == nullptr || sc.mlp_grad == nullptr)
+        return fail(DASH_ERR_INVALID_ARG, "scene %d: a backward pointer is NULL", s);
+      if ((reinterpret_cast<uintptr_t>(sc.fwd_state) & 15u) != 0 || (reinterpret_cast<uintptr_t>(sc.table_grad) & 15u) != 0)
+        return fail(DASH_ERR_INVALID_ARG, "scene %d: fwd_state and table_grad must be 16-byte aligned", s);
+      host[s].ddelta = sc.ddelta;
+      host[s].state = static_cast<uint8_t*>(sc.fwd_state);
+      host[s].table_grad = sc.table_grad;
+      host[s].mlp_grad = sc.mlp_grad;
+    }
     counts[s] = sc.n;
     total_n += sc.n;
     total_k += sc.K;
@@ -391,6 +605,7 @@ int dash_batch_plan_create(const dash_batch_desc* desc, dash_batch_plan** out) {
   cudaGetDevice(&p->device);
   p->table_dtype = desc->table_dtype;
   p->form = 0;
+  p->with_bwd = with_bwd ? 1 : 0;
   p->d_scenes = nullptr;
   p->d_counts = nullptr;
   p->graph = nullptr;
@@ -407,7 +622,15 @@ int dash_batch_plan_create(const dash_batch_desc* desc, dash_batch_plan** out) {
     a.scenes = p->d_scenes;
     a.counts = p->d_counts;
     p->args = a;
-    char sig[256];
+    fused::BatchBwdArgs b;
+    memset(&b, 0, sizeof(b));
+    b.g = a.g;
+    b.D = a.D, b.Dp = a.Dp, b.O = a.O, b.n_scenes = a.n_scenes;
+    b.scenes = a.scenes;
+    b.counts = a.counts;
+    b.flags = a.flags;
+    p->bargs = b;
+    char sig[512];
     cudaDeviceProp prop;
     cudaGetDeviceProperties(&prop, p->device);
     snprintf(sig, sizeof(sig), "%s|L%d F%d T%d D%d O%d|dt%d|S%d N%lld K%lld", prop.name, a.g.L, a.g.F,

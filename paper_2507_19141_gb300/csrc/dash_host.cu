@@ -115,7 +115,7 @@ const char* dash_status_string(int s) {
 
 const char* dash_last_error(void) { return dash::g_last_error; }
 
-int dash_version(void) { return 100; }
+int dash_version(void) { return 101; }
 
 int dash_set_option(int option, int value) {
   switch (option) {

@@ -21,7 +21,7 @@
 //      over all tiles of the CTA and flushed with one atomic per weight.
 //   5. table_grad[corner] += w * (df_h + smoothness term) with vector FP32
 //      reductions (red.global.add.v2.f32 for F = 2).
-#include "deform_common.cuh"
+#include "deform_bwd_common.cuh"
 
 namespace dash {
 namespace fused {
@@ -29,12 +29,19 @@ namespace {
 
 __device__ unsigned int g_bwd_flags;  // bit 0: an MMA completion wait gave up
 
-constexpr int kKH = kHidden + 16;        // h2 tile and W3 tile K: [h | 1, 0..]
-constexpr int kKH2 = 2 * kHidden + 16;   // h1 tile and W2 tile K: [hi | 1, 0.. | lo]
-constexpr int kKG = kHidden;             // dz tile K
-constexpr int kKO = kOutPad;             // ddelta tile K
-constexpr uint32_t kTmemCols = 256;      // S (64) | dW1 (64) | dW2 (64) | dW3 (16)
-constexpr uint32_t kColS = 0, kColW1 = 64, kColW2 = 128, kColW3 = 192;
+// tile extents, TMEM columns and MMA helpers of the backward (deform_bwd_common.cuh)
+constexpr int kKH = bwdk::kKH;
+constexpr int kKH2 = bwdk::kKH2;
+constexpr int kKG = bwdk::kKG;
+constexpr int kKO = bwdk::kKO;
+constexpr uint32_t kTmemCols = bwdk::kTmemCols;
+constexpr uint32_t kColS = bwdk::kColS, kColW1 = bwdk::kColW1, kColW2 = bwdk::kColW2, kColW3 = bwdk::kColW3;
+using bwdk::issue;
+using bwdk::kmajor;
+using bwdk::mnmajor;
+using bwdk::Op;
+using bwdk::wait_mma;
+using bwdk::scatter_levels_paired;
 
 struct BwdArgs {
   Geom g;
@@ -57,36 +64,6 @@ struct BwdArgs {
   uint32_t off_w2, off_w3, off_f, off_h1, off_x, off_g3, off_ring, off_bar;
 };
 
-__device__ __forceinline__ bool wait_mma(uint32_t bar, uint32_t phase, unsigned int* flags, volatile int* abort) {
-  if (tc::mbar_wait(bar, phase, kWaitIters)) return true;
-  atomicOr(flags, 1u);
-  *abort = 1;
-  return false;
-}
-
-// One MMA chain over K (step 16) with per-operand descriptor strides.
-struct Op {
-  uint32_t addr, lbo, sbo, kstep;  // kstep: start-address advance per 16 K
-};
-
-__device__ __forceinline__ void issue(uint32_t tmem, Op a, Op b, int K, uint32_t idesc, bool accumulate) {
-  for (int k = 0; k < K; k += 16) {
-    const uint32_t s = (uint32_t)(k / 16);
-    const uint64_t ad = tc::smem_desc(a.addr + s * a.kstep, a.lbo, a.sbo);
-    const uint64_t bd = tc::smem_desc(b.addr + s * b.kstep, b.lbo, b.sbo);
-    tc::mma_bf16(tmem, ad, bd, idesc, (accumulate || k > 0) ? 1u : 0u);
-  }
-}
-
-// K-major operand (rows = MN axis, tile K extent KE).
-__device__ __forceinline__ Op kmajor(const uint8_t* t, int KE) {
-  return Op{tc::smem_addr(t), 128u, (uint32_t)KE * 16u, 256u};
-}
-// The same tile read transposed: its rows become the K axis.
-__device__ __forceinline__ Op mnmajor(const uint8_t* t, int KE) {
-  return Op{tc::smem_addr(t), (uint32_t)KE * 16u, 128u, (uint32_t)KE * 32u};
-}
-
 template <int F>
 __device__ __forceinline__ void scatter_level(float* __restrict__ grad, long long off, const uint32_t idx[16],
                                               const float w[16], const float d[F]) {
@@ -105,22 +82,6 @@ __device__ __forceinline__ void scatter_level(float* __restrict__ grad, long lon
           red_add_v4(e + f, w[b] * d[f], w[b] * d[f + 1], w[b] * d[f + 2], w[b] * d[f + 3]);
       }
     }
-  }
-}
-
-// The F = 2 table-gradient scatter of a lane pair's two Gaussians over all
-// levels (scatter2_level_paired).  p is this lane's own Gaussian; dfp points
-// at A's column of the transposed [D][kRows] dL/df_h stage (B's is the next
-// one); va / vb say whether A / B exist; pm names the pair's lanes.
-__device__ __forceinline__ void scatter_levels_paired(const Geom& g, float* __restrict__ grad, float4 p,
-                                                      const float* dfp, uint32_t xb, bool va, bool vb,
-                                                      unsigned int pm) {
-  float4 pa, pb;
-  pair_points(p, xb, pm, pa, pb);
-  for (int l = 0; l < g.L; ++l) {
-    const float2 f0 = *reinterpret_cast<const float2*>(dfp + (2 * l) * kRows);      // (A, B) feature 0
-    const float2 f1 = *reinterpret_cast<const float2*>(dfp + (2 * l + 1) * kRows);  // (A, B) feature 1
-    scatter2_level_paired(g, l, pa, pb, xb, va, vb, grad + g.offset[l] * 2, f0.x, f1.x, f0.y, f1.y);
   }
 }
 
@@ -580,17 +541,8 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_bwd_ws_kernel(const
   volatile int* abort_flag = reinterpret_cast<volatile int*>(mma_bar + 1) + 1;
   const int stage_floats = a.Dp * kRows;
 
-  const float* W1 = a.params;
-  const float* b1 = W1 + kHidden * a.D;
-  const float* W2 = b1 + kHidden;
-  const float* b2 = W2 + kHidden * kHidden;
-  const float* W3 = b2 + kHidden;
-  const float* b3 = W3 + a.O * kHidden;
-  if (tid < kRows) {
-    build_weight_tile(w1, kHidden, KF, a.Dp, true, a.D, kHidden, W1, b1, tid, kRows);
-    build_weight_tile(w2, kHidden, kKH2, kHidden, true, kHidden, kHidden, W2, b2, tid, kRows);
-    build_weight_tile(w3, kOutPad, kKH, kHidden, false, kHidden, a.O, W3, b3, tid, kRows);
-  }
+  const bwdk::Tiles tl{w1, w2, w3, Ft, H1, X, G3, KF, a.D, a.Dp, a.O};
+  if (tid < kRows) bwdk::build_weights(tl, a.params, tid, kRows);
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
       tc::mbar_init(tc::smem_addr(&full[s]), kRows);
@@ -621,175 +573,14 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_bwd_ws_kernel(const
     const uint32_t bar = tc::smem_addr(mma_bar);
     uint32_t phase = 0;
     bool had_tile = false;
-    const uint32_t id_fwd = tc::idesc_bf16(kRows, kHidden, 0, 0);
-    const uint32_t id_dh = tc::idesc_bf16(kRows, kHidden, 0, 1);
-    const uint32_t id_df = tc::idesc_bf16(kRows, a.Dp, 0, 1);
-    const uint32_t id_w = tc::idesc_bf16(kRows, kHidden, 1, 1);
-    const uint32_t id_w3 = tc::idesc_bf16(kRows, kOutPad, 1, 1);
+    const bwdk::Ids ids = bwdk::make_ids(a.Dp);
     for (long long j = 0; j < my_tiles; ++j) {
       const long long row = (blockIdx.x + j * gridDim.x) * kRows + r;
       const bool valid = row < n;
       const uint8_t* srow = valid ? a.state + row * state_stride(a.D) : nullptr;
-      // f_h [hi | 1 | 0] from the state, masks from the forward
-      const __nv_bfloat16* fs = reinterpret_cast<const __nv_bfloat16*>(srow);
-      for (int c = 0; c < a.Dp / 8; ++c) {
-        uint4 hv;
-        if (srow != nullptr && 8 * c + 8 <= a.D) {
-          hv = __ldcs(reinterpret_cast<const uint4*>(fs + 8 * c));  // rows are 16-byte aligned
-        } else {
-          uint32_t h[4];
-#pragma unroll
-          for (int jj = 0; jj < 4; ++jj) {
-            const int k = 8 * c + 2 * jj;
-            const float v0 = (srow != nullptr && k < a.D) ? __bfloat162float(__ldcs(fs + k)) : 0.0f;
-            const float v1 = (srow != nullptr && k + 1 < a.D) ? __bfloat162float(__ldcs(fs + k + 1)) : 0.0f;
-            h[jj] = pack_bf16x2(v0, v1);
-          }
-          hv = make_uint4(h[0], h[1], h[2], h[3]);
-        }
-        *reinterpret_cast<uint4*>(Ft + tile_off(r, 8 * c, KF)) = hv;
-        *reinterpret_cast<uint4*>(Ft + tile_off(r, a.Dp + 16 + 8 * c, KF)) = make_uint4(0u, 0u, 0u, 0u);
-      }
-      write_ones(Ft, r, a.Dp, KF);
-      uint32_t m1[2] = {0u, 0u}, m2[2] = {0u, 0u};
-      if (srow != nullptr) {
-        const uint4 m = __ldcs(reinterpret_cast<const uint4*>(srow + state_mask_off(a.D)));
-        m1[0] = m.x;
-        m1[1] = m.y;
-        m2[0] = m.z;
-        m2[1] = m.w;
-      }
-      tc::fence_async_smem();
-      tc::named_sync(1, kRows);
-      if (*abort_flag) break;
-      if (r == 0) {
-        tc::fence_after_sync();
-        issue(tbase + kColS, kmajor(Ft, KF), kmajor(w1, KF), KF, id_fwd, false);
-        tc::mma_commit(bar);
-      }
-      wait_mma(bar, phase, a.flags, abort_flag);
-      phase ^= 1u;
-      tc::fence_after_sync();
-      // h1 = relu(z1) with the forward's mask -> H1 [hi | 1 | lo]
-#pragma unroll
-      for (int c = 0; c < kHidden / 16; ++c) {
-        float v[16];
-        tc::tmem_ld16(trow + kColS + 16 * c, v);
-#pragma unroll
-        for (int jj = 0; jj < 16; ++jj)
-          v[jj] = ((m1[c >> 1] >> ((c & 1) * 16 + jj)) & 1u) ? fmaxf(v[jj], 0.0f) : 0.0f;
-        uint4 h0, l0, h1, l1;
-        split_hi_lo8(v, h0, l0);
-        split_hi_lo8(v + 8, h1, l1);
-        *reinterpret_cast<uint4*>(H1 + tile_off(r, 16 * c, kKH2)) = h0;
-        *reinterpret_cast<uint4*>(H1 + tile_off(r, 16 * c + 8, kKH2)) = h1;
-        *reinterpret_cast<uint4*>(H1 + tile_off(r, kHidden + 16 + 16 * c, kKH2)) = l0;
-        *reinterpret_cast<uint4*>(H1 + tile_off(r, kHidden + 16 + 16 * c + 8, kKH2)) = l1;
-      }
-      write_ones(H1, r, kHidden, kKH2);
-      tc::fence_before_sync();
-      tc::fence_async_smem();
-      tc::named_sync(1, kRows);
-      if (*abort_flag) break;
-      if (r == 0) {
-        tc::fence_after_sync();
-        issue(tbase + kColS, kmajor(H1, kKH2), kmajor(w2, kKH2), kKH2, id_fwd, false);
-        tc::mma_commit(bar);
-      }
-      wait_mma(bar, phase, a.flags, abort_flag);
-      phase ^= 1u;
-      tc::fence_after_sync();
-      // h2 -> X [h2 | 1]; ddelta -> G3
-#pragma unroll
-      for (int c = 0; c < kHidden / 16; ++c) {
-        float v[16];
-        tc::tmem_ld16(trow + kColS + 16 * c, v);
-#pragma unroll
-        for (int jj = 0; jj < 16; ++jj)
-          v[jj] = ((m2[c >> 1] >> ((c & 1) * 16 + jj)) & 1u) ? fmaxf(v[jj], 0.0f) : 0.0f;
-        uint32_t h[8];
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) h[jj] = pack_bf16x2(v[2 * jj], v[2 * jj + 1]);
-        *reinterpret_cast<uint4*>(X + tile_off(r, 16 * c, kKH)) = make_uint4(h[0], h[1], h[2], h[3]);
-        *reinterpret_cast<uint4*>(X + tile_off(r, 16 * c + 8, kKH)) = make_uint4(h[4], h[5], h[6], h[7]);
-      }
-      write_ones(X, r, kHidden, kKH);
-      {
-        float d[16];
-#pragma unroll
-        for (int jj = 0; jj < 16; ++jj)
-          d[jj] = (valid && jj < a.O) ? __ldcs(a.ddelta + (long long)jj * a.n_cap + row) : 0.0f;
-        uint32_t h[8];
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) h[jj] = pack_bf16x2(d[2 * jj], d[2 * jj + 1]);
-        *reinterpret_cast<uint4*>(G3 + tile_off(r, 0, kKO)) = make_uint4(h[0], h[1], h[2], h[3]);
-        *reinterpret_cast<uint4*>(G3 + tile_off(r, 8, kKO)) = make_uint4(h[4], h[5], h[6], h[7]);
-      }
-      tc::fence_before_sync();
-      tc::fence_async_smem();
-      tc::named_sync(1, kRows);
-      if (*abort_flag) break;
-      if (r == 0) {
-        tc::fence_after_sync();
-        issue(tbase + kColS, kmajor(G3, kKO), mnmajor(w3, kKH), kKO, id_dh, false);
-        issue(tbase + kColW3, mnmajor(X, kKH), mnmajor(G3, kKO), kRows, id_w3, had_tile);
-        tc::mma_commit(bar);
-      }
-      wait_mma(bar, phase, a.flags, abort_flag);
-      phase ^= 1u;
-      tc::fence_after_sync();
-      // dz2 = dh2 * m2 -> X
-#pragma unroll
-      for (int c = 0; c < kHidden / 16; ++c) {
-        float v[16];
-        tc::tmem_ld16(trow + kColS + 16 * c, v);
-#pragma unroll
-        for (int jj = 0; jj < 16; ++jj) v[jj] = ((m2[c >> 1] >> ((c & 1) * 16 + jj)) & 1u) ? v[jj] : 0.0f;
-        uint32_t h[8];
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) h[jj] = pack_bf16x2(v[2 * jj], v[2 * jj + 1]);
-        *reinterpret_cast<uint4*>(X + tile_off(r, 16 * c, kKG)) = make_uint4(h[0], h[1], h[2], h[3]);
-        *reinterpret_cast<uint4*>(X + tile_off(r, 16 * c + 8, kKG)) = make_uint4(h[4], h[5], h[6], h[7]);
-      }
-      tc::fence_before_sync();
-      tc::fence_async_smem();
-      tc::named_sync(1, kRows);
-      if (*abort_flag) break;
-      if (r == 0) {
-        tc::fence_after_sync();
-        issue(tbase + kColS, kmajor(X, kKG), mnmajor(w2, kKH2), kKG, id_dh, false);
-        issue(tbase + kColW2, mnmajor(H1, kKH2), mnmajor(X, kKG), kRows, id_w, had_tile);
-        tc::mma_commit(bar);
-      }
-      wait_mma(bar, phase, a.flags, abort_flag);
-      phase ^= 1u;
-      tc::fence_after_sync();
-      // dz1 = dh1 * m1 -> H1
-#pragma unroll
-      for (int c = 0; c < kHidden / 16; ++c) {
-        float v[16];
-        tc::tmem_ld16(trow + kColS + 16 * c, v);
-#pragma unroll
-        for (int jj = 0; jj < 16; ++jj) v[jj] = ((m1[c >> 1] >> ((c & 1) * 16 + jj)) & 1u) ? v[jj] : 0.0f;
-        uint32_t h[8];
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) h[jj] = pack_bf16x2(v[2 * jj], v[2 * jj + 1]);
-        *reinterpret_cast<uint4*>(H1 + tile_off(r, 16 * c, kKG)) = make_uint4(h[0], h[1], h[2], h[3]);
-        *reinterpret_cast<uint4*>(H1 + tile_off(r, 16 * c + 8, kKG)) = make_uint4(h[4], h[5], h[6], h[7]);
-      }
-      tc::fence_before_sync();
-      tc::fence_async_smem();
-      tc::named_sync(1, kRows);
-      if (*abort_flag) break;
-      if (r == 0) {
-        tc::fence_after_sync();
-        issue(tbase + kColS, kmajor(H1, kKG), mnmajor(w1, KF), kKG, id_df, false);
-        issue(tbase + kColW1, mnmajor(Ft, KF), mnmajor(H1, kKG), kRows, id_w, had_tile);
-        tc::mma_commit(bar);
-      }
-      wait_mma(bar, phase, a.flags, abort_flag);
-      phase ^= 1u;
-      tc::fence_after_sync();
+      if (!bwdk::decoder_tile(tl, ids, tbase, trow, r, bar, phase, a.flags, abort_flag, srow, a.ddelta + row,
+                              a.n_cap, valid, had_tile))
+        break;
       had_tile = true;
       // publish dL/df_h of this tile to the scatter groups
       const int s = (int)(j % S);
@@ -798,49 +589,14 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_bwd_ws_kernel(const
         atomicOr(a.flags, 1u);
         *abort_flag = 1;
       }
-      float* stage = ring + (size_t)s * stage_floats;
-      for (int c = 0; c < a.Dp / 16; ++c) {
-        float v[16];
-        tc::tmem_ld16(trow + kColS + 16 * c, v);
-#pragma unroll
-        for (int jj = 0; jj < 16; ++jj) stage[(16 * c + jj) * kRows + r] = v[jj];
-      }
+      bwdk::publish(ring + (size_t)s * stage_floats, trow, r, a.Dp);
       tc::fence_before_sync();
       tc::mbar_arrive(tc::smem_addr(&full[s]));
     }
     // flush the CTA's weight gradients (rows = input unit, columns = output unit)
     tc::named_sync(1, kRows);
     tc::fence_after_sync();
-    if (had_tile && !*abort_flag) {
-      float* gW1 = a.mlp_grad;
-      float* gb1 = gW1 + kHidden * a.D;
-      float* gW2 = gb1 + kHidden;
-      float* gb2 = gW2 + kHidden * kHidden;
-      float* gW3 = gb2 + kHidden;
-      float* gb3 = gW3 + a.O * kHidden;
-#pragma unroll 1
-      for (int c = 0; c < 4; ++c) {
-        float v[16];
-        tc::tmem_ld16(trow + kColW1 + 16 * c, v);
-        for (int jj = 0; jj < 16; ++jj) {
-          const int o = 16 * c + jj;
-          if (r < a.D) atomicAdd(gW1 + o * a.D + r, v[jj]);
-          else if (r == a.Dp) atomicAdd(gb1 + o, v[jj]);
-        }
-        tc::tmem_ld16(trow + kColW2 + 16 * c, v);
-        for (int jj = 0; jj < 16; ++jj) {
-          const int o = 16 * c + jj;
-          if (r < kHidden) atomicAdd(gW2 + o * kHidden + r, v[jj]);
-          else if (r == kHidden) atomicAdd(gb2 + o, v[jj]);
-        }
-      }
-      float v[16];
-      tc::tmem_ld16(trow + kColW3, v);
-      for (int jj = 0; jj < a.O; ++jj) {
-        if (r < kHidden) atomicAdd(gW3 + jj * kHidden + r, v[jj]);
-        else if (r == kHidden) atomicAdd(gb3 + jj, v[jj]);
-      }
-    }
+    if (had_tile && !*abort_flag) bwdk::flush_dw(trow, r, a.D, a.Dp, a.O, a.mlp_grad);
   } else {
     // ------------------------------------------------------ scatter groups
     const int pg = tid / kRows - 1, r = tid % kRows;

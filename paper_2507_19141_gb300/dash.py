@@ -102,13 +102,14 @@ class dash_batch_scene(ctypes.Structure):
     _fields_ = [("table", ctypes.c_void_p), ("params", ctypes.c_void_p), ("x", ctypes.c_void_p),
                 ("y", ctypes.c_void_p), ("z", ctypes.c_void_p), ("timestamps", ctypes.c_void_p),
                 ("delta_out", ctypes.c_void_p), ("n", ctypes.c_int64), ("K", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reserved", ctypes.c_int32), ("ddelta", ctypes.c_void_p), ("fwd_state", ctypes.c_void_p),
+                ("table_grad", ctypes.c_void_p), ("mlp_grad", ctypes.c_void_p)]
 
 
 class dash_batch_desc(ctypes.Structure):
     _fields_ = [("layout", ctypes.c_void_p), ("table_dtype", ctypes.c_int32), ("d_in", ctypes.c_int32),
                 ("d_hidden", ctypes.c_int32), ("d_out", ctypes.c_int32), ("n_scenes", ctypes.c_int32),
-                ("scenes", ctypes.c_void_p)]
+                ("scenes", ctypes.c_void_p), ("with_backward", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -588,22 +589,33 @@ def dash_batch_plan_destroy(plan) -> None:
 
 class BatchPlan:
     """Owner of a dash_batch_plan.  scenes: list of dicts with CUDA tensors
-    table, params, x, y, z, timestamps [K], delta_out [K][O][n] (the plan
-    keeps references to all of them)."""
+    table, params, x, y, z, timestamps [K], delta_out [K][O][n]; with
+    backward=True also ddelta [K][O][n] (upstream gradient), table_grad and
+    mlp_grad (FP32, accumulated), and fwd_state [K][n][state size] uint8,
+    allocated here when absent (the plan keeps references to all of them)."""
 
-    def __init__(self, layout: dash_layout, scenes, d_in=32, d_hidden=64, d_out=10):
+    def __init__(self, layout: dash_layout, scenes, d_in=32, d_hidden=64, d_out=10, backward=False):
         self.layout = layout
         self.scenes = scenes
         arr = (dash_batch_scene * len(scenes))()
         dt = None
+        stride = int(_lib.dash_deform_state_size(ctypes.byref(dash_mlp(d_in, d_hidden, d_out, 0, None)))) \
+            if backward else 0
         for i, sc in enumerate(scenes):
             dt = _DTYPE_CODE[sc["table"].dtype]
+            n, K = sc["x"].numel(), sc["timestamps"].numel()
+            bw = [None, None, None, None]
+            if backward:
+                if sc.get("fwd_state") is None:
+                    sc["fwd_state"] = torch.empty((K, n, stride), dtype=torch.uint8, device=sc["x"].device)
+                bw = [sc["ddelta"].data_ptr(), sc["fwd_state"].data_ptr(), sc["table_grad"].data_ptr(),
+                      sc["mlp_grad"].data_ptr()]
             arr[i] = dash_batch_scene(sc["table"].data_ptr(), sc["params"].data_ptr(), sc["x"].data_ptr(),
                                       sc["y"].data_ptr(), sc["z"].data_ptr(), sc["timestamps"].data_ptr(),
-                                      sc["delta_out"].data_ptr(), sc["x"].numel(), sc["timestamps"].numel(), 0)
+                                      sc["delta_out"].data_ptr(), n, K, 0, *bw)
         self._arr = arr
         desc = dash_batch_desc(ctypes.addressof(layout), dt, d_in, d_hidden, d_out, len(scenes),
-                               ctypes.addressof(arr))
+                               ctypes.addressof(arr), 1 if backward else 0, 0)
         self.handle = dash_batch_plan_create(desc)
 
     def counts(self) -> torch.Tensor:
