@@ -45,7 +45,7 @@ STEP_BYTES = 2 + 4 + FWD_BYTES + BWD_BYTES
 # (profiles/warp_specialised_kernels_1M.md), valid while the kernel's sources
 # hash to the captured value; otherwise the benchmark reports no traffic.
 NCU_TRAFFIC = {
-    "bwd": {"bytes": (196.7 + 3.7) * 1e6, "n": 1_000_000, "sha256_16": "f6868470811792cc",
+    "bwd": {"bytes": (195.9 + 1.1) * 1e6, "n": 1_000_000, "sha256_16": "3277ecf08f5a6a58",
             "sources": ("deform_bwd.cu", "deform_bwd_common.cuh", "deform_common.cuh", "dash_internal.cuh",
                         "tc_ptx.cuh")},
     "fwd": {"bytes": (45.5 + 72.0) * 1e6, "n": 1_000_000, "sha256_16": "758ded77607693f1",
@@ -843,7 +843,7 @@ def run_batched(torch, stream):
         sc["table_grad"] = torch.zeros((lay.total, grid.F), dtype=torch.float32, device="cuda")
         sc["mlp_grad"] = torch.zeros(mlpc.n_params, dtype=torch.float32, device="cuda")
     plan = dash.BatchPlan(lay, scenes, backward=True)
-    plan.autotune(cache)
+    form_b = plan.autotune(cache)  # forward form + 16 * backward form
     plan.run()
     torch.cuda.synchronize()
     ms_b = time_steps(torch, plan.run, 3, stream)
@@ -851,7 +851,8 @@ def run_batched(torch, stream):
     return {"batched_scenes": len(counts), "batched_counts": counts, "batched_timestamps": len(tss[0]),
             "batched_evaluations": evals, "batched_launch_ms": ms, "batched_form": form,
             "batched_evaluations_per_s": evals / (ms / 1e3),
-            "batched_fwd_bwd_launch_ms": ms_b, "batched_fwd_bwd_evaluations_per_s": evals / (ms_b / 1e3)}
+            "batched_fwd_bwd_launch_ms": ms_b, "batched_fwd_bwd_form": form_b,
+            "batched_fwd_bwd_evaluations_per_s": evals / (ms_b / 1e3)}
 
 
 # ------------------------------------------------------------ CPU oracle --
@@ -942,7 +943,8 @@ def profile_case(n):
     1 GB on the device, two launches each of the encoder forward/backward, the
     fused forward/backward (the backward once more with the coordinate
     gradient and once with the Eq. 11 term), the decomposition with its top-k mask and its backward, one
-    occupancy count, and
+    occupancy count, two runs of a batched forward + backward plan (2 scenes
+    of 600k and 400k, 2 timestamps each), and
     two render frames (1352 x 1014, 106.6k Gaussians) with the renderer's
     backward."""
     import numpy as np
@@ -983,6 +985,22 @@ def profile_case(n):
         mask, _ = dash.dash_topk_mask(norm, 50.0)
         dash.dash_decomp_bwd(lay3, pts.x, pts.y, pts.z, table3, dec, tg3, pg3, d_dp=d_dp, mask=mask, lambda_s=1.0)
     dash.dash_hash4d_collision_stats(lay, pts)
+    # the batched forward + backward: 2 scenes (600k, 400k) x 2 timestamps
+    scenes = []
+    for m in (600_000, 400_000):
+        bx, by, bz, _ = synth.scene_coords(rng, m)
+        scenes.append({"table": dev(synth.table_values(rng, lay.total, grid.F, np.float16)),
+                       "params": dev(synth.mlp_params(rng, mlpc)), "x": dev(bx), "y": dev(by), "z": dev(bz),
+                       "timestamps": dev(np.array([0.25, 0.75], dtype=np.float32)),
+                       "delta_out": torch.empty((2, mlpc.d_out, m), device="cuda"),
+                       "ddelta": torch.randn((2, mlpc.d_out, m), device="cuda"),
+                       "table_grad": torch.zeros((lay.total, grid.F), device="cuda"),
+                       "mlp_grad": torch.zeros(mlpc.n_params, device="cuda")})
+    plan = dash.BatchPlan(lay, scenes, backward=True)
+    for _ in range(2):
+        plan.run()
+    torch.cuda.synchronize()
+    plan.close()
     # render frames at 1352 x 1014 with 106.6k Gaussians, and the renderer's backward
     f = render_frame_setup(torch)
     _, rws, cap, pairs = dash.dash_raster_fwd(f["cam"], f["G"], image=f["image"])

@@ -494,14 +494,21 @@ int dash_batch_plan_create(const dash_batch_desc* desc, dash_batch_plan** out);
 int64_t* dash_batch_counts(dash_batch_plan* plan);
 /* Replays the captured graph on `stream`. */
 int dash_batch_run(dash_batch_plan* plan, void* stream);
-/* Kernel form in use (index into the compiled (gather groups, ring stages)
- * forms the autotuner chooses from). */
+/* Kernel forms in use: f + 16 * b, f the forward form (index into the
+ * compiled (gather groups, ring stages) forms {(4,4), (3,6), (3,3), (2,4),
+ * (2,2)}), b the backward form (into the (scatter groups, ring stages) forms
+ * {(3,3), (2,2), (2,4), (3,4)}; 0 without a backward). */
 int dash_batch_form(const dash_batch_plan* plan);
 /* Autotuner: if cache_json_path holds an entry for this plan's signature
- * (GPU, grid shape, scenes, counts, timestamps) that form is used; otherwise
- * every compiled form is timed on this plan's own work (one warm-up and three
- * timed launches on `stream`), the fastest kept, and the cache file rewritten
- * with it.  The graph is re-captured for the chosen form.  Synchronous. */
+ * (GPU, grid shape, scenes, counts, timestamps, with or without backward)
+ * those forms are used; otherwise every compiled forward form is timed on
+ * this plan's own work (one warm-up and three timed launches on `stream`)
+ * and the fastest kept, then, with a backward, every backward form on the
+ * state of one forward run.  The gradient buffers are copied aside before
+ * the backward runs and restored after them, so tuning leaves them as they
+ * were (a temporary device buffer of the scenes' gradient size).  The cache
+ * file is rewritten with the choice (the value f + 16 * b) and the graph
+ * re-captured for it.  Synchronous. */
 int dash_batch_autotune(dash_batch_plan* plan, const char* cache_json_path, void* stream);
 int dash_batch_plan_destroy(dash_batch_plan* plan);
 

@@ -19,6 +19,7 @@
 #include <string.h>
 
 #include <string>
+#include <vector>
 
 #include "deform_bwd_common.cuh"
 
@@ -454,15 +455,17 @@ int launch_batch(int form, int table_dtype, BatchArgs& a, cudaStream_t st) {
   }
 }
 
-// The batched backward in the single-scene default shape: three scatter
-// groups, three ring stages.
-template <typename TT>
-int launch_bwd_tt(BatchBwdArgs a, cudaStream_t st) {
+// Compiled forms of the batched backward: (scatter groups P, ring stages S);
+// the first is the single-scene default.
+constexpr Form kBwdForms[] = {{3, 3}, {2, 2}, {2, 4}, {3, 4}};
+constexpr int kNumBwdForms = sizeof(kBwdForms) / sizeof(kBwdForms[0]);
+
+template <typename TT, int P, int S>
+int launch_bwd_form(BatchBwdArgs a, cudaStream_t st) {
   using bwdk::kKG;
   using bwdk::kKH;
   using bwdk::kKH2;
   using bwdk::kKO;
-  constexpr int P = 3, S = 3;
   const int KF = 2 * a.Dp + 16;
   uint32_t off = (uint32_t)kHidden * KF * 2;
   a.off_w2 = (off + 127) & ~127u;
@@ -487,8 +490,18 @@ int launch_bwd_tt(BatchBwdArgs a, cudaStream_t st) {
   return launch_status("batch_bwd_kernel");
 }
 
-int launch_batch_bwd(int table_dtype, const BatchBwdArgs& a, cudaStream_t st) {
-  return table_dtype == DASH_F16 ? launch_bwd_tt<__half>(a, st) : launch_bwd_tt<float>(a, st);
+template <typename TT>
+int launch_bwd_tt(int form, const BatchBwdArgs& a, cudaStream_t st) {
+  switch (form) {
+    case 0: return launch_bwd_form<TT, 3, 3>(a, st);
+    case 1: return launch_bwd_form<TT, 2, 2>(a, st);
+    case 2: return launch_bwd_form<TT, 2, 4>(a, st);
+    default: return launch_bwd_form<TT, 3, 4>(a, st);
+  }
+}
+
+int launch_batch_bwd(int form, int table_dtype, const BatchBwdArgs& a, cudaStream_t st) {
+  return table_dtype == DASH_F16 ? launch_bwd_tt<__half>(form, a, st) : launch_bwd_tt<float>(form, a, st);
 }
 
 unsigned int* batch_flags_ptr() {
@@ -506,11 +519,15 @@ struct dash_batch_plan {
   int device;
   int table_dtype;
   int form;
+  int bform;  // backward form (plans with a backward)
   int with_bwd;
   dash::fused::BatchArgs args;
   dash::fused::BatchBwdArgs bargs;
   dash::fused::SceneDev* d_scenes;
   long long* d_counts;
+  std::vector<dash::fused::SceneDev> h_scenes;  // host copy (gradient pointers for the autotuner)
+  long long grad_floats;                         // table entries * F per scene
+  long long param_floats;                        // decoder parameters per scene
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   std::string signature;
@@ -525,6 +542,20 @@ void destroy_graph(dash_batch_plan* p) {
   p->graph = nullptr;
 }
 
+// One warm-up launch, then the mean of three timed launches on st.
+template <typename Launch>
+int time_form(Launch launch, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, float* ms) {
+  using namespace dash;
+  int rc = launch();
+  if (rc != DASH_OK) return rc;
+  rc = cuda_status(cudaEventRecord(e0, st), "cudaEventRecord");
+  for (int rep = 0; rep < 3 && rc == DASH_OK; ++rep) rc = launch();
+  if (rc == DASH_OK) rc = cuda_status(cudaEventRecord(e1, st), "cudaEventRecord");
+  if (rc == DASH_OK) rc = cuda_status(cudaEventSynchronize(e1), "cudaEventSynchronize");
+  if (rc == DASH_OK) rc = cuda_status(cudaEventElapsedTime(ms, e0, e1), "cudaEventElapsedTime");
+  return rc;
+}
+
 // Captures one launch of the current form into a graph on a private stream.
 int capture(dash_batch_plan* p) {
   using namespace dash;
@@ -534,7 +565,7 @@ int capture(dash_batch_plan* p) {
   int rc = cuda_status(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
   if (rc == DASH_OK) {
     int lr = fused::launch_batch(p->form, p->table_dtype, p->args, cs);
-    if (lr == DASH_OK && p->with_bwd) lr = fused::launch_batch_bwd(p->table_dtype, p->bargs, cs);
+    if (lr == DASH_OK && p->with_bwd) lr = fused::launch_batch_bwd(p->bform, p->table_dtype, p->bargs, cs);
     const int er = cuda_status(cudaStreamEndCapture(cs, &p->graph), "cudaStreamEndCapture");
     rc = lr != DASH_OK ? lr : er;
   }
@@ -604,7 +635,12 @@ int dash_batch_plan_create(const dash_batch_desc* desc, dash_batch_plan** out) {
   p->device = 0;
   cudaGetDevice(&p->device);
   p->table_dtype = desc->table_dtype;
+  p->h_scenes.assign(host, host + desc->n_scenes);
+  p->grad_floats = desc->layout->offset[a.g.L] * a.g.F;
+  p->param_floats = (long long)fused::kHidden * D + fused::kHidden + (long long)fused::kHidden * fused::kHidden +
+                    fused::kHidden + (long long)a.O * fused::kHidden + a.O;
   p->form = 0;
+  p->bform = 0;
   p->with_bwd = with_bwd ? 1 : 0;
   p->d_scenes = nullptr;
   p->d_counts = nullptr;
@@ -633,8 +669,9 @@ int dash_batch_plan_create(const dash_batch_desc* desc, dash_batch_plan** out) {
     char sig[512];
     cudaDeviceProp prop;
     cudaGetDeviceProperties(&prop, p->device);
-    snprintf(sig, sizeof(sig), "%s|L%d F%d T%d D%d O%d|dt%d|S%d N%lld K%lld", prop.name, a.g.L, a.g.F,
-             desc->layout->log2_T, D, a.O, desc->table_dtype, desc->n_scenes, total_n, total_k);
+    snprintf(sig, sizeof(sig), "%s|L%d F%d T%d D%d O%d|dt%d|S%d N%lld K%lld%s", prop.name, a.g.L, a.g.F,
+             desc->layout->log2_T, D, a.O, desc->table_dtype, desc->n_scenes, total_n, total_k,
+             with_bwd ? "|bwd" : "");
     p->signature = sig;
     rc = capture(p);
   }
@@ -665,7 +702,7 @@ int dash_batch_plan_destroy(dash_batch_plan* plan) {
   return DASH_OK;
 }
 
-int dash_batch_form(const dash_batch_plan* plan) { return plan == nullptr ? -1 : plan->form; }
+int dash_batch_form(const dash_batch_plan* plan) { return plan == nullptr ? -1 : plan->form + 16 * plan->bform; }
 
 int dash_batch_autotune(dash_batch_plan* plan, const char* cache_json_path, void* stream) {
   using namespace dash;
@@ -681,10 +718,13 @@ int dash_batch_autotune(dash_batch_plan* plan, const char* cache_json_path, void
     }
     const size_t at = cache.find(key);
     if (at != std::string::npos) {
-      const int form = atoi(cache.c_str() + at + key.size());
-      if (form >= 0 && form < fused::kNumForms) {
-        if (form != plan->form) {
+      // the entry: forward form + 16 * backward form
+      const int code = atoi(cache.c_str() + at + key.size());
+      const int form = code % 16, bform = code / 16;
+      if (code >= 0 && form < fused::kNumForms && bform < fused::kNumBwdForms && (plan->with_bwd || bform == 0)) {
+        if (form != plan->form || bform != plan->bform) {
           plan->form = form;
+          plan->bform = bform;
           return capture(plan);
         }
         return DASH_OK;
@@ -699,31 +739,71 @@ int dash_batch_autotune(dash_batch_plan* plan, const char* cache_json_path, void
     cudaEventDestroy(e0);
     return s;
   }
+  int rc = DASH_OK;
   int best = plan->form;
   float best_ms = 1e30f;
-  int rc = DASH_OK;
   for (int form = 0; form < fused::kNumForms && rc == DASH_OK; ++form) {
-    int lr = fused::launch_batch(form, plan->table_dtype, plan->args, st);
-    if (lr == DASH_ERR_UNSUPPORTED) continue;  // does not fit this shape
-    if (lr != DASH_OK) {
-      rc = lr;
-      break;
-    }
-    rc = cuda_status(cudaEventRecord(e0, st), "cudaEventRecord");
-    for (int rep = 0; rep < 3 && rc == DASH_OK; ++rep) rc = fused::launch_batch(form, plan->table_dtype, plan->args, st);
-    if (rc == DASH_OK) rc = cuda_status(cudaEventRecord(e1, st), "cudaEventRecord");
-    if (rc == DASH_OK) rc = cuda_status(cudaEventSynchronize(e1), "cudaEventSynchronize");
     float ms = 0.0f;
-    if (rc == DASH_OK) rc = cuda_status(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+    const int lr = time_form([&] { return fused::launch_batch(form, plan->table_dtype, plan->args, st); }, st, e0,
+                             e1, &ms);
+    if (lr == DASH_ERR_UNSUPPORTED) continue;  // does not fit this shape
+    rc = lr;
     if (rc == DASH_OK && ms < best_ms) {
       best_ms = ms;
       best = form;
     }
   }
+  if (rc == DASH_OK) plan->form = best;
+  if (rc == DASH_OK && plan->with_bwd) {
+    // the backward forms run on the state of one forward; every run adds
+    // into the caller's gradients, so those are saved first and put back
+    const long long per = plan->grad_floats + plan->param_floats;
+    const int ns = (int)plan->h_scenes.size();
+    float* saved = nullptr;
+    rc = cuda_status(cudaMalloc(&saved, sizeof(float) * per * ns), "cudaMalloc");
+    for (int s = 0; s < ns && rc == DASH_OK; ++s) {
+      const fused::SceneDev& sc = plan->h_scenes[s];
+      rc = cuda_status(cudaMemcpyAsync(saved + s * per, sc.table_grad, sizeof(float) * plan->grad_floats,
+                                       cudaMemcpyDeviceToDevice, st), "cudaMemcpyAsync");
+      if (rc == DASH_OK)
+        rc = cuda_status(cudaMemcpyAsync(saved + s * per + plan->grad_floats, sc.mlp_grad,
+                                         sizeof(float) * plan->param_floats, cudaMemcpyDeviceToDevice, st),
+                         "cudaMemcpyAsync");
+    }
+    if (rc == DASH_OK) rc = fused::launch_batch(plan->form, plan->table_dtype, plan->args, st);
+    int bbest = plan->bform;
+    best_ms = 1e30f;
+    for (int form = 0; form < fused::kNumBwdForms && rc == DASH_OK; ++form) {
+      float ms = 0.0f;
+      const int lr = time_form([&] { return fused::launch_batch_bwd(form, plan->table_dtype, plan->bargs, st); },
+                               st, e0, e1, &ms);
+      if (lr == DASH_ERR_UNSUPPORTED) continue;
+      rc = lr;
+      if (rc == DASH_OK && ms < best_ms) {
+        best_ms = ms;
+        bbest = form;
+      }
+    }
+    for (int s = 0; s < ns && saved != nullptr; ++s) {  // put the gradients back, also after an error
+      const fused::SceneDev& sc = plan->h_scenes[s];
+      const int r1 = cuda_status(cudaMemcpyAsync(sc.table_grad, saved + s * per, sizeof(float) * plan->grad_floats,
+                                                 cudaMemcpyDeviceToDevice, st), "cudaMemcpyAsync");
+      const int r2 = cuda_status(cudaMemcpyAsync(sc.mlp_grad, saved + s * per + plan->grad_floats,
+                                                 sizeof(float) * plan->param_floats, cudaMemcpyDeviceToDevice, st),
+                                 "cudaMemcpyAsync");
+      if (rc == DASH_OK) rc = r1 != DASH_OK ? r1 : r2;
+    }
+    if (saved != nullptr) {
+      const int r = cuda_status(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+      if (rc == DASH_OK) rc = r;
+      cudaFree(saved);
+    }
+    if (rc == DASH_OK) plan->bform = bbest;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != DASH_OK) return rc;
-  plan->form = best;
+  const int code = plan->form + 16 * plan->bform;
   if (cache_json_path != nullptr) {
     // keep the other entries; replace or append this signature
     std::string body;
@@ -742,7 +822,7 @@ int dash_batch_autotune(dash_batch_plan* plan, const char* cache_json_path, void
       entries += "  " + line.substr(first) + ",\n";
     }
     char mine[512];
-    snprintf(mine, sizeof(mine), "  %s%d\n", key.c_str(), best);
+    snprintf(mine, sizeof(mine), "  %s%d\n", key.c_str(), code);
     if (FILE* f = fopen(cache_json_path, "wb")) {
       fprintf(f, "{\n%s%s}\n", entries.c_str(), mine);
       fclose(f);

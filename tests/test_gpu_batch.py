@@ -188,3 +188,38 @@ def test_batched_backward_rejects_unsupported(dashlib):
     with pytest.raises(dashlib.DashError):
         dashlib.BatchPlan(lay, scenes, d_in=16, backward=True)
     dashlib.BatchPlan(lay, scenes, d_in=16).close()  # the forward alone is supported
+
+
+def test_batched_backward_autotune_keeps_gradients(dashlib, tmp_path):
+    """Tuning the backward forms runs the backward several times; the
+    caller's gradient buffers must come out as they went in, and the chosen
+    forms must compute the same gradients."""
+    grid, mlpc = synth.PAPER_GRID, synth.PAPER_MLP
+    counts, Ks = [20_000, 3_000], [3, 2]
+    _, scenes = _scenes(dashlib, grid, mlpc, counts, Ks, np.float16, 60)
+    lay = dashlib.layout_from(grid)
+    _with_backward(scenes, lay, mlpc.d_out, np.random.default_rng(61))
+    plan = dashlib.BatchPlan(lay, scenes, backward=True)
+    plan.run()
+    torch.cuda.synchronize()
+    once = [(sc["table_grad"].clone(), sc["mlp_grad"].clone()) for sc in scenes]
+    cache = tmp_path / "tune.json"
+    code = plan.autotune(cache)
+    torch.cuda.synchronize()
+    assert 0 <= code % 16 < 5 and 0 <= code // 16 < 4 and cache.exists()
+    for sc, (tg, pg) in zip(scenes, once):
+        assert torch.equal(sc["table_grad"], tg) and torch.equal(sc["mlp_grad"], pg)
+        sc["table_grad"].zero_()
+        sc["mlp_grad"].zero_()
+    plan.run()
+    torch.cuda.synchronize()
+    for sc, (tg, pg) in zip(scenes, once):
+        assert rel_err(sc["table_grad"].cpu().numpy(), tg.cpu().numpy()) < 1e-5
+        assert rel_err(sc["mlp_grad"].cpu().numpy(), pg.cpu().numpy()) < 1e-5
+    plan2 = dashlib.BatchPlan(lay, scenes, backward=True)
+    assert plan2.autotune(cache) == code     # taken from the cache
+    fwd_only = dashlib.BatchPlan(lay, scenes)
+    assert fwd_only.autotune(cache) < 16     # its own entry, forward forms only
+    plan.close()
+    plan2.close()
+    fwd_only.close()
