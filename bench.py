@@ -479,10 +479,17 @@ def run_extras(torch, wl, args, stream):
         wl.forward()
     res["fwd_ms"] = time_steps(torch, wl.forward, reps, stream)
     loss = torch.zeros(1, dtype=torch.float32, device=wl.table.device)
-    smooth = (1.0, (1 / 2048, 1 / 2048, 1 / 2048), 1 / 300, loss)
+    # dL/df_h handed to the Eq. 11 kernel through a workspace (the default) ...
+    sws = torch.empty(dash.dash_smooth_workspace_size(wl.layout, wl.pts.n), dtype=torch.uint8,
+                      device=wl.table.device)
+    smooth = (1.0, (1 / 2048, 1 / 2048, 1 / 2048), 1 / 300, loss, sws)
     wl.backward(smooth)
     res["bwd_smooth_ms"] = time_steps(torch, lambda: wl.backward(smooth), reps, stream)
     res["fwd_bwd_smooth_gaussians_per_s"] = n / ((res["fwd_ms"] + res["bwd_smooth_ms"]) / 1e3)
+    # ... and scattered by the fused backward, the Eq. 11 kernel scattering its own term
+    smooth_sep = (1.0, (1 / 2048, 1 / 2048, 1 / 2048), 1 / 300, loss, False)
+    wl.backward(smooth_sep)
+    res["bwd_smooth_separate_ms"] = time_steps(torch, lambda: wl.backward(smooth_sep), reps, stream)
     # backward that also returns d loss / d(x, y, z, t) (gathers the corner entries as well)
     cgrad = torch.empty((4, wl.n_all), dtype=torch.float32, device=wl.table.device)
 

@@ -119,13 +119,21 @@ typedef struct dash_apply {
  * e_s = (eps_s[0], eps_s[1], eps_s[2], 0), e_t = (0, 0, 0, eps_t); perturbed
  * coordinates are clamp(fl32(clamp(p) + e)).  The perturbed encodings are
  * recomputed by the backward, never stored.  loss_out (device
- * float, may be NULL) accumulates lambda_r * L_r. */
+ * float, may be NULL) accumulates lambda_r * L_r.  ws (device, 16-byte
+ * aligned, may be NULL) of ws_bytes >= dash_smooth_workspace_size bytes
+ * lets the backward hand dL/df_h to the Eq. 11 kernel instead of
+ * scattering it (see dash_deform_mlp_bwd). */
 typedef struct dash_smooth {
   float lambda_r;
   float eps_s[3];
   float eps_t;
   float* loss_out;
+  void* ws;
+  size_t ws_bytes;
 } dash_smooth;
+
+/* Bytes of dash_smooth.ws for n points: dL/df_h as FP32 SoA [L*F][n]. */
+size_t dash_smooth_workspace_size(const dash_layout* layout, int64_t n);
 
 /* ----------------------------------------------------------- utilities -- */
 
@@ -303,7 +311,11 @@ int dash_deform_apply_bwd(const dash_points* pts, int d_out, const float* dattrs
  * With smooth != NULL and lambda_r != 0 also adds the Eq. 11 term,
  * re-encoding p, p + e_s and p + e_t (for F = 2 with a forward state in a
  * second kernel launched right after, on the same stream; otherwise inside
- * the backward kernel).  Shapes as the forward.
+ * the backward kernel).  In the two-kernel case with smooth->ws set, the
+ * backward kernel writes dL/df_h to ws instead of scattering it, and the
+ * Eq. 11 kernel adds it to the Eq. 11 gradient at p's corners, so each of
+ * those corners takes one reduction instead of two (DASH_ERR_WORKSPACE if
+ * ws_bytes is too small); ws is ignored otherwise.  Shapes as the forward.
  * coord_grad (may be NULL): SoA [4][pts->n] FP32 receives d loss / d(x, y,
  * z, t) of each compact point as dash_hash4d_coord_grad defines it (the
  * scatter step also gathers the corner entries); not available together with

@@ -577,6 +577,6 @@ __device__ __forceinline__ void scatter2_pairs(float* __restrict__ base, const u
 // Backward of the Eq. 11 smoothness term for F = 2 (smooth.cu): adds its
 // table gradient into table_grad and lambda_r L_r into sm->loss_out.
 int launch_smooth2(const Geom& g, const Pts& pts, const void* table, int table_dtype, float* table_grad,
-                   const dash_smooth* sm, cudaStream_t st);
+                   const dash_smooth* sm, const float* dfh, long long dfh_ld, cudaStream_t st);
 
 }  // namespace dash

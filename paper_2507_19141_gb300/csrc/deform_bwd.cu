@@ -61,6 +61,7 @@ struct BwdArgs {
   float* coord_grad;  // optional SoA [4][n_cap]: d loss / d(x, y, z, t)
   unsigned int* flags;
   int paired;  // F = 2 scatter by lane pairs (no Eq. 11 term, no coordinate gradient)
+  float* dfh_out;  // optional SoA [D][n_cap]: dL/df_h stored instead of scattered
   uint32_t off_w2, off_w3, off_f, off_h1, off_x, off_g3, off_ring, off_bar;
 };
 
@@ -616,8 +617,13 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_bwd_ws_kernel(const
       // stage is handed back once the tile's reductions are issued
       const float* stage = ring + (size_t)s * stage_floats;
       bool done = false;
+      if (a.dfh_out != nullptr) {  // hand dL/df_h to the Eq. 11 kernel
+        if (row < n)
+          for (int d = 0; d < a.D; ++d) a.dfh_out[(long long)d * a.n_cap + row] = stage[d * kRows + r];
+        done = true;
+      }
       if constexpr (F == 2) {
-        if (a.paired) {
+        if (a.paired && !done) {
           const long long row_a = row - (r & 1);  // the pair's even row; both lanes agree on row_a < n
           const uint32_t xb = (uint32_t)(r & 1);
           const unsigned int pm = 3u << (r & 30);
@@ -843,12 +849,28 @@ extern "C" int dash_deform_mlp_bwd(const dash_layout* layout, const dash_points*
   // kernel after the df_h scatter (both add into table_grad)
   const bool smooth_apart = ws && a.g.F == 2 && a.lambda_r != 0.0f;
   BwdArgs b = a;
+  const float* dfh = nullptr;
   if (smooth_apart) {
     b.lambda_r = 0.0f;
     b.loss_out = nullptr;
     b.paired = g_opt_access_form == 0 ? 1 : 0;
+    if (smooth->ws != nullptr) {
+      // dL/df_h goes through the workspace and is scattered with the Eq. 11 gradient
+      if (smooth->ws_bytes < dash_smooth_workspace_size(layout, a.n_cap))
+        return fail(DASH_ERR_WORKSPACE, "smooth workspace %zu B < %zu B", smooth->ws_bytes,
+                    dash_smooth_workspace_size(layout, a.n_cap));
+      if ((reinterpret_cast<uintptr_t>(smooth->ws) & 15u) != 0)
+        return fail(DASH_ERR_INVALID_ARG, "smooth workspace must be 16-byte aligned");
+      b.dfh_out = static_cast<float*>(smooth->ws);
+      dfh = b.dfh_out;
+    }
   }
   const int s = table_dtype == DASH_F32 ? dispatch<float>(a.g.F, ws, b, st) : dispatch<__half>(a.g.F, ws, b, st);
   if (s != DASH_OK || !smooth_apart) return s;
-  return launch_smooth2(a.g, a.pts, table, table_dtype, table_grad, smooth, st);
+  return launch_smooth2(a.g, a.pts, table, table_dtype, table_grad, smooth, dfh, a.n_cap, st);
+}
+
+extern "C" size_t dash_smooth_workspace_size(const dash_layout* layout, int64_t n) {
+  if (layout == nullptr || n <= 0) return 0;
+  return (size_t)layout->L * (size_t)layout->F * (size_t)n * sizeof(float);
 }

@@ -15,6 +15,9 @@
 // also give f(p + e), and its gradient joins p's in one reduction per corner.
 // A thread keeps one level of one Gaussian live at a time.  Without the
 // fused backward's shared-memory ring the whole L1 serves the gathers.
+// Given dL/df_h (SoA [L*2][n], written by the fused backward in place of its
+// scatter), p's corners take w * (dL/df_h + the Eq. 11 gradient) in one
+// reduction each.
 #include "dash_internal.cuh"
 
 namespace dash {
@@ -31,6 +34,8 @@ struct SmoothArgs {
   float eps_t;
   float lambda_r;
   float* loss_out;
+  const float* dfh;  // optional SoA [L*2][dfh_ld]
+  long long dfh_ld;
 };
 
 __device__ __forceinline__ float4 perturbed(float4 p, float ex, float ey, float ez, float et) {
@@ -72,6 +77,11 @@ __global__ void __launch_bounds__(kThreads, 2) smooth_bwd_kernel(const __grid_co
   for (int l = 0; has_a && l < a.g.L; ++l) {
     const TT* base = table + a.g.offset[l] * 2;
     float* gbase = a.grad + a.g.offset[l] * 2;
+    float h0 = 0.0f, h1 = 0.0f;  // this lane's Gaussian's dL/df_h at level l
+    if (a.dfh != nullptr && i < n) {
+      h0 = __ldg(a.dfh + (2 * l) * a.dfh_ld + i);
+      h1 = __ldg(a.dfh + (2 * l + 1) * a.dfh_ld + i);
+    }
 #pragma unroll 1
     for (int G = 0; G < 2; ++G) {  // one Gaussian of the pair at a time keeps the registers down
       if (G == 1 && !has_b) break;  // the same on both lanes
@@ -120,7 +130,10 @@ __global__ void __launch_bounds__(kThreads, 2) smooth_bwd_kernel(const __grid_co
         loss = fmaf(dt0, dt0, loss);
         loss = fmaf(dt1, dt1, loss);
       }
-      const float gp0 = fmaf(scale, dt0, scale * ds0), gp1 = fmaf(scale, dt1, scale * ds1);
+      // Gaussian G's dL/df_h lives on lane xb = G of the pair
+      const float hg0 = __shfl_sync(pm, h0, (threadIdx.x & 30u) | (uint32_t)G);
+      const float hg1 = __shfl_sync(pm, h1, (threadIdx.x & 30u) | (uint32_t)G);
+      const float gp0 = fmaf(scale, dt0, scale * ds0) + hg0, gp1 = fmaf(scale, dt1, scale * ds1) + hg1;
       const float gs0 = -scale * ds0, gs1 = -scale * ds1, gt0 = -scale * dt0, gt1 = -scale * dt1;
       // ---- scatter: p's corners (joined by p + e where it shares them), then p + e's own
       {
@@ -177,7 +190,7 @@ __global__ void __launch_bounds__(kThreads, 2) smooth_bwd_kernel(const __grid_co
 }  // namespace
 
 int launch_smooth2(const Geom& g, const Pts& pts, const void* table, int table_dtype, float* table_grad,
-                   const dash_smooth* sm, cudaStream_t st) {
+                   const dash_smooth* sm, const float* dfh, long long dfh_ld, cudaStream_t st) {
   SmoothArgs a;
   a.g = g;
   a.pts = pts;
@@ -187,6 +200,8 @@ int launch_smooth2(const Geom& g, const Pts& pts, const void* table, int table_d
   a.eps_t = sm->eps_t;
   a.lambda_r = sm->lambda_r;
   a.loss_out = sm->loss_out;
+  a.dfh = dfh;
+  a.dfh_ld = dfh_ld;
   const unsigned grid = (unsigned)((pts.n + kThreads - 1) / kThreads);
   // two CTAs per SM (128 registers a thread): capping the registers lower to
   // fit more CTAs spills and was measured slower

@@ -437,3 +437,86 @@ def test_backward_device_count_broadcast_t(dashlib, coord):
         assert np.all(c[:, live:] == 7.0)
     else:
         assert abs(float(loss.item()) - rl) <= 1e-2 * abs(rl)
+
+
+@pytest.mark.parametrize("n", [1, 2, 129])
+def test_fused_backward_tiny_and_ragged(dashlib, n):
+    """One Gaussian (a lane pair with one member), one pair, and one past a
+    128-row tile: forward and backward (+ Eq. 11) against the oracle."""
+    grid, mlpc = synth.PAPER_GRID, synth.PAPER_MLP
+    errs = _grad_errors(dashlib, grid, mlpc, n, np.float16, 90 + n, True,
+                        smooth=(0.5, (1 / 2048, 1 / 2048, 1 / 2048), 1 / 300))
+    assert all(v < 1e-2 for v in errs.values()), errs
+
+
+@pytest.mark.parametrize("how", ["host", "device"])
+def test_fused_empty_is_a_no_op(dashlib, how):
+    """n = 0 on the host, or a device count of 0 under a capacity of 500:
+    the forward writes nothing, the backward (with Eq. 11, and again with
+    the coordinate gradient) adds nothing, the loss stays 0."""
+    grid, mlpc = synth.PAPER_GRID, synth.PAPER_MLP
+    g, coords, _, table, params, dd = _case(grid, mlpc, 500, np.float16, 95)
+    lay = dashlib.layout_from(grid)
+    x, y, z, t = (to_dev(c) for c in coords)
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    pts = dashlib.Points(x, y, z, t, n=0) if how == "host" else dashlib.Points(x, y, z, t, n=500, n_dev=cnt)
+    mlp = dashlib.Mlp(to_dev(params), mlpc.d_in, mlpc.d_hidden, mlpc.d_out)
+    tab = to_dev(table)
+    out = torch.full((10, 500), 5.0, device="cuda")
+    st = dashlib.deform_state(mlp, 500, "cuda")
+    dashlib.dash_deform_mlp_fwd(lay, pts, tab, mlp, delta_out=out, fwd_state=st)
+    tg = torch.zeros((g.total, 2), dtype=torch.float32, device="cuda")
+    pg = torch.zeros(mlpc.n_params, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    ddev = to_dev(dd)
+    dashlib.dash_deform_mlp_bwd(lay, pts, tab, mlp, ddev, tg, pg, fwd_state=st,
+                                smooth=(1.0, (1 / 2048,) * 3, 1 / 300, loss))
+    cg = torch.full((4, 500), 3.0, device="cuda")
+    dashlib.dash_deform_mlp_bwd(lay, pts, tab, mlp, ddev, tg, pg, fwd_state=st, coord_grad=cg)
+    torch.cuda.synchronize()
+    assert torch.all(out == 5.0) and torch.all(cg == 3.0)
+    assert not torch.any(tg) and not torch.any(pg) and float(loss.item()) == 0.0
+
+
+@pytest.mark.parametrize("tdtype", [np.float16, np.float32])
+def test_smoothness_workspace_form_agrees(dashlib, tdtype):
+    """Eq. 11 with and without the workspace hand-over of dL/df_h (the
+    default when a forward state is given): the same gradients up to the
+    order of the additions and the same loss, through an index list whose
+    device count (2999) is below the capacity (4001, the workspace's row
+    stride); a workspace one byte short is refused."""
+    grid, mlpc = synth.PAPER_GRID, synth.PAPER_MLP
+    rng = np.random.default_rng(97)
+    n_all, cap, live = 9000, 4001, 2999
+    g = oracle_grid(grid)
+    x, y, z, t = synth.scene_coords(rng, n_all)
+    idx = np.sort(rng.choice(n_all, size=cap, replace=False)).astype(np.int32)
+    table = synth.table_values(rng, g.total, grid.F, tdtype)
+    params = synth.mlp_params(rng, mlpc)
+    dd = to_dev(synth.upstream_grad(rng, mlpc.d_out, cap))
+    lay = dashlib.layout_from(grid)
+    cnt = torch.tensor([live], dtype=torch.int64, device="cuda")
+    pts = dashlib.Points(to_dev(x), to_dev(y), to_dev(z), to_dev(t), idx=to_dev(idx), n=cap, n_dev=cnt)
+    mlp = dashlib.Mlp(to_dev(params), mlpc.d_in, mlpc.d_hidden, mlpc.d_out)
+    tab = to_dev(table)
+    st = dashlib.deform_state(mlp, cap, "cuda")
+    dashlib.dash_deform_mlp_fwd(lay, pts, tab, mlp, fwd_state=st)
+    es, et = (1 / 2048, 1 / 2048, 1 / 2048), 1 / 300
+    out = []
+    for ws in (None, False):
+        tg = torch.zeros((g.total, 2), dtype=torch.float32, device="cuda")
+        pg = torch.zeros(mlpc.n_params, dtype=torch.float32, device="cuda")
+        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        dashlib.dash_deform_mlp_bwd(lay, pts, tab, mlp, dd, tg, pg, fwd_state=st, smooth=(0.8, es, et, loss, ws))
+        out.append((tg.cpu().numpy(), pg.cpu().numpy(), float(loss.item())))
+    (tg1, pg1, l1), (tg2, pg2, l2) = out
+    assert rel_err(tg1, tg2) < 1e-5 and rel_err(pg1, pg2) < 1e-6
+    assert abs(l1 - l2) <= 1e-6 * abs(l2)
+    opts = oracle.Points(x, y, z, t, idx=idx[:live])
+    rtg, _, rl = oracle.deform_bwd(g, opts, table.astype(np.float64), 64, 10, params.astype(np.float64),
+                                   dd[:, :live].cpu().numpy().astype(np.float64), 0.8, es, et)
+    assert rel_err(tg1, rtg) < 1e-2 and abs(l1 - rl) <= 1e-2 * abs(rl)
+    short = torch.empty(dashlib.dash_smooth_workspace_size(lay, cap) - 1, dtype=torch.uint8, device="cuda")
+    with pytest.raises(dashlib.DashError) as e:
+        dashlib.dash_deform_mlp_bwd(lay, pts, tab, mlp, dd, tg, pg, fwd_state=st, smooth=(0.8, es, et, None, short))
+    assert e.value.status == dashlib.ERR_WORKSPACE
