@@ -517,13 +517,17 @@ __global__ void __launch_bounds__(kRows, 1) deform_bwd_kernel(const __grid_const
 // P scatter groups drain the ring: each thread takes one Gaussian, recomputes
 // its corners and issues the vector reductions into the tables; with the
 // smoothness term on they also encode p, p + e_s, p + e_t and scatter the
-// perturbed points' gradients.  Requires the forward state.
+// perturbed points' gradients.  With P = 0 (no ring) the decoder group
+// stores dL/df_h to a.dfh_out for the Eq. 11 kernel to scatter; that form's
+// 110 KB of shared memory lets two CTAs share an SM.  Requires the forward
+// state.
 // ---------------------------------------------------------------------------
 template <typename TT, int F, int P, int S>
 __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_bwd_ws_kernel(const __grid_constant__ BwdArgs a) {
   // tile j uses stage j % S and group j % P; the mbarrier waits tell phases
   // apart only by parity, so no two groups may wait on one stage at once
   static_assert(S >= P, "the ring needs at least one stage per scatter group");
+  static_assert(P > 0 || S == 0, "the store-only form has no ring");
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tid = threadIdx.x;
   const int KF = 2 * a.Dp + 16;
@@ -583,22 +587,26 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_bwd_ws_kernel(const
                               a.n_cap, valid, had_tile))
         break;
       had_tile = true;
-      // publish dL/df_h of this tile to the scatter groups
-      const int s = (int)(j % S);
-      const uint32_t round = (uint32_t)(j / S);
-      if (!tc::mbar_wait(tc::smem_addr(&empty[s]), (round & 1u) ^ 1u, kWaitIters)) {
-        atomicOr(a.flags, 1u);
-        *abort_flag = 1;
+      if constexpr (P == 0) {
+        bwdk::store_dfh(a.dfh_out, trow, a.D, a.Dp, a.n_cap, row, valid);
+      } else {
+        // publish dL/df_h of this tile to the scatter groups
+        const int s = (int)(j % S);
+        const uint32_t round = (uint32_t)(j / S);
+        if (!tc::mbar_wait(tc::smem_addr(&empty[s]), (round & 1u) ^ 1u, kWaitIters)) {
+          atomicOr(a.flags, 1u);
+          *abort_flag = 1;
+        }
+        bwdk::publish(ring + (size_t)s * stage_floats, trow, r, a.Dp);
+        tc::fence_before_sync();
+        tc::mbar_arrive(tc::smem_addr(&full[s]));
       }
-      bwdk::publish(ring + (size_t)s * stage_floats, trow, r, a.Dp);
-      tc::fence_before_sync();
-      tc::mbar_arrive(tc::smem_addr(&full[s]));
     }
     // flush the CTA's weight gradients (rows = input unit, columns = output unit)
     tc::named_sync(1, kRows);
     tc::fence_after_sync();
     if (had_tile && !*abort_flag) bwdk::flush_dw(trow, r, a.D, a.Dp, a.O, a.mlp_grad);
-  } else {
+  } else if constexpr (P > 0) {
     // ------------------------------------------------------ scatter groups
     const int pg = tid / kRows - 1, r = tid % kRows;
     const TT* table = static_cast<const TT*>(a.table);
@@ -617,13 +625,8 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_bwd_ws_kernel(const
       // stage is handed back once the tile's reductions are issued
       const float* stage = ring + (size_t)s * stage_floats;
       bool done = false;
-      if (a.dfh_out != nullptr) {  // hand dL/df_h to the Eq. 11 kernel
-        if (row < n)
-          for (int d = 0; d < a.D; ++d) a.dfh_out[(long long)d * a.n_cap + row] = stage[d * kRows + r];
-        done = true;
-      }
       if constexpr (F == 2) {
-        if (a.paired && !done) {
+        if (a.paired) {
           const long long row_a = row - (r & 1);  // the pair's even row; both lanes agree on row_a < n
           const uint32_t xb = (uint32_t)(r & 1);
           const unsigned int pm = 3u << (r & 30);
@@ -709,7 +712,7 @@ int launch_ws(BwdArgs a, cudaStream_t st) {
                           "cudaFuncSetAttribute(deform_bwd_ws)"))
     return s;
   const long long ntiles = (a.n_cap + kRows - 1) / kRows;
-  long long grid = sm_count();
+  long long grid = (P == 0 ? 2 : 1) * (long long)sm_count();  // the store-only form fits two CTAs per SM
   grid = ntiles < grid ? (ntiles > 0 ? ntiles : 1) : grid;
   kern<<<(unsigned)grid, (P + 1) * kRows, smem, st>>>(a);
   return launch_status("deform_bwd_ws_kernel");
@@ -865,7 +868,11 @@ extern "C" int dash_deform_mlp_bwd(const dash_layout* layout, const dash_points*
       dfh = b.dfh_out;
     }
   }
-  const int s = table_dtype == DASH_F32 ? dispatch<float>(a.g.F, ws, b, st) : dispatch<__half>(a.g.F, ws, b, st);
+  int s;
+  if (dfh != nullptr)  // the decoder alone, dL/df_h stored for the Eq. 11 kernel
+    s = table_dtype == DASH_F32 ? launch_ws<float, 2, 0, 0>(b, st) : launch_ws<__half, 2, 0, 0>(b, st);
+  else
+    s = table_dtype == DASH_F32 ? dispatch<float>(a.g.F, ws, b, st) : dispatch<__half>(a.g.F, ws, b, st);
   if (s != DASH_OK || !smooth_apart) return s;
   return launch_smooth2(a.g, a.pts, table, table_dtype, table_grad, smooth, dfh, a.n_cap, st);
 }

@@ -268,6 +268,23 @@ __device__ __forceinline__ void publish(float* stage, uint32_t trow, int r, int 
   }
 }
 
+// dL/df_h of the tile (TMEM columns kColS..) straight to global memory, SoA
+// [D][ld] FP32 at column `row` (the rows of a warp are consecutive, so each
+// feature's stores coalesce).  Warp-collective: every lane takes part in the
+// TMEM loads; only valid rows store.
+__device__ __forceinline__ void store_dfh(float* __restrict__ dst, uint32_t trow, int D, int Dp, long long ld,
+                                          long long row, bool valid) {
+  for (int c = 0; c < Dp / 16; ++c) {
+    float v[16];
+    tc::tmem_ld16(trow + kColS + 16 * c, v);
+    if (valid) {
+#pragma unroll
+      for (int jj = 0; jj < 16; ++jj)
+        if (16 * c + jj < D) dst[(long long)(16 * c + jj) * ld + row] = v[jj];
+    }
+  }
+}
+
 // Adds the weight gradients accumulated in TMEM (rows = input unit, columns
 // = output unit) into mlp_grad (packed as the parameters), one atomic per
 // weight.
