@@ -238,6 +238,9 @@ class Workload:
         self.mlp = dash.Mlp(self.params, self.mlpc.d_in, self.mlpc.d_hidden, self.mlpc.d_out)
         self.fsave = dash.deform_state(self.mlp, n_all, device)
         self.pts = dash.Points(self.x, self.y, self.z, self.t, idx=self.idx, n=n_all, n_dev=self.count)
+        # the backward's workspace: replicas of the dense levels' gradients
+        self.bws = torch.empty(dash.dash_deform_bwd_workspace_size(self.layout, n_all), dtype=torch.uint8,
+                               device=device)
         self.dash = dash
 
     def compact(self):
@@ -247,9 +250,10 @@ class Workload:
         self.dash.dash_deform_mlp_fwd(self.layout, self.pts, self.table, self.mlp, delta_out=self.delta,
                                       fwd_state=self.fsave, apply=(self.attrs_in, self.attrs_out))
 
-    def backward(self, smooth=None):
+    def backward(self, smooth=None, ws=None):
         self.dash.dash_deform_mlp_bwd(self.layout, self.pts, self.table, self.mlp, self.ddelta, self.table_grad,
-                                      self.mlp_grad, fwd_state=self.fsave, smooth=smooth)
+                                      self.mlp_grad, fwd_state=self.fsave, smooth=smooth,
+                                      ws=self.bws if ws is None else ws)
 
     def step(self):
         self.compact()
@@ -257,7 +261,7 @@ class Workload:
         self.backward()
 
 
-LAUNCHES_PER_STEP = 5  # compaction count/scan/write, fused forward, fused backward
+LAUNCHES_PER_STEP = 6  # compaction count/scan/write, fused forward, fused backward, replica sum
 
 
 def morton3(x, y, z, bits=10):
@@ -392,6 +396,7 @@ class Slot:
         self.count = torch.zeros_like(wl.count)
         self.ws = torch.empty_like(wl.ws)
         self.state = torch.empty_like(wl.fsave)
+        self.bws = torch.empty_like(wl.bws)
         self.pts = dash.Points(self.x, self.y, self.z, self.t, idx=self.idx, n=wl.n_all, n_dev=self.count)
 
     def step(self):
@@ -400,7 +405,7 @@ class Slot:
         d.dash_deform_mlp_fwd(wl.layout, self.pts, wl.table, wl.mlp, delta_out=self.delta, fwd_state=self.state,
                               apply=(wl.attrs_in, wl.attrs_out))
         d.dash_deform_mlp_bwd(wl.layout, self.pts, wl.table, wl.mlp, self.ddelta, wl.table_grad, wl.mlp_grad,
-                              fwd_state=self.state)
+                              fwd_state=self.state, ws=self.bws)
 
 
 def run_e2e(torch, wl, args, stream):
@@ -479,17 +484,19 @@ def run_extras(torch, wl, args, stream):
         wl.forward()
     res["fwd_ms"] = time_steps(torch, wl.forward, reps, stream)
     loss = torch.zeros(1, dtype=torch.float32, device=wl.table.device)
-    # dL/df_h handed to the Eq. 11 kernel through a workspace (the default) ...
-    sws = torch.empty(dash.dash_smooth_workspace_size(wl.layout, wl.pts.n), dtype=torch.uint8,
+    smooth = (1.0, (1 / 2048, 1 / 2048, 1 / 2048), 1 / 300, loss)
+    # dL/df_h handed to the Eq. 11 kernel through the workspace, gradient replicas (the default) ...
+    sws = torch.empty(dash.dash_deform_bwd_workspace_size(wl.layout, wl.pts.n, smooth), dtype=torch.uint8,
                       device=wl.table.device)
-    smooth = (1.0, (1 / 2048, 1 / 2048, 1 / 2048), 1 / 300, loss, sws)
-    wl.backward(smooth)
-    res["bwd_smooth_ms"] = time_steps(torch, lambda: wl.backward(smooth), reps, stream)
+    wl.backward(smooth, sws)
+    res["bwd_smooth_ms"] = time_steps(torch, lambda: wl.backward(smooth, sws), reps, stream)
     res["fwd_bwd_smooth_gaussians_per_s"] = n / ((res["fwd_ms"] + res["bwd_smooth_ms"]) / 1e3)
-    # ... and scattered by the fused backward, the Eq. 11 kernel scattering its own term
-    smooth_sep = (1.0, (1 / 2048, 1 / 2048, 1 / 2048), 1 / 300, loss, False)
-    wl.backward(smooth_sep)
-    res["bwd_smooth_separate_ms"] = time_steps(torch, lambda: wl.backward(smooth_sep), reps, stream)
+    # ... and without a workspace: the fused backward scatters dL/df_h, the Eq. 11 kernel its own term
+    wl.backward(smooth, False)
+    res["bwd_smooth_separate_ms"] = time_steps(torch, lambda: wl.backward(smooth, False), reps, stream)
+    # the plain backward without the gradient replicas
+    wl.backward(None, False)
+    res["bwd_no_replicas_ms"] = time_steps(torch, lambda: wl.backward(None, False), reps, stream)
     # backward that also returns d loss / d(x, y, z, t) (gathers the corner entries as well)
     cgrad = torch.empty((4, wl.n_all), dtype=torch.float32, device=wl.table.device)
 

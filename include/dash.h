@@ -15,7 +15,8 @@
  * Conventions shared by every entry point
  *   - All pointers are DEVICE pointers unless a comment says "host".
  *   - The caller owns all memory.  Nothing here allocates device memory
- *     except dash_batch_plan_create (the plan's descriptors and graph);
+ *     except dash_batch_plan_create (the plan's descriptors, graph and
+ *     gradient replicas);
  *     scratch comes from caller workspaces sized by the *_workspace_size
  *     calls.
  *   - Every call is asynchronous on the CUDA stream passed as `void* stream`
@@ -119,21 +120,13 @@ typedef struct dash_apply {
  * e_s = (eps_s[0], eps_s[1], eps_s[2], 0), e_t = (0, 0, 0, eps_t); perturbed
  * coordinates are clamp(fl32(clamp(p) + e)).  The perturbed encodings are
  * recomputed by the backward, never stored.  loss_out (device
- * float, may be NULL) accumulates lambda_r * L_r.  ws (device, 16-byte
- * aligned, may be NULL) of ws_bytes >= dash_smooth_workspace_size bytes
- * lets the backward hand dL/df_h to the Eq. 11 kernel instead of
- * scattering it (see dash_deform_mlp_bwd). */
+ * float, may be NULL) accumulates lambda_r * L_r. */
 typedef struct dash_smooth {
   float lambda_r;
   float eps_s[3];
   float eps_t;
   float* loss_out;
-  void* ws;
-  size_t ws_bytes;
 } dash_smooth;
-
-/* Bytes of dash_smooth.ws for n points: dL/df_h as FP32 SoA [L*F][n]. */
-size_t dash_smooth_workspace_size(const dash_layout* layout, int64_t n);
 
 /* ----------------------------------------------------------- utilities -- */
 
@@ -169,9 +162,19 @@ int dash_version(void);
  * gathers are paired too).  A batched plan keeps the value current when it
  * was created.  (The F = 2 Eq. 11 kernel and the encoder-only kernels always
  * use lane pairs.)
+ * DASH_OPT_GRAD_REPLICAS (0..64, default 8): k, the number of replicas of
+ * the FP32 gradients of each leading dense level of at most 2^17 entries
+ * (levels 0 and 1 at the paper shape) that dash_deform_mlp_bwd uses when it
+ * is given a workspace (see there); 0 or 1 = none.  It sizes
+ * dash_deform_bwd_workspace_size, so set it before sizing.
  * dash_get_option returns the current value (negative status for an
  * unknown option). */
-enum dash_option { DASH_OPT_FWD_FORM = 1, DASH_OPT_BWD_FORM = 2, DASH_OPT_ACCESS_FORM = 3 };
+enum dash_option {
+  DASH_OPT_FWD_FORM = 1,
+  DASH_OPT_BWD_FORM = 2,
+  DASH_OPT_ACCESS_FORM = 3,
+  DASH_OPT_GRAD_REPLICAS = 4
+};
 int dash_set_option(int option, int value);
 int dash_get_option(int option);
 
@@ -311,20 +314,34 @@ int dash_deform_apply_bwd(const dash_points* pts, int d_out, const float* dattrs
  * With smooth != NULL and lambda_r != 0 also adds the Eq. 11 term,
  * re-encoding p, p + e_s and p + e_t (for F = 2 with a forward state in a
  * second kernel launched right after, on the same stream; otherwise inside
- * the backward kernel).  In the two-kernel case with smooth->ws set, the
- * backward kernel writes dL/df_h to ws instead of scattering it, and the
- * Eq. 11 kernel adds it to the Eq. 11 gradient at p's corners, so each of
- * those corners takes one reduction instead of two (DASH_ERR_WORKSPACE if
- * ws_bytes is too small); ws is ignored otherwise.  Shapes as the forward.
+ * the backward kernel).  Shapes as the forward.
  * coord_grad (may be NULL): SoA [4][pts->n] FP32 receives d loss / d(x, y,
  * z, t) of each compact point as dash_hash4d_coord_grad defines it (the
  * scatter step also gathers the corner entries); not available together with
- * the Eq. 11 term (DASH_ERR_UNSUPPORTED). */
+ * the Eq. 11 term (DASH_ERR_UNSUPPORTED).
+ * ws (device, 16-byte aligned, may be NULL) of ws_bytes >=
+ * dash_deform_bwd_workspace_size bytes (DASH_ERR_WORKSPACE otherwise)
+ * enables, for F = 2 with a forward state and lane-paired accesses:
+ *  - replicas of the coarsest dense levels' gradients
+ *    (DASH_OPT_GRAD_REPLICAS = k):
+ *    the lane-paired scatter and the Eq. 11 kernel reduce from CTA b into
+ *    replica b % k, which the call zeroes first and adds into table_grad
+ *    last (a memset and one more kernel on the stream);
+ *  - with the Eq. 11 term: the backward kernel writes dL/df_h to ws instead
+ *    of scattering it, and the Eq. 11 kernel adds it to the Eq. 11 gradient
+ *    at p's corners (one reduction per corner instead of two).
+ * Without ws, or on other paths, the gradients are reduced straight into
+ * table_grad.  The results agree up to the order of the additions. */
 int dash_deform_mlp_bwd(const dash_layout* layout, const dash_points* pts,
                         const void* table, int table_dtype, const dash_mlp* mlp,
                         const float* ddelta, const void* fwd_state, float* table_grad,
                         float* mlp_grad, const dash_smooth* smooth, float* coord_grad,
-                        void* stream);
+                        void* ws, size_t ws_bytes, void* stream);
+/* Bytes of workspace dash_deform_mlp_bwd can use for n points: the
+ * gradient replicas (with the current DASH_OPT_GRAD_REPLICAS) plus, when
+ * smooth has lambda_r != 0, dL/df_h as FP32 SoA [L*F][n]; 0 if neither
+ * applies (F != 2). */
+size_t dash_deform_bwd_workspace_size(const dash_layout* layout, int64_t n, const dash_smooth* smooth);
 
 /* ------------- decomposition producing the mask (Sec. 4.1, Eqs. 3-5) ---- */
 
@@ -483,7 +500,10 @@ typedef struct dash_batch_scene {
  * with_backward = 1 adds, after the forward, the fused backward (a9-a10:
  * decoder gradients, lane-paired table-gradient scatter) of every (scene,
  * timestamp, tile) in a second persistent kernel of the same graph; F = 2
- * and L*F <= 32 only. */
+ * and L*F <= 32 only.  The plan then also owns replicas of each scene's
+ * coarsest dense levels' gradients (DASH_OPT_GRAD_REPLICAS when it is
+ * created; see dash_deform_mlp_bwd), cleared before the backward kernel
+ * and added into table_grad after it, inside the graph. */
 typedef struct dash_batch_desc {
   const dash_layout* layout;
   int32_t table_dtype;

@@ -49,6 +49,7 @@ struct SceneDev {
   uint8_t* state;
   float* table_grad;
   float* mlp_grad;
+  float* rep_base;  // this scene's gradient replicas (see Replicas), or NULL
 };
 
 struct BatchArgs {
@@ -273,6 +274,7 @@ struct BatchBwdArgs {
   const SceneDev* scenes;
   const long long* counts;
   unsigned int* flags;
+  Replicas rep;  // replica layout; each scene's base is SceneDev::rep_base
   uint32_t off_w2, off_w3, off_f, off_h1, off_x, off_g3, off_ring, off_bar, off_tab;
 };
 
@@ -383,8 +385,11 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) batch_bwd_kernel(const __g
       }
       if (*abort_flag) break;
       const long long row_a = row - (r & 1);  // the pair's even row; both lanes agree on row_a < cnt
+      Replicas rep = a.rep;
+      rep.base = sc.rep_base;
+      if (rep.base == nullptr) rep.levels = 0;
       if (row_a < cnt)
-        bwdk::scatter_levels_paired(a.g, sc.table_grad, p, ring + (size_t)s * stage_floats + (r & ~1),
+        bwdk::scatter_levels_paired(a.g, sc.table_grad, rep, p, ring + (size_t)s * stage_floats + (r & ~1),
                                     (uint32_t)(r & 1), true, row_a + 1 < cnt, 3u << (r & 30));
       tc::mbar_arrive(tc::smem_addr(&empty[s]));
     }
@@ -525,6 +530,8 @@ struct dash_batch_plan {
   dash::fused::BatchBwdArgs bargs;
   dash::fused::SceneDev* d_scenes;
   long long* d_counts;
+  float* d_rep;      // gradient replicas of every scene (plans with a backward), or NULL
+  size_t rep_bytes;  // per scene
   std::vector<dash::fused::SceneDev> h_scenes;  // host copy (gradient pointers for the autotuner)
   long long grad_floats;                         // table entries * F per scene
   long long param_floats;                        // decoder parameters per scene
@@ -565,7 +572,17 @@ int capture(dash_batch_plan* p) {
   int rc = cuda_status(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
   if (rc == DASH_OK) {
     int lr = fused::launch_batch(p->form, p->table_dtype, p->args, cs);
-    if (lr == DASH_OK && p->with_bwd) lr = fused::launch_batch_bwd(p->bform, p->table_dtype, p->bargs, cs);
+    if (lr == DASH_OK && p->with_bwd) {
+      const Replicas& rep = p->bargs.rep;
+      if (p->d_rep != nullptr)
+        lr = cuda_status(cudaMemsetAsync(p->d_rep, 0, p->rep_bytes * p->h_scenes.size(), cs), "cudaMemsetAsync");
+      if (lr == DASH_OK) lr = fused::launch_batch_bwd(p->bform, p->table_dtype, p->bargs, cs);
+      for (size_t s = 0; lr == DASH_OK && p->d_rep != nullptr && s < p->h_scenes.size(); ++s) {
+        Replicas r = rep;
+        r.base = p->h_scenes[s].rep_base;
+        lr = replica_sum(p->bargs.g, r, p->h_scenes[s].table_grad, cs);
+      }
+    }
     const int er = cuda_status(cudaStreamEndCapture(cs, &p->graph), "cudaStreamEndCapture");
     rc = lr != DASH_OK ? lr : er;
   }
@@ -616,7 +633,7 @@ int dash_batch_plan_create(const dash_batch_desc* desc, dash_batch_plan** out) {
     if ((reinterpret_cast<uintptr_t>(sc.table) & 15u) != 0)
       return fail(DASH_ERR_INVALID_ARG, "scene %d: table must be 16-byte aligned", s);
     host[s] = fused::SceneDev{sc.table, sc.params, sc.x, sc.y, sc.z, sc.timestamps, sc.delta_out, sc.n, sc.K, 0,
-                              nullptr, nullptr, nullptr, nullptr};
+                              nullptr, nullptr, nullptr, nullptr, nullptr};
     if (with_bwd) {
       if (sc.ddelta == nullptr || sc.fwd_state == nullptr || sc.table_grad == nullptr || sc.mlp_grad == nullptr)
         return fail(DASH_ERR_INVALID_ARG, "scene %d: a backward pointer is NULL", s);
@@ -635,7 +652,6 @@ int dash_batch_plan_create(const dash_batch_desc* desc, dash_batch_plan** out) {
   p->device = 0;
   cudaGetDevice(&p->device);
   p->table_dtype = desc->table_dtype;
-  p->h_scenes.assign(host, host + desc->n_scenes);
   p->grad_floats = desc->layout->offset[a.g.L] * a.g.F;
   p->param_floats = (long long)fused::kHidden * D + fused::kHidden + (long long)fused::kHidden * fused::kHidden +
                     fused::kHidden + (long long)a.O * fused::kHidden + a.O;
@@ -646,7 +662,23 @@ int dash_batch_plan_create(const dash_batch_desc* desc, dash_batch_plan** out) {
   p->d_counts = nullptr;
   p->graph = nullptr;
   p->exec = nullptr;
-  int rc = cuda_status(cudaMalloc(&p->d_scenes, sizeof(fused::SceneDev) * desc->n_scenes), "cudaMalloc");
+  p->d_rep = nullptr;
+  p->rep_bytes = 0;
+  int rc = DASH_OK;
+  // replicas of the coarsest dense levels' gradients, one set per scene
+  // (the backward's scatter is lane-paired)
+  Replicas rep;
+  memset(&rep, 0, sizeof(rep));
+  if (with_bwd) {
+    rep = replica_plan(desc->layout, g_opt_grad_replicas, &p->rep_bytes);
+    if (rep.levels > 0) {
+      rc = cuda_status(cudaMalloc(&p->d_rep, p->rep_bytes * desc->n_scenes), "cudaMalloc");
+      for (int s = 0; rc == DASH_OK && s < desc->n_scenes; ++s)
+        host[s].rep_base = reinterpret_cast<float*>(reinterpret_cast<char*>(p->d_rep) + p->rep_bytes * s);
+    }
+  }
+  p->h_scenes.assign(host, host + desc->n_scenes);
+  if (rc == DASH_OK) rc = cuda_status(cudaMalloc(&p->d_scenes, sizeof(fused::SceneDev) * desc->n_scenes), "cudaMalloc");
   if (rc == DASH_OK) rc = cuda_status(cudaMalloc(&p->d_counts, sizeof(long long) * desc->n_scenes), "cudaMalloc");
   if (rc == DASH_OK)
     rc = cuda_status(cudaMemcpy(p->d_scenes, host, sizeof(fused::SceneDev) * desc->n_scenes, cudaMemcpyHostToDevice),
@@ -665,6 +697,7 @@ int dash_batch_plan_create(const dash_batch_desc* desc, dash_batch_plan** out) {
     b.scenes = a.scenes;
     b.counts = a.counts;
     b.flags = a.flags;
+    b.rep = rep;
     p->bargs = b;
     char sig[512];
     cudaDeviceProp prop;
@@ -697,6 +730,7 @@ int dash_batch_plan_destroy(dash_batch_plan* plan) {
   if (plan == nullptr) return DASH_OK;
   destroy_graph(plan);
   if (plan->d_scenes != nullptr) cudaFree(plan->d_scenes);
+  if (plan->d_rep != nullptr) cudaFree(plan->d_rep);
   if (plan->d_counts != nullptr) cudaFree(plan->d_counts);
   delete plan;
   return DASH_OK;

@@ -14,6 +14,7 @@ static thread_local char g_last_error[512] = "";
 int g_opt_fwd_form = 0;
 int g_opt_bwd_form = 0;
 int g_opt_access_form = 0;
+int g_opt_grad_replicas = 8;
 
 void set_error(const char* fmt, ...) {
   va_list ap;
@@ -115,7 +116,7 @@ const char* dash_status_string(int s) {
 
 const char* dash_last_error(void) { return dash::g_last_error; }
 
-int dash_version(void) { return 101; }
+int dash_version(void) { return 102; }
 
 int dash_set_option(int option, int value) {
   switch (option) {
@@ -134,6 +135,11 @@ int dash_set_option(int option, int value) {
         return dash::fail(DASH_ERR_INVALID_ARG, "access form %d not in {0, 1}", value);
       dash::g_opt_access_form = value;
       return DASH_OK;
+    case DASH_OPT_GRAD_REPLICAS:
+      if (value < 0 || value > 64)
+        return dash::fail(DASH_ERR_INVALID_ARG, "gradient replicas %d not in [0, 64]", value);
+      dash::g_opt_grad_replicas = value;
+      return DASH_OK;
     default: return dash::fail(DASH_ERR_INVALID_ARG, "unknown option %d", option);
   }
 }
@@ -143,6 +149,7 @@ int dash_get_option(int option) {
     case DASH_OPT_FWD_FORM: return dash::g_opt_fwd_form;
     case DASH_OPT_BWD_FORM: return dash::g_opt_bwd_form;
     case DASH_OPT_ACCESS_FORM: return dash::g_opt_access_form;
+    case DASH_OPT_GRAD_REPLICAS: return dash::g_opt_grad_replicas;
     default: return dash::fail(DASH_ERR_INVALID_ARG, "unknown option %d", option);
   }
 }

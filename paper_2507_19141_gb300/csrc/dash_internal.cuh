@@ -29,6 +29,7 @@ int sm_count();
 extern int g_opt_fwd_form;
 extern int g_opt_bwd_form;
 extern int g_opt_access_form;
+extern int g_opt_grad_replicas;
 
 // ------------------------------------------------ kernel-side geometry ----
 // Level layout in the form the kernels read it (by-value kernel argument).
@@ -574,9 +575,38 @@ __device__ __forceinline__ void scatter2_pairs(float* __restrict__ base, const u
   }
 }
 
+// Replicas of the coarsest dense levels' FP32 gradients (F = 2).  Those
+// levels are small and every Gaussian reduces into 16 of their entries, so
+// their entries take hundreds of reductions each per call, which the L2
+// serialises; CTA b reduces into replica b % k of its level instead, and
+// replica_sum adds the k replicas into the gradient buffer afterwards.
+constexpr int kMaxRepLevels = 4;
+struct Replicas {
+  float* base;                      // NULL / levels = 0: no replicas
+  int levels, k;                    // levels 0 .. levels-1, k replicas each
+  long long off[kMaxRepLevels];     // floats from base to replica 0 of level l
+  long long stride[kMaxRepLevels];  // floats between consecutive replicas of level l
+  long long size[kMaxRepLevels];    // entries of level l
+  // where CTA blockIdx.x reduces level l's gradients ([entries][2] FP32)
+  __device__ __forceinline__ float* level_base(float* grad, const Geom& g, int l) const {
+    if (l < levels) return base + off[l] + (long long)(blockIdx.x % (unsigned)k) * stride[l];
+    return grad + g.offset[l] * 2;
+  }
+};
+
+// Host: the replica layout for k replicas of the leading dense levels of at
+// most 2^17 entries (none for F != 2, k < 2 or no such level) and its size
+// in bytes; base unset.
+Replicas replica_plan(const dash_layout* layout, int k, size_t* bytes);
+// Zeroes the replicas (before the kernels that reduce into them).
+int replica_clear(const Replicas& rp, size_t bytes, cudaStream_t st);
+// grad[level l] += sum of the k replicas of level l, for every replicated level.
+int replica_sum(const Geom& g, const Replicas& rp, float* grad, cudaStream_t st);
+
 // Backward of the Eq. 11 smoothness term for F = 2 (smooth.cu): adds its
-// table gradient into table_grad and lambda_r L_r into sm->loss_out.
+// table gradient into table_grad (or, for the replicated levels, into the
+// replicas) and lambda_r L_r into sm->loss_out.
 int launch_smooth2(const Geom& g, const Pts& pts, const void* table, int table_dtype, float* table_grad,
-                   const dash_smooth* sm, const float* dfh, long long dfh_ld, cudaStream_t st);
+                   const dash_smooth* sm, const float* dfh, long long dfh_ld, const Replicas& rp, cudaStream_t st);
 
 }  // namespace dash

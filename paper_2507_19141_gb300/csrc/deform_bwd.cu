@@ -62,6 +62,7 @@ struct BwdArgs {
   unsigned int* flags;
   int paired;  // F = 2 scatter by lane pairs (no Eq. 11 term, no coordinate gradient)
   float* dfh_out;  // optional SoA [D][n_cap]: dL/df_h stored instead of scattered
+  Replicas rep;    // the paired scatter's dense levels go to replicas
   uint32_t off_w2, off_w3, off_f, off_h1, off_x, off_g3, off_ring, off_bar;
 };
 
@@ -632,7 +633,7 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_bwd_ws_kernel(const
           const unsigned int pm = 3u << (r & 30);
           if (row_a < n) {
             if (a.coord_grad == nullptr) {
-              scatter_levels_paired(a.g, a.table_grad, p, stage + (r & ~1), xb, true, row_a + 1 < n, pm);
+              scatter_levels_paired(a.g, a.table_grad, a.rep, p, stage + (r & ~1), xb, true, row_a + 1 < n, pm);
             } else {
               const float4 cg = scatter_coord_levels_paired<TT>(a.g, table, a.table_grad, p, stage + (r & ~1), xb,
                                                                 row_a + 1 < n, pm);
@@ -791,6 +792,21 @@ int dispatch(int F, bool ws, BwdArgs& a, cudaStream_t st) {
 
 int check_fused_mlp(const dash_mlp* mlp, int D);
 
+// The backward's workspace: the gradient replicas, then (with the Eq. 11
+// term) dL/df_h as FP32 SoA [L*F][n], 256-byte aligned.
+struct BwdWorkspace {
+  Replicas rep;
+  size_t rep_bytes, dfh_off, total;
+};
+
+BwdWorkspace bwd_workspace(const dash_layout* layout, long long n, bool with_dfh) {
+  BwdWorkspace w;
+  w.rep = replica_plan(layout, g_opt_grad_replicas, &w.rep_bytes);
+  w.dfh_off = (w.rep_bytes + 255) & ~(size_t)255;
+  w.total = with_dfh ? w.dfh_off + (size_t)layout->L * layout->F * (size_t)n * sizeof(float) : w.rep_bytes;
+  return w;
+}
+
 unsigned int* bwd_flags_ptr() {
   void* p = nullptr;
   if (cudaGetSymbolAddress(&p, g_bwd_flags) != cudaSuccess) return nullptr;
@@ -803,7 +819,7 @@ unsigned int* bwd_flags_ptr() {
 extern "C" int dash_deform_mlp_bwd(const dash_layout* layout, const dash_points* pts, const void* table,
                                    int table_dtype, const dash_mlp* mlp, const float* ddelta, const void* fwd_state,
                                    float* table_grad, float* mlp_grad, const dash_smooth* smooth,
-                                   float* coord_grad, void* stream) {
+                                   float* coord_grad, void* ws_buf, size_t ws_bytes, void* stream) {
   using namespace dash;
   using namespace dash::fused;
   BwdArgs a;
@@ -852,32 +868,46 @@ extern "C" int dash_deform_mlp_bwd(const dash_layout* layout, const dash_points*
   // kernel after the df_h scatter (both add into table_grad)
   const bool smooth_apart = ws && a.g.F == 2 && a.lambda_r != 0.0f;
   BwdArgs b = a;
-  const float* dfh = nullptr;
   if (smooth_apart) {
     b.lambda_r = 0.0f;
     b.loss_out = nullptr;
     b.paired = g_opt_access_form == 0 ? 1 : 0;
-    if (smooth->ws != nullptr) {
-      // dL/df_h goes through the workspace and is scattered with the Eq. 11 gradient
-      if (smooth->ws_bytes < dash_smooth_workspace_size(layout, a.n_cap))
-        return fail(DASH_ERR_WORKSPACE, "smooth workspace %zu B < %zu B", smooth->ws_bytes,
-                    dash_smooth_workspace_size(layout, a.n_cap));
-      if ((reinterpret_cast<uintptr_t>(smooth->ws) & 15u) != 0)
-        return fail(DASH_ERR_INVALID_ARG, "smooth workspace must be 16-byte aligned");
-      b.dfh_out = static_cast<float*>(smooth->ws);
+  }
+  // the workspace: replicas of the dense levels' gradients, and dL/df_h for
+  // the Eq. 11 kernel; used by the lane-paired F = 2 paths only
+  const float* dfh = nullptr;
+  Replicas rep;
+  memset(&rep, 0, sizeof(rep));
+  size_t rep_bytes = 0;
+  if (ws_buf != nullptr && ws && a.g.F == 2 && g_opt_access_form == 0 && (smooth_apart || coord_grad == nullptr)) {
+    const BwdWorkspace wl = bwd_workspace(layout, a.n_cap, smooth_apart);
+    if (ws_bytes < wl.total)
+      return fail(DASH_ERR_WORKSPACE, "backward workspace %zu B < %zu B", ws_bytes, wl.total);
+    if ((reinterpret_cast<uintptr_t>(ws_buf) & 15u) != 0)
+      return fail(DASH_ERR_INVALID_ARG, "backward workspace must be 16-byte aligned");
+    rep = wl.rep;
+    rep.base = static_cast<float*>(ws_buf);
+    rep_bytes = wl.rep_bytes;
+    if (smooth_apart) {
+      b.dfh_out = reinterpret_cast<float*>(static_cast<char*>(ws_buf) + wl.dfh_off);
       dfh = b.dfh_out;
+    } else {
+      b.rep = rep;
     }
   }
+  if (int r = replica_clear(rep, rep_bytes, st)) return r;
   int s;
   if (dfh != nullptr)  // the decoder alone, dL/df_h stored for the Eq. 11 kernel
     s = table_dtype == DASH_F32 ? launch_ws<float, 2, 0, 0>(b, st) : launch_ws<__half, 2, 0, 0>(b, st);
   else
     s = table_dtype == DASH_F32 ? dispatch<float>(a.g.F, ws, b, st) : dispatch<__half>(a.g.F, ws, b, st);
-  if (s != DASH_OK || !smooth_apart) return s;
-  return launch_smooth2(a.g, a.pts, table, table_dtype, table_grad, smooth, dfh, a.n_cap, st);
+  if (s == DASH_OK && smooth_apart)
+    s = launch_smooth2(a.g, a.pts, table, table_dtype, table_grad, smooth, dfh, a.n_cap, rep, st);
+  if (s != DASH_OK) return s;
+  return replica_sum(a.g, rep, table_grad, st);
 }
 
-extern "C" size_t dash_smooth_workspace_size(const dash_layout* layout, int64_t n) {
-  if (layout == nullptr || n <= 0) return 0;
-  return (size_t)layout->L * (size_t)layout->F * (size_t)n * sizeof(float);
+extern "C" size_t dash_deform_bwd_workspace_size(const dash_layout* layout, int64_t n, const dash_smooth* smooth) {
+  if (layout == nullptr || layout->F != 2 || n < 0) return 0;
+  return dash::fused::bwd_workspace(layout, n, smooth != nullptr && smooth->lambda_r != 0.0f).total;
 }

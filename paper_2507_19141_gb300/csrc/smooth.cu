@@ -36,6 +36,7 @@ struct SmoothArgs {
   float* loss_out;
   const float* dfh;  // optional SoA [L*2][dfh_ld]
   long long dfh_ld;
+  Replicas rep;  // the dense levels' reductions go to replicas
 };
 
 __device__ __forceinline__ float4 perturbed(float4 p, float ex, float ey, float ez, float et) {
@@ -76,7 +77,7 @@ __global__ void __launch_bounds__(kThreads, 2) smooth_bwd_kernel(const __grid_co
   float loss = 0.0f;
   for (int l = 0; has_a && l < a.g.L; ++l) {
     const TT* base = table + a.g.offset[l] * 2;
-    float* gbase = a.grad + a.g.offset[l] * 2;
+    float* gbase = a.rep.level_base(a.grad, a.g, l);
     float h0 = 0.0f, h1 = 0.0f;  // this lane's Gaussian's dL/df_h at level l
     if (a.dfh != nullptr && i < n) {
       h0 = __ldg(a.dfh + (2 * l) * a.dfh_ld + i);
@@ -190,7 +191,8 @@ __global__ void __launch_bounds__(kThreads, 2) smooth_bwd_kernel(const __grid_co
 }  // namespace
 
 int launch_smooth2(const Geom& g, const Pts& pts, const void* table, int table_dtype, float* table_grad,
-                   const dash_smooth* sm, const float* dfh, long long dfh_ld, cudaStream_t st) {
+                   const dash_smooth* sm, const float* dfh, long long dfh_ld, const Replicas& rp,
+                   cudaStream_t st) {
   SmoothArgs a;
   a.g = g;
   a.pts = pts;
@@ -202,6 +204,7 @@ int launch_smooth2(const Geom& g, const Pts& pts, const void* table, int table_d
   a.loss_out = sm->loss_out;
   a.dfh = dfh;
   a.dfh_ld = dfh_ld;
+  a.rep = rp;
   const unsigned grid = (unsigned)((pts.n + kThreads - 1) / kThreads);
   // two CTAs per SM (128 registers a thread): capping the registers lower to
   // fit more CTAs spills and was measured slower

@@ -77,7 +77,7 @@ class dash_apply(ctypes.Structure):
 
 class dash_smooth(ctypes.Structure):
     _fields_ = [("lambda_r", ctypes.c_float), ("eps_s", ctypes.c_float * 3), ("eps_t", ctypes.c_float),
-                ("loss_out", ctypes.c_void_p), ("ws", ctypes.c_void_p), ("ws_bytes", ctypes.c_size_t)]
+                ("loss_out", ctypes.c_void_p)]
 
 
 class dash_camera(ctypes.Structure):
@@ -137,10 +137,10 @@ _SIGS = {
     "dash_raster_bwd": ([_P, _P, _P, _P, _SZ, _I64, _P, _P], _I),
     "dash_hash4d_collision_stats": ([_P, _P, _P, _P, _SZ, _P], _I),
     "dash_deform_state_size": ([_P], _SZ),
-    "dash_smooth_workspace_size": ([_P, _I64], _SZ),
+    "dash_deform_bwd_workspace_size": ([_P, _I64, _P], _SZ),
     "dash_deform_apply_bwd": ([_P, _I, _P, _I64, _P, _P], _I),
     "dash_deform_mlp_fwd": ([_P, _P, _P, _I, _P, _P, _P, _P, _P], _I),
-    "dash_deform_mlp_bwd": ([_P, _P, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P], _I),
+    "dash_deform_mlp_bwd": ([_P, _P, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P], _I),
     "dash_batch_plan_create": ([_P, _P], _I),
     "dash_batch_counts": ([_P], ctypes.c_void_p),
     "dash_batch_run": ([_P, _P], _I),
@@ -200,6 +200,7 @@ def dash_last_error() -> str:
 OPT_FWD_FORM = 1
 OPT_BWD_FORM = 2
 OPT_ACCESS_FORM = 3
+OPT_GRAD_REPLICAS = 4
 
 
 def dash_set_option(option: int, value: int) -> None:
@@ -422,30 +423,37 @@ def dash_deform_apply_bwd(pts: Points, dattrs: torch.Tensor, ddelta=None):
     return ddelta
 
 
-def dash_smooth_workspace_size(layout, n) -> int:
-    return int(_lib.dash_smooth_workspace_size(ctypes.byref(layout), int(n)))
+def _smooth_struct(smooth):
+    if smooth is None:
+        return None
+    lam, es, et, lo = smooth
+    return dash_smooth(float(lam), (ctypes.c_float * 3)(*es), float(et), None if lo is None else lo.data_ptr())
+
+
+def dash_deform_bwd_workspace_size(layout, n, smooth=None) -> int:
+    """smooth: the (lambda_r, eps_s, eps_t, loss_out) tuple the backward will get, or None."""
+    sm = _smooth_struct(smooth)
+    return int(_lib.dash_deform_bwd_workspace_size(ctypes.byref(layout), int(n),
+                                                   None if sm is None else ctypes.byref(sm)))
 
 
 def dash_deform_mlp_bwd(layout, pts, table, mlp: Mlp, ddelta, table_grad, mlp_grad, fwd_state=None, smooth=None,
-                        coord_grad=None):
-    """smooth: optional (lambda_r, (eps_x, eps_y, eps_z), eps_t, loss_out float32 [1] tensor or None[, ws]).
-    ws: a uint8 CUDA tensor of dash_smooth_workspace_size bytes, None to allocate one (when a
-    forward state is given and F = 2, where it is used), or False for the form without it.
-    coord_grad: optional float32 [4][n] CUDA tensor receiving d loss / d(x, y, z, t)."""
-    sm = None
-    if smooth is not None:
-        lam, es, et, lo = smooth[:4]
-        ws = smooth[4] if len(smooth) > 4 else None
-        if ws is None and fwd_state is not None and layout.F == 2 and float(lam) != 0.0:
-            ws = torch.empty(dash_smooth_workspace_size(layout, pts.n), dtype=torch.uint8, device=table.device)
-        if ws is False:
-            ws = None
-        sm = dash_smooth(float(lam), (ctypes.c_float * 3)(*es), float(et), None if lo is None else lo.data_ptr(),
-                         None if ws is None else ws.data_ptr(), 0 if ws is None else ws.numel() * ws.element_size())
+                        coord_grad=None, ws=None):
+    """smooth: optional (lambda_r, (eps_x, eps_y, eps_z), eps_t, loss_out float32 [1] tensor or None).
+    coord_grad: optional float32 [4][n] CUDA tensor receiving d loss / d(x, y, z, t).
+    ws: a uint8 CUDA tensor of dash_deform_bwd_workspace_size bytes (gradient replicas and, with
+    the Eq. 11 term, the dL/df_h hand-over), None to allocate one where it is used (a forward
+    state given, F = 2), or False for the forms without it."""
+    sm = _smooth_struct(smooth)
+    if ws is None and fwd_state is not None and layout.F == 2:
+        size = dash_deform_bwd_workspace_size(layout, pts.n, smooth)
+        ws = torch.empty(size, dtype=torch.uint8, device=table.device) if size > 0 else False
+    if ws is False:
+        ws = None
     _check(_lib.dash_deform_mlp_bwd(ctypes.byref(layout), ctypes.byref(pts.c), _ptr(table), _DTYPE_CODE[table.dtype],
                                     ctypes.byref(mlp.c), _ptr(ddelta), _ptr(fwd_state), _ptr(table_grad),
                                     _ptr(mlp_grad), None if sm is None else ctypes.byref(sm), _ptr(coord_grad),
-                                    _stream()),
+                                    _ptr(ws), 0 if ws is None else ws.numel() * ws.element_size(), _stream()),
            "dash_deform_mlp_bwd")
 
 

@@ -92,3 +92,28 @@ def test_host_layout3_equals_oracle(cfg):
     ref = oracle.layout3(L, F, lt, a, b).as_dict()
     got["res_t"] = ref["res_t"]  # unused by a 3-D layout
     assert got == ref
+
+
+def test_replica_workspace_size():
+    """Replicas cover the leading dense levels of at most 2^17 entries
+    (levels 0 and 1 of the three dense ones at the paper shape): k copies of
+    each level's FP32 [entries][2] rows, 256-byte aligned; the Eq. 11
+    hand-over adds L * F * n floats."""
+    from paper_2507_19141_gb300 import dash, synth
+    lay = dash.layout_from(synth.PAPER_GRID)
+    old = dash.dash_get_option(dash.OPT_GRAD_REPLICAS)
+    try:
+        dash.dash_set_option(dash.OPT_GRAD_REPLICAS, 8)
+        rows = [-(-int(lay.size[l]) * 2 // 64) * 64 for l in range(2)]
+        assert all(bool(lay.dense[l]) for l in range(3)) and not lay.dense[3]
+        assert lay.size[1] <= 1 << 17 < lay.size[2]
+        assert dash.dash_deform_bwd_workspace_size(lay, 1000) == 8 * 4 * sum(rows)
+        sm = (1.0, (0.0, 0.0, 0.0), 0.0, None)
+        rep = 8 * 4 * sum(rows)
+        assert dash.dash_deform_bwd_workspace_size(lay, 1000, sm) == -(-rep // 256) * 256 + 32 * 1000 * 4
+        dash.dash_set_option(dash.OPT_GRAD_REPLICAS, 0)
+        assert dash.dash_deform_bwd_workspace_size(lay, 1000) == 0
+        with pytest.raises(dash.DashError):
+            dash.dash_set_option(dash.OPT_GRAD_REPLICAS, 65)
+    finally:
+        dash.dash_set_option(dash.OPT_GRAD_REPLICAS, old)

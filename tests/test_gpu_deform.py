@@ -479,12 +479,16 @@ def test_fused_empty_is_a_no_op(dashlib, how):
 
 
 @pytest.mark.parametrize("tdtype", [np.float16, np.float32])
-def test_smoothness_workspace_form_agrees(dashlib, tdtype):
-    """Eq. 11 with and without the workspace hand-over of dL/df_h (the
-    default when a forward state is given): the same gradients up to the
+@pytest.mark.parametrize("smooth_on", [False, True])
+@pytest.mark.parametrize("replicas", [0, 7, 16])
+def test_backward_workspace_forms_agree(dashlib, tdtype, smooth_on, replicas):
+    """The backward with and without its workspace: the gradient replicas
+    of the dense levels (k = 0 / 7 / 16) and, with the Eq. 11 term, the
+    hand-over of dL/df_h to the Eq. 11 kernel.  Same gradients up to the
     order of the additions and the same loss, through an index list whose
     device count (2999) is below the capacity (4001, the workspace's row
-    stride); a workspace one byte short is refused."""
+    stride), into gradient buffers that already hold values; against the
+    oracle too; a workspace one byte short is refused."""
     grid, mlpc = synth.PAPER_GRID, synth.PAPER_MLP
     rng = np.random.default_rng(97)
     n_all, cap, live = 9000, 4001, 2999
@@ -494,6 +498,7 @@ def test_smoothness_workspace_form_agrees(dashlib, tdtype):
     table = synth.table_values(rng, g.total, grid.F, tdtype)
     params = synth.mlp_params(rng, mlpc)
     dd = to_dev(synth.upstream_grad(rng, mlpc.d_out, cap))
+    tg0 = rng.standard_normal((g.total, 2)).astype(np.float32)
     lay = dashlib.layout_from(grid)
     cnt = torch.tensor([live], dtype=torch.int64, device="cuda")
     pts = dashlib.Points(to_dev(x), to_dev(y), to_dev(z), to_dev(t), idx=to_dev(idx), n=cap, n_dev=cnt)
@@ -502,21 +507,39 @@ def test_smoothness_workspace_form_agrees(dashlib, tdtype):
     st = dashlib.deform_state(mlp, cap, "cuda")
     dashlib.dash_deform_mlp_fwd(lay, pts, tab, mlp, fwd_state=st)
     es, et = (1 / 2048, 1 / 2048, 1 / 2048), 1 / 300
-    out = []
-    for ws in (None, False):
-        tg = torch.zeros((g.total, 2), dtype=torch.float32, device="cuda")
-        pg = torch.zeros(mlpc.n_params, dtype=torch.float32, device="cuda")
-        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
-        dashlib.dash_deform_mlp_bwd(lay, pts, tab, mlp, dd, tg, pg, fwd_state=st, smooth=(0.8, es, et, loss, ws))
-        out.append((tg.cpu().numpy(), pg.cpu().numpy(), float(loss.item())))
-    (tg1, pg1, l1), (tg2, pg2, l2) = out
-    assert rel_err(tg1, tg2) < 1e-5 and rel_err(pg1, pg2) < 1e-6
-    assert abs(l1 - l2) <= 1e-6 * abs(l2)
-    opts = oracle.Points(x, y, z, t, idx=idx[:live])
-    rtg, _, rl = oracle.deform_bwd(g, opts, table.astype(np.float64), 64, 10, params.astype(np.float64),
-                                   dd[:, :live].cpu().numpy().astype(np.float64), 0.8, es, et)
-    assert rel_err(tg1, rtg) < 1e-2 and abs(l1 - rl) <= 1e-2 * abs(rl)
-    short = torch.empty(dashlib.dash_smooth_workspace_size(lay, cap) - 1, dtype=torch.uint8, device="cuda")
-    with pytest.raises(dashlib.DashError) as e:
-        dashlib.dash_deform_mlp_bwd(lay, pts, tab, mlp, dd, tg, pg, fwd_state=st, smooth=(0.8, es, et, None, short))
-    assert e.value.status == dashlib.ERR_WORKSPACE
+    lam = 0.8 if smooth_on else 0.0
+    old = dashlib.dash_get_option(dashlib.OPT_GRAD_REPLICAS)
+    dashlib.dash_set_option(dashlib.OPT_GRAD_REPLICAS, replicas)
+    try:
+        out = []
+        for use_ws in (True, False):
+            tg = to_dev(tg0)
+            pg = torch.zeros(mlpc.n_params, dtype=torch.float32, device="cuda")
+            loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+            sm = (lam, es, et, loss)
+            ws = None
+            if use_ws:
+                size = dashlib.dash_deform_bwd_workspace_size(lay, cap, sm)
+                assert size > 0 or (replicas < 2 and not smooth_on)
+                ws = torch.full((max(size, 1),), 255, dtype=torch.uint8, device="cuda")  # not zeroed
+            for _ in range(2):  # a second call adds the same gradients again
+                dashlib.dash_deform_mlp_bwd(lay, pts, tab, mlp, dd, tg, pg, fwd_state=st, smooth=sm,
+                                            ws=ws if use_ws else False)
+            out.append((tg.cpu().numpy() - tg0, pg.cpu().numpy(), float(loss.item())))
+        (tg1, pg1, l1), (tg2, pg2, l2) = out
+        assert rel_err(tg1, tg2) < 1e-5 and rel_err(pg1, pg2) < 1e-6
+        assert abs(l1 - l2) <= 1e-6 * max(abs(l2), 1e-30)
+        opts = oracle.Points(x, y, z, t, idx=idx[:live])
+        rtg, _, rl = oracle.deform_bwd(g, opts, table.astype(np.float64), 64, 10, params.astype(np.float64),
+                                       dd[:, :live].cpu().numpy().astype(np.float64), lam, es, et)
+        assert rel_err(tg1, 2 * rtg) < 1e-2 and abs(l1 - 2 * rl) <= 1e-2 * max(abs(rl), 1e-30)
+        size = dashlib.dash_deform_bwd_workspace_size(lay, cap, (lam, es, et, None))
+        if size > 0:
+            short = torch.empty(size - 1, dtype=torch.uint8, device="cuda")
+            with pytest.raises(dashlib.DashError) as e:
+                dashlib.dash_deform_mlp_bwd(lay, pts, tab, mlp, dd, tg, pg, fwd_state=st,
+                                            smooth=(lam, es, et, None), ws=short)
+            assert e.value.status == dashlib.ERR_WORKSPACE
+    finally:
+        dashlib.dash_set_option(dashlib.OPT_GRAD_REPLICAS, old)
+
