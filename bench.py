@@ -42,13 +42,13 @@ BWD_BYTES = 16 + 4 + 80 + 40 + 2048
 STEP_BYTES = 2 + 4 + FWD_BYTES + BWD_BYTES
 
 # DRAM bytes read + written per launch at 1M Gaussians from one ncu capture
-# (profiles/warp_specialised_kernels_1M.md), valid while the kernel's sources
+# (profiles/dram_traffic_fused_and_batched.md), valid while the kernel's sources
 # hash to the captured value; otherwise the benchmark reports no traffic.
 NCU_TRAFFIC = {
-    "bwd": {"bytes": (195.9 + 1.1) * 1e6, "n": 1_000_000, "sha256_16": "3277ecf08f5a6a58",
+    "bwd": {"bytes": (204.6 + 2.0) * 1e6, "n": 1_000_000, "sha256_16": "c75a347ba081a30f",
             "sources": ("deform_bwd.cu", "deform_bwd_common.cuh", "deform_common.cuh", "dash_internal.cuh",
-                        "tc_ptx.cuh")},
-    "fwd": {"bytes": (45.5 + 72.0) * 1e6, "n": 1_000_000, "sha256_16": "758ded77607693f1",
+                        "tc_ptx.cuh", "replicas.cu")},
+    "fwd": {"bytes": (45.5 + 70.6) * 1e6, "n": 1_000_000, "sha256_16": "f49d2416b37907e9",
             "sources": ("deform_fwd.cu", "deform_common.cuh", "dash_internal.cuh", "tc_ptx.cuh")},
 }
 
@@ -563,6 +563,7 @@ def run_extras(torch, wl, args, stream):
     res["scatter_fp16_rel_err_vs_fp32"] = float((g16.float() - g32).norm() / g32.norm())
     del g32, g16, dfeat
     res.update(run_morton(torch, args, stream))
+    res.update(run_one_frame(torch, args, stream))
     res.update(run_decomp(torch, wl, stream))
     res.update(run_wo_dec(torch, stream))
     res.update(run_render(torch, stream))
@@ -585,6 +586,27 @@ def run_morton(torch, args, stream):
     res["morton_gaussians_per_s"] = args.n_dyn / (res["morton_step_ms"] / 1e3)
     del wl
     torch.cuda.empty_cache()
+    return res
+
+
+def run_one_frame(torch, args, stream):
+    """The benchmark step with one timestamp for all Gaussians (t = 0.37
+    broadcast, as when a training step renders one frame), in input order
+    and in Z order."""
+    from paper_2507_19141_gb300 import dash
+    res = {}
+    for key, morton in (("one_frame", False), ("one_frame_morton", True)):
+        wl = Workload(seed=2, n_all=args.n_all, n_dyn=args.n_dyn, device=torch.device("cuda"), morton=morton)
+        wl.t1 = torch.full((1,), 0.37, dtype=torch.float32, device="cuda")
+        wl.pts = dash.Points(wl.x, wl.y, wl.z, wl.t1, idx=wl.idx, n=wl.n_all, n_dev=wl.count)
+        for _ in range(3):
+            wl.step()
+        res[f"{key}_step_ms"] = time_steps(torch, wl.step, 50, stream)
+        res[f"{key}_bwd_ms"] = time_steps(torch, wl.backward, 50, stream)
+        res[f"{key}_bwd_no_replicas_ms"] = time_steps(torch, lambda: wl.backward(None, False), 50, stream)
+        res[f"{key}_gaussians_per_s"] = args.n_dyn / (res[f"{key}_step_ms"] / 1e3)
+        del wl
+        torch.cuda.empty_cache()
     return res
 
 
