@@ -375,6 +375,7 @@ def run_ours(args):
     if rank == 0 and not args.no_extras:
         out["extras"] = run_extras(torch, wl, args, stream)
         out["cpu_baseline"] = cpu_baseline(args, wl)
+        out["cpu_baseline_all_cores"] = cpu_baseline_all_cores(out["cpu_baseline"]["value"])
     if rank == 0:
         print(json.dumps(out), flush=True)
     barrier()
@@ -936,6 +937,44 @@ def cpu_baseline(args, wl=None):
     return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{n} dynamic Gaussians of the same distribution, forward + backward, {dt:.1f} s, "
                       f"1 host thread of {os.cpu_count()} cores"}
+
+
+def _oracle_process(n, seed, barrier, queue):
+    """One host process of the all-cores oracle timing (spawned)."""
+    timer = OracleTimer()
+    timer.run(200, seed=seed + 10_000)
+    barrier.wait(timeout=300)
+    _, dt = timer.run(n, seed)
+    queue.put((n, dt))
+
+
+def cpu_baseline_all_cores(per_core_rate, seconds=5.0):
+    """The same oracle in one single-threaded process per host core, all
+    started together (spawned processes: the parent holds a CUDA context),
+    each on its own sample of about `seconds` of work; the rate is the
+    Gaussians of all samples over the slowest process's time."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    n = int(min(max(per_core_rate * seconds, 1000), 500_000))
+    ctx = mp.get_context("spawn")
+    barrier, queue = ctx.Barrier(cores), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_process, args=(n, 500 + i, barrier, queue), daemon=True)
+             for i in range(cores)]
+    for pr in procs:
+        pr.start()
+    try:
+        res = [queue.get(timeout=600) for _ in procs]
+    except Exception as e:  # a process that died: report, do not hang the benchmark
+        for pr in procs:
+            pr.terminate()
+        return {"unavailable": f"all-cores oracle timing failed: {type(e).__name__}"}
+    for pr in procs:
+        pr.join(timeout=60)
+    wall = max(dt for _, dt in res)
+    total = sum(k for k, _ in res)
+    return {"value": total / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} processes x {n} dynamic Gaussians of the same distribution, forward + backward, "
+                      f"{wall:.1f} s (one single-threaded oracle per host core)"}
 
 
 def run_reference(args):
