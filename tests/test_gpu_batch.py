@@ -223,3 +223,32 @@ def test_batched_backward_autotune_keeps_gradients(dashlib, tmp_path):
     plan.close()
     plan2.close()
     fwd_only.close()
+
+
+@pytest.mark.parametrize("k", [0, 5])
+def test_batched_backward_replica_counts_agree(dashlib, k):
+    """Batched plans created with k gradient replicas per scene (0 = none,
+    5 = an odd count) give the gradients of the default plan (8) up to the
+    order of the additions."""
+    grid, mlpc = synth.PAPER_GRID, synth.PAPER_MLP
+    counts, Ks = [7000, 2500], [2, 3]
+    _, scenes = _scenes(dashlib, grid, mlpc, counts, Ks, np.float16, 62)
+    lay = dashlib.layout_from(grid)
+    _with_backward(scenes, lay, mlpc.d_out, np.random.default_rng(63))
+    old = dashlib.dash_get_option(dashlib.OPT_GRAD_REPLICAS)
+    out = []
+    try:
+        for kk in (old, k):
+            dashlib.dash_set_option(dashlib.OPT_GRAD_REPLICAS, kk)
+            for sc in scenes:
+                sc["table_grad"].zero_()
+                sc["mlp_grad"].zero_()
+            plan = dashlib.BatchPlan(lay, scenes, backward=True)
+            plan.run()
+            torch.cuda.synchronize()
+            out.append([(sc["table_grad"].cpu().numpy(), sc["mlp_grad"].cpu().numpy()) for sc in scenes])
+            plan.close()
+    finally:
+        dashlib.dash_set_option(dashlib.OPT_GRAD_REPLICAS, old)
+    for (tg1, pg1), (tg2, pg2) in zip(*out):
+        assert rel_err(tg2, tg1) < 1e-5 and rel_err(pg2, pg1) < 1e-6
