@@ -47,7 +47,7 @@ STEP_BYTES = 2 + 4 + FWD_BYTES + BWD_BYTES
 NCU_TRAFFIC = {
     "bwd": {"bytes": (204.6 + 2.0) * 1e6, "n": 1_000_000, "sha256_16": "c75a347ba081a30f",
             "sources": ("deform_bwd.cu", "deform_bwd_common.cuh", "deform_common.cuh", "dash_internal.cuh",
-                        "tc_ptx.cuh", "replicas.cu")},
+                        "tc_ptx.cuh", "replicas.cu", "dash_host.cu")},
     "fwd": {"bytes": (45.5 + 70.6) * 1e6, "n": 1_000_000, "sha256_16": "f49d2416b37907e9",
             "sources": ("deform_fwd.cu", "deform_common.cuh", "dash_internal.cuh", "tc_ptx.cuh")},
 }

@@ -162,7 +162,7 @@ int dash_version(void);
  * gathers are paired too).  A batched plan keeps the value current when it
  * was created.  (The F = 2 Eq. 11 kernel and the encoder-only kernels always
  * use lane pairs.)
- * DASH_OPT_GRAD_REPLICAS (0..64, default 8): k, the number of replicas of
+ * DASH_OPT_GRAD_REPLICAS (0..64, default 16): k, the number of replicas of
  * the FP32 gradients of each leading dense level of at most 2^17 entries
  * (levels 0 and 1 at the paper shape) that dash_deform_mlp_bwd uses when it
  * is given a workspace (see there); 0 or 1 = none.  It sizes

@@ -14,7 +14,7 @@ static thread_local char g_last_error[512] = "";
 int g_opt_fwd_form = 0;
 int g_opt_bwd_form = 0;
 int g_opt_access_form = 0;
-int g_opt_grad_replicas = 8;
+int g_opt_grad_replicas = 16;
 
 void set_error(const char* fmt, ...) {
   va_list ap;
