@@ -578,25 +578,26 @@ __device__ __forceinline__ void scatter2_pairs(float* __restrict__ base, const u
 // Replicas of the coarsest dense levels' FP32 gradients (F = 2).  Those
 // levels are small and every Gaussian reduces into 16 of their entries, so
 // their entries take hundreds of reductions each per call, which the L2
-// serialises; CTA b reduces into replica b % k of its level instead, and
-// replica_sum adds the k replicas into the gradient buffer afterwards.
+// serialises; CTA b reduces into replica b % k[l] of level l instead, and
+// replica_sum adds the replicas into the gradient buffer afterwards.
 constexpr int kMaxRepLevels = 4;
 struct Replicas {
   float* base;                      // NULL / levels = 0: no replicas
-  int levels, k;                    // levels 0 .. levels-1, k replicas each
+  int levels;                       // levels 0 .. levels-1 are replicated
+  int k[kMaxRepLevels];             // replicas of level l
   long long off[kMaxRepLevels];     // floats from base to replica 0 of level l
   long long stride[kMaxRepLevels];  // floats between consecutive replicas of level l
   long long size[kMaxRepLevels];    // entries of level l
   // where CTA blockIdx.x reduces level l's gradients ([entries][2] FP32)
   __device__ __forceinline__ float* level_base(float* grad, const Geom& g, int l) const {
-    if (l < levels) return base + off[l] + (long long)(blockIdx.x % (unsigned)k) * stride[l];
+    if (l < levels) return base + off[l] + (long long)(blockIdx.x % (unsigned)k[l]) * stride[l];
     return grad + g.offset[l] * 2;
   }
 };
 
-// Host: the replica layout for k replicas of the leading dense levels of at
-// most 2^17 entries (none for F != 2, k < 2 or no such level) and its size
-// in bytes; base unset.
+// Host: the replica layout for the leading dense levels — k replicas of
+// each level of at most 2^17 entries, k / 2 of each larger one of at most
+// 2^19 (none for F != 2 or k < 2) — and its size in bytes; base unset.
 Replicas replica_plan(const dash_layout* layout, int k, size_t* bytes);
 // Zeroes the replicas (before the kernels that reduce into them).
 int replica_clear(const Replicas& rp, size_t bytes, cudaStream_t st);

@@ -1,11 +1,11 @@
 // replicas.cu -- replicated gradient buffers for the dense levels (F = 2).
 //
-// The coarsest dense levels hold few entries (44k and 122k at the paper
-// shape), and every Gaussian reduces into 16 of them per level, so within a
-// backward call each of their entries takes hundreds of FP32 reductions; the
-// L2 applies reductions to one address one after another.  The backward
-// kernels therefore reduce from CTA b into replica b % k of each dense
-// level (see Replicas in dash_internal.cuh); this file lays the replicas out
+// The coarsest dense levels hold few entries (44k, 122k and 357k at the
+// paper shape), and every Gaussian reduces into 16 of them per level, so
+// within a backward call each of their entries takes hundreds of FP32
+// reductions; the L2 applies reductions to one address one after another.
+// The backward kernels therefore reduce from CTA b into replica b % k[l] of
+// each such level (see Replicas in dash_internal.cuh); this file lays the replicas out
 // in the caller's workspace, clears them before the kernels and adds them
 // into the gradient buffer after.  The sum is exact up to the order of the
 // FP32 additions.
@@ -15,29 +15,33 @@
 
 namespace dash {
 
-constexpr long long kRepMaxEntries = 1ll << 17;
+constexpr long long kRepSmall = 1ll << 17;
+constexpr long long kRepLarge = 1ll << 19;
 
 Replicas replica_plan(const dash_layout* layout, int k, size_t* bytes) {
   Replicas r;
   memset(&r, 0, sizeof(r));
   *bytes = 0;
   if (layout == nullptr || layout->F != 2 || k < 2) return r;
+  // the leading dense levels small enough for their entries to take many
+  // reductions each per call: k replicas up to 2^17 entries, k / 2 up to
+  // 2^19 (measured: more copies, or larger levels, cost more L2 room and
+  // clearing than the contention they remove)
   int lv = 0;
-  // the leading dense levels small enough for their entries to take
-  // hundreds of reductions each per call (the larger ones gained nothing
-  // measurable and cost L2 room)
-  while (lv < layout->L && lv < kMaxRepLevels && layout->dense[lv] && layout->size[lv] <= kRepMaxEntries) ++lv;
-  if (lv == 0) return r;
   long long off = 0;
-  for (int l = 0; l < lv; ++l) {
-    const long long stride = (layout->size[l] * 2 + 63) & ~63ll;  // floats; replicas start 256-byte aligned
-    r.off[l] = off;
-    r.stride[l] = stride;
-    r.size[l] = layout->size[l];
-    off += stride * k;
+  while (lv < layout->L && lv < kMaxRepLevels && layout->dense[lv]) {
+    const long long size = layout->size[lv];
+    const int kl = size <= kRepSmall ? k : (size <= kRepLarge ? k / 2 : 0);
+    if (kl < 2) break;
+    const long long stride = (size * 2 + 63) & ~63ll;  // floats; replicas start 256-byte aligned
+    r.k[lv] = kl;
+    r.off[lv] = off;
+    r.stride[lv] = stride;
+    r.size[lv] = size;
+    off += stride * kl;
+    ++lv;
   }
   r.levels = lv;
-  r.k = k;
   *bytes = (size_t)off * sizeof(float);
   return r;
 }
@@ -70,7 +74,7 @@ __global__ void __launch_bounds__(256) replica_sum_kernel(const __grid_constant_
     }
     const float* src = a.rp.base + a.rp.off[l] + 2 * i;
     float sx = 0.0f, sy = 0.0f;
-    for (int r = 0; r < a.rp.k; ++r) {
+    for (int r = 0; r < a.rp.k[l]; ++r) {
       const float2 v = __ldcs(reinterpret_cast<const float2*>(src + (long long)r * a.rp.stride[l]));
       sx += v.x;
       sy += v.y;
