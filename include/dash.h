@@ -163,11 +163,10 @@ int dash_version(void);
  * was created.  (The F = 2 Eq. 11 kernel and the encoder-only kernels always
  * use lane pairs.)
  * DASH_OPT_GRAD_REPLICAS (0..64, default 16): k, the number of replicas of
- * the FP32 gradients of each leading dense level of at most 2^17 entries,
- * k / 2 for those of at most 2^19 (levels 0-1 and level 2 at the paper
- * shape), that dash_deform_mlp_bwd uses when it is given a workspace (see
- * there); 0 or 1 = none.  It sizes dash_deform_bwd_workspace_size, so set
- * it before sizing.
+ * the FP32 gradients of each leading dense level of at most 2^17 entries
+ * (levels 0 and 1 at the paper shape) that dash_deform_mlp_bwd uses when it
+ * is given a workspace (see there); 0 or 1 = none.  It sizes
+ * dash_deform_bwd_workspace_size, so set it before sizing.
  * dash_get_option returns the current value (negative status for an
  * unknown option). */
 enum dash_option {

@@ -595,9 +595,9 @@ struct Replicas {
   }
 };
 
-// Host: the replica layout for the leading dense levels — k replicas of
-// each level of at most 2^17 entries, k / 2 of each larger one of at most
-// 2^19 (none for F != 2 or k < 2) — and its size in bytes; base unset.
+// Host: the replica layout for the leading dense levels of at most 2^17
+// entries, k replicas each (none for F != 2 or k < 2), and its size in
+// bytes; base unset.
 Replicas replica_plan(const dash_layout* layout, int k, size_t* bytes);
 // Zeroes the replicas (before the kernels that reduce into them).
 int replica_clear(const Replicas& rp, size_t bytes, cudaStream_t st);

@@ -1,7 +1,7 @@
 // replicas.cu -- replicated gradient buffers for the dense levels (F = 2).
 //
-// The coarsest dense levels hold few entries (44k, 122k and 357k at the
-// paper shape), and every Gaussian reduces into 16 of them per level, so
+// The coarsest dense levels hold few entries (44k and 122k at the paper
+// shape), and every Gaussian reduces into 16 of them per level, so
 // within a backward call each of their entries takes hundreds of FP32
 // reductions; the L2 applies reductions to one address one after another.
 // The backward kernels therefore reduce from CTA b into replica b % k[l] of
@@ -16,7 +16,6 @@
 namespace dash {
 
 constexpr long long kRepSmall = 1ll << 17;
-constexpr long long kRepLarge = 1ll << 19;
 
 Replicas replica_plan(const dash_layout* layout, int k, size_t* bytes) {
   Replicas r;
@@ -24,14 +23,15 @@ Replicas replica_plan(const dash_layout* layout, int k, size_t* bytes) {
   *bytes = 0;
   if (layout == nullptr || layout->F != 2 || k < 2) return r;
   // the leading dense levels small enough for their entries to take many
-  // reductions each per call: k replicas up to 2^17 entries, k / 2 up to
-  // 2^19 (measured: more copies, or larger levels, cost more L2 room and
-  // clearing than the contention they remove)
+  // reductions each per call: k replicas of each level of at most 2^17
+  // entries (measured inside the benchmark step: replicating the next,
+  // 357k-entry level as well took enough L2 room from the gradients and
+  // the forward's tables to make the step slower)
   int lv = 0;
   long long off = 0;
   while (lv < layout->L && lv < kMaxRepLevels && layout->dense[lv]) {
     const long long size = layout->size[lv];
-    const int kl = size <= kRepSmall ? k : (size <= kRepLarge ? k / 2 : 0);
+    const int kl = size <= kRepSmall ? k : 0;
     if (kl < 2) break;
     const long long stride = (size * 2 + 63) & ~63ll;  // floats; replicas start 256-byte aligned
     r.k[lv] = kl;

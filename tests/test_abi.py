@@ -95,23 +95,23 @@ def test_host_layout3_equals_oracle(cfg):
 
 
 def test_replica_workspace_size():
-    """Replicas cover the leading dense levels: k copies of each level of at
-    most 2^17 entries and k / 2 of each of at most 2^19 (levels 0-1 and 2
-    of the paper shape), each copy the level's FP32 [entries][2] rows,
-    256-byte aligned; the Eq. 11 hand-over adds L * F * n floats."""
+    """Replicas cover the leading dense levels of at most 2^17 entries
+    (levels 0 and 1 of the three dense ones at the paper shape): k copies of
+    each level's FP32 [entries][2] rows, 256-byte aligned; the Eq. 11
+    hand-over adds L * F * n floats."""
     from paper_2507_19141_gb300 import dash, synth
     lay = dash.layout_from(synth.PAPER_GRID)
     old = dash.dash_get_option(dash.OPT_GRAD_REPLICAS)
     try:
         dash.dash_set_option(dash.OPT_GRAD_REPLICAS, 8)
-        rows = [-(-int(lay.size[l]) * 2 // 64) * 64 for l in range(3)]
+        rows = [-(-int(lay.size[l]) * 2 // 64) * 64 for l in range(2)]
         assert all(bool(lay.dense[l]) for l in range(3)) and not lay.dense[3]
-        assert lay.size[1] <= 1 << 17 < lay.size[2] <= 1 << 19
-        rep = 4 * (8 * rows[0] + 8 * rows[1] + 4 * rows[2])
+        assert lay.size[1] <= 1 << 17 < lay.size[2]
+        rep = 4 * 8 * (rows[0] + rows[1])
         assert dash.dash_deform_bwd_workspace_size(lay, 1000) == rep
         sm = (1.0, (0.0, 0.0, 0.0), 0.0, None)
         assert dash.dash_deform_bwd_workspace_size(lay, 1000, sm) == -(-rep // 256) * 256 + 32 * 1000 * 4
-        dash.dash_set_option(dash.OPT_GRAD_REPLICAS, 3)  # k / 2 = 1: level 2 without replicas
+        dash.dash_set_option(dash.OPT_GRAD_REPLICAS, 3)
         assert dash.dash_deform_bwd_workspace_size(lay, 1000) == 4 * 3 * (rows[0] + rows[1])
         dash.dash_set_option(dash.OPT_GRAD_REPLICAS, 0)
         assert dash.dash_deform_bwd_workspace_size(lay, 1000) == 0
