@@ -13,7 +13,8 @@
 // tensor cores and rebuilds its BF16 weight tiles when the scene changes.
 // With a backward the forward also writes each item's per-Gaussian state,
 // and a second persistent kernel in the same graph runs the fused backward
-// (a9-a10) over the same work list.
+// (a9-a10) over the same work list, between a clear of the plan's
+// per-scene gradient replicas and their sum into each scene's gradients.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>

@@ -21,6 +21,14 @@
 //      over all tiles of the CTA and flushed with one atomic per weight.
 //   5. table_grad[corner] += w * (df_h + smoothness term) with vector FP32
 //      reductions (red.global.add.v2.f32 for F = 2).
+//
+// For F = 2 with a forward state the warp-specialised kernel splits this:
+// a decoder group (steps 2-4) hands df_h per tile through a shared-memory
+// ring to scatter groups (step 5, lane pairs); the smoothness term runs in
+// smooth.cu.  With the caller's workspace the coarsest dense levels reduce
+// into replicas (replicas.cu), and with the smoothness term the decoder
+// group alone stores df_h there for smooth.cu to scatter with its own
+// gradient.
 #include "deform_bwd_common.cuh"
 
 namespace dash {
