@@ -543,3 +543,39 @@ def test_backward_workspace_forms_agree(dashlib, tdtype, smooth_on, replicas):
     finally:
         dashlib.dash_set_option(dashlib.OPT_GRAD_REPLICAS, old)
 
+
+
+def test_backward_replicas_under_contention(dashlib):
+    """Gaussians sorted by position with one broadcast t, so neighbouring
+    lanes and CTAs reduce into the same coarse entries: the backward with
+    the gradient replicas equals the one without (up to the order of the
+    additions) and the oracle."""
+    grid, mlpc = synth.PAPER_GRID, synth.PAPER_MLP
+    rng = np.random.default_rng(99)
+    n = 40_000
+    g = oracle_grid(grid)
+    x, y, z, _ = synth.scene_coords(rng, n)
+    order = np.lexsort((z, y, x))
+    x, y, z = x[order], y[order], z[order]
+    t = np.array([0.41], dtype=np.float32)
+    table = synth.table_values(rng, g.total, grid.F, np.float16)
+    params = synth.mlp_params(rng, mlpc)
+    dd = synth.upstream_grad(rng, mlpc.d_out, n)
+    lay = dashlib.layout_from(grid)
+    pts = dashlib.Points(to_dev(x), to_dev(y), to_dev(z), to_dev(t), n=n)
+    mlp = dashlib.Mlp(to_dev(params), mlpc.d_in, mlpc.d_hidden, mlpc.d_out)
+    tab = to_dev(table)
+    st = dashlib.deform_state(mlp, n, "cuda")
+    dashlib.dash_deform_mlp_fwd(lay, pts, tab, mlp, fwd_state=st)
+    out = []
+    for ws in (None, False):
+        tg = torch.zeros((g.total, 2), dtype=torch.float32, device="cuda")
+        pg = torch.zeros(mlpc.n_params, dtype=torch.float32, device="cuda")
+        dashlib.dash_deform_mlp_bwd(lay, pts, tab, mlp, to_dev(dd), tg, pg, fwd_state=st, ws=ws)
+        out.append(tg.cpu().numpy())
+    assert rel_err(out[0], out[1]) < 1e-5
+    rtg, _, _ = oracle.deform_bwd(g, oracle.Points(x, y, z, t, t_stride=0), table.astype(np.float64), 64, 10,
+                                  params.astype(np.float64), dd.astype(np.float64))
+    assert rel_err(out[0], rtg) < 1e-2
+    dense = slice(0, int(lay.offset[2]) * 2)  # levels 0-1, the replicated ones
+    assert rel_err(out[0].reshape(-1)[dense], rtg.reshape(-1)[dense]) < 1e-2
