@@ -119,3 +119,21 @@ def test_replica_workspace_size():
             dash.dash_set_option(dash.OPT_GRAD_REPLICAS, 65)
     finally:
         dash.dash_set_option(dash.OPT_GRAD_REPLICAS, old)
+
+
+def test_replica_workspace_edge_layouts():
+    """No replicas where no leading level is dense (the tiny grid's level 0
+    has 44,217 vertices > T = 2^14, so every level is hashed) or F != 2; the
+    Eq. 11 hand-over alone then sizes the workspace; the replicas do not
+    depend on n."""
+    from paper_2507_19141_gb300 import dash, synth
+    tiny = dash.layout_from(synth.TINY_GRID)
+    assert not any(bool(tiny.dense[l]) for l in range(tiny.L))
+    sm = (1.0, (0.0, 0.0, 0.0), 0.0, None)
+    assert dash.dash_deform_bwd_workspace_size(tiny, 5000) == 0
+    assert dash.dash_deform_bwd_workspace_size(tiny, 5000, sm) == 4 * 2 * 5000 * 4
+    f4 = dash.dash_hash4d_layout(4, 4, 14, 16, 128, 8, 32)
+    assert dash.dash_deform_bwd_workspace_size(f4, 5000, sm) == 0
+    paper = dash.layout_from(synth.PAPER_GRID)
+    assert dash.dash_deform_bwd_workspace_size(paper, 0) == dash.dash_deform_bwd_workspace_size(paper, 10)
+    assert dash.dash_deform_bwd_workspace_size(paper, 0, sm) % 256 == 0
