@@ -323,7 +323,7 @@ int dash_deform_apply_bwd(const dash_points* pts, int d_out, const float* dattrs
  * dash_deform_bwd_workspace_size bytes (DASH_ERR_WORKSPACE otherwise)
  * enables, for F = 2 with a forward state and lane-paired accesses:
  *  - replicas of the coarsest dense levels' gradients
- *    (DASH_OPT_GRAD_REPLICAS = k):
+ *    (DASH_OPT_GRAD_REPLICAS = k; not with coord_grad):
  *    the lane-paired scatter and the Eq. 11 kernel reduce from CTA b into
  *    replica b % k, which the call zeroes first and adds into table_grad
  *    last (a memset and one more kernel on the stream);

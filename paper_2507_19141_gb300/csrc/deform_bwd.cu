@@ -103,7 +103,8 @@ __device__ __forceinline__ void scatter_level(float* __restrict__ grad, long lon
 // the clamp mask).  Matches level_coord_grad up to the order of additions.
 template <typename TT>
 __device__ __forceinline__ float4 scatter_coord_levels_paired(const Geom& g, const TT* __restrict__ table,
-                                                              float* __restrict__ grad, float4 p, const float* dfp,
+                                                              float* __restrict__ grad, const Replicas& rp,
+                                                              float4 p, const float* dfp,
                                                               uint32_t xb, bool vb, unsigned int pm) {
   float4 pa, pb;
   pair_points(p, xb, pm, pa, pb);
@@ -112,7 +113,7 @@ __device__ __forceinline__ float4 scatter_coord_levels_paired(const Geom& g, con
     const float2 f0 = *reinterpret_cast<const float2*>(dfp + (2 * l) * kRows);
     const float2 f1 = *reinterpret_cast<const float2*>(dfp + (2 * l + 1) * kRows);
     const TT* base = table + g.offset[l] * 2;
-    float* gbase = grad + g.offset[l] * 2;
+    float* gbase = rp.level_base(grad, g, l);
     const float ns = (float)g.res_s[l], nt = (float)g.res_t[l];
 #pragma unroll 1
     for (int G = 0; G < 2; ++G) {
@@ -643,7 +644,7 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_bwd_ws_kernel(const
             if (a.coord_grad == nullptr) {
               scatter_levels_paired(a.g, a.table_grad, a.rep, p, stage + (r & ~1), xb, true, row_a + 1 < n, pm);
             } else {
-              const float4 cg = scatter_coord_levels_paired<TT>(a.g, table, a.table_grad, p, stage + (r & ~1), xb,
+              const float4 cg = scatter_coord_levels_paired<TT>(a.g, table, a.table_grad, a.rep, p, stage + (r & ~1), xb,
                                                                 row_a + 1 < n, pm);
               if (row < n) store_coord_grad(a, row, cg);
             }
@@ -887,6 +888,8 @@ extern "C" int dash_deform_mlp_bwd(const dash_layout* layout, const dash_points*
   Replicas rep;
   memset(&rep, 0, sizeof(rep));
   size_t rep_bytes = 0;
+  // (not with the coordinate gradient: its table gathers share the L2 with
+  // the replicas, and ncu showed 3x the DRAM traffic for no time gained)
   if (ws_buf != nullptr && ws && a.g.F == 2 && g_opt_access_form == 0 && (smooth_apart || coord_grad == nullptr)) {
     const BwdWorkspace wl = bwd_workspace(layout, a.n_cap, smooth_apart);
     if (ws_bytes < wl.total)

@@ -120,3 +120,33 @@ def test_fused_backward_coord_grad_rejects_smoothness(dashlib):
                                     smooth=(0.1, (1e-3, 1e-3, 1e-3), 1e-3, None),
                                     coord_grad=torch.zeros((4, 256), device="cuda"))
     assert e.value.status == dashlib.ERR_UNSUPPORTED
+
+
+def test_fused_backward_coord_grad_with_and_without_workspace(dashlib):
+    """The coordinate-gradient backward given the binding's default
+    workspace and given none: the same table gradients up to the order of
+    the additions and the same coordinate gradients (the workspace is not
+    used on this path)."""
+    grid, mlpc = synth.PAPER_GRID, synth.PAPER_MLP
+    rng = np.random.default_rng(71)
+    n = 6000
+    g = oracle_grid(grid)
+    coords = synth.scene_coords(rng, n)
+    table = synth.table_values(rng, g.total, grid.F, np.float16)
+    params = synth.mlp_params(rng, mlpc)
+    dd = to_dev(synth.upstream_grad(rng, mlpc.d_out, n))
+    lay = dashlib.layout_from(grid)
+    pts = dashlib.Points(*(to_dev(c) for c in coords), n=n)
+    mlp = dashlib.Mlp(to_dev(params), mlpc.d_in, mlpc.d_hidden, mlpc.d_out)
+    tab = to_dev(table)
+    st = dashlib.deform_state(mlp, n, "cuda")
+    dashlib.dash_deform_mlp_fwd(lay, pts, tab, mlp, fwd_state=st)
+    out = []
+    for ws in (None, False):
+        tg = torch.zeros((g.total, 2), dtype=torch.float32, device="cuda")
+        pg = torch.zeros(mlpc.n_params, dtype=torch.float32, device="cuda")
+        cg = torch.zeros((4, n), dtype=torch.float32, device="cuda")
+        dashlib.dash_deform_mlp_bwd(lay, pts, tab, mlp, dd, tg, pg, fwd_state=st, coord_grad=cg, ws=ws)
+        out.append((tg.cpu().numpy(), cg.cpu().numpy()))
+    assert rel_err(out[0][0], out[1][0]) < 1e-5
+    assert rel_err(out[0][1], out[1][1]) < 1e-6
