@@ -12,7 +12,9 @@
 // (one L1 lookup / one L2 reduction when they share a sector).  The lanes
 // swap partial sums so both hold each Gaussian's full encodings.  Where p + e
 // lies in p's hypervoxel (the same 16 corners) the entries loaded for f(p)
-// also give f(p + e), and its gradient joins p's in one reduction per corner.
+// also give f(p + e), and its gradient joins p's in one reduction per corner;
+// where p + e_t lies in the next or previous temporal cell, the 8 corners of
+// the face the two hypervoxels share are treated the same way.
 // A thread keeps one level of one Gaussian live at a time.  Without the
 // fused backward's shared-memory ring the whole L1 serves the gathers.
 // Given dL/df_h (SoA [L*2][n], written by the fused backward in place of its
@@ -93,6 +95,10 @@ __global__ void __launch_bounds__(kThreads, 2) smooth_bwd_kernel(const __grid_co
       level_cell(a.g, l, perturbed(pp, a.eps_s[0], a.eps_s[1], a.eps_s[2], 0.0f), cs, fs);
       level_cell(a.g, l, perturbed(pp, 0.0f, 0.0f, 0.0f, a.eps_t), ct, ft);
       const bool ss = same_cell(cs, cp), st = same_cell(ct, cp);
+      // p + e_t one temporal cell up (dt = 1) or down (dt = -1): its corners
+      // with t bit 0 (q < 4) are p's with t bit 1 (q + 4), or the reverse,
+      // in the same lane (the x bit is unchanged)
+      const int dt = (!st && ct[0] == cp[0] && ct[1] == cp[1] && ct[2] == cp[2]) ? ct[3] - cp[3] : 0;
       // ---- gather this lane's x half of p, and of p + e where it has its own corners
       float2 sp, sq_s, sq_t;
       {
@@ -111,7 +117,11 @@ __global__ void __launch_bounds__(kThreads, 2) smooth_bwd_kernel(const __grid_co
         if (!st) {
           cell_index_x(a.g, l, ct, xb, idx);
 #pragma unroll
-          for (int q = 0; q < 8; ++q) et[q] = Entry2<TT>::load(base + (size_t)idx[q] * 2);
+          for (int q = 0; q < 8; ++q) {
+            if (dt == 1 && q < 4) et[q] = e[q + 4];
+            else if (dt == -1 && q >= 4) et[q] = e[q - 4];
+            else et[q] = Entry2<TT>::load(base + (size_t)idx[q] * 2);
+          }
         }
         level_weights_x(fp, xb, w);
         sp = half_sum<TT>(w, e);
@@ -163,6 +173,15 @@ __global__ void __launch_bounds__(kThreads, 2) smooth_bwd_kernel(const __grid_co
             c0[q] = fmaf(v[q], gt0, c0[q]);
             c1[q] = fmaf(v[q], gt1, c1[q]);
           }
+        } else if (dt == 1 || dt == -1) {  // the shared face joins p's reductions
+          level_weights_x(ft, xb, v);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int qt = dt == 1 ? q : q + 4;  // p + e_t's corner on the shared face
+            const int qp = dt == 1 ? q + 4 : q;  // the same corner of p
+            c0[qp] = fmaf(v[qt], gt0, c0[qp]);
+            c1[qp] = fmaf(v[qt], gt1, c1[qp]);
+          }
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q) red_add_v2(gbase + (size_t)idx[q] * 2, c0[q], c1[q]);
@@ -176,7 +195,9 @@ __global__ void __launch_bounds__(kThreads, 2) smooth_bwd_kernel(const __grid_co
           cell_index_x(a.g, l, ct, xb, idx);
           level_weights_x(ft, xb, v);
 #pragma unroll
-          for (int q = 0; q < 8; ++q) red_add_v2(gbase + (size_t)idx[q] * 2, v[q] * gt0, v[q] * gt1);
+          for (int q = 0; q < 8; ++q)
+            if (!((dt == 1 && q < 4) || (dt == -1 && q >= 4)))
+              red_add_v2(gbase + (size_t)idx[q] * 2, v[q] * gt0, v[q] * gt1);
         }
       }
     }
