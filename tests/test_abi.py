@@ -137,3 +137,26 @@ def test_replica_workspace_edge_layouts():
     paper = dash.layout_from(synth.PAPER_GRID)
     assert dash.dash_deform_bwd_workspace_size(paper, 0) == dash.dash_deform_bwd_workspace_size(paper, 10)
     assert dash.dash_deform_bwd_workspace_size(paper, 0, sm) % 256 == 0
+
+
+@pytest.mark.parametrize("cfg", [(16, 2, 19, 16, 2048, 8, 150), (8, 2, 20, 8, 512, 4, 64), (12, 2, 17, 4, 1024, 2, 40),
+                                 (3, 2, 22, 16, 64, 8, 16)])
+@pytest.mark.parametrize("k", [2, 5, 16])
+def test_replica_plan_follows_the_layout(cfg, k):
+    """Replicas cover exactly the leading run of dense levels of at most
+    2^17 entries (at most 4 levels), k copies each, rows rounded up to 64
+    floats: the size the library reports equals this count for layouts with
+    1 to 4 such levels."""
+    from paper_2507_19141_gb300 import dash
+    lay = dash.dash_hash4d_layout(*cfg)
+    old = dash.dash_get_option(dash.OPT_GRAD_REPLICAS)
+    try:
+        dash.dash_set_option(dash.OPT_GRAD_REPLICAS, k)
+        floats = 0
+        for l in range(min(lay.L, 4)):
+            if not lay.dense[l] or lay.size[l] > 1 << 17:
+                break
+            floats += k * (-(-int(lay.size[l]) * 2 // 64) * 64)
+        assert dash.dash_deform_bwd_workspace_size(lay, 777) == 4 * floats
+    finally:
+        dash.dash_set_option(dash.OPT_GRAD_REPLICAS, old)
