@@ -136,6 +136,13 @@ const char* dash_status_string(int status);
 const char* dash_last_error(void);
 /* ABI version (major * 100 + minor). */
 int dash_version(void);
+/* Device-side failure report: synchronises `stream`, then reads and clears
+ * the flag words the persistent kernels (fused forward and backward,
+ * batched plans) set when a bounded wait (an MMA completion or a ring
+ * stage, 2^22 polls) gives up — the kernel then stops issuing, frees its
+ * TMEM and returns, leaving that launch's outputs incomplete.  Returns
+ * DASH_ERR_TIMEOUT if any flag was set since the last call, else DASH_OK. */
+int dash_device_status(void* stream);
 
 /* Process-wide kernel-form options (host; take effect at the next launch).
  * DASH_OPT_FWD_FORM selects the fused forward kernel: 0 = warp-specialised

@@ -510,13 +510,13 @@ int launch_batch_bwd(int form, int table_dtype, const BatchBwdArgs& a, cudaStrea
   return table_dtype == DASH_F16 ? launch_bwd_tt<__half>(form, a, st) : launch_bwd_tt<float>(form, a, st);
 }
 
+}  // namespace
+
 unsigned int* batch_flags_ptr() {
   void* p = nullptr;
   if (cudaGetSymbolAddress(&p, g_batch_flags) != cudaSuccess) return nullptr;
   return static_cast<unsigned int*>(p);
 }
-
-}  // namespace
 
 }  // namespace fused
 }  // namespace dash

@@ -144,6 +144,24 @@ int dash_set_option(int option, int value) {
   }
 }
 
+int dash_device_status(void* stream) {
+  using namespace dash;
+  if (int s = cuda_status(cudaStreamSynchronize(as_stream(stream)), "cudaStreamSynchronize")) return s;
+  unsigned int* words[3] = {fused::fwd_flags_ptr(), fused::bwd_flags_ptr(), fused::batch_flags_ptr()};
+  unsigned int seen = 0u;
+  for (unsigned int* w : words) {
+    if (w == nullptr) return fail(DASH_ERR_CUDA, "cannot resolve a device flag word");
+    unsigned int v = 0u;
+    if (int s = cuda_status(cudaMemcpy(&v, w, sizeof(v), cudaMemcpyDeviceToHost), "cudaMemcpy(flags)")) return s;
+    if (v != 0u) {
+      seen |= v;
+      if (int s = cuda_status(cudaMemset(w, 0, sizeof(v)), "cudaMemset(flags)")) return s;
+    }
+  }
+  if (seen != 0u) return fail(DASH_ERR_TIMEOUT, "a bounded device-side wait gave up (flags %#x); outputs of that launch are incomplete", seen);
+  return DASH_OK;
+}
+
 int dash_get_option(int option) {
   switch (option) {
     case DASH_OPT_FWD_FORM: return dash::g_opt_fwd_form;

@@ -604,6 +604,14 @@ int replica_clear(const Replicas& rp, size_t bytes, cudaStream_t st);
 // grad[level l] += sum of the k replicas of level l, for every replicated level.
 int replica_sum(const Geom& g, const Replicas& rp, float* grad, cudaStream_t st);
 
+namespace fused {
+// Device words the persistent kernels set (bit 0) when a bounded wait gives
+// up (deform_fwd.cu, deform_bwd.cu, batch.cu); read by dash_device_status.
+unsigned int* fwd_flags_ptr();
+unsigned int* bwd_flags_ptr();
+unsigned int* batch_flags_ptr();
+}  // namespace fused
+
 // Backward of the Eq. 11 smoothness term for F = 2 (smooth.cu): adds its
 // table gradient into table_grad (or, for the replicated levels, into the
 // replicas) and lambda_r L_r into sm->loss_out.

@@ -121,6 +121,7 @@ _SIGS = {
     "dash_last_error": ([], ctypes.c_char_p),
     "dash_version": ([], _I),
     "dash_set_option": ([_I, _I], _I),
+    "dash_device_status": ([_P], _I),
     "dash_get_option": ([_I], _I),
     "dash_hash4d_layout": ([_P, _P], _I),
     "dash_compact_workspace_size": ([_I64], _SZ),
@@ -201,6 +202,13 @@ OPT_FWD_FORM = 1
 OPT_BWD_FORM = 2
 OPT_ACCESS_FORM = 3
 OPT_GRAD_REPLICAS = 4
+
+
+def dash_device_status() -> None:
+    """Raises DashError (ERR_TIMEOUT) if a bounded device-side wait of a
+    persistent kernel gave up since the last call (synchronises the current
+    stream)."""
+    _check(_lib.dash_device_status(_stream()), "dash_device_status")
 
 
 def dash_set_option(option: int, value: int) -> None:

@@ -579,3 +579,28 @@ def test_backward_replicas_under_contention(dashlib):
     assert rel_err(out[0], rtg) < 1e-2
     dense = slice(0, int(lay.offset[2]) * 2)  # levels 0-1, the replicated ones
     assert rel_err(out[0].reshape(-1)[dense], rtg.reshape(-1)[dense]) < 1e-2
+
+
+def test_device_status_after_fused_and_batched_runs(dashlib):
+    """The bounded waits of the persistent kernels never give up on valid
+    work: after a fused forward + backward and a batched plan the device
+    flag words read clear (dash_device_status raises on a set flag)."""
+    grid, mlpc = synth.PAPER_GRID, synth.PAPER_MLP
+    g, coords, _, table, params, dd = _case(grid, mlpc, 3000, np.float16, 101)
+    lay = dashlib.layout_from(grid)
+    pts = _dev_points(dashlib, coords, None, 3000)
+    mlp = dashlib.Mlp(to_dev(params), mlpc.d_in, mlpc.d_hidden, mlpc.d_out)
+    tab = to_dev(table)
+    st = dashlib.deform_state(mlp, 3000, "cuda")
+    dashlib.dash_deform_mlp_fwd(lay, pts, tab, mlp, fwd_state=st)
+    tg = torch.zeros((g.total, 2), dtype=torch.float32, device="cuda")
+    pg = torch.zeros(mlpc.n_params, dtype=torch.float32, device="cuda")
+    dashlib.dash_deform_mlp_bwd(lay, pts, tab, mlp, to_dev(dd), tg, pg, fwd_state=st)
+    dashlib.dash_device_status()
+    x, y, z, t = (to_dev(c) for c in coords)
+    scenes = [{"table": tab, "params": to_dev(params), "x": x, "y": y, "z": z, "timestamps": t[:2].contiguous(),
+               "delta_out": torch.empty((2, mlpc.d_out, 3000), device="cuda")}]
+    plan = dashlib.BatchPlan(lay, scenes)
+    plan.run()
+    dashlib.dash_device_status()
+    plan.close()
