@@ -1,14 +1,14 @@
 // replicas.cu -- replicated gradient buffers for the dense levels (F = 2).
 //
 // The coarsest dense levels hold few entries (44k and 122k at the paper
-// shape), and every Gaussian reduces into 16 of them per level, so
-// within a backward call each of their entries takes hundreds of FP32
-// reductions; the L2 applies reductions to one address one after another.
-// The backward kernels therefore reduce from CTA b into replica b % k[l] of
-// each such level (see Replicas in dash_internal.cuh); this file lays the replicas out
-// in the caller's workspace, clears them before the kernels and adds them
-// into the gradient buffer after.  The sum is exact up to the order of the
-// FP32 additions.
+// shape), and every Gaussian reduces into 16 of them per level, so within a
+// backward call each of their entries takes hundreds of FP32 reductions;
+// the L2 applies reductions to one address one after another.  The backward
+// kernels therefore reduce from CTA b into replica b % k[l] of each such
+// level (see Replicas in dash_internal.cuh); this file lays the replicas
+// out in the caller's workspace, clears them before the kernels and adds
+// them into the gradient buffer after.  The sum is exact up to the order of
+// the FP32 additions.
 #include "dash_internal.cuh"
 
 #include <string.h>
