@@ -45,10 +45,10 @@ STEP_BYTES = 2 + 4 + FWD_BYTES + BWD_BYTES
 # (profiles/dram_traffic_fused_and_batched.md), valid while the kernel's sources
 # hash to the captured value; otherwise the benchmark reports no traffic.
 NCU_TRAFFIC = {
-    "bwd": {"bytes": (214.2 + 5.9) * 1e6, "n": 1_000_000, "sha256_16": "10e829d17e10c059",
+    "bwd": {"bytes": (214.2 + 5.9) * 1e6, "n": 1_000_000, "sha256_16": "361e8c1af2703654",
             "sources": ("deform_bwd.cu", "deform_bwd_common.cuh", "deform_common.cuh", "dash_internal.cuh",
                         "tc_ptx.cuh", "replicas.cu", "dash_host.cu")},
-    "fwd": {"bytes": (45.4 + 70.6) * 1e6, "n": 1_000_000, "sha256_16": "5a0adf1b05c0b48f",
+    "fwd": {"bytes": (45.4 + 70.6) * 1e6, "n": 1_000_000, "sha256_16": "a06590f7364eeaf6",
             "sources": ("deform_fwd.cu", "deform_common.cuh", "dash_internal.cuh", "tc_ptx.cuh")},
 }
 
