@@ -56,3 +56,13 @@ def test_max_over_ranks_gloo_world_size_2():
     for p in procs:
         p.join(timeout=60)
     assert res == [(0, 2, 2.0), (1, 2, 2.0)]
+
+
+def test_all_cores_oracle_timing():
+    """One single-threaded oracle process per host core, started together:
+    the line reports every core and a positive rate."""
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.cpu_baseline_all_cores(20_000.0, seconds=0.05)
+    assert r["kind"] == "oracle" and r["cores"] == (os.cpu_count() or 1) and r["value"] > 0
+    assert r["unit"] == "Gaussians/s" and "processes" in r["sample"]
