@@ -138,11 +138,62 @@ const char* dash_last_error(void);
 int dash_version(void);
 /* Device-side failure report: synchronises `stream`, then reads and clears
  * the flag words the persistent kernels (fused forward and backward,
- * batched plans) set when a bounded wait (an MMA completion or a ring
+ * batched plans; and the wait self-test below) set when a bounded wait (an MMA completion or a ring
  * stage, 2^22 polls) gives up — the kernel then stops issuing, frees its
  * TMEM and returns, leaving that launch's outputs incomplete.  Returns
  * DASH_ERR_TIMEOUT if any flag was set since the last call, else DASH_OK. */
 int dash_device_status(void* stream);
+
+/* Failure-path checks; the paper has no counterpart.
+ *
+ * dash_selftest_wait: launches one thread on `stream` that waits, with a
+ * bound of `polls` (1 .. 2^22) polls, on a shared-memory mbarrier that
+ * nothing arrives at -- the bounded wait of the persistent kernels, made to
+ * run out.  It then sets its device flag word and returns, so the next
+ * dash_device_status returns DASH_ERR_TIMEOUT (and clears the flag); the
+ * context stays usable.  Errors: INVALID_ARG (polls out of range), CUDA.
+ *
+ * dash_debug_fail_cuda_call: fault injection on the host.  With n >= 1 the
+ * n-th CUDA runtime call that the library checks from now on (counted over
+ * all threads: allocations, copies, memsets, stream and graph calls,
+ * launch checks) is not made and fails, so that call's entry point returns
+ * DASH_ERR_CUDA with "injected failure" in dash_last_error, after releasing
+ * what it had acquired.  n = 0 disarms the hook; either value restarts the
+ * count that dash_debug_cuda_call_count returns (checked calls since the
+ * last dash_debug_fail_cuda_call).  Not for concurrent use with other
+ * library calls that must not fail. */
+int dash_selftest_wait(int64_t polls, void* stream);
+
+/* Rate probes of the access patterns that bound the fused kernels (the
+ * paper has no counterpart: a measuring tool).  One launch of
+ * dash_probe_threads(kind) threads (8 CTAs of 256 per SM), each issuing
+ * `iters` (1 .. 65536) operations at pseudo-random 16-byte groups of buf
+ * (device, 16-byte aligned, buf_bytes >= 16; size it like the tables or the
+ * gradient buffer so it stays L2-resident).  *ops_out (host) receives the
+ * number of lane operations issued; the caller times the launch.  The
+ * reduction kinds add 1.0 into buf (its contents change); the gather kinds
+ * only read buf and write one float per thread to sink (device, required
+ * for them, NULL allowed otherwise).
+ *   DASH_PROBE_RED8          8-byte FP32 vector reduction, each lane its own
+ *                            random entry
+ *   DASH_PROBE_RED16         16-byte FP32 vector reduction, random group
+ *   DASH_PROBE_RED8_PAIRED   lanes 2j, 2j+1: 8 bytes each into the two halves
+ *                            of one 16-byte group, same instruction
+ *   DASH_PROBE_GATHER4       4-byte load, each lane its own random entry
+ *   DASH_PROBE_GATHER4_PAIRED lanes 2j, 2j+1: neighbouring 4-byte entries
+ * Errors: INVALID_ARG, CUDA. */
+enum {
+  DASH_PROBE_RED8 = 1,
+  DASH_PROBE_RED16 = 2,
+  DASH_PROBE_RED8_PAIRED = 3,
+  DASH_PROBE_GATHER4 = 4,
+  DASH_PROBE_GATHER4_PAIRED = 5
+};
+int dash_probe_threads(int kind);
+int dash_probe_rate(int kind, float* buf, size_t buf_bytes, int iters, float* sink, int64_t* ops_out,
+                    void* stream);
+int dash_debug_fail_cuda_call(int64_t n);
+int64_t dash_debug_cuda_call_count(void);
 
 /* Process-wide kernel-form options (host; take effect at the next launch).
  * DASH_OPT_FWD_FORM selects the fused forward kernel: 0 = warp-specialised
@@ -213,10 +264,18 @@ int dash_compact_dynamic(const uint8_t* mask, int64_t n, int32_t* idx_out, int64
  * library, held by every GPU that loads it until the process exits; n is
  * limited to 268,435,456 mask entries (DASH_ERR_UNSUPPORTED beyond).  The
  * first call on a device resolves the array's device address (one
- * cudaGetSymbolAddress, with that device current), so make that first call
- * before any stream capture.  All calls share the array: calls whose kernels
- * overlap on the GPU (other streams, other host threads) race and corrupt
- * each other's results; serialise them.  Output and errors as
+ * cudaGetSymbolAddress, with that device current) and, because CUDA loads
+ * device code lazily, may load this part of the library onto the device --
+ * and so allocate (the code and the array).  Make one warm-up call per
+ * device with a nonempty mask (n >= 1, so that all three of its kernels
+ * run once) before entering a region that must not allocate and before any
+ * stream capture; every later call allocates nothing.  The address is
+ * cached per process and per device ordinal: call from the device's primary
+ * context (the runtime API's default) and do not cudaDeviceReset the device
+ * between calls, which would leave the cached address pointing at memory
+ * this library no longer owns.  All calls share the array: calls whose
+ * kernels overlap on the GPU (other streams, other host threads) race and
+ * corrupt each other's results; serialise them.  Output and errors as
  * dash_compact_dynamic. */
 int dash_compact_dynamic_noalloc(const uint8_t* mask, int64_t n, int32_t* idx_out,
                                  int64_t* count_out, void* stream);

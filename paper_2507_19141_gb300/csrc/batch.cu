@@ -426,7 +426,7 @@ int launch_form(BatchArgs a, cudaStream_t st) {
   const size_t smem = smem_for(P, S, a.Dp, &a);
   if (smem > 227 * 1024) return fail(DASH_ERR_UNSUPPORTED, "batched form P=%d S=%d needs %zu B of shared memory", P, S, smem);
   auto kern = batch_fwd_kernel<TT, F, P, S>;
-  if (int s = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+  if (int s = cuda_status(DASH_RT(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)),
                           "cudaFuncSetAttribute(batch)"))
     return s;
   kern<<<(unsigned)sm_count(), (P + 1) * kRows, smem, st>>>(a);
@@ -489,7 +489,7 @@ int launch_bwd_form(BatchBwdArgs a, cudaStream_t st) {
   const size_t smem = a.off_tab + sizeof(long long) * (2 * kMaxScenes + 1);
   if (smem > 227 * 1024) return fail(DASH_ERR_UNSUPPORTED, "batched backward needs %zu B of shared memory", smem);
   auto kern = batch_bwd_kernel<TT, P, S>;
-  if (int s = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+  if (int s = cuda_status(DASH_RT(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)),
                           "cudaFuncSetAttribute(batch_bwd)"))
     return s;
   kern<<<(unsigned)sm_count(), (P + 1) * kRows, smem, st>>>(a);
@@ -556,11 +556,11 @@ int time_form(Launch launch, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, fl
   using namespace dash;
   int rc = launch();
   if (rc != DASH_OK) return rc;
-  rc = cuda_status(cudaEventRecord(e0, st), "cudaEventRecord");
+  rc = cuda_status(DASH_RT(cudaEventRecord(e0, st)), "cudaEventRecord");
   for (int rep = 0; rep < 3 && rc == DASH_OK; ++rep) rc = launch();
-  if (rc == DASH_OK) rc = cuda_status(cudaEventRecord(e1, st), "cudaEventRecord");
-  if (rc == DASH_OK) rc = cuda_status(cudaEventSynchronize(e1), "cudaEventSynchronize");
-  if (rc == DASH_OK) rc = cuda_status(cudaEventElapsedTime(ms, e0, e1), "cudaEventElapsedTime");
+  if (rc == DASH_OK) rc = cuda_status(DASH_RT(cudaEventRecord(e1, st)), "cudaEventRecord");
+  if (rc == DASH_OK) rc = cuda_status(DASH_RT(cudaEventSynchronize(e1)), "cudaEventSynchronize");
+  if (rc == DASH_OK) rc = cuda_status(DASH_RT(cudaEventElapsedTime(ms, e0, e1)), "cudaEventElapsedTime");
   return rc;
 }
 
@@ -569,14 +569,14 @@ int capture(dash_batch_plan* p) {
   using namespace dash;
   destroy_graph(p);
   cudaStream_t cs = nullptr;
-  if (int s = cuda_status(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "cudaStreamCreate")) return s;
-  int rc = cuda_status(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+  if (int s = cuda_status(DASH_RT(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)), "cudaStreamCreate")) return s;
+  int rc = cuda_status(DASH_RT(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)), "cudaStreamBeginCapture");
   if (rc == DASH_OK) {
     int lr = fused::launch_batch(p->form, p->table_dtype, p->args, cs);
     if (lr == DASH_OK && p->with_bwd) {
       const Replicas& rep = p->bargs.rep;
       if (p->d_rep != nullptr)
-        lr = cuda_status(cudaMemsetAsync(p->d_rep, 0, p->rep_bytes * p->h_scenes.size(), cs), "cudaMemsetAsync");
+        lr = cuda_status(DASH_RT(cudaMemsetAsync(p->d_rep, 0, p->rep_bytes * p->h_scenes.size(), cs)), "cudaMemsetAsync");
       if (lr == DASH_OK) lr = fused::launch_batch_bwd(p->bform, p->table_dtype, p->bargs, cs);
       for (size_t s = 0; lr == DASH_OK && p->d_rep != nullptr && s < p->h_scenes.size(); ++s) {
         Replicas r = rep;
@@ -587,7 +587,7 @@ int capture(dash_batch_plan* p) {
     const int er = cuda_status(cudaStreamEndCapture(cs, &p->graph), "cudaStreamEndCapture");
     rc = lr != DASH_OK ? lr : er;
   }
-  if (rc == DASH_OK) rc = cuda_status(cudaGraphInstantiate(&p->exec, p->graph, 0), "cudaGraphInstantiate");
+  if (rc == DASH_OK) rc = cuda_status(DASH_RT(cudaGraphInstantiate(&p->exec, p->graph, 0)), "cudaGraphInstantiate");
   cudaStreamDestroy(cs);
   if (rc != DASH_OK) destroy_graph(p);
   return rc;
@@ -673,19 +673,19 @@ int dash_batch_plan_create(const dash_batch_desc* desc, dash_batch_plan** out) {
   if (with_bwd) {
     rep = replica_plan(desc->layout, g_opt_grad_replicas, &p->rep_bytes);
     if (rep.levels > 0) {
-      rc = cuda_status(cudaMalloc(&p->d_rep, p->rep_bytes * desc->n_scenes), "cudaMalloc");
+      rc = cuda_status(DASH_RT(cudaMalloc(&p->d_rep, p->rep_bytes * desc->n_scenes)), "cudaMalloc");
       for (int s = 0; rc == DASH_OK && s < desc->n_scenes; ++s)
         host[s].rep_base = reinterpret_cast<float*>(reinterpret_cast<char*>(p->d_rep) + p->rep_bytes * s);
     }
   }
   p->h_scenes.assign(host, host + desc->n_scenes);
-  if (rc == DASH_OK) rc = cuda_status(cudaMalloc(&p->d_scenes, sizeof(fused::SceneDev) * desc->n_scenes), "cudaMalloc");
-  if (rc == DASH_OK) rc = cuda_status(cudaMalloc(&p->d_counts, sizeof(long long) * desc->n_scenes), "cudaMalloc");
+  if (rc == DASH_OK) rc = cuda_status(DASH_RT(cudaMalloc(&p->d_scenes, sizeof(fused::SceneDev) * desc->n_scenes)), "cudaMalloc");
+  if (rc == DASH_OK) rc = cuda_status(DASH_RT(cudaMalloc(&p->d_counts, sizeof(long long) * desc->n_scenes)), "cudaMalloc");
   if (rc == DASH_OK)
-    rc = cuda_status(cudaMemcpy(p->d_scenes, host, sizeof(fused::SceneDev) * desc->n_scenes, cudaMemcpyHostToDevice),
+    rc = cuda_status(DASH_RT(cudaMemcpy(p->d_scenes, host, sizeof(fused::SceneDev) * desc->n_scenes, cudaMemcpyHostToDevice)),
                      "cudaMemcpy");
   if (rc == DASH_OK)
-    rc = cuda_status(cudaMemcpy(p->d_counts, counts, sizeof(long long) * desc->n_scenes, cudaMemcpyHostToDevice),
+    rc = cuda_status(DASH_RT(cudaMemcpy(p->d_counts, counts, sizeof(long long) * desc->n_scenes, cudaMemcpyHostToDevice)),
                      "cudaMemcpy");
   if (rc == DASH_OK) {
     a.scenes = p->d_scenes;
@@ -724,7 +724,7 @@ int64_t* dash_batch_counts(dash_batch_plan* plan) {
 int dash_batch_run(dash_batch_plan* plan, void* stream) {
   using namespace dash;
   if (plan == nullptr || plan->exec == nullptr) return fail(DASH_ERR_INVALID_ARG, "plan is NULL or not instantiated");
-  return cuda_status(cudaGraphLaunch(plan->exec, as_stream(stream)), "cudaGraphLaunch");
+  return cuda_status(DASH_RT(cudaGraphLaunch(plan->exec, as_stream(stream))), "cudaGraphLaunch");
 }
 
 int dash_batch_plan_destroy(dash_batch_plan* plan) {
@@ -769,8 +769,8 @@ int dash_batch_autotune(dash_batch_plan* plan, const char* cache_json_path, void
   // time every compiled form on this plan's work: one warm-up and three timed runs each
   cudaStream_t st = as_stream(stream);
   cudaEvent_t e0, e1;
-  if (int s = cuda_status(cudaEventCreate(&e0), "cudaEventCreate")) return s;
-  if (int s = cuda_status(cudaEventCreate(&e1), "cudaEventCreate")) {
+  if (int s = cuda_status(DASH_RT(cudaEventCreate(&e0)), "cudaEventCreate")) return s;
+  if (int s = cuda_status(DASH_RT(cudaEventCreate(&e1)), "cudaEventCreate")) {
     cudaEventDestroy(e0);
     return s;
   }
@@ -795,14 +795,14 @@ int dash_batch_autotune(dash_batch_plan* plan, const char* cache_json_path, void
     const long long per = plan->grad_floats + plan->param_floats;
     const int ns = (int)plan->h_scenes.size();
     float* saved = nullptr;
-    rc = cuda_status(cudaMalloc(&saved, sizeof(float) * per * ns), "cudaMalloc");
+    rc = cuda_status(DASH_RT(cudaMalloc(&saved, sizeof(float) * per * ns)), "cudaMalloc");
     for (int s = 0; s < ns && rc == DASH_OK; ++s) {
       const fused::SceneDev& sc = plan->h_scenes[s];
-      rc = cuda_status(cudaMemcpyAsync(saved + s * per, sc.table_grad, sizeof(float) * plan->grad_floats,
-                                       cudaMemcpyDeviceToDevice, st), "cudaMemcpyAsync");
+      rc = cuda_status(DASH_RT(cudaMemcpyAsync(saved + s * per, sc.table_grad, sizeof(float) * plan->grad_floats,
+                                       cudaMemcpyDeviceToDevice, st)), "cudaMemcpyAsync");
       if (rc == DASH_OK)
-        rc = cuda_status(cudaMemcpyAsync(saved + s * per + plan->grad_floats, sc.mlp_grad,
-                                         sizeof(float) * plan->param_floats, cudaMemcpyDeviceToDevice, st),
+        rc = cuda_status(DASH_RT(cudaMemcpyAsync(saved + s * per + plan->grad_floats, sc.mlp_grad,
+                                         sizeof(float) * plan->param_floats, cudaMemcpyDeviceToDevice, st)),
                          "cudaMemcpyAsync");
     }
     if (rc == DASH_OK) rc = fused::launch_batch(plan->form, plan->table_dtype, plan->args, st);
@@ -821,15 +821,15 @@ int dash_batch_autotune(dash_batch_plan* plan, const char* cache_json_path, void
     }
     for (int s = 0; s < ns && saved != nullptr; ++s) {  // put the gradients back, also after an error
       const fused::SceneDev& sc = plan->h_scenes[s];
-      const int r1 = cuda_status(cudaMemcpyAsync(sc.table_grad, saved + s * per, sizeof(float) * plan->grad_floats,
-                                                 cudaMemcpyDeviceToDevice, st), "cudaMemcpyAsync");
-      const int r2 = cuda_status(cudaMemcpyAsync(sc.mlp_grad, saved + s * per + plan->grad_floats,
-                                                 sizeof(float) * plan->param_floats, cudaMemcpyDeviceToDevice, st),
+      const int r1 = cuda_status(DASH_RT(cudaMemcpyAsync(sc.table_grad, saved + s * per, sizeof(float) * plan->grad_floats,
+                                                 cudaMemcpyDeviceToDevice, st)), "cudaMemcpyAsync");
+      const int r2 = cuda_status(DASH_RT(cudaMemcpyAsync(sc.mlp_grad, saved + s * per + plan->grad_floats,
+                                                 sizeof(float) * plan->param_floats, cudaMemcpyDeviceToDevice, st)),
                                  "cudaMemcpyAsync");
       if (rc == DASH_OK) rc = r1 != DASH_OK ? r1 : r2;
     }
     if (saved != nullptr) {
-      const int r = cuda_status(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+      const int r = cuda_status(DASH_RT(cudaStreamSynchronize(st)), "cudaStreamSynchronize");
       if (rc == DASH_OK) rc = r;
       cudaFree(saved);
     }

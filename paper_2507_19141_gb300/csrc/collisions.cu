@@ -163,14 +163,14 @@ int dash_hash4d_collision_stats(const dash_layout* layout, const dash_points* pt
   w.count = reinterpret_cast<unsigned int*>(base + w.slots * 8u);
   const size_t count_bytes = ((size_t)max_level_size(layout) * 4u + 255u) & ~(size_t)255u;
   w.flag = reinterpret_cast<unsigned int*>(base + w.slots * 8u + count_bytes);
-  if (int s = cuda_status(cudaMemsetAsync(stats_out, 0, sizeof(int64_t) * 3u * (size_t)g.L, st), "cudaMemsetAsync"))
+  if (int s = cuda_status(DASH_RT(cudaMemsetAsync(stats_out, 0, sizeof(int64_t) * 3u * (size_t)g.L, st)), "cudaMemsetAsync"))
     return s;
   const unsigned grid = (unsigned)((p.n + kThreads - 1) / kThreads);
   for (int l = 0; l < g.L; ++l) {
     const long long size = layout->size[l];
-    if (int s = cuda_status(cudaMemsetAsync(w.set, 0xFF, (size_t)w.slots * 8u, st), "cudaMemsetAsync")) return s;
-    if (int s = cuda_status(cudaMemsetAsync(w.count, 0, (size_t)size * 4u, st), "cudaMemsetAsync")) return s;
-    if (int s = cuda_status(cudaMemsetAsync(w.flag, 0, 4u, st), "cudaMemsetAsync")) return s;
+    if (int s = cuda_status(DASH_RT(cudaMemsetAsync(w.set, 0xFF, (size_t)w.slots * 8u, st)), "cudaMemsetAsync")) return s;
+    if (int s = cuda_status(DASH_RT(cudaMemsetAsync(w.count, 0, (size_t)size * 4u, st)), "cudaMemsetAsync")) return s;
+    if (int s = cuda_status(DASH_RT(cudaMemsetAsync(w.flag, 0, 4u, st)), "cudaMemsetAsync")) return s;
     if (p.n > 0) {
       touch_kernel<<<grid, kThreads, 0, st>>>(g, p, l, w);
       if (int s = launch_status("touch_kernel")) return s;

@@ -202,7 +202,11 @@ int dash_compact_dynamic(const uint8_t* mask, int64_t n, int32_t* idx_out, int64
 // front, or code that runs inside a memory allocator's own callbacks, where a
 // cudaMalloc would re-enter that allocator.  The per-CTA counts live in this
 // file-scope array instead of a caller workspace; every GPU that loads the
-// library holds it (256 KB) until the process exits.
+// library holds it (256 KB) until the process exits.  Its device address is
+// resolved once per device and cached for the life of the process: valid
+// for the device's primary context and until a cudaDeviceReset of that
+// device.  Device code is loaded lazily, so the first call on a device may
+// itself allocate; callers warm up with one call per device (n >= 1).
 // ---------------------------------------------------------------------------
 #include <mutex>
 
@@ -222,12 +226,12 @@ int* g_noalloc_ptr[64] = {nullptr};
 // stand-in, not device memory).
 int noalloc_scratch(int** out) {
   int dev = 0;
-  if (int s = cuda_status(cudaGetDevice(&dev), "cudaGetDevice")) return s;
+  if (int s = cuda_status(DASH_RT(cudaGetDevice(&dev)), "cudaGetDevice")) return s;
   if (dev < 0 || dev >= 64) return fail(DASH_ERR_UNSUPPORTED, "device ordinal %d >= 64", dev);
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
   if (g_noalloc_ptr[dev] == nullptr) {
     void* p = nullptr;
-    if (int s = cuda_status(cudaGetSymbolAddress(&p, g_noalloc_cta_counts), "cudaGetSymbolAddress")) return s;
+    if (int s = cuda_status(DASH_RT(cudaGetSymbolAddress(&p, g_noalloc_cta_counts)), "cudaGetSymbolAddress")) return s;
     g_noalloc_ptr[dev] = static_cast<int*>(p);
   }
   *out = g_noalloc_ptr[dev];

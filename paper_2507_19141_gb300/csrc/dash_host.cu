@@ -5,6 +5,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
+
 #include "dash_internal.cuh"
 
 namespace dash {
@@ -31,12 +33,32 @@ int fail(int status, const char* fmt, ...) {
   return status;
 }
 
+// Fault injection: g_fault_at > 0 names the g_fault_at-th checked runtime
+// call after arming; g_rt_calls counts the checked calls since then.
+static std::atomic<long long> g_fault_at{0};
+static std::atomic<long long> g_rt_calls{0};
+static thread_local bool g_injected = false;
+
+bool fault_due() {
+  const long long k = g_rt_calls.fetch_add(1, std::memory_order_relaxed) + 1;
+  const long long at = g_fault_at.load(std::memory_order_relaxed);
+  if (at > 0 && k == at) {
+    g_injected = true;
+    return true;
+  }
+  return false;
+}
+
 int cuda_status(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return DASH_OK;
+  if (g_injected) {
+    g_injected = false;
+    return fail(DASH_ERR_CUDA, "%s: injected failure (dash_debug_fail_cuda_call), call not made", what);
+  }
   return fail(DASH_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
 }
 
-int launch_status(const char* what) { return cuda_status(cudaGetLastError(), what); }
+int launch_status(const char* what) { return cuda_status(DASH_RT(cudaGetLastError()), what); }
 
 int sm_count() {
   static int cached[64] = {0};
@@ -116,6 +138,16 @@ const char* dash_status_string(int s) {
 
 const char* dash_last_error(void) { return dash::g_last_error; }
 
+int dash_debug_fail_cuda_call(int64_t n) {
+  if (n < 0) return dash::fail(DASH_ERR_INVALID_ARG, "n=%lld < 0", (long long)n);
+  dash::g_fault_at.store(0, std::memory_order_relaxed);
+  dash::g_rt_calls.store(0, std::memory_order_relaxed);
+  dash::g_fault_at.store((long long)n, std::memory_order_relaxed);
+  return DASH_OK;
+}
+
+int64_t dash_debug_cuda_call_count(void) { return (int64_t)dash::g_rt_calls.load(std::memory_order_relaxed); }
+
 int dash_version(void) { return 102; }
 
 int dash_set_option(int option, int value) {
@@ -146,16 +178,17 @@ int dash_set_option(int option, int value) {
 
 int dash_device_status(void* stream) {
   using namespace dash;
-  if (int s = cuda_status(cudaStreamSynchronize(as_stream(stream)), "cudaStreamSynchronize")) return s;
-  unsigned int* words[3] = {fused::fwd_flags_ptr(), fused::bwd_flags_ptr(), fused::batch_flags_ptr()};
+  if (int s = cuda_status(DASH_RT(cudaStreamSynchronize(as_stream(stream))), "cudaStreamSynchronize")) return s;
+  unsigned int* words[4] = {fused::fwd_flags_ptr(), fused::bwd_flags_ptr(), fused::batch_flags_ptr(),
+                            fused::selftest_flags_ptr()};
   unsigned int seen = 0u;
   for (unsigned int* w : words) {
     if (w == nullptr) return fail(DASH_ERR_CUDA, "cannot resolve a device flag word");
     unsigned int v = 0u;
-    if (int s = cuda_status(cudaMemcpy(&v, w, sizeof(v), cudaMemcpyDeviceToHost), "cudaMemcpy(flags)")) return s;
+    if (int s = cuda_status(DASH_RT(cudaMemcpy(&v, w, sizeof(v), cudaMemcpyDeviceToHost)), "cudaMemcpy(flags)")) return s;
     if (v != 0u) {
       seen |= v;
-      if (int s = cuda_status(cudaMemset(w, 0, sizeof(v)), "cudaMemset(flags)")) return s;
+      if (int s = cuda_status(DASH_RT(cudaMemset(w, 0, sizeof(v))), "cudaMemset(flags)")) return s;
     }
   }
   if (seen != 0u) return fail(DASH_ERR_TIMEOUT, "a bounded device-side wait gave up (flags %#x); outputs of that launch are incomplete", seen);

@@ -17,6 +17,13 @@ void set_error(const char* fmt, ...);
 int fail(int status, const char* fmt, ...);
 // Records a CUDA failure (launch or runtime call) and returns DASH_ERR_CUDA.
 int cuda_status(cudaError_t e, const char* what);
+// Fault-injection hook (dash_debug_fail_cuda_call): counts the checked CUDA
+// runtime calls and returns true for the one the hook names.
+bool fault_due();
+// A checked CUDA runtime call: made unless the fault-injection hook names
+// it, in which case it is not made and fails (cuda_status then reports an
+// injected failure).  Every runtime call the library checks goes through it.
+#define DASH_RT(call) (::dash::fault_due() ? ::cudaErrorUnknown : (call))
 // Checks the last launch on this thread.
 int launch_status(const char* what);
 
@@ -610,6 +617,8 @@ namespace fused {
 unsigned int* fwd_flags_ptr();
 unsigned int* bwd_flags_ptr();
 unsigned int* batch_flags_ptr();
+// The same for the wait self-test (selftest.cu, dash_selftest_wait).
+unsigned int* selftest_flags_ptr();
 }  // namespace fused
 
 // Backward of the Eq. 11 smoothness term for F = 2 (smooth.cu): adds its

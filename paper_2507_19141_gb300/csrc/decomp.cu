@@ -699,7 +699,7 @@ int dash_decomp_bwd(const dash_layout* layout, const float* x, const float* y, c
   a.table_grad = table_grad;
   a.mlp_grad = mlp_grad;
   if (a.mask != nullptr) {
-    if (int s = cuda_status(cudaMemsetAsync(ws, 0, 8, st), "cudaMemsetAsync")) return s;
+    if (int s = cuda_status(DASH_RT(cudaMemsetAsync(ws, 0, 8, st)), "cudaMemsetAsync")) return s;
     long long blocks = (n + kThreads - 1) / kThreads;
     const long long cap = 4ll * sm_count();
     blocks = blocks < cap ? blocks : cap;
@@ -714,7 +714,7 @@ int dash_decomp_bwd(const dash_layout* layout, const float* x, const float* y, c
 #define DASH_DECOMP_BWD(TT, FF)                                                                                     \
   {                                                                                                                 \
     auto kern = decomp_bwd_kernel<TT, FF>;                                                                          \
-    if (int s = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),     \
+    if (int s = cuda_status(DASH_RT(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)),     \
                             "cudaFuncSetAttribute(decomp_bwd)"))                                                     \
       return s;                                                                                                     \
     kern<<<(unsigned)grid, kBwdThreads, smem, st>>>(a);                                                             \

@@ -630,10 +630,10 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_bwd_ws_kernel(const
         atomicOr(a.flags, 1u);
         *abort_flag = 1;
       }
-      if (*abort_flag) break;
       // dL/df_h of this tile is read from the stage level by level; the
       // stage is handed back once the tile's reductions are issued
       const float* stage = ring + (size_t)s * stage_floats;
+      if (*abort_flag) break;
       bool done = false;
       if constexpr (F == 2) {
         if (a.paired) {
@@ -718,7 +718,7 @@ int launch_ws(BwdArgs a, cudaStream_t st) {
   const size_t smem = a.off_bar + 8 * (2 * S + 1) + 16;
   if (smem > 227 * 1024) return fail(DASH_ERR_UNSUPPORTED, "backward form needs %zu B of shared memory", smem);
   auto kern = deform_bwd_ws_kernel<TT, F, P, S>;
-  if (int s = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+  if (int s = cuda_status(DASH_RT(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)),
                           "cudaFuncSetAttribute(deform_bwd_ws)"))
     return s;
   const long long ntiles = (a.n_cap + kRows - 1) / kRows;
@@ -744,11 +744,11 @@ int launch(BwdArgs a, cudaStream_t st) {
   a.off_bar = a.off_g3 + (uint32_t)kRows * kKO * 2;
   const size_t smem = a.off_bar + 64;
   auto kern = deform_bwd_kernel<TT, F>;
-  if (int s = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+  if (int s = cuda_status(DASH_RT(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)),
                           "cudaFuncSetAttribute(deform_bwd)"))
     return s;
   int per_sm = 0;
-  if (int s = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRows, smem),
+  if (int s = cuda_status(DASH_RT(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRows, smem)),
                           "occupancy(deform_bwd)"))
     return s;
   per_sm = per_sm < 1 ? 1 : per_sm;

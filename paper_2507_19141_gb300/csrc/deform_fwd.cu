@@ -335,7 +335,7 @@ int launch_ws(FwdArgs a, cudaStream_t st) {
   a.off_a = p.off_ring;
   a.off_bar = p.off_bar;
   auto kern = deform_fwd_ws_kernel<TT, F, P, S>;
-  if (int s = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem),
+  if (int s = cuda_status(DASH_RT(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem)),
                           "cudaFuncSetAttribute(deform_fwd_ws)"))
     return s;
   const long long ntiles = (a.n_cap + kRows - 1) / kRows;
@@ -370,11 +370,11 @@ int launch(FwdArgs a, cudaStream_t st) {
   a.off_a = p.off_a;
   a.off_bar = p.off_bar;
   auto kern = deform_fwd_kernel<TT, F, G>;
-  if (int s = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem),
+  if (int s = cuda_status(DASH_RT(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem)),
                           "cudaFuncSetAttribute(deform_fwd)"))
     return s;
   int per_sm = 0;
-  if (int s = cuda_status(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G * kRows, p.smem),
+  if (int s = cuda_status(DASH_RT(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G * kRows, p.smem)),
                           "occupancy(deform_fwd)"))
     return s;
   per_sm = per_sm < 1 ? 1 : per_sm;

@@ -242,8 +242,8 @@ int dash_plain_mlp_fwd(const dash_mlp* mlp, const float* feat, int64_t n, const 
   if (n == 0) return DASH_OK;
   if (feat == nullptr || delta_out == nullptr) return fail(DASH_ERR_INVALID_ARG, "feat/delta_out is NULL");
   const size_t smem = point_smem(m);
-  if (int s = cuda_status(cudaFuncSetAttribute(plain_mlp_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem),
+  if (int s = cuda_status(DASH_RT(cudaFuncSetAttribute(plain_mlp_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem)),
                           "cudaFuncSetAttribute"))
     return s;
   plain_mlp_fwd_kernel<<<grid_points(n), kThreads, smem, as_stream(stream)>>>(
@@ -277,7 +277,7 @@ int dash_plain_mlp_bwd(const dash_mlp* mlp, const float* feat, int64_t n, const 
   float* dz2s = dz1s + (size_t)m.H * n;
   const long long* nd = reinterpret_cast<const long long*>(n_dev);
   const size_t smem = point_smem(m);
-  int s = cuda_status(cudaFuncSetAttribute(plain_mlp_bwd_points, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+  int s = cuda_status(DASH_RT(cudaFuncSetAttribute(plain_mlp_bwd_points, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)),
                       "cudaFuncSetAttribute");
   if (s == DASH_OK) {
     plain_mlp_bwd_points<<<grid_points(n), kThreads, smem, st>>>(m, mlp->params, feat, n, nd, ddelta, dfeat_out, h1s,

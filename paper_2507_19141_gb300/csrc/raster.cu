@@ -322,8 +322,8 @@ int dash_raster_fwd(const dash_camera* cam, const dash_gaussians* gs, float* ima
   cudaStream_t st = as_stream(stream);
   Ws w = bind(ws, gs->n, c.W, c.H, max_pairs);
   const int tiles = w.tiles_x * w.tiles_y;
-  if (int s = cuda_status(cudaMemsetAsync(w.count, 0, (size_t)tiles * 4u, st), "cudaMemsetAsync")) return s;
-  if (int s = cuda_status(cudaMemsetAsync(w.cursor, 0, (size_t)tiles * 4u, st), "cudaMemsetAsync")) return s;
+  if (int s = cuda_status(DASH_RT(cudaMemsetAsync(w.count, 0, (size_t)tiles * 4u, st)), "cudaMemsetAsync")) return s;
+  if (int s = cuda_status(DASH_RT(cudaMemsetAsync(w.cursor, 0, (size_t)tiles * 4u, st)), "cudaMemsetAsync")) return s;
   const unsigned grid_g = (unsigned)((gs->n + kThreads - 1) / kThreads);
   if (gs->n > 0) {
     preprocess_kernel<<<grid_g, kThreads, 0, st>>>(c, *gs, w);
@@ -340,7 +340,7 @@ int dash_raster_fwd(const dash_camera* cam, const dash_gaussians* gs, float* ima
   render_kernel<<<(unsigned)tiles, kTilePix, 0, st>>>(c, gs->n, gs->opacity, w, image);
   if (int s = launch_status("render_kernel")) return s;
   if (pairs_needed != nullptr &&
-      cuda_status(cudaMemcpyAsync(pairs_needed, w.pairs_needed, 8u, cudaMemcpyDeviceToDevice, st), "cudaMemcpyAsync"))
+      cuda_status(DASH_RT(cudaMemcpyAsync(pairs_needed, w.pairs_needed, 8u, cudaMemcpyDeviceToDevice, st)), "cudaMemcpyAsync"))
     return DASH_ERR_CUDA;
   return DASH_OK;
 }

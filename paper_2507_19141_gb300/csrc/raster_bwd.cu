@@ -350,7 +350,7 @@ extern "C" int dash_raster_bwd(const dash_camera* cam, const dash_gaussians* gs,
   Ws w = bind(ws, gs->n, c.W, c.H, max_pairs);
   const Layout L = layout_for(gs->n, c.W, c.H, max_pairs);
   // dmean2d, dconic, dcolor are contiguous in the layout
-  if (int s = cuda_status(cudaMemsetAsync(w.dmean2d, 0, L.count - L.dmean2d, st), "cudaMemsetAsync")) return s;
+  if (int s = cuda_status(DASH_RT(cudaMemsetAsync(w.dmean2d, 0, L.count - L.dmean2d, st)), "cudaMemsetAsync")) return s;
   const int tiles = w.tiles_x * w.tiles_y;
   render_bwd_kernel<<<(unsigned)tiles, kTilePix, 0, st>>>(c, gs->n, gs->opacity, w, dimage, grads->opacity);
   if (int s = launch_status("render_bwd_kernel")) return s;

@@ -48,7 +48,7 @@ Replicas replica_plan(const dash_layout* layout, int k, size_t* bytes) {
 
 int replica_clear(const Replicas& rp, size_t bytes, cudaStream_t st) {
   if (rp.levels == 0 || bytes == 0) return DASH_OK;
-  return cuda_status(cudaMemsetAsync(rp.base, 0, bytes, st), "cudaMemsetAsync(gradient replicas)");
+  return cuda_status(DASH_RT(cudaMemsetAsync(rp.base, 0, bytes, st)), "cudaMemsetAsync(gradient replicas)");
 }
 
 namespace {

@@ -122,6 +122,11 @@ _SIGS = {
     "dash_version": ([], _I),
     "dash_set_option": ([_I, _I], _I),
     "dash_device_status": ([_P], _I),
+    "dash_selftest_wait": ([_I64, _P], _I),
+    "dash_debug_fail_cuda_call": ([_I64], _I),
+    "dash_debug_cuda_call_count": ([], _I64),
+    "dash_probe_threads": ([_I], _I),
+    "dash_probe_rate": ([_I, _P, _SZ, _I, _P, _P, _P], _I),
     "dash_get_option": ([_I], _I),
     "dash_hash4d_layout": ([_P, _P], _I),
     "dash_compact_workspace_size": ([_I64], _SZ),
@@ -211,6 +216,45 @@ def dash_device_status() -> None:
     _check(_lib.dash_device_status(_stream()), "dash_device_status")
 
 
+def dash_selftest_wait(polls: int = 1000) -> None:
+    """Launches the wait self-test on the current stream: a bounded wait on an
+    mbarrier nothing arrives at, which runs out after `polls` polls and sets
+    a flag that the next dash_device_status reports as ERR_TIMEOUT."""
+    _check(_lib.dash_selftest_wait(int(polls), _stream()), "dash_selftest_wait")
+
+
+def dash_debug_fail_cuda_call(n: int) -> None:
+    """Host fault injection: the n-th checked CUDA runtime call from now on
+    is not made and fails (n = 0 disarms); restarts the call count."""
+    _check(_lib.dash_debug_fail_cuda_call(int(n)), "dash_debug_fail_cuda_call")
+
+
+def dash_debug_cuda_call_count() -> int:
+    """Checked CUDA runtime calls since the last dash_debug_fail_cuda_call."""
+    return int(_lib.dash_debug_cuda_call_count())
+
+
+PROBE_RED8, PROBE_RED16, PROBE_RED8_PAIRED, PROBE_GATHER4, PROBE_GATHER4_PAIRED = 1, 2, 3, 4, 5
+
+
+def dash_probe_rate(kind: int, buf: torch.Tensor, iters: int, sink=None) -> int:
+    """Launches one rate probe over the float32 device buffer buf on the
+    current stream; returns the number of lane operations it issued."""
+    assert buf.is_cuda and buf.dtype == torch.float32 and buf.is_contiguous()
+    if kind in (PROBE_GATHER4, PROBE_GATHER4_PAIRED):
+        need = int(_lib.dash_probe_threads(kind))
+        assert sink is not None and sink.is_cuda and sink.dtype == torch.float32 and sink.numel() >= need, \
+            f"sink: {need} float32 on the device"
+    ops = ctypes.c_int64(0)
+    _check(_lib.dash_probe_rate(kind, _ptr(buf), buf.numel() * 4, int(iters), _ptr(sink), ctypes.byref(ops),
+                                _stream()), "dash_probe_rate")
+    return int(ops.value)
+
+
+def dash_probe_threads(kind: int) -> int:
+    return int(_lib.dash_probe_threads(kind))
+
+
 def dash_set_option(option: int, value: int) -> None:
     _check(_lib.dash_set_option(option, value), "dash_set_option")
 
@@ -285,6 +329,16 @@ def dash_compact_workspace_size(n: int) -> int:
     return int(_lib.dash_compact_workspace_size(n))
 
 
+def _check_compact_outputs(mask, idx_out, count_out):
+    """The kernels write mask.numel() indices and one count: refuse buffers
+    that could not hold them before anything is launched."""
+    assert idx_out.device == mask.device and idx_out.dtype == torch.int32 and idx_out.is_contiguous(), \
+        "idx_out: contiguous int32 on the mask's device"
+    assert idx_out.numel() >= mask.numel(), f"idx_out holds {idx_out.numel()} < {mask.numel()} entries"
+    assert count_out.device == mask.device and count_out.dtype == torch.int64 and count_out.numel() >= 1, \
+        "count_out: int64 on the mask's device"
+
+
 def dash_compact_dynamic(mask: torch.Tensor, idx_out=None, count_out=None, ws=None):
     """Ascending dynamic index list of a uint8 device mask; returns (idx int32 [n] buffer, count int64 [1])."""
     assert mask.is_cuda and mask.dtype == torch.uint8 and mask.is_contiguous()
@@ -292,8 +346,11 @@ def dash_compact_dynamic(mask: torch.Tensor, idx_out=None, count_out=None, ws=No
     dev = mask.device
     idx_out = torch.empty(max(n, 1), dtype=torch.int32, device=dev) if idx_out is None else idx_out
     count_out = torch.empty(1, dtype=torch.int64, device=dev) if count_out is None else count_out
+    _check_compact_outputs(mask, idx_out, count_out)
     need = dash_compact_workspace_size(n)
     ws = torch.empty(need, dtype=torch.uint8, device=dev) if ws is None else ws
+    assert ws.device == dev and ws.dtype == torch.uint8 and ws.is_contiguous(), \
+        "ws: contiguous uint8 on the mask's device"
     _check(_lib.dash_compact_dynamic(_ptr(mask), n, _ptr(idx_out), _ptr(count_out), _ptr(ws), ws.numel(),
                                      _stream()), "dash_compact_dynamic")
     return idx_out, count_out
@@ -303,6 +360,7 @@ def dash_compact_dynamic_noalloc(mask: torch.Tensor, idx_out: torch.Tensor, coun
     """Like dash_compact_dynamic, with the library's built-in scratch array
     instead of a workspace; the caller passes the (pre-allocated) outputs."""
     assert mask.is_cuda and mask.dtype == torch.uint8 and mask.is_contiguous()
+    _check_compact_outputs(mask, idx_out, count_out)
     _check(_lib.dash_compact_dynamic_noalloc(_ptr(mask), mask.numel(), _ptr(idx_out), _ptr(count_out), _stream()),
            "dash_compact_dynamic_noalloc")
     return idx_out, count_out
