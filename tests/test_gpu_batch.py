@@ -10,7 +10,7 @@ import torch
 
 import oracle
 from paper_2507_19141_gb300 import synth
-from gpu_helpers import oracle_grid, rel_err, to_dev
+from gpu_helpers import oracle_grid, rel_err, to_dev, zero_ambiguous
 
 pytestmark = pytest.mark.gpu
 
@@ -100,10 +100,18 @@ def test_batched_autotune_and_cache(dashlib, tmp_path):
     plan2.close()
 
 
-def _with_backward(scenes, lay, O, rng):
+def _with_backward(scenes, lay, O, rng, g=None):
+    """Upstream gradients and zeroed gradient buffers per scene; given the
+    oracle grid g, the (timestamp, Gaussian) pairs whose ReLU decisions are
+    ambiguous get a zero upstream gradient (gpu_helpers.RELU_MARGIN)."""
     for sc in scenes:
         K, n = sc["delta_out"].shape[0], sc["x"].numel()
         sc["dd_np"] = rng.standard_normal((K, O, n)).astype(np.float32)
+        if g is not None:
+            x, y, z, ts, table, params = sc["np"]
+            for k in range(K):
+                zero_ambiguous(sc["dd_np"][k], g, oracle.Points(x, y, z, ts[k:k + 1], t_stride=0), table, params,
+                               64, O)
         sc["ddelta"] = to_dev(sc["dd_np"])
         sc["table_grad"] = torch.zeros((lay.total, 2), dtype=torch.float32, device="cuda")
         sc["mlp_grad"] = torch.zeros(sc["params"].numel(), dtype=torch.float32, device="cuda")
@@ -128,7 +136,7 @@ def test_batched_backward_matches_single_scene_and_oracle(dashlib):
     counts, Ks = [5000, 300, 129, 1], [3, 2, 4, 1]
     g, scenes = _scenes(dashlib, grid, mlpc, counts, Ks, np.float16, 54)
     lay = dashlib.layout_from(grid)
-    _with_backward(scenes, lay, mlpc.d_out, np.random.default_rng(55))
+    _with_backward(scenes, lay, mlpc.d_out, np.random.default_rng(55), g)
     plan = dashlib.BatchPlan(lay, scenes, backward=True)
     plan.run()
     torch.cuda.synchronize()

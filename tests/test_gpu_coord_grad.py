@@ -7,7 +7,7 @@ import torch
 
 import oracle
 from paper_2507_19141_gb300 import synth
-from gpu_helpers import edge_coords, oracle_grid, rel_err, to_dev
+from gpu_helpers import edge_coords, oracle_grid, rel_err, to_dev, zero_ambiguous
 
 pytestmark = pytest.mark.gpu
 
@@ -77,6 +77,7 @@ def test_fused_backward_coord_grad_matches_oracle(dashlib, form, use_state):
     table = synth.table_values(rng, g.total, 2, np.float16)
     params = synth.mlp_params(rng, mlpc)
     dd = synth.upstream_grad(rng, mlpc.d_out, n)
+    zero_ambiguous(dd, g, oracle.Points(x, y, z, t, idx=idx), table, params, 64, 10)
     lay = dashlib.layout_from(grid)
     pts = dashlib.Points(to_dev(x), to_dev(y), to_dev(z), to_dev(t), idx=to_dev(idx), n=n)
     mlp = dashlib.Mlp(to_dev(params), 32, 64, 10)

@@ -1,14 +1,15 @@
 """GPU parity of the fused deformation path (encoder + tensor-core decoder,
 Eqs. 8-10; backward and Eq. 11) against the FP64 oracle through the C ABI.
-Targets: outputs within 1e-3 normwise relative error per head, gradients
-within 1e-2."""
+Targets: outputs within 1e-3 relative error per head, gradients within 1e-2,
+each bound holding normwise and for every element against the largest
+reference value, with the same table entries touched (gpu_helpers.rel_err)."""
 import numpy as np
 import pytest
 import torch
 
 import oracle
 from paper_2507_19141_gb300 import synth
-from gpu_helpers import edge_coords, oracle_grid, rel_err, to_dev
+from gpu_helpers import edge_coords, oracle_grid, rel_err, to_dev, zero_ambiguous
 
 pytestmark = pytest.mark.gpu
 
@@ -31,6 +32,9 @@ def _case(grid, mlpc, n, tdtype, seed, coords=None, n_all=None):
     table = synth.table_values(rng, g.total, grid.F, tdtype)
     params = synth.mlp_params(rng, mlpc)
     dd = synth.upstream_grad(rng, mlpc.d_out, n)
+    # Gaussians whose ReLU decisions the GPU and the oracle could take
+    # differently get no upstream gradient (gpu_helpers.RELU_MARGIN)
+    zero_ambiguous(dd, g, oracle.Points(*coords, idx=idx), table, params, mlpc.d_hidden, mlpc.d_out)
     return g, coords, idx, table, params, dd
 
 
@@ -406,6 +410,7 @@ def test_backward_device_count_broadcast_t(dashlib, coord):
     table = synth.table_values(rng, g.total, grid.F, np.float16)
     params = synth.mlp_params(rng, mlpc)
     dd = synth.upstream_grad(rng, mlpc.d_out, cap)
+    zero_ambiguous(dd, g, oracle.Points(x, y, z, t, idx=idx[:live], t_stride=0), table, params, 64, 10)
     lay = dashlib.layout_from(grid)
     cnt = torch.tensor([live], dtype=torch.int64, device="cuda")
     pts = dashlib.Points(to_dev(x), to_dev(y), to_dev(z), to_dev(t), idx=to_dev(idx), n=cap, n_dev=cnt)
@@ -497,7 +502,9 @@ def test_backward_workspace_forms_agree(dashlib, tdtype, smooth_on, replicas):
     idx = np.sort(rng.choice(n_all, size=cap, replace=False)).astype(np.int32)
     table = synth.table_values(rng, g.total, grid.F, tdtype)
     params = synth.mlp_params(rng, mlpc)
-    dd = to_dev(synth.upstream_grad(rng, mlpc.d_out, cap))
+    dd_h = synth.upstream_grad(rng, mlpc.d_out, cap)
+    zero_ambiguous(dd_h, g, oracle.Points(x, y, z, t, idx=idx[:live]), table, params, 64, 10)
+    dd = to_dev(dd_h)
     tg0 = rng.standard_normal((g.total, 2)).astype(np.float32)
     lay = dashlib.layout_from(grid)
     cnt = torch.tensor([live], dtype=torch.int64, device="cuda")
@@ -527,12 +534,14 @@ def test_backward_workspace_forms_agree(dashlib, tdtype, smooth_on, replicas):
                                             ws=ws if use_ws else False)
             out.append((tg.cpu().numpy() - tg0, pg.cpu().numpy(), float(loss.item())))
         (tg1, pg1, l1), (tg2, pg2, l2) = out
-        assert rel_err(tg1, tg2) < 1e-5 and rel_err(pg1, pg2) < 1e-6
+        # the buffers started from nonzero values: their differences are
+        # compared without the touched-entry check (gpu_helpers.rel_err)
+        assert rel_err(tg1, tg2, touched=False) < 1e-5 and rel_err(pg1, pg2) < 1e-6
         assert abs(l1 - l2) <= 1e-6 * max(abs(l2), 1e-30)
         opts = oracle.Points(x, y, z, t, idx=idx[:live])
         rtg, _, rl = oracle.deform_bwd(g, opts, table.astype(np.float64), 64, 10, params.astype(np.float64),
                                        dd[:, :live].cpu().numpy().astype(np.float64), lam, es, et)
-        assert rel_err(tg1, 2 * rtg) < 1e-2 and abs(l1 - 2 * rl) <= 1e-2 * max(abs(rl), 1e-30)
+        assert rel_err(tg1, 2 * rtg, touched=False) < 1e-2 and abs(l1 - 2 * rl) <= 1e-2 * max(abs(rl), 1e-30)
         size = dashlib.dash_deform_bwd_workspace_size(lay, cap, (lam, es, et, None))
         if size > 0:
             short = torch.empty(size - 1, dtype=torch.uint8, device="cuda")
@@ -561,6 +570,7 @@ def test_backward_replicas_under_contention(dashlib):
     table = synth.table_values(rng, g.total, grid.F, np.float16)
     params = synth.mlp_params(rng, mlpc)
     dd = synth.upstream_grad(rng, mlpc.d_out, n)
+    zero_ambiguous(dd, g, oracle.Points(x, y, z, t, t_stride=0), table, params, 64, 10)
     lay = dashlib.layout_from(grid)
     pts = dashlib.Points(to_dev(x), to_dev(y), to_dev(z), to_dev(t), n=n)
     mlp = dashlib.Mlp(to_dev(params), mlpc.d_in, mlpc.d_hidden, mlpc.d_out)

