@@ -280,8 +280,9 @@ def morton3(x, y, z, bits=10):
     return spread(q(x)) | (spread(q(y)) << np.uint64(1)) | (spread(q(z)) << np.uint64(2))
 
 
-def time_steps(torch, fn, steps, stream):
-    """Times `steps` calls of fn with CUDA events on `stream`; returns ms per step."""
+def time_region(torch, fn, steps, stream):
+    """The contract's timed region: `steps` calls of fn between one pair of
+    CUDA events on `stream`; returns ms per step (the mean over the region)."""
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
     start.record(stream)
@@ -290,6 +291,73 @@ def time_steps(torch, fn, steps, stream):
     end.record(stream)
     end.synchronize()
     return start.elapsed_time(end) / steps
+
+
+MIN_REPS, WARMUP_REPS = 20, 5
+
+
+def time_steps(torch, fn, reps, stream):
+    """A secondary row: WARMUP_REPS untimed calls of fn, then at least
+    MIN_REPS calls each bracketed by its own pair of CUDA events on `stream`;
+    returns the median in ms."""
+    for _ in range(WARMUP_REPS):
+        fn()
+    E = lambda: torch.cuda.Event(enable_timing=True)
+    evs = [(E(), E()) for _ in range(max(reps, MIN_REPS))]
+    for a, b in evs:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    evs[-1][1].synchronize()
+    return statistics.median(a.elapsed_time(b) for a, b in evs)
+
+
+# L2/L1 operations per dynamic Gaussian of the fused kernels' table accesses
+# (L = 16 levels, 16 corners, F = 2).  The lane pairs put an x-neighbour
+# pair's two accesses in one warp instruction; the hardware serves them as
+# one sector operation when both entries share a 32-byte sector.  With
+# pi_1 = 1 (and on dense levels) the pair's entries are c and
+# c ^ (2^(k+1) - 1), k the trailing one bits of the lower x coordinate:
+#   backward, 8-byte FP32 gradient entries (4 per sector): shared unless
+#   k >= 2, probability 1/4 -> 8 pairs x 1.25 = 10 sector reductions a level;
+#   forward, 4-byte FP16 entries (8 per sector): shared unless k >= 3,
+#   probability 1/8 -> 8 x 1.125 = 9 sector loads a level.
+LEVELS, CORNERS = 16, 16
+BWD_RED_SECTORS = LEVELS * 8 * 1.25   # 160 per Gaussian
+FWD_GATHER_SECTORS = LEVELS * 8 * 1.125  # 144 per Gaussian
+
+
+def measure_ceilings(torch, stream, entries):
+    """Measured rates (median of 20 launches after 5 warm-ups) of the access
+    patterns that bound the fused kernels, on buffers sized like the
+    gradient buffer (entries x 8 B) and the FP16 table (entries x 4 B), both
+    L2-resident: random 8- and 16-byte FP32 reductions (sector operations/s),
+    lane-paired 8-byte reductions (lane reductions/s), random and lane-paired
+    4-byte gathers (lane loads/s)."""
+    from paper_2507_19141_gb300 import dash
+    grad = torch.zeros(entries * 2, dtype=torch.float32, device="cuda")
+    tab = torch.rand(entries, dtype=torch.float32, device="cuda")
+    sink = torch.empty(dash.dash_probe_threads(dash.PROBE_GATHER4), dtype=torch.float32, device="cuda")
+    iters = 256
+    out = {}
+    for key, kind, buf in (("red8", dash.PROBE_RED8, grad), ("red16", dash.PROBE_RED16, grad),
+                           ("red8_paired", dash.PROBE_RED8_PAIRED, grad), ("gather4", dash.PROBE_GATHER4, tab),
+                           ("gather4_paired", dash.PROBE_GATHER4_PAIRED, tab)):
+        ops = [0]
+
+        def once():
+            ops[0] = dash.dash_probe_rate(kind, buf, iters, sink)
+
+        ms = time_steps(torch, once, MIN_REPS, stream)
+        out[f"{key}_per_s"] = ops[0] / (ms / 1e3)
+    del grad, tab, sink
+    torch.cuda.empty_cache()
+    # a sector operation serves two paired lanes; the best measured rate of each unit
+    out["l2_red_sector_peak_per_s"] = max(out["red8_per_s"], out["red16_per_s"], out["red8_paired_per_s"] / 2)
+    out["l1_gather_sector_peak_per_s"] = max(out["gather4_per_s"], out["gather4_paired_per_s"] / 2)
+    out["buffers"] = f"{entries} entries: {entries * 8 / 1e6:.1f} MB FP32 pairs (reductions), " \
+                     f"{entries * 4 / 1e6:.1f} MB (gathers); {dash.dash_probe_threads(1)} threads x {iters} ops"
+    return out
 
 
 def step_config(args, ws):
@@ -317,7 +385,7 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     # ---- timed region: K steps, per-kernel events, clocks sampled meanwhile
-    ev = {k: [] for k in ("compact", "fwd", "bwd")}
+    ev = {k: [] for k in ("compact", "fwd", "bwd", "step")}
     E = lambda: torch.cuda.Event(enable_timing=True)
 
     def step_events():
@@ -332,25 +400,30 @@ def run_ours(args):
         ev["compact"].append((marks[0], marks[1]))
         ev["fwd"].append((marks[1], marks[2]))
         ev["bwd"].append((marks[2], marks[3]))
+        ev["step"].append((marks[0], marks[3]))
 
     with ClockSampler(local) as clk:
         barrier()
         torch.cuda.synchronize()
         t0 = time.time()
-        ms = time_steps(torch, step_events, args.steps, stream)
+        ms = time_region(torch, step_events, args.steps, stream)
         torch.cuda.synchronize()
         barrier()
         t1 = time.time()
     ms = max_over_ranks(ms, device)
     clocks = clk.summary(t0, t1)
-    per_kernel = {k: statistics.mean(a.elapsed_time(b) for a, b in v) for k, v in ev.items()}
+    # per-kernel and per-step medians over the K timed steps (each bracketed by its own events)
+    per_kernel = {k: statistics.median(a.elapsed_time(b) for a, b in v) for k, v in ev.items()}
+    per_kernel_mean = {k: statistics.mean(a.elapsed_time(b) for a, b in v) for k, v in ev.items()}
+    step_median = per_kernel.pop("step")
+    per_kernel_mean.pop("step")
 
     n_units = args.n_dyn * ws
     value = n_units / (ms / 1e3)
     peak, peak_kind = measured_hbm_peak()
-    dom = max(("fwd", "bwd"), key=lambda k: per_kernel[k])
+    dom = max(("fwd", "bwd"), key=lambda k: per_kernel_mean[k])
     dom_bytes = (FWD_BYTES if dom == "fwd" else BWD_BYTES) * args.n_dyn
-    achieved = dom_bytes / (per_kernel[dom] / 1e3) / 1e9
+    achieved = dom_bytes / (per_kernel_mean[dom] / 1e3) / 1e9  # the average launch over the timed region
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -358,7 +431,9 @@ def run_ours(args):
         "data": "synthetic (seeded; stands in for Neural 3D Video / Technicolor scenes)",
         "config": step_config(args, ws),
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
-        "per_kernel_ms": per_kernel,
+        "ms_per_step_median": step_median,
+        "per_kernel_ms": per_kernel, "per_kernel_stat": f"median of the {args.steps} timed steps",
+        "per_kernel_mean_ms": per_kernel_mean,
         "roofline": {"bound": "hbm", "kernel": f"fused {dom}", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
                      "algorithmic_bytes_per_gaussian": FWD_BYTES if dom == "fwd" else BWD_BYTES,
@@ -370,12 +445,31 @@ def run_ours(args):
                           "frac": STEP_BYTES * value / 1e9 / peak,
                           "gaussians_per_s_at_peak": peak * 1e9 / STEP_BYTES},
     }
+    # the binding units: the L2's reduction rate (backward) and the L1's
+    # gather rate (forward), measured in this process after the timed region
+    ceil = measure_ceilings(torch, stream, wl.layout.total)
+    n_b, t_b = args.n_dyn, per_kernel_mean["bwd"] / 1e3
+    n_f, t_f = args.n_dyn, per_kernel_mean["fwd"] / 1e3
+    out["roofline_l2"] = {"bound": "l2_reductions", "kernel": "fused bwd", "unit": "sector reductions/s",
+                          "ops_per_gaussian": BWD_RED_SECTORS, "achieved": BWD_RED_SECTORS * n_b / t_b,
+                          "peak": ceil["l2_red_sector_peak_per_s"],
+                          "frac": BWD_RED_SECTORS * n_b / t_b / ceil["l2_red_sector_peak_per_s"],
+                          "lane_reductions_per_gaussian": LEVELS * CORNERS,
+                          "peak_source": "measured in this process (dash_probe_rate, best of RED8/RED16/RED8_PAIRED)"}
+    out["roofline_l1"] = {"bound": "l1_gather_sectors", "kernel": "fused fwd", "unit": "sector loads/s",
+                          "ops_per_gaussian": FWD_GATHER_SECTORS, "achieved": FWD_GATHER_SECTORS * n_f / t_f,
+                          "peak": ceil["l1_gather_sector_peak_per_s"],
+                          "frac": FWD_GATHER_SECTORS * n_f / t_f / ceil["l1_gather_sector_peak_per_s"],
+                          "lane_loads_per_gaussian": LEVELS * CORNERS,
+                          "peak_source": "measured in this process (dash_probe_rate, GATHER4 / GATHER4_PAIRED)"}
+    out["ceilings"] = ceil
     if rank == 0:
         out["e2e"] = run_e2e(torch, wl, args, stream)
     if rank == 0 and not args.no_extras:
         out["extras"] = run_extras(torch, wl, args, stream)
         out["cpu_baseline"] = cpu_baseline(args, wl)
         out["cpu_baseline_all_cores"] = cpu_baseline_all_cores(out["cpu_baseline"]["value"])
+        out["cpu_baseline_configs"] = oracle_plain_configs()
     if rank == 0:
         print(json.dumps(out), flush=True)
     barrier()
@@ -535,7 +629,9 @@ def run_extras(torch, wl, args, stream):
     # cold L2: write 512 MB before every step, time only the step
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=wl.table.device)
     cold = []
-    for _ in range(10):
+    for _ in range(WARMUP_REPS):
+        wl.step()
+    for _ in range(MIN_REPS):
         flush.fill_(1)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -568,6 +664,7 @@ def run_extras(torch, wl, args, stream):
     res.update(run_decomp(torch, wl, stream))
     res.update(run_wo_dec(torch, stream))
     res.update(run_render(torch, stream))
+    res.update(run_plain_configs(torch, stream))
     res.update(run_batched(torch, stream))
     return res
 
@@ -892,6 +989,88 @@ def run_batched(torch, stream):
             "batched_fwd_bwd_evaluations_per_s": evals / (ms_b / 1e3)}
 
 
+# --------------------------------------- the two plain FP32 configurations --
+PLAIN_CONFIGS = {
+    "tiny": "N=10k, xyzt ~ U[0,1], L=4 F=2 T=2^14, res 16->128 / 8->32, decoder 8-64-64-10, FP32 tables and "
+            "weights, seed 0",
+    "paper_plain": "600k Gaussians, Bernoulli(0.5) mask (~300k dynamic), scene coordinates, L=16 F=2 T=2^19, "
+                   "res 16->2048 / 8->150, decoder 32-64-64-10, FP32 tables and weights, seed 1",
+}
+
+
+def plain_config(name, total):
+    """Seeded inputs of one plain FP32 configuration: the synth workload, an
+    FP32 table of `total` entries, FP32 decoder weights and the upstream
+    gradient of its dynamic Gaussians (the GPU and oracle legs draw the same)."""
+    import numpy as np
+    from paper_2507_19141_gb300 import synth
+    wl = synth.tiny() if name == "tiny" else synth.paper_plain()
+    rng = np.random.default_rng(1000 + wl.seed)
+    table = synth.table_values(rng, total, wl.grid.F, np.float32)
+    params = synth.mlp_params(rng, wl.mlp, bf16=False)
+    n_dyn = len(wl.coords[0]) if wl.mask is None else int(np.count_nonzero(wl.mask))
+    dd = synth.upstream_grad(rng, wl.mlp.d_out, n_dyn)
+    return wl, table, params, dd
+
+
+def run_plain_configs(torch, stream):
+    """The plain FP32 GPU form and the fused form on the two plain FP32
+    configurations, one step each (compaction where the configuration has a
+    mask, encoder + decoder forward, decoder + encoder backward)."""
+    import numpy as np
+    from paper_2507_19141_gb300 import dash
+    res = {}
+    for name in PLAIN_CONFIGS:
+        from paper_2507_19141_gb300 import synth
+        grid = (synth.tiny() if name == "tiny" else synth.paper_plain()).grid
+        lay = dash.layout_from(grid)
+        wl, table, params, dd_h = plain_config(name, lay.total)
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        n_all, n = len(wl.coords[0]), dd_h.shape[1]
+        D, H, O = wl.mlp.d_in, wl.mlp.d_hidden, wl.mlp.d_out
+        x, y, z, t = (dev(c) for c in wl.coords)
+        tab, dd = dev(table), dev(dd_h)
+        mlp = dash.Mlp(dev(params), D, H, O)
+        idx = torch.arange(n_all, dtype=torch.int32, device="cuda")
+        cnt = torch.full((1,), n, dtype=torch.int64, device="cuda")
+        mask = None if wl.mask is None else dev(wl.mask)
+        cws = torch.empty(dash.dash_compact_workspace_size(n_all), dtype=torch.uint8, device="cuda")
+        pts = dash.Points(x, y, z, t, idx=idx, n=n, n_dev=cnt)
+        feat = torch.empty((n, D), dtype=torch.float32, device="cuda")
+        dfeat = torch.empty_like(feat)
+        delta = torch.empty((O, n), dtype=torch.float32, device="cuda")
+        tg = torch.zeros((lay.total, grid.F), dtype=torch.float32, device="cuda")
+        pg = torch.zeros(wl.mlp.n_params, dtype=torch.float32, device="cuda")
+        wsz = torch.empty(4 * H * n * 4, dtype=torch.uint8, device="cuda")
+        state = dash.deform_state(mlp, n, "cuda")
+
+        def compact():
+            if mask is not None:
+                dash.dash_compact_dynamic(mask, idx_out=idx, count_out=cnt, ws=cws)
+
+        def plain():
+            compact()
+            dash.dash_plain_hash4d_fwd(lay, pts, tab, out=feat)
+            dash.dash_plain_mlp_fwd(mlp, feat, out=delta)
+            dash.dash_plain_mlp_bwd(mlp, feat, dd, pg, dfeat=dfeat, ws=wsz)
+            dash.dash_plain_hash4d_bwd(lay, pts, dfeat, tg)
+
+        def fused():
+            compact()
+            dash.dash_deform_mlp_fwd(lay, pts, tab, mlp, delta_out=delta, fwd_state=state)
+            dash.dash_deform_mlp_bwd(lay, pts, tab, mlp, dd, tg, pg, fwd_state=state)
+
+        for key, fn in (("plain_fp32", plain), ("fused", fused)):
+            ms = time_steps(torch, fn, MIN_REPS, stream)
+            res[f"{name}_{key}_step_ms"] = ms
+            res[f"{name}_{key}_gaussians_per_s"] = n / (ms / 1e3)
+        res[f"{name}_n_dynamic"] = n
+        del tab, tg, state, wsz
+        torch.cuda.empty_cache()
+    res["plain_configs"] = PLAIN_CONFIGS
+    return res
+
+
 # ------------------------------------------------------------ CPU oracle --
 class OracleTimer:
     """The FP64 oracle's forward + backward (one host thread) on samples of
@@ -975,6 +1154,83 @@ def cpu_baseline_all_cores(per_core_rate, seconds=5.0):
     return {"value": total / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{cores} processes x {n} dynamic Gaussians of the same distribution, forward + backward, "
                       f"{wall:.1f} s (one single-threaded oracle per host core)"}
+
+
+class PlainOracle:
+    """The FP64 oracle on one plain FP32 configuration: compaction of its
+    mask (where it has one), forward and backward of its dynamic Gaussians
+    (or of the slice [lo, hi) of them) into an FP64 table gradient."""
+
+    def __init__(self, name):
+        import numpy as np
+        import oracle
+        from paper_2507_19141_gb300 import synth
+        grid = (synth.tiny() if name == "tiny" else synth.paper_plain()).grid
+        self.np, self.oracle = np, oracle
+        self.g = oracle.layout(grid.L, grid.F, grid.log2_T, grid.nmin_s, grid.nmax_s, grid.nmin_t, grid.nmax_t)
+        self.wl, table, params, self.dd = plain_config(name, self.g.total)
+        self.table, self.params = table.astype(np.float64), params.astype(np.float64)
+        self.dd = self.dd.astype(np.float64)
+        self.tg = np.zeros((self.g.total, grid.F))
+
+    def run(self, lo=0, hi=None):
+        """Returns (Gaussians evaluated, seconds)."""
+        np, oracle, wl = self.np, self.oracle, self.wl
+        t0 = time.perf_counter()
+        if wl.mask is None:
+            idx = np.arange(len(wl.coords[0]), dtype=np.int32)
+        else:
+            idx, _ = oracle.compact(wl.mask)
+        hi = len(idx) if hi is None else hi
+        pts = oracle.Points(*wl.coords, idx=idx[lo:hi])
+        oracle.deform_fwd(self.g, pts, self.table, wl.mlp.d_hidden, wl.mlp.d_out, self.params)
+        oracle.deform_bwd(self.g, pts, self.table, wl.mlp.d_hidden, wl.mlp.d_out, self.params,
+                          np.ascontiguousarray(self.dd[:, lo:hi]), table_grad=self.tg)
+        return hi - lo, time.perf_counter() - t0
+
+
+def _plain_oracle_process(name, lo, hi, barrier, queue):
+    """One host process of the all-cores timing of a plain configuration (spawned)."""
+    po = PlainOracle(name)
+    barrier.wait(timeout=300)
+    queue.put(po.run(lo, hi))
+
+
+def oracle_plain_configs():
+    """The FP64 oracle on the two plain FP32 configurations in full: one host
+    thread, and one single-threaded process per host core, each on its own
+    contiguous slice of the dynamic Gaussians (the rate is all Gaussians over
+    the slowest process's time)."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    out = {}
+    for name in PLAIN_CONFIGS:
+        po = PlainOracle(name)
+        n, dt = po.run()
+        out[f"{name}_oracle_1_thread"] = {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                          "sample": f"all {n} dynamic Gaussians (compaction + forward + "
+                                                    f"backward), {dt:.2f} s"}
+        ctx = mp.get_context("spawn")
+        barrier, queue = ctx.Barrier(cores), ctx.Queue()
+        cuts = [n * i // cores for i in range(cores + 1)]
+        procs = [ctx.Process(target=_plain_oracle_process, args=(name, cuts[i], cuts[i + 1], barrier, queue),
+                             daemon=True) for i in range(cores)]
+        for pr in procs:
+            pr.start()
+        try:
+            res = [queue.get(timeout=600) for _ in procs]
+        except Exception as e:  # a process that died: report, do not hang the benchmark
+            for pr in procs:
+                pr.terminate()
+            out[f"{name}_oracle_all_cores"] = {"unavailable": f"all-cores oracle timing failed: {type(e).__name__}"}
+            continue
+        for pr in procs:
+            pr.join(timeout=60)
+        wall = max(d for _, d in res)
+        out[f"{name}_oracle_all_cores"] = {"value": n / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                           "sample": f"all {n} dynamic Gaussians in {cores} slices, one "
+                                                     f"single-threaded process per core, {wall:.2f} s"}
+    return out
 
 
 def run_reference(args):
