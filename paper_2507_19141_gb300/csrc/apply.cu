@@ -23,6 +23,7 @@ __global__ void __launch_bounds__(kThreads) apply_bwd_kernel(Pts pts, int O, con
 
 extern "C" int dash_deform_apply_bwd(const dash_points* pts, int d_out, const float* dattrs, int64_t n_all,
                                      float* ddelta, void* stream) {
+  DASH_NVTX_RANGE("dash_deform_apply_bwd");
   using namespace dash;
   Pts p;
   if (int s = make_pts(pts, &p)) return s;

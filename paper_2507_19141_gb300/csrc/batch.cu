@@ -598,6 +598,7 @@ int capture(dash_batch_plan* p) {
 extern "C" {
 
 int dash_batch_plan_create(const dash_batch_desc* desc, dash_batch_plan** out) {
+  DASH_NVTX_RANGE("dash_batch_plan_create");
   using namespace dash;
   if (out == nullptr || desc == nullptr || desc->scenes == nullptr) return fail(DASH_ERR_INVALID_ARG, "NULL argument");
   *out = nullptr;
@@ -722,6 +723,7 @@ int64_t* dash_batch_counts(dash_batch_plan* plan) {
 }
 
 int dash_batch_run(dash_batch_plan* plan, void* stream) {
+  DASH_NVTX_RANGE("dash_batch_run");
   using namespace dash;
   if (plan == nullptr || plan->exec == nullptr) return fail(DASH_ERR_INVALID_ARG, "plan is NULL or not instantiated");
   return cuda_status(DASH_RT(cudaGraphLaunch(plan->exec, as_stream(stream))), "cudaGraphLaunch");
@@ -740,6 +742,7 @@ int dash_batch_plan_destroy(dash_batch_plan* plan) {
 int dash_batch_form(const dash_batch_plan* plan) { return plan == nullptr ? -1 : plan->form + 16 * plan->bform; }
 
 int dash_batch_autotune(dash_batch_plan* plan, const char* cache_json_path, void* stream) {
+  DASH_NVTX_RANGE("dash_batch_autotune");
   using namespace dash;
   if (plan == nullptr) return fail(DASH_ERR_INVALID_ARG, "plan is NULL");
   const std::string key = "\"" + plan->signature + "\": ";

@@ -142,6 +142,7 @@ size_t dash_collision_workspace_size(const dash_layout* layout, int64_t n) {
 
 int dash_hash4d_collision_stats(const dash_layout* layout, const dash_points* pts, int64_t* stats_out, void* ws,
                                 size_t ws_bytes, void* stream) {
+  DASH_NVTX_RANGE("dash_hash4d_collision_stats");
   using namespace dash;
   Geom g;
   Pts p;

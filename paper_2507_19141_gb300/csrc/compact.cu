@@ -182,6 +182,7 @@ size_t dash_compact_workspace_size(int64_t n) {
 
 int dash_compact_dynamic(const uint8_t* mask, int64_t n, int32_t* idx_out, int64_t* count_out, void* ws,
                          size_t ws_bytes, void* stream) {
+  DASH_NVTX_RANGE("dash_compact_dynamic");
   using dash::fail;
   if (n < 0) return fail(DASH_ERR_INVALID_ARG, "n=%lld < 0", (long long)n);
   if (n >= (1ll << 31)) return fail(DASH_ERR_UNSUPPORTED, "n >= 2^31");

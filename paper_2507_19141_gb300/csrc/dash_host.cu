@@ -177,6 +177,7 @@ int dash_set_option(int option, int value) {
 }
 
 int dash_device_status(void* stream) {
+  DASH_NVTX_RANGE("dash_device_status");
   using namespace dash;
   if (int s = cuda_status(DASH_RT(cudaStreamSynchronize(as_stream(stream))), "cudaStreamSynchronize")) return s;
   unsigned int* words[4] = {fused::fwd_flags_ptr(), fused::bwd_flags_ptr(), fused::batch_flags_ptr(),

@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "dash.h"
@@ -28,6 +29,17 @@ bool fault_due();
 int launch_status(const char* what);
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// An NVTX range over one C-ABI call (header-only NVTX; costs nothing
+// measurable unless a profiler is attached), so timelines show which
+// library entry point issued which kernels.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define DASH_NVTX_RANGE(name) ::dash::NvtxRange dash_nvtx_range_(name)
 
 // Number of SMs of the current device (cached per device).
 int sm_count();

@@ -616,6 +616,7 @@ int dash_hash3d_layout(const dash_hash4d_cfg* cfg, dash_layout* out) {
 int dash_decomp_fwd(const dash_layout* layout, const float* x, const float* y, const float* z, int64_t n,
                     const void* table, int table_dtype, const dash_mlp* mlp, float* dp_out, float* norm_out,
                     const float* t, int64_t t_stride, float* pt_out, void* stream) {
+  DASH_NVTX_RANGE("dash_decomp_fwd");
   using namespace dash;
   if (layout == nullptr || layout->dims != 3) return fail(DASH_ERR_INVALID_ARG, "needs a 3-D layout (dash_hash3d_layout)");
   dash_layout as4 = *layout;
@@ -667,6 +668,7 @@ size_t dash_decomp_bwd_workspace_size(void) { return 256; }
 int dash_decomp_bwd(const dash_layout* layout, const float* x, const float* y, const float* z, int64_t n,
                     const void* table, int table_dtype, const dash_mlp* mlp, const float* d_dp, const uint8_t* mask,
                     float lambda_s, float* table_grad, float* mlp_grad, void* ws, size_t ws_bytes, void* stream) {
+  DASH_NVTX_RANGE("dash_decomp_bwd");
   using namespace dash;
   if (layout == nullptr || layout->dims != 3) return fail(DASH_ERR_INVALID_ARG, "needs a 3-D layout (dash_hash3d_layout)");
   dash_layout as4 = *layout;
@@ -744,6 +746,7 @@ size_t dash_topk_workspace_size(void) { return (sizeof(dash::TopkState) + 255) /
 
 int dash_topk_mask(const float* values, int64_t n, double k_percent, uint8_t* mask_out, float* tau_out,
                    float* static_loss_out, void* ws, size_t ws_bytes, void* stream) {
+  DASH_NVTX_RANGE("dash_topk_mask");
   using namespace dash;
   if (n < 0 || !(k_percent >= 0.0) || k_percent > 100.0)
     return fail(DASH_ERR_INVALID_ARG, "n < 0 or k_percent outside [0, 100]");

@@ -829,6 +829,7 @@ extern "C" int dash_deform_mlp_bwd(const dash_layout* layout, const dash_points*
                                    int table_dtype, const dash_mlp* mlp, const float* ddelta, const void* fwd_state,
                                    float* table_grad, float* mlp_grad, const dash_smooth* smooth,
                                    float* coord_grad, void* ws_buf, size_t ws_bytes, void* stream) {
+  DASH_NVTX_RANGE("dash_deform_mlp_bwd");
   using namespace dash;
   using namespace dash::fused;
   BwdArgs a;

@@ -457,6 +457,7 @@ extern "C" size_t dash_deform_state_size(const dash_mlp* mlp) {
 extern "C" int dash_deform_mlp_fwd(const dash_layout* layout, const dash_points* pts, const void* table,
                                    int table_dtype, const dash_mlp* mlp, float* delta_out, void* fwd_state,
                                    const dash_apply* apply, void* stream) {
+  DASH_NVTX_RANGE("dash_deform_mlp_fwd");
   using namespace dash;
   using namespace dash::fused;
   FwdArgs a;

@@ -303,6 +303,7 @@ extern "C" {
 
 int dash_hash4d_fwd(const dash_layout* layout, const dash_points* pts, const void* table, int table_dtype,
                     void* feat_out, int feat_dtype, void* stream) {
+  DASH_NVTX_RANGE("dash_hash4d_fwd");
   using namespace dash;
   Geom g;
   Pts p;
@@ -319,6 +320,7 @@ int dash_hash4d_fwd(const dash_layout* layout, const dash_points* pts, const voi
 
 int dash_hash4d_bwd(const dash_layout* layout, const dash_points* pts, const float* dfeat,
                     float* table_grad, void* stream) {
+  DASH_NVTX_RANGE("dash_hash4d_bwd");
   using namespace dash;
   Geom g;
   Pts p;
@@ -340,6 +342,7 @@ int dash_hash4d_bwd(const dash_layout* layout, const dash_points* pts, const flo
 
 int dash_hash4d_coord_grad(const dash_layout* layout, const dash_points* pts, const void* table, int table_dtype,
                            const float* dfeat, float* dcoord, void* stream) {
+  DASH_NVTX_RANGE("dash_hash4d_coord_grad");
   using namespace dash;
   Geom g;
   Pts p;
@@ -370,6 +373,7 @@ int dash_hash4d_coord_grad(const dash_layout* layout, const dash_points* pts, co
 
 int dash_hash4d_bwd_half(const dash_layout* layout, const dash_points* pts, const float* dfeat, void* table_grad,
                          void* stream) {
+  DASH_NVTX_RANGE("dash_hash4d_bwd_half");
   using namespace dash;
   Geom g;
   Pts p;
@@ -386,6 +390,7 @@ int dash_hash4d_bwd_half(const dash_layout* layout, const dash_points* pts, cons
 
 int dash_hash4d_indices(const dash_layout* layout, const dash_points* pts, uint32_t* idx_out, float* w_out,
                         void* stream) {
+  DASH_NVTX_RANGE("dash_hash4d_indices");
   using namespace dash;
   Geom g;
   Pts p;
@@ -397,6 +402,7 @@ int dash_hash4d_indices(const dash_layout* layout, const dash_points* pts, uint3
 
 int dash_plain_hash4d_fwd(const dash_layout* layout, const dash_points* pts, const float* table,
                           float* feat_out, void* stream) {
+  DASH_NVTX_RANGE("dash_plain_hash4d_fwd");
   using namespace dash;
   Geom g;
   Pts p;
@@ -408,6 +414,7 @@ int dash_plain_hash4d_fwd(const dash_layout* layout, const dash_points* pts, con
 
 int dash_plain_hash4d_bwd(const dash_layout* layout, const dash_points* pts, const float* dfeat,
                           float* table_grad, void* stream) {
+  DASH_NVTX_RANGE("dash_plain_hash4d_bwd");
   using namespace dash;
   Geom g;
   Pts p;

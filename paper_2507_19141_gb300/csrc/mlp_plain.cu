@@ -235,6 +235,7 @@ extern "C" {
 
 int dash_plain_mlp_fwd(const dash_mlp* mlp, const float* feat, int64_t n, const int64_t* n_dev, float* delta_out,
                        void* stream) {
+  DASH_NVTX_RANGE("dash_plain_mlp_fwd");
   using namespace dash;
   MlpShape m;
   if (int s = check_mlp(mlp, &m)) return s;
@@ -259,6 +260,7 @@ size_t dash_plain_mlp_bwd_workspace_size(const dash_mlp* mlp, int64_t n) {
 int dash_plain_mlp_bwd(const dash_mlp* mlp, const float* feat, int64_t n, const int64_t* n_dev,
                        const float* ddelta, float* dfeat_out, float* mlp_grad, void* ws, size_t ws_bytes,
                        void* stream) {
+  DASH_NVTX_RANGE("dash_plain_mlp_bwd");
   using namespace dash;
   MlpShape m;
   if (int s = check_mlp(mlp, &m)) return s;

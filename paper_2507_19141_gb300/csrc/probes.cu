@@ -69,6 +69,7 @@ extern "C" int dash_probe_threads(int kind) {
 
 extern "C" int dash_probe_rate(int kind, float* buf, size_t buf_bytes, int iters, float* sink, int64_t* ops_out,
                                void* stream) {
+  DASH_NVTX_RANGE("dash_probe_rate");
   using namespace dash;
   if (buf == nullptr || ops_out == nullptr) return fail(DASH_ERR_INVALID_ARG, "buf/ops_out is NULL");
   if ((reinterpret_cast<uintptr_t>(buf) & 15u) != 0) return fail(DASH_ERR_INVALID_ARG, "buf must be 16-byte aligned");

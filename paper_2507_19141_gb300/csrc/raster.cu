@@ -310,6 +310,7 @@ size_t dash_raster_workspace_size(const dash_camera* cam, int64_t n, int64_t max
 
 int dash_raster_fwd(const dash_camera* cam, const dash_gaussians* gs, float* image, void* ws, size_t ws_bytes,
                     int64_t max_pairs, int64_t* pairs_needed, void* stream) {
+  DASH_NVTX_RANGE("dash_raster_fwd");
   using namespace dash;
   using namespace dash::raster;
   Cam c;

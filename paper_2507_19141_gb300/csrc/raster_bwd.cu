@@ -335,6 +335,7 @@ __global__ void __launch_bounds__(kThreads) preprocess_bwd_kernel(Cam c, dash_ga
 
 extern "C" int dash_raster_bwd(const dash_camera* cam, const dash_gaussians* gs, const float* dimage, void* ws,
                                size_t ws_bytes, int64_t max_pairs, const dash_gaussian_grads* grads, void* stream) {
+  DASH_NVTX_RANGE("dash_raster_bwd");
   using namespace dash;
   using namespace dash::raster;
   Cam c;

@@ -38,6 +38,7 @@ unsigned int* selftest_flags_ptr() {
 }  // namespace dash
 
 extern "C" int dash_selftest_wait(int64_t polls, void* stream) {
+  DASH_NVTX_RANGE("dash_selftest_wait");
   using namespace dash;
   if (polls < 1 || polls > (1ll << 22)) return fail(DASH_ERR_INVALID_ARG, "polls=%lld outside [1, 2^22]", (long long)polls);
   unsigned int* flags = fused::selftest_flags_ptr();
