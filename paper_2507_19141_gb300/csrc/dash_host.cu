@@ -17,6 +17,7 @@ int g_opt_fwd_form = 0;
 int g_opt_bwd_form = 0;
 int g_opt_access_form = 0;
 int g_opt_grad_replicas = 16;
+int g_opt_decomp_bwd_form = 0;
 
 void set_error(const char* fmt, ...) {
   va_list ap;
@@ -172,6 +173,11 @@ int dash_set_option(int option, int value) {
         return dash::fail(DASH_ERR_INVALID_ARG, "gradient replicas %d not in [0, 64]", value);
       dash::g_opt_grad_replicas = value;
       return DASH_OK;
+    case DASH_OPT_DECOMP_BWD_FORM:
+      if (!(value == 0 || value == 1))
+        return dash::fail(DASH_ERR_INVALID_ARG, "decomposition backward form %d not in {0, 1}", value);
+      dash::g_opt_decomp_bwd_form = value;
+      return DASH_OK;
     default: return dash::fail(DASH_ERR_INVALID_ARG, "unknown option %d", option);
   }
 }
@@ -180,8 +186,8 @@ int dash_device_status(void* stream) {
   DASH_NVTX_RANGE("dash_device_status");
   using namespace dash;
   if (int s = cuda_status(DASH_RT(cudaStreamSynchronize(as_stream(stream))), "cudaStreamSynchronize")) return s;
-  unsigned int* words[4] = {fused::fwd_flags_ptr(), fused::bwd_flags_ptr(), fused::batch_flags_ptr(),
-                            fused::selftest_flags_ptr()};
+  unsigned int* words[5] = {fused::fwd_flags_ptr(), fused::bwd_flags_ptr(), fused::batch_flags_ptr(),
+                            fused::selftest_flags_ptr(), fused::decomp_flags_ptr()};
   unsigned int seen = 0u;
   for (unsigned int* w : words) {
     if (w == nullptr) return fail(DASH_ERR_CUDA, "cannot resolve a device flag word");
@@ -202,6 +208,7 @@ int dash_get_option(int option) {
     case DASH_OPT_BWD_FORM: return dash::g_opt_bwd_form;
     case DASH_OPT_ACCESS_FORM: return dash::g_opt_access_form;
     case DASH_OPT_GRAD_REPLICAS: return dash::g_opt_grad_replicas;
+    case DASH_OPT_DECOMP_BWD_FORM: return dash::g_opt_decomp_bwd_form;
     default: return dash::fail(DASH_ERR_INVALID_ARG, "unknown option %d", option);
   }
 }

@@ -49,6 +49,7 @@ extern int g_opt_fwd_form;
 extern int g_opt_bwd_form;
 extern int g_opt_access_form;
 extern int g_opt_grad_replicas;
+extern int g_opt_decomp_bwd_form;
 
 // ------------------------------------------------ kernel-side geometry ----
 // Level layout in the form the kernels read it (by-value kernel argument).
@@ -629,8 +630,10 @@ namespace fused {
 unsigned int* fwd_flags_ptr();
 unsigned int* bwd_flags_ptr();
 unsigned int* batch_flags_ptr();
-// The same for the wait self-test (selftest.cu, dash_selftest_wait).
+// The same for the wait self-test (selftest.cu, dash_selftest_wait) and the
+// tensor-core decomposition backward (decomp.cu).
 unsigned int* selftest_flags_ptr();
+unsigned int* decomp_flags_ptr();
 }  // namespace fused
 
 // Backward of the Eq. 11 smoothness term for F = 2 (smooth.cu): adds its

@@ -9,7 +9,7 @@
 // tau is found exactly by a radix select over the norms' bit patterns.
 #include <math.h>
 
-#include "dash_internal.cuh"
+#include "deform_bwd_common.cuh"
 
 namespace dash {
 namespace {
@@ -569,7 +569,453 @@ __global__ void topk_static_loss(const TopkState* st, float* ls_out) {
   *ls_out = c != 0ull ? (float)(st->static_sum / (double)c) : 0.0f;
 }
 
+// ------------------------------------------- backward on the tensor cores --
+// The same gradients as decomp_bwd_kernel, with phi_p's three contractions
+// on tcgen05 (BF16 operands, FP32 accumulators in TMEM), warp-specialised:
+// one CTA per SM, warps 0-3 the decoder group (thread r = tile row r = TMEM
+// lane r), warps 4.. kWorkers worker groups of 4 warps.  Worker group w
+// takes tiles j = w, w + kWorkers, ... and owns ring stage w:
+//   worker:  p -> f = G_3D(p) (FP32) -> F tile [f_hi | 1, 0.. | f_lo] of its
+//            stage; arrive F-full; wait D-full; dL/df from the stage's
+//            transposed [Dp][128] FP32 block -> table gradients
+//   decoder: wait F-full; z = [f_hi | 1 | f_lo] [W1_hi | b1_hi | W1_hi]^T +
+//            [f_hi | 1] [W1_lo | b1_lo]^T (every product but f_lo W1_lo);
+//            h = relu(z), dp = W2 h + b2, |dp|, the dp gradient gd (upstream
+//            + Eq. 5), dz = (W2^T gd) * [z > 0] -> dz tile [dz_hi | dz_lo];
+//            dL/df = dz_hi W1_hi + dz_lo W1_hi + dz_hi W1_lo and
+//            dW1^T += F^T [dz_hi | dz_lo] (accumulated in TMEM over the CTA's
+//            tiles; the F tile's ones column gives db1, its lo rows are added
+//            at the flush); dW2, db2 summed per warp by shuffles while those
+//            MMAs run; dL/df published into the stage; arrive D-full.
+// The decoder has finished reading a stage's F tile when it publishes that
+// stage's dL/df, and a worker writes its stage again only after scattering,
+// so each stage needs just the two barriers.  Requires L F <= 48 (the F
+// tile's hi, ones and lo columns within the 128 rows of the transposed read).
+namespace dtc {
+
+using fused::kRows;
+using fused::split_hi_lo8;
+using fused::tile_off;
+constexpr int kWorkers = 3;               // worker groups = ring stages
+constexpr int kThreadsWs = (kWorkers + 1) * kRows;
+constexpr uint32_t kCols = 256;           // TMEM: z 0..63, dL/df 64..111, dW1^T 128..191
+constexpr uint32_t kColZ = 0, kColDF = 64, kColW = 128;
+constexpr int kMaxDp = 48;
+
+struct Args {
+  Geom g;
+  const float* x;
+  const float* y;
+  const float* z;
+  long long n;
+  const void* table;
+  const float* params;
+  int D, Dp;
+  const float* d_dp;
+  const uint8_t* mask;
+  float lambda_s;
+  const unsigned long long* n_static;
+  float* table_grad;
+  float* mlp_grad;
+  unsigned int* flags;
+  uint32_t off_w1lo, off_w2, off_dz, off_stage, stage_bytes, off_df, off_bar;
+};
+
+__device__ unsigned int g_decomp_flags;  // bit 0: a bounded wait gave up
+
+__device__ __forceinline__ uint16_t bf16_bits(float v) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  return *reinterpret_cast<const uint16_t*>(&h);
+}
+__device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+// F = 2 scatter of one 3-D level for a lane pair's two Gaussians: lane xb
+// issues the corners with x bit xb of A (pa, gradient (a0, a1)) and of B
+// (pb, (b0, b1)), so an x-neighbour pair's two reductions leave in one
+// warp instruction.  va / vb: A / B exist.
+__device__ __forceinline__ void scatter2_level3_paired(const Geom& g, int l, float3 pa, float3 pb, uint32_t xb,
+                                                       bool va, bool vb, float* __restrict__ base, float a0,
+                                                       float a1, float b0, float b1) {
+  uint32_t ia[4], ib[4];
+  float fa[3], fb[3], wa[4], wb[4];
+  level_index3_x(g, l, pa, xb, ia, fa);
+  level_weights3_x(fa, xb, wa);
+  level_index3_x(g, l, pb, xb, ib, fb);
+  level_weights3_x(fb, xb, wb);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (va) red_add_v2(base + (size_t)ia[q] * 2, wa[q] * a0, wa[q] * a1);
+    if (vb) red_add_v2(base + (size_t)ib[q] * 2, wb[q] * b0, wb[q] * b1);
+  }
+}
+
+// The sum over the warp of v[0..32) ends with lane k holding the sum of
+// every lane's v[k] (a recursive-halving reduce-scatter: 31 shuffles).
+__device__ __forceinline__ float warp_reduce_scatter32(float v[32], uint32_t lane) {
+#pragma unroll
+  for (int half = 16; half >= 1; half >>= 1) {
+    const bool upper = (lane & (uint32_t)half) != 0u;
+#pragma unroll
+    for (int k = 0; k < half; ++k) {
+      // keep the half that this lane owns, send the other half to the partner
+      const float send = upper ? v[k] : v[k + half];
+      const float keep = upper ? v[k + half] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, half);
+    }
+  }
+  return v[0];
+}
+
+template <typename TT, int F>
+__global__ void __launch_bounds__(kThreadsWs, 1) decomp_bwd_ws_kernel(const __grid_constant__ Args a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int tid = threadIdx.x;
+  const int D = a.D, Dp = a.Dp, KZ = 2 * Dp + 16, KL = Dp + 16;
+  constexpr int H = kHidden3;
+  uint8_t* w1a = smem;                                      // [64][KZ]: W1_hi | b1_hi, 0.. | W1_hi
+  uint8_t* w1lo = smem + a.off_w1lo;                        // [64][KL]: W1_lo | b1_lo, 0..
+  float* W2s = reinterpret_cast<float*>(smem + a.off_w2);  // W2 [3][64], b2 [3]
+  uint8_t* Dz = smem + a.off_dz;                            // [128][128]: dz_hi | dz_lo
+  uint64_t* ffull = reinterpret_cast<uint64_t*>(smem + a.off_bar);
+  uint64_t* dfull = ffull + kWorkers;
+  uint64_t* mma_bar = dfull + kWorkers;
+  volatile uint32_t* holder = reinterpret_cast<volatile uint32_t*>(mma_bar + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(mma_bar + 1) + 1;
+  auto stage_f = [&](int s) { return smem + a.off_stage + (size_t)s * a.stage_bytes; };
+  auto stage_df = [&](int s) { return reinterpret_cast<float*>(smem + a.off_stage + (size_t)s * a.stage_bytes + a.off_df); };
+
+  // weight tiles: W1 [64][D] row-major, b1 [64], W2 [3][64], b2 [3]
+  const float* W1 = a.params;
+  const float* b1 = W1 + H * D;
+  for (int e = tid; e < H * KZ; e += kThreadsWs) {
+    const int nn = e / KZ, k = e % KZ;
+    float v = 0.0f;
+    if (k < D) v = W1[nn * D + k];
+    else if (k == Dp) v = b1[nn];
+    else if (k >= Dp + 16 && k - Dp - 16 < D) v = W1[nn * D + (k - Dp - 16)];
+    *reinterpret_cast<uint16_t*>(w1a + tile_off(nn, k, KZ)) = bf16_bits(v);
+  }
+  for (int e = tid; e < H * KL; e += kThreadsWs) {
+    const int nn = e / KL, k = e % KL;
+    float v = 0.0f;
+    if (k < D) v = W1[nn * D + k];
+    else if (k == Dp) v = b1[nn];
+    *reinterpret_cast<uint16_t*>(w1lo + tile_off(nn, k, KL)) = bf16_bits((k < D || k == Dp) ? v - bf16_round(v) : 0.0f);
+  }
+  for (int e = tid; e < 3 * H + 3; e += kThreadsWs) W2s[e] = b1[H + e];
+  if (tid == 0) {
+    for (int s = 0; s < kWorkers; ++s) {
+      tc::mbar_init(tc::smem_addr(&ffull[s]), kRows);
+      tc::mbar_init(tc::smem_addr(&dfull[s]), kRows);
+    }
+    tc::mbar_init(tc::smem_addr(mma_bar), 1);
+    tc::mbar_init_fence();
+    *abort_flag = 0;
+  }
+  if (tid < 32) tc::tmem_alloc(tc::smem_addr(const_cast<uint32_t*>(holder)), kCols);
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *holder;
+
+  const long long ntiles = (a.n + kRows - 1) / kRows;
+  const long long my_tiles = ntiles > blockIdx.x ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const int r = tid % kRows;
+  const uint32_t lane = (uint32_t)(r & 31);
+  float* gW1 = a.mlp_grad;
+  float* gb1 = gW1 + H * D;
+  float* gW2 = gb1 + H;
+  float* gb2 = gW2 + 3 * H;
+
+  if (tid < kRows) {
+    // ------------------------------------------------------- decoder group
+    const uint32_t trow = tbase + ((uint32_t)((r >> 5) * 32) << 16);
+    const uint32_t bar = tc::smem_addr(mma_bar);
+    uint32_t phase = 0;
+    const float inv_ns = (a.mask != nullptr && *a.n_static > 0ull) ? 1.0f / (float)*a.n_static : 0.0f;
+    const uint32_t idz = tc::idesc_bf16(kRows, H, 0, 0);
+    const uint32_t iddf = tc::idesc_bf16(kRows, Dp, 0, 1);
+    const uint32_t idw = tc::idesc_bf16(kRows, H, 1, 1);
+    float accw[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dW2 outputs 32 q + lane of this warp's rows
+    float accb[3] = {0.f, 0.f, 0.f};                 // db2 (lane 0)
+    bool had_tile = false;
+    for (long long j = 0; j < my_tiles; ++j) {
+      const int s = (int)(j % kWorkers);
+      const uint32_t round = (uint32_t)(j / kWorkers);
+      const long long i = (blockIdx.x + j * gridDim.x) * kRows + r;
+      const bool valid = i < a.n;
+      bool ok = tc::mbar_wait(tc::smem_addr(&ffull[s]), round & 1u, fused::kWaitIters);
+      uint8_t* Ft = stage_f(s);
+      if (tc::named_sync_any(1, kRows, !ok || *abort_flag)) {
+        *abort_flag = 1;
+        break;
+      }
+      tc::fence_after_sync();
+      if (r == 0) {
+        fused::bwdk::issue(tbase + kColZ, fused::bwdk::kmajor(Ft, KZ), fused::bwdk::kmajor(w1a, KZ), KZ, idz, false);
+        fused::bwdk::issue(tbase + kColZ, fused::bwdk::kmajor(Ft, KZ), fused::bwdk::kmajor(w1lo, KL), KL, idz, true);
+        tc::mma_commit(bar);
+      }
+      ok = tc::mbar_wait(bar, phase, fused::kWaitIters);
+      phase ^= 1u;
+      if (tc::named_sync_any(1, kRows, !ok)) {
+        *abort_flag = 1;
+        break;
+      }
+      tc::fence_after_sync();
+      // dp = W2 relu(z) + b2 and the ReLU mask, chunk by chunk from TMEM
+      float dp[3] = {W2s[3 * H], W2s[3 * H + 1], W2s[3 * H + 2]};
+      uint32_t mk[2] = {0u, 0u};
+#pragma unroll
+      for (int c = 0; c < H / 16; ++c) {
+        float zz[16];
+        tc::tmem_ld16(trow + kColZ + 16 * c, zz);
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+          const int jn = 16 * c + jj;
+          if (zz[jj] > 0.0f) mk[c >> 1] |= 1u << ((c & 1) * 16 + jj);
+          const float h = fmaxf(zz[jj], 0.0f);
+#pragma unroll
+          for (int cc = 0; cc < 3; ++cc) dp[cc] = fmaf(W2s[cc * H + jn], h, dp[cc]);
+        }
+      }
+      const float norm = sqrtf(fmaf(dp[0], dp[0], fmaf(dp[1], dp[1], dp[2] * dp[2])));
+      float gd[3] = {0.f, 0.f, 0.f};
+      if (valid) {
+        const bool stat = a.mask != nullptr && a.mask[i] == 0 && norm > 0.f;
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+          gd[cc] = a.d_dp != nullptr ? __ldg(a.d_dp + (long long)cc * a.n + i) : 0.f;
+          if (stat) gd[cc] = fmaf(a.lambda_s * inv_ns, dp[cc] / norm, gd[cc]);
+        }
+      }
+      // dz = (W2^T gd) * mask -> Dz [dz_hi | dz_lo]
+#pragma unroll
+      for (int c8 = 0; c8 < H / 8; ++c8) {
+        float d8[8];
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
+          const int jn = 8 * c8 + jj;
+          const float dh = W2s[jn] * gd[0] + W2s[H + jn] * gd[1] + W2s[2 * H + jn] * gd[2];
+          d8[jj] = ((mk[jn >> 5] >> (jn & 31)) & 1u) ? dh : 0.0f;
+        }
+        uint4 hi, lo;
+        split_hi_lo8(d8, hi, lo);
+        *reinterpret_cast<uint4*>(Dz + tile_off(r, 8 * c8, 2 * H)) = hi;
+        *reinterpret_cast<uint4*>(Dz + tile_off(r, H + 8 * c8, 2 * H)) = lo;
+      }
+      tc::fence_async_smem();
+      tc::fence_before_sync();
+      tc::named_sync(1, kRows);
+      tc::fence_after_sync();
+      if (r == 0) {
+        using fused::bwdk::issue;
+        using fused::bwdk::kmajor;
+        using fused::bwdk::mnmajor;
+        fused::bwdk::Op dzh = kmajor(Dz, 2 * H), dzl = dzh;
+        dzl.addr += (uint32_t)tile_off(0, H, 2 * H);
+        issue(tbase + kColDF, dzh, mnmajor(w1a, KZ), H, iddf, false);
+        issue(tbase + kColDF, dzl, mnmajor(w1a, KZ), H, iddf, true);
+        issue(tbase + kColDF, dzh, mnmajor(w1lo, KL), H, iddf, true);
+        fused::bwdk::Op bh = mnmajor(Dz, 2 * H), bl = bh;
+        bl.addr += (uint32_t)tile_off(0, H, 2 * H);
+        issue(tbase + kColW, mnmajor(Ft, KZ), bh, kRows, idw, had_tile);
+        issue(tbase + kColW, mnmajor(Ft, KZ), bl, kRows, idw, true);
+        tc::mma_commit(bar);
+      }
+      // dW2 = sum over the rows of gd (x) relu(z), db2 = sum of gd: this
+      // warp's 32 rows reduced by shuffles while the MMAs run (z stays in
+      // TMEM columns 0..63)
+#pragma unroll 1
+      for (int q = 0; q < 6; ++q) {
+        const int cq = q >> 1, j0 = (q & 1) * 32;
+        float v[32];
+        float zz[16];
+        tc::tmem_ld16(trow + kColZ + j0, zz);
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) v[jj] = gd[cq] * fmaxf(zz[jj], 0.0f);
+        tc::tmem_ld16(trow + kColZ + j0 + 16, zz);
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) v[16 + jj] = gd[cq] * fmaxf(zz[jj], 0.0f);
+        accw[q] += warp_reduce_scatter32(v, lane);
+      }
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) {
+        float t = gd[cc];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        accb[cc] += t;
+      }
+      ok = tc::mbar_wait(bar, phase, fused::kWaitIters);
+      phase ^= 1u;
+      if (tc::named_sync_any(1, kRows, !ok)) {
+        *abort_flag = 1;
+        break;
+      }
+      tc::fence_after_sync();
+      had_tile = true;
+      // publish dL/df to the stage, transposed [Dp][128]
+      float* dst = stage_df(s);
+      for (int c = 0; c < Dp / 16; ++c) {
+        float t[16];
+        tc::tmem_ld16(trow + kColDF + 16 * c, t);
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) dst[(16 * c + jj) * kRows + r] = t[jj];
+      }
+      tc::fence_before_sync();
+      tc::mbar_arrive(tc::smem_addr(&dfull[s]));
+    }
+    // flush: dW1 rows from TMEM lanes (hi rows r < D, lo rows Dp + 16 + k,
+    // the ones row Dp = db1), dW2 and db2 from the per-warp sums
+    tc::named_sync(1, kRows);
+    tc::fence_after_sync();
+    if (had_tile && *abort_flag == 0) {
+      const uint32_t trow2 = trow;
+      const int col = r < D ? r : (r >= Dp + 16 && r < Dp + 16 + D ? r - Dp - 16 : -1);
+#pragma unroll 1
+      for (int c = 0; c < H / 16; ++c) {
+        float v[16];
+        tc::tmem_ld16(trow2 + kColW + 16 * c, v);
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+          const int jn = 16 * c + jj;
+          if (col >= 0 && v[jj] != 0.f) atomicAdd(gW1 + jn * D + col, v[jj]);
+          else if (r == Dp && v[jj] != 0.f) atomicAdd(gb1 + jn, v[jj]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 6; ++q)
+        if (accw[q] != 0.f) atomicAdd(gW2 + 32 * q + (int)lane, accw[q]);
+      if (lane == 0)
+        for (int cc = 0; cc < 3; ++cc)
+          if (accb[cc] != 0.f) atomicAdd(gb2 + cc, accb[cc]);
+    }
+  } else {
+    // -------------------------------------------------------- worker groups
+    const int w = tid / kRows - 1;
+    const uint32_t xb = lane & 1u;
+    const unsigned int pm = 3u << (lane & 30u);
+    const TT* table = static_cast<const TT*>(a.table);
+    uint8_t* Ft = stage_f(w);
+    const float* dfs = stage_df(w);
+    for (long long j = w; j < my_tiles; j += kWorkers) {
+      const uint32_t round = (uint32_t)(j / kWorkers);
+      const long long i = (blockIdx.x + j * gridDim.x) * kRows + r;
+      const bool valid = i < a.n;
+      float3 p = make_float3(0.f, 0.f, 0.f);
+      if (valid) p = make_float3(clamp01(__ldg(a.x + i)), clamp01(__ldg(a.y + i)), clamp01(__ldg(a.z + i)));
+      float3 pa = p, pb = p;
+      bool live = valid;
+      if constexpr (F == 2) {
+        const float3 q = make_float3(__shfl_xor_sync(pm, p.x, 1), __shfl_xor_sync(pm, p.y, 1),
+                                     __shfl_xor_sync(pm, p.z, 1));
+        pa = xb ? q : p;
+        pb = xb ? p : q;
+        live = __shfl_xor_sync(pm, valid ? 1 : 0, 1) != 0 || valid;
+      }
+      // f = G_3D(p) into the stage's F tile, 8 features at a time
+      constexpr int kLevelsPerChunk = 8 / F;
+      for (int c = 0; c < Dp / 8; ++c) {
+        float v[8];
+#pragma unroll
+        for (int jl = 0; jl < kLevelsPerChunk; ++jl) {
+          const int l = c * kLevelsPerChunk + jl;
+          float acc[F];
+#pragma unroll
+          for (int f = 0; f < F; ++f) acc[f] = 0.0f;
+          if constexpr (F == 2) {
+            if (live && l < a.g.L) {
+              gather2_level3_paired<TT>(a.g, l, pa, pb, xb, table + a.g.offset[l] * 2, pm, acc);
+              if (!valid) acc[0] = acc[1] = 0.0f;
+            }
+          } else {
+            if (valid && l < a.g.L) {
+              uint32_t idx[8];
+              float wt[8];
+              level_corners3(a.g, l, p, idx, wt);
+              const TT* base = table + a.g.offset[l] * F;
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                float e[F];
+                load_entry<TT, F>(base + (size_t)idx[q] * F, e);
+#pragma unroll
+                for (int f = 0; f < F; ++f) acc[f] = fmaf(wt[q], e[f], acc[f]);
+              }
+            }
+          }
+#pragma unroll
+          for (int f = 0; f < F; ++f) v[jl * F + f] = acc[f];
+        }
+        uint4 hi, lo;
+        split_hi_lo8(v, hi, lo);
+        *reinterpret_cast<uint4*>(Ft + tile_off(r, 8 * c, KZ)) = hi;
+        *reinterpret_cast<uint4*>(Ft + tile_off(r, Dp + 16 + 8 * c, KZ)) = lo;
+      }
+      fused::write_ones(Ft, r, Dp, KZ);
+      tc::fence_async_smem();
+      tc::mbar_arrive(tc::smem_addr(&ffull[w]));
+      if (!tc::mbar_wait(tc::smem_addr(&dfull[w]), round & 1u, fused::kWaitIters)) {
+        atomicOr(a.flags, 1u);
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      // dL/df of this tile into the tables
+      if constexpr (F == 2) {
+        const long long ia0 = i - (r & 1);  // the pair's even row; both lanes agree on ia0 < n
+        if (ia0 < a.n) {
+          for (int l = 0; l < a.g.L; ++l) {
+            const float2 f0 = *reinterpret_cast<const float2*>(dfs + (2 * l) * kRows + (r & ~1));      // (A, B)
+            const float2 f1 = *reinterpret_cast<const float2*>(dfs + (2 * l + 1) * kRows + (r & ~1));  // (A, B)
+            scatter2_level3_paired(a.g, l, pa, pb, xb, true, ia0 + 1 < a.n, a.table_grad + a.g.offset[l] * 2,
+                                   f0.x, f1.x, f0.y, f1.y);
+          }
+        }
+      } else {
+        if (valid) {
+          for (int l = 0; l < a.g.L; ++l) {
+            float d[F];
+#pragma unroll
+            for (int f = 0; f < F; ++f) d[f] = dfs[(l * F + f) * kRows + r];
+            uint32_t idx[8];
+            float wt[8];
+            level_corners3(a.g, l, p, idx, wt);
+            float* gbase = a.table_grad + a.g.offset[l] * F;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              float* e = gbase + (size_t)idx[q] * F;
+              if constexpr (F == 1) {
+                atomicAdd(e, wt[q] * d[0]);
+              } else {
+#pragma unroll
+                for (int f = 0; f < F; f += 4)
+                  red_add_v4(e + f, wt[q] * d[f], wt[q] * d[f + 1], wt[q] * d[f + 2], wt[q] * d[f + 3]);
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+  if (*abort_flag) atomicOr(a.flags, 1u);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (tid < 32) tc::tmem_dealloc(tbase, kCols);
+}
+
+}  // namespace dtc
+
 }  // namespace
+
+namespace fused {
+unsigned int* decomp_flags_ptr() {
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, dtc::g_decomp_flags) != cudaSuccess) return nullptr;
+  return static_cast<unsigned int*>(p);
+}
+}  // namespace fused
 }  // namespace dash
 
 extern "C" {
@@ -707,6 +1153,64 @@ int dash_decomp_bwd(const dash_layout* layout, const float* x, const float* y, c
     blocks = blocks < cap ? blocks : cap;
     count_static_kernel<<<(unsigned)blocks, kThreads, 0, st>>>(a.mask, n, static_cast<unsigned long long*>(ws));
     if (int s = launch_status("count_static_kernel")) return s;
+  }
+  const int Dp = fused::pad16(D);
+  if (Dp <= dtc::kMaxDp && g_opt_decomp_bwd_form == 0) {
+    // phi_p's contractions on the tensor cores (dtc::decomp_bwd_ws_kernel)
+    dtc::Args b;
+    b.g = a.g;
+    b.x = x, b.y = y, b.z = z, b.n = n;
+    b.table = table;
+    b.params = mlp->params;
+    b.D = D, b.Dp = Dp;
+    b.d_dp = d_dp;
+    b.mask = a.mask;
+    b.lambda_s = lambda_s;
+    b.n_static = a.n_static;
+    b.table_grad = table_grad;
+    b.mlp_grad = mlp_grad;
+    b.flags = fused::decomp_flags_ptr();
+    if (b.flags == nullptr) return fail(DASH_ERR_CUDA, "cannot resolve the device flag word");
+    const uint32_t KZ = 2 * Dp + 16, KL = Dp + 16;
+    auto al = [](uint32_t v) { return (v + 127u) & ~127u; };
+    b.off_w1lo = al(64u * KZ * 2u);
+    b.off_w2 = al(b.off_w1lo + 64u * KL * 2u);
+    b.off_dz = al(b.off_w2 + (3u * 64u + 3u) * 4u);
+    b.off_stage = al(b.off_dz + (uint32_t)fused::kRows * 128u * 2u);
+    b.off_df = al((uint32_t)fused::kRows * KZ * 2u);  // the stage's dL/df block right after its F tile
+    b.stage_bytes = al(b.off_df + (uint32_t)Dp * fused::kRows * 4u);
+    b.off_bar = al(b.off_stage + (uint32_t)dtc::kWorkers * b.stage_bytes);
+    const size_t tsmem = b.off_bar + 8u * (2u * dtc::kWorkers + 1u) + 16u;
+    const long long ntiles_tc = (n + fused::kRows - 1) / fused::kRows;
+    long long grid_tc = sm_count();
+    grid_tc = ntiles_tc < grid_tc ? ntiles_tc : grid_tc;
+#define DASH_DECOMP_BWD_TC(TT, FF)                                                                                   \
+  {                                                                                                                  \
+    auto kern = dtc::decomp_bwd_ws_kernel<TT, FF>;                                                                   \
+    if (int s = cuda_status(DASH_RT(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem)), \
+                            "cudaFuncSetAttribute(decomp_bwd_ws)"))                                                  \
+      return s;                                                                                                      \
+    kern<<<(unsigned)grid_tc, dtc::kThreadsWs, tsmem, st>>>(b);                                                      \
+  }
+    if (table_dtype == DASH_F16) {
+      switch (a.g.F) {
+        case 1: DASH_DECOMP_BWD_TC(__half, 1) break;
+        case 2: DASH_DECOMP_BWD_TC(__half, 2) break;
+        case 4: DASH_DECOMP_BWD_TC(__half, 4) break;
+        default: DASH_DECOMP_BWD_TC(__half, 8) break;
+      }
+    } else if (table_dtype == DASH_F32) {
+      switch (a.g.F) {
+        case 1: DASH_DECOMP_BWD_TC(float, 1) break;
+        case 2: DASH_DECOMP_BWD_TC(float, 2) break;
+        case 4: DASH_DECOMP_BWD_TC(float, 4) break;
+        default: DASH_DECOMP_BWD_TC(float, 8) break;
+      }
+    } else {
+      return fail(DASH_ERR_UNSUPPORTED, "table_dtype %d (F32 or F16)", table_dtype);
+    }
+#undef DASH_DECOMP_BWD_TC
+    return launch_status("decomp_bwd_ws_kernel");
   }
   const size_t smem = sizeof(float) * ((size_t)kHidden3 * D + kHidden3 + 3 * kHidden3 + 4 +
                                        (size_t)kBwdRows * ((D + 4) + 2 * (kHidden3 + 1) + 4));

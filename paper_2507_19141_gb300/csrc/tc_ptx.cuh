@@ -118,5 +118,18 @@ __device__ __forceinline__ void named_sync(uint32_t id, uint32_t count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
+// Named barrier over `count` threads that also ORs a predicate across them:
+// every thread gets the same answer (a uniform decision, e.g. to stop).
+__device__ __forceinline__ bool named_sync_any(uint32_t id, uint32_t count, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n.reg .pred pi, po;\nsetp.ne.u32 pi, %1, 0;\nbarrier.cta.red.or.pred po, %2, %3, pi;\n"
+      "selp.u32 %0, 1, 0, po;\n}"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(id), "r"(count)
+      : "memory");
+  return r != 0u;
+}
+
 }  // namespace tc
 }  // namespace dash

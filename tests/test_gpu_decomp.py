@@ -8,7 +8,7 @@ import torch
 
 import oracle
 from paper_2507_19141_gb300 import synth
-from gpu_helpers import rel_err, to_dev
+from gpu_helpers import RELU_MARGIN, rel_err, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -22,6 +22,28 @@ def _decomp_inputs(rng, n, tdtype=np.float16):
     D, H = 32, 64
     params = rng.uniform(-1 / np.sqrt(D), 1 / np.sqrt(D), H * D + H + 3 * H + 3).astype(np.float32)
     return g, (x, y, z), table, params
+
+
+def _unambiguous(g, x, y, z, table, params, D, margin=RELU_MARGIN):
+    """Per Gaussian: True where every hidden pre-activation of phi_p (on the
+    oracle's FP64 G_3D encoding, a plain matrix product) is at least
+    `margin` from 0, so the GPU and the oracle take the same ReLU decisions
+    (the tensor-core backward forms them from hi + lo BF16 splits)."""
+    f = oracle.encode3(g, x, y, z, np.asarray(table, np.float64))
+    p = np.asarray(params, np.float64)
+    W1, b1 = p[:64 * D].reshape(64, D), p[64 * D:64 * D + 64]
+    return (np.abs(f @ W1.T + b1) >= margin).all(axis=1)
+
+
+def _clear_ambiguous(keep, d_dp, mask):
+    """Gaussians whose ReLU decisions are ambiguous get no upstream gradient
+    and are made dynamic (no Eq. 5 term), on both sides."""
+    d_dp[:, ~keep] = 0.0
+    if mask is not None:
+        m = mask.cpu().numpy().copy()
+        m[~keep] = 1
+        mask = to_dev(m)
+    return d_dp, mask
 
 
 @pytest.mark.parametrize("tdtype", [np.float16, np.float32])
@@ -165,6 +187,7 @@ def test_decomposition_backward_matches_oracle(dashlib, tdtype, with_up, with_ls
     _, norm = dashlib.dash_decomp_fwd(lay, xd, yd, zd, td, mlp)
     mask, _ = dashlib.dash_topk_mask(norm, 40.0)
     d_dp = rng.standard_normal((3, n)).astype(np.float32)
+    d_dp, mask = _clear_ambiguous(_unambiguous(g, x, y, z, table, params, 32), d_dp, mask)
     tg = torch.zeros((g.total, 2), device="cuda")
     pg = torch.zeros(params.size, device="cuda")
     dashlib.dash_decomp_bwd(lay, xd, yd, zd, td, mlp, tg, pg, d_dp=to_dev(d_dp) if with_up else None,
@@ -197,6 +220,7 @@ def test_decomposition_backward_feature_widths(dashlib, L, F, tdtype, n):
     _, norm = dashlib.dash_decomp_fwd(lay, xd, yd, zd, td, mlp)
     mask, _ = dashlib.dash_topk_mask(norm, 30.0)
     d_dp = rng.standard_normal((3, n)).astype(np.float32)
+    d_dp, mask = _clear_ambiguous(_unambiguous(g, x, y, z, table, params, D), d_dp, mask)
     tg = torch.zeros((g.total, F), device="cuda")
     pg = torch.zeros(params.size, device="cuda")
     dashlib.dash_decomp_bwd(lay, xd, yd, zd, td, mlp, tg, pg, d_dp=to_dev(d_dp), mask=mask, lambda_s=0.5)
@@ -207,3 +231,43 @@ def test_decomposition_backward_feature_widths(dashlib, L, F, tdtype, n):
     pgn = pg.cpu().numpy()
     for a, b in zip(bounds[:-1], bounds[1:]):
         assert rel_err(pgn[a:b], rpg[a:b]) < 1e-4, (a, b, rel_err(pgn[a:b], rpg[a:b]))
+
+
+@pytest.mark.parametrize("n,F,tdtype", [(30_001, 2, np.float16), (4_097, 1, np.float32), (129, 4, np.float16)])
+def test_decomposition_backward_forms_agree(dashlib, n, F, tdtype):
+    """The tensor-core backward (default) and the CUDA-core one give the
+    same gradients up to rounding, and both match the oracle."""
+    rng = np.random.default_rng(95 + n)
+    L = 32 // F
+    cfg = dict(L=L, F=F, log2_T=17, nmin=16, nmax=1024)
+    g = oracle.layout3(**cfg)
+    x, y, z, _ = synth.scene_coords(rng, n)
+    table = synth.table_values(rng, g.total, F, tdtype)
+    params = rng.uniform(-1 / np.sqrt(32), 1 / np.sqrt(32), 64 * 32 + 64 + 3 * 64 + 3).astype(np.float32)
+    lay = dashlib.dash_hash3d_layout(**cfg)
+    mlp = dashlib.Mlp(to_dev(params), 32, 64, 3)
+    xd, yd, zd, td = to_dev(x), to_dev(y), to_dev(z), to_dev(table)
+    _, norm = dashlib.dash_decomp_fwd(lay, xd, yd, zd, td, mlp)
+    mask, _ = dashlib.dash_topk_mask(norm, 45.0)
+    d_dp = rng.standard_normal((3, n)).astype(np.float32)
+    d_dp, mask = _clear_ambiguous(_unambiguous(g, x, y, z, table, params, 32), d_dp, mask)
+    out = []
+    old = dashlib.dash_get_option(dashlib.OPT_DECOMP_BWD_FORM)
+    try:
+        for form in (0, 1):
+            dashlib.dash_set_option(dashlib.OPT_DECOMP_BWD_FORM, form)
+            tg = torch.zeros((g.total, F), device="cuda")
+            pg = torch.zeros(params.size, device="cuda")
+            dashlib.dash_decomp_bwd(lay, xd, yd, zd, td, mlp, tg, pg, d_dp=to_dev(d_dp), mask=mask, lambda_s=0.6)
+            out.append((tg.cpu().numpy(), pg.cpu().numpy()))
+    finally:
+        dashlib.dash_set_option(dashlib.OPT_DECOMP_BWD_FORM, old)
+    dashlib.dash_device_status()
+    rtg, rpg = oracle.decomp_bwd(g, x, y, z, table.astype(np.float64), 64, params.astype(np.float64),
+                                 d_dp.astype(np.float64), mask.cpu().numpy(), 0.6)
+    bounds = np.cumsum([0, 64 * 32, 64, 3 * 64, 3])
+    for tg, pg in out:
+        assert rel_err(tg, rtg) < 1e-4
+        for a, b in zip(bounds[:-1], bounds[1:]):
+            assert rel_err(pg[a:b], rpg[a:b]) < 1e-4, (a, b, rel_err(pg[a:b], rpg[a:b]))
+    assert rel_err(out[0][0], out[1][0]) < 1e-4 and rel_err(out[0][1], out[1][1]) < 1e-4
