@@ -225,9 +225,10 @@ int64_t dash_debug_cuda_call_count(void);
  * (levels 0 and 1 at the paper shape) that dash_deform_mlp_bwd uses when it
  * is given a workspace (see there); 0 or 1 = none.  It sizes
  * dash_deform_bwd_workspace_size, so set it before sizing.
- * DASH_OPT_DECOMP_BWD_FORM (0 or 1, default 0): dash_decomp_bwd runs phi_p's
- * three contractions on the tensor cores (0; for L*F <= 48) or on the CUDA
- * cores (1; always for L*F > 48).  Same gradients up to rounding.
+ * DASH_OPT_DECOMP_FORM (0 or 1, default 0): dash_decomp_fwd and
+ * dash_decomp_bwd run phi_p's contractions on the tensor cores (0; the
+ * backward for L*F <= 48) or on the CUDA cores (1; the backward always for
+ * L*F > 48).  Same results up to rounding.
  * dash_get_option returns the current value (negative status for an
  * unknown option). */
 enum dash_option {
@@ -235,7 +236,7 @@ enum dash_option {
   DASH_OPT_BWD_FORM = 2,
   DASH_OPT_ACCESS_FORM = 3,
   DASH_OPT_GRAD_REPLICAS = 4,
-  DASH_OPT_DECOMP_BWD_FORM = 5
+  DASH_OPT_DECOMP_FORM = 5
 };
 int dash_set_option(int option, int value);
 int dash_get_option(int option);

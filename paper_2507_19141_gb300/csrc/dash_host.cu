@@ -17,7 +17,7 @@ int g_opt_fwd_form = 0;
 int g_opt_bwd_form = 0;
 int g_opt_access_form = 0;
 int g_opt_grad_replicas = 16;
-int g_opt_decomp_bwd_form = 0;
+int g_opt_decomp_form = 0;
 
 void set_error(const char* fmt, ...) {
   va_list ap;
@@ -173,10 +173,10 @@ int dash_set_option(int option, int value) {
         return dash::fail(DASH_ERR_INVALID_ARG, "gradient replicas %d not in [0, 64]", value);
       dash::g_opt_grad_replicas = value;
       return DASH_OK;
-    case DASH_OPT_DECOMP_BWD_FORM:
+    case DASH_OPT_DECOMP_FORM:
       if (!(value == 0 || value == 1))
-        return dash::fail(DASH_ERR_INVALID_ARG, "decomposition backward form %d not in {0, 1}", value);
-      dash::g_opt_decomp_bwd_form = value;
+        return dash::fail(DASH_ERR_INVALID_ARG, "decomposition form %d not in {0, 1}", value);
+      dash::g_opt_decomp_form = value;
       return DASH_OK;
     default: return dash::fail(DASH_ERR_INVALID_ARG, "unknown option %d", option);
   }
@@ -208,7 +208,7 @@ int dash_get_option(int option) {
     case DASH_OPT_BWD_FORM: return dash::g_opt_bwd_form;
     case DASH_OPT_ACCESS_FORM: return dash::g_opt_access_form;
     case DASH_OPT_GRAD_REPLICAS: return dash::g_opt_grad_replicas;
-    case DASH_OPT_DECOMP_BWD_FORM: return dash::g_opt_decomp_bwd_form;
+    case DASH_OPT_DECOMP_FORM: return dash::g_opt_decomp_form;
     default: return dash::fail(DASH_ERR_INVALID_ARG, "unknown option %d", option);
   }
 }

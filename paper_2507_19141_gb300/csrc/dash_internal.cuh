@@ -49,7 +49,7 @@ extern int g_opt_fwd_form;
 extern int g_opt_bwd_form;
 extern int g_opt_access_form;
 extern int g_opt_grad_replicas;
-extern int g_opt_decomp_bwd_form;
+extern int g_opt_decomp_form;
 
 // ------------------------------------------------ kernel-side geometry ----
 // Level layout in the form the kernels read it (by-value kernel argument).

@@ -1007,6 +1007,291 @@ __global__ void __launch_bounds__(kThreadsWs, 1) decomp_bwd_ws_kernel(const __gr
 
 }  // namespace dtc
 
+// ---------------------------------------------- forward on the tensor cores --
+// phi_p of the decomposition forward on tcgen05, warp-specialised like the
+// backward: worker groups gather G_3D into F tiles, one decoder group (TMEM
+// lanes) forms z = W1 f + b1 and the outputs.  To keep Delta p at FP32
+// accuracy each operand is split into three BF16 parts (a = a1 + a2 + a3,
+// exact for FP32) and the products of total order at most 2 are kept:
+//   chain 1  [f1 | 1 1 1 | f2 | f3] x [W1 | b1 b2 b3 | W1 | W1]
+//   chain 2  [f1 | 1 0 0 | f2]      x [W2 | 0 0 0    | W2]
+//   chain 3  [f1]                   x [W3]
+// (f2 W3, f3 W2, f3 W3 dropped: relative 2^-24).  Then on the CUDA cores:
+// h = relu(z), Delta p = W2 h + b2, |Delta p| and Eq. 4's p(t).  Worker w
+// owns stage w; the decoder releases a stage with tcgen05.commit once the
+// z MMA has read it.
+namespace dfw {
+
+using fused::kRows;
+using fused::tile_off;
+constexpr int kWorkers = 3;
+constexpr int kThreadsWs = (kWorkers + 1) * kRows;
+constexpr uint32_t kCols = 64;  // z
+constexpr int kMaxDp = 48;
+
+struct Args {
+  Geom g;
+  const float* x;
+  const float* y;
+  const float* z;
+  long long n;
+  const void* table;
+  const float* params;
+  int D, Dp;
+  float* dp_out;
+  float* norm_out;
+  const float* ts;
+  long long t_stride;
+  float* pt_out;
+  unsigned int* flags;
+  uint32_t off_wb, off_wc, off_w2, off_stage, stage_bytes, off_bar;
+};
+
+// v = v1 + v2 + v3 in BF16 (exact for FP32 up to the last bits of v3).
+__device__ __forceinline__ void split3(float v, float& a1, float& a2, float& a3) {
+  a1 = dtc::bf16_round(v);
+  const float r1 = v - a1;
+  a2 = dtc::bf16_round(r1);
+  a3 = dtc::bf16_round(r1 - a2);
+}
+
+__device__ __forceinline__ uint32_t pack2(float a, float b) { return fused::pack_bf16x2(a, b); }
+
+template <typename TT, int F>
+__global__ void __launch_bounds__(kThreadsWs, 1) decomp_fwd_ws_kernel(const __grid_constant__ Args a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int tid = threadIdx.x;
+  const int D = a.D, Dp = a.Dp;
+  const int KA = 3 * Dp + 16, KB = 2 * Dp + 16, KC = Dp;
+  constexpr int H = kHidden3;
+  uint8_t* wa = smem;                                      // [64][KA]
+  uint8_t* wb = smem + a.off_wb;                           // [64][KB]
+  uint8_t* wc = smem + a.off_wc;                           // [64][KC]
+  float* W2s = reinterpret_cast<float*>(smem + a.off_w2);  // W2 [3][64], b2 [3]
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + a.off_bar);
+  uint64_t* empty = full + kWorkers;
+  uint64_t* mma_bar = empty + kWorkers;
+  volatile uint32_t* holder = reinterpret_cast<volatile uint32_t*>(mma_bar + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(mma_bar + 1) + 1;
+  auto stage = [&](int s) { return smem + a.off_stage + (size_t)s * a.stage_bytes; };
+
+  // weight tiles from W1 [64][D], b1 [64]
+  const float* W1 = a.params;
+  const float* b1 = W1 + H * D;
+  for (int e = tid; e < H * KA; e += kThreadsWs) {
+    const int nn = e / KA, k = e % KA;
+    float v = 0.0f;
+    if (k < D) {
+      v = W1[nn * D + k];
+      float p1, p2, p3;
+      split3(v, p1, p2, p3);
+      v = p1;
+    } else if (k >= Dp && k < Dp + 3) {
+      float p[3];
+      split3(b1[nn], p[0], p[1], p[2]);
+      v = p[k - Dp];
+    } else if (k >= Dp + 16 && k < Dp + 16 + D) {
+      float p1, p2, p3;
+      split3(W1[nn * D + (k - Dp - 16)], p1, p2, p3);
+      v = p1;
+    } else if (k >= 2 * Dp + 16 && k < 2 * Dp + 16 + D) {
+      float p1, p2, p3;
+      split3(W1[nn * D + (k - 2 * Dp - 16)], p1, p2, p3);
+      v = p1;
+    }
+    *reinterpret_cast<uint16_t*>(wa + tile_off(nn, k, KA)) = dtc::bf16_bits(v);
+  }
+  for (int e = tid; e < H * KB; e += kThreadsWs) {
+    const int nn = e / KB, k = e % KB;
+    float v = 0.0f, p1, p2, p3;
+    if (k < D) {
+      split3(W1[nn * D + k], p1, p2, p3);
+      v = p2;
+    } else if (k >= Dp + 16 && k < Dp + 16 + D) {
+      split3(W1[nn * D + (k - Dp - 16)], p1, p2, p3);
+      v = p2;
+    }
+    *reinterpret_cast<uint16_t*>(wb + tile_off(nn, k, KB)) = dtc::bf16_bits(v);
+  }
+  for (int e = tid; e < H * KC; e += kThreadsWs) {
+    const int nn = e / KC, k = e % KC;
+    float v = 0.0f, p1, p2, p3;
+    if (k < D) {
+      split3(W1[nn * D + k], p1, p2, p3);
+      v = p3;
+    }
+    *reinterpret_cast<uint16_t*>(wc + tile_off(nn, k, KC)) = dtc::bf16_bits(v);
+  }
+  for (int e = tid; e < 3 * H + 3; e += kThreadsWs) W2s[e] = b1[H + e];
+  if (tid == 0) {
+    for (int s = 0; s < kWorkers; ++s) {
+      tc::mbar_init(tc::smem_addr(&full[s]), kRows);
+      tc::mbar_init(tc::smem_addr(&empty[s]), 1);
+    }
+    tc::mbar_init(tc::smem_addr(mma_bar), 1);
+    tc::mbar_init_fence();
+    *abort_flag = 0;
+  }
+  if (tid < 32) tc::tmem_alloc(tc::smem_addr(const_cast<uint32_t*>(holder)), kCols);
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *holder;
+  const long long ntiles = (a.n + kRows - 1) / kRows;
+  const long long my_tiles = ntiles > blockIdx.x ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const int r = tid % kRows;
+  const uint32_t lane = (uint32_t)(r & 31);
+
+  if (tid < kRows) {
+    // ------------------------------------------------------- decoder group
+    const uint32_t trow = tbase + ((uint32_t)((r >> 5) * 32) << 16);
+    const uint32_t bar = tc::smem_addr(mma_bar);
+    uint32_t phase = 0;
+    const uint32_t idz = tc::idesc_bf16(kRows, H, 0, 0);
+    for (long long j = 0; j < my_tiles; ++j) {
+      const int s = (int)(j % kWorkers);
+      const uint32_t round = (uint32_t)(j / kWorkers);
+      const long long i = (blockIdx.x + j * gridDim.x) * kRows + r;
+      bool ok = tc::mbar_wait(tc::smem_addr(&full[s]), round & 1u, fused::kWaitIters);
+      if (tc::named_sync_any(1, kRows, !ok || *abort_flag)) {
+        *abort_flag = 1;
+        break;
+      }
+      tc::fence_after_sync();
+      if (r == 0) {
+        uint8_t* Ft = stage(s);
+        using fused::bwdk::issue;
+        using fused::bwdk::kmajor;
+        issue(tbase, kmajor(Ft, KA), kmajor(wa, KA), KA, idz, false);
+        issue(tbase, kmajor(Ft, KA), kmajor(wb, KB), KB, idz, true);
+        issue(tbase, kmajor(Ft, KA), kmajor(wc, KC), KC, idz, true);
+        tc::mma_commit(bar);
+        tc::mma_commit(tc::smem_addr(&empty[s]));  // the stage is free once these have read it
+      }
+      ok = tc::mbar_wait(bar, phase, fused::kWaitIters);
+      phase ^= 1u;
+      if (tc::named_sync_any(1, kRows, !ok)) {
+        *abort_flag = 1;
+        break;
+      }
+      tc::fence_after_sync();
+      float dp[3] = {W2s[3 * H], W2s[3 * H + 1], W2s[3 * H + 2]};
+#pragma unroll
+      for (int c = 0; c < H / 16; ++c) {
+        float zz[16];
+        tc::tmem_ld16(trow + 16 * c, zz);
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+          const float h = fmaxf(zz[jj], 0.0f);
+#pragma unroll
+          for (int cc = 0; cc < 3; ++cc) dp[cc] = fmaf(W2s[cc * H + 16 * c + jj], h, dp[cc]);
+        }
+      }
+      tc::fence_before_sync();
+      if (i < a.n) {
+        float s2 = 0.0f;
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+          if (a.dp_out != nullptr) __stcs(a.dp_out + (long long)cc * a.n + i, dp[cc]);
+          s2 = fmaf(dp[cc], dp[cc], s2);
+        }
+        __stcs(a.norm_out + i, sqrtf(s2));
+        if (a.pt_out != nullptr) {  // Eq. 4: p(t) = p + t dp, p as given
+          const float t = __ldg(a.ts + i * a.t_stride);
+          __stcs(a.pt_out + i, fmaf(t, dp[0], __ldg(a.x + i)));
+          __stcs(a.pt_out + a.n + i, fmaf(t, dp[1], __ldg(a.y + i)));
+          __stcs(a.pt_out + 2 * a.n + i, fmaf(t, dp[2], __ldg(a.z + i)));
+        }
+      }
+    }
+  } else {
+    // -------------------------------------------------------- worker groups
+    const int w = tid / kRows - 1;
+    const uint32_t xb = lane & 1u;
+    const unsigned int pm = 3u << (lane & 30u);
+    const TT* table = static_cast<const TT*>(a.table);
+    uint8_t* Ft = stage(w);
+    for (long long j = w; j < my_tiles; j += kWorkers) {
+      const uint32_t round = (uint32_t)(j / kWorkers);
+      // the decoder's MMAs of this stage's previous tile have read it
+      if (!tc::mbar_wait(tc::smem_addr(&empty[w]), (round & 1u) ^ 1u, fused::kWaitIters)) {
+        atomicOr(a.flags, 1u);
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      const long long i = (blockIdx.x + j * gridDim.x) * kRows + r;
+      const bool valid = i < a.n;
+      float3 p = make_float3(0.f, 0.f, 0.f);
+      if (valid) p = make_float3(clamp01(__ldcs(a.x + i)), clamp01(__ldcs(a.y + i)), clamp01(__ldcs(a.z + i)));
+      float3 pa = p, pb = p;
+      bool live = valid;
+      if constexpr (F == 2) {
+        const float3 q = make_float3(__shfl_xor_sync(pm, p.x, 1), __shfl_xor_sync(pm, p.y, 1),
+                                     __shfl_xor_sync(pm, p.z, 1));
+        pa = xb ? q : p;
+        pb = xb ? p : q;
+        live = __shfl_xor_sync(pm, valid ? 1 : 0, 1) != 0 || valid;
+      }
+      constexpr int kLevelsPerChunk = 8 / F;
+      for (int c = 0; c < Dp / 8; ++c) {
+        float v[8];
+#pragma unroll
+        for (int jl = 0; jl < kLevelsPerChunk; ++jl) {
+          const int l = c * kLevelsPerChunk + jl;
+          float acc[F];
+#pragma unroll
+          for (int f = 0; f < F; ++f) acc[f] = 0.0f;
+          if constexpr (F == 2) {
+            if (live && l < a.g.L) {
+              gather2_level3_paired<TT>(a.g, l, pa, pb, xb, table + a.g.offset[l] * 2, pm, acc);
+              if (!valid) acc[0] = acc[1] = 0.0f;
+            }
+          } else {
+            if (valid && l < a.g.L) {
+              uint32_t idx[8];
+              float wt[8];
+              level_corners3(a.g, l, p, idx, wt);
+              const TT* base = table + a.g.offset[l] * F;
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                float e[F];
+                load_entry<TT, F>(base + (size_t)idx[q] * F, e);
+#pragma unroll
+                for (int f = 0; f < F; ++f) acc[f] = fmaf(wt[q], e[f], acc[f]);
+              }
+            }
+          }
+#pragma unroll
+          for (int f = 0; f < F; ++f) v[jl * F + f] = acc[f];
+        }
+        float p1[8], p2[8], p3[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) split3(v[q], p1[q], p2[q], p3[q]);
+        *reinterpret_cast<uint4*>(Ft + tile_off(r, 8 * c, KA)) =
+            make_uint4(pack2(p1[0], p1[1]), pack2(p1[2], p1[3]), pack2(p1[4], p1[5]), pack2(p1[6], p1[7]));
+        *reinterpret_cast<uint4*>(Ft + tile_off(r, Dp + 16 + 8 * c, KA)) =
+            make_uint4(pack2(p2[0], p2[1]), pack2(p2[2], p2[3]), pack2(p2[4], p2[5]), pack2(p2[6], p2[7]));
+        *reinterpret_cast<uint4*>(Ft + tile_off(r, 2 * Dp + 16 + 8 * c, KA)) =
+            make_uint4(pack2(p3[0], p3[1]), pack2(p3[2], p3[3]), pack2(p3[4], p3[5]), pack2(p3[6], p3[7]));
+      }
+      // the ones block: 1 at columns Dp, Dp + 1, Dp + 2 (the bias's three parts), 0 to Dp + 15
+      *reinterpret_cast<uint4*>(Ft + tile_off(r, Dp, KA)) = make_uint4(0x3F803F80u, 0x3F80u, 0u, 0u);
+      *reinterpret_cast<uint4*>(Ft + tile_off(r, Dp + 8, KA)) = make_uint4(0u, 0u, 0u, 0u);
+      tc::fence_async_smem();
+      tc::mbar_arrive(tc::smem_addr(&full[w]));
+    }
+  }
+  if (*abort_flag) atomicOr(a.flags, 1u);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (tid < 32) tc::tmem_dealloc(tbase, kCols);
+}
+
+}  // namespace dfw
+
 }  // namespace
 
 namespace fused {
@@ -1082,9 +1367,65 @@ int dash_decomp_fwd(const dash_layout* layout, const float* x, const float* y, c
   if (pt_out != nullptr && (t == nullptr || t_stride < 0 || t_stride > 1))
     return fail(DASH_ERR_INVALID_ARG, "p(t) needs t with t_stride 0 or 1");
   if (n > 0x7FFFFFFFll) return fail(DASH_ERR_UNSUPPORTED, "n=%lld above 2^31 - 1", (long long)n);
+  cudaStream_t st = as_stream(stream);
+  if (g_opt_decomp_form == 0) {
+    // phi_p on the tensor cores (dfw::decomp_fwd_ws_kernel)
+    const int Dp = fused::pad16(D);
+    dfw::Args b;
+    b.g = g;
+    b.x = x, b.y = y, b.z = z, b.n = n;
+    b.table = table;
+    b.params = mlp->params;
+    b.D = D, b.Dp = Dp;
+    b.dp_out = dp_out;
+    b.norm_out = norm_out;
+    b.ts = t;
+    b.t_stride = t_stride;
+    b.pt_out = pt_out;
+    b.flags = fused::decomp_flags_ptr();
+    if (b.flags == nullptr) return fail(DASH_ERR_CUDA, "cannot resolve the device flag word");
+    const uint32_t KA = 3 * Dp + 16, KB = 2 * Dp + 16, KC = Dp;
+    auto al = [](uint32_t v) { return (v + 127u) & ~127u; };
+    b.off_wb = al(64u * KA * 2u);
+    b.off_wc = al(b.off_wb + 64u * KB * 2u);
+    b.off_w2 = al(b.off_wc + 64u * KC * 2u);
+    b.off_stage = al(b.off_w2 + (3u * 64u + 3u) * 4u);
+    b.stage_bytes = al((uint32_t)fused::kRows * KA * 2u);
+    b.off_bar = al(b.off_stage + (uint32_t)dfw::kWorkers * b.stage_bytes);
+    const size_t tsmem = b.off_bar + 8u * (2u * dfw::kWorkers + 1u) + 16u;
+    const long long ntiles_tc = (n + fused::kRows - 1) / fused::kRows;
+    long long grid_tc = sm_count();
+    grid_tc = ntiles_tc < grid_tc ? ntiles_tc : grid_tc;
+#define DASH_DECOMP_FWD_TC(TT, FF)                                                                                   \
+  {                                                                                                                  \
+    auto kern = dfw::decomp_fwd_ws_kernel<TT, FF>;                                                                   \
+    if (int s = cuda_status(DASH_RT(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem)), \
+                            "cudaFuncSetAttribute(decomp_fwd_ws)"))                                                  \
+      return s;                                                                                                      \
+    kern<<<(unsigned)grid_tc, dfw::kThreadsWs, tsmem, st>>>(b);                                                      \
+  }
+    if (table_dtype == DASH_F16) {
+      switch (g.F) {
+        case 1: DASH_DECOMP_FWD_TC(__half, 1) break;
+        case 2: DASH_DECOMP_FWD_TC(__half, 2) break;
+        case 4: DASH_DECOMP_FWD_TC(__half, 4) break;
+        default: DASH_DECOMP_FWD_TC(__half, 8) break;
+      }
+    } else if (table_dtype == DASH_F32) {
+      switch (g.F) {
+        case 1: DASH_DECOMP_FWD_TC(float, 1) break;
+        case 2: DASH_DECOMP_FWD_TC(float, 2) break;
+        case 4: DASH_DECOMP_FWD_TC(float, 4) break;
+        default: DASH_DECOMP_FWD_TC(float, 8) break;
+      }
+    } else {
+      return fail(DASH_ERR_UNSUPPORTED, "table_dtype %d (F32 or F16)", table_dtype);
+    }
+#undef DASH_DECOMP_FWD_TC
+    return launch_status("decomp_fwd_ws_kernel");
+  }
   const size_t smem = sizeof(float) * (size_t)(kHidden3 * D + kHidden3 + 3 * kHidden3 + 3);
   const unsigned grid = (unsigned)((n + kThreads - 1) / kThreads);
-  cudaStream_t st = as_stream(stream);
 #define DASH_DECOMP_LAUNCH(TT, FF)                                                                             \
   decomp_fwd_kernel<TT, FF><<<grid, kThreads, smem, st>>>(g, x, y, z, n, static_cast<const TT*>(table),        \
                                                           mlp->params, D, dp_out, norm_out, t, t_stride, pt_out)
@@ -1155,7 +1496,7 @@ int dash_decomp_bwd(const dash_layout* layout, const float* x, const float* y, c
     if (int s = launch_status("count_static_kernel")) return s;
   }
   const int Dp = fused::pad16(D);
-  if (Dp <= dtc::kMaxDp && g_opt_decomp_bwd_form == 0) {
+  if (Dp <= dtc::kMaxDp && g_opt_decomp_form == 0) {
     // phi_p's contractions on the tensor cores (dtc::decomp_bwd_ws_kernel)
     dtc::Args b;
     b.g = a.g;

@@ -207,7 +207,7 @@ OPT_FWD_FORM = 1
 OPT_BWD_FORM = 2
 OPT_ACCESS_FORM = 3
 OPT_GRAD_REPLICAS = 4
-OPT_DECOMP_BWD_FORM = 5
+OPT_DECOMP_FORM = 5
 
 
 def dash_device_status() -> None:

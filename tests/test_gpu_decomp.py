@@ -252,16 +252,16 @@ def test_decomposition_backward_forms_agree(dashlib, n, F, tdtype):
     d_dp = rng.standard_normal((3, n)).astype(np.float32)
     d_dp, mask = _clear_ambiguous(_unambiguous(g, x, y, z, table, params, 32), d_dp, mask)
     out = []
-    old = dashlib.dash_get_option(dashlib.OPT_DECOMP_BWD_FORM)
+    old = dashlib.dash_get_option(dashlib.OPT_DECOMP_FORM)
     try:
         for form in (0, 1):
-            dashlib.dash_set_option(dashlib.OPT_DECOMP_BWD_FORM, form)
+            dashlib.dash_set_option(dashlib.OPT_DECOMP_FORM, form)
             tg = torch.zeros((g.total, F), device="cuda")
             pg = torch.zeros(params.size, device="cuda")
             dashlib.dash_decomp_bwd(lay, xd, yd, zd, td, mlp, tg, pg, d_dp=to_dev(d_dp), mask=mask, lambda_s=0.6)
             out.append((tg.cpu().numpy(), pg.cpu().numpy()))
     finally:
-        dashlib.dash_set_option(dashlib.OPT_DECOMP_BWD_FORM, old)
+        dashlib.dash_set_option(dashlib.OPT_DECOMP_FORM, old)
     dashlib.dash_device_status()
     rtg, rpg = oracle.decomp_bwd(g, x, y, z, table.astype(np.float64), 64, params.astype(np.float64),
                                  d_dp.astype(np.float64), mask.cpu().numpy(), 0.6)
@@ -271,3 +271,38 @@ def test_decomposition_backward_forms_agree(dashlib, n, F, tdtype):
         for a, b in zip(bounds[:-1], bounds[1:]):
             assert rel_err(pg[a:b], rpg[a:b]) < 1e-4, (a, b, rel_err(pg[a:b], rpg[a:b]))
     assert rel_err(out[0][0], out[1][0]) < 1e-4 and rel_err(out[0][1], out[1][1]) < 1e-4
+
+
+@pytest.mark.parametrize("n,L,F,tdtype", [(20_001, 16, 2, np.float16), (3_000, 32, 1, np.float32),
+                                          (129, 8, 4, np.float16), (1, 4, 8, np.float32)])
+def test_decomposition_forward_forms_agree(dashlib, n, L, F, tdtype):
+    """The tensor-core forward (default; three-part BF16 splits, every
+    product of total order up to 2 kept) and the CUDA-core forward give the
+    same Delta p, norms and Eq. 4 p(t) to FP32 accuracy, and both match the
+    oracle."""
+    rng = np.random.default_rng(120 + n)
+    cfg = dict(L=L, F=F, log2_T=17, nmin=16, nmax=1024)
+    g = oracle.layout3(**cfg)
+    x, y, z, _ = synth.scene_coords(rng, n)
+    t = rng.random(n).astype(np.float32)
+    table = synth.table_values(rng, g.total, F, tdtype)
+    D = L * F
+    params = rng.uniform(-1 / np.sqrt(D), 1 / np.sqrt(D), 64 * D + 64 + 3 * 64 + 3).astype(np.float32)
+    lay = dashlib.dash_hash3d_layout(**cfg)
+    mlp = dashlib.Mlp(to_dev(params), D, 64, 3)
+    out = []
+    old = dashlib.dash_get_option(dashlib.OPT_DECOMP_FORM)
+    try:
+        for form in (0, 1):
+            dashlib.dash_set_option(dashlib.OPT_DECOMP_FORM, form)
+            res = dashlib.dash_decomp_fwd(lay, to_dev(x), to_dev(y), to_dev(z), to_dev(table), mlp, t=to_dev(t))
+            out.append([v.cpu().numpy() for v in res])
+    finally:
+        dashlib.dash_set_option(dashlib.OPT_DECOMP_FORM, old)
+    dashlib.dash_device_status()
+    rdp, rnorm = oracle.decomp_fwd(g, x, y, z, table.astype(np.float64), 64, params.astype(np.float64))
+    for dp, norm, pt in out:
+        assert rel_err(dp, rdp) < 1e-5 and rel_err(norm, rnorm) < 1e-5
+        assert rel_err(pt - np.stack([x, y, z]), t * rdp) < 1e-5
+    for a, b in zip(out[0], out[1]):
+        assert rel_err(a, b) < 1e-5
