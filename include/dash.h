@@ -195,6 +195,18 @@ int dash_probe_rate(int kind, float* buf, size_t buf_bytes, int iters, float* si
 int dash_debug_fail_cuda_call(int64_t n);
 int64_t dash_debug_cuda_call_count(void);
 
+/* Bounds-checked build (libdash_debug.so, compiled with -DDASH_DEBUG): the
+ * point rows the kernels read (dash_points.idx entries, or 0..n-1) are
+ * checked against `rows`, the length of the x, y, z (and per-point t)
+ * arrays, before each access: a row outside [0, rows) sets a device flag,
+ * the access is skipped (the point reads as (0, 0, 0, 0) and its Eq. 10
+ * update is not written), and the next dash_device_status returns
+ * DASH_ERR_BOUNDS.  rows = -1 (the default) turns the check off.  The
+ * release library (libdash.so) compiles no check and returns
+ * DASH_ERR_UNSUPPORTED here.  Process-wide; set it before the launches it
+ * should cover.  The paper has no counterpart. */
+int dash_debug_set_point_rows(int64_t rows);
+
 /* Process-wide kernel-form options (host; take effect at the next launch).
  * DASH_OPT_FWD_FORM selects the fused forward kernel: 0 = warp-specialised
  * (one decoder group fed by gather groups through a shared-memory ring;

@@ -36,25 +36,29 @@ def _deps():
     return _sources() + glob.glob(os.path.join(SRC_DIR, "*.cuh")) + [os.path.join(ROOT, "include", "dash.h")]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+DEBUG_DIR = os.path.join(HERE, "_build_debug")
+DEBUG_LIB = os.path.join(DEBUG_DIR, "libdash_debug.so")
+
+
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def _build_variant(out_dir: str, lib: str, extra: list, verbose: bool, ex) -> list:
+    """Compiles every source into out_dir (through the shared executor) and
+    returns a callable that links them into lib."""
+    os.makedirs(out_dir, exist_ok=True)
     cc = nvcc()
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
-                     "-I" + os.path.join(ROOT, "include"), "-I" + SRC_DIR]
+                     "-I" + os.path.join(ROOT, "include"), "-I" + SRC_DIR] + extra
     if verbose:
         common += ["-Xptxas", "-v"]
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [cc] + common + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -63,15 +67,34 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(r.stderr)
         return obj
 
-    srcs = _sources()
-    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
-        objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs
-    r = subprocess.run(cmd, capture_output=True, text=True)
+    return [ex.submit(compile_one, src) for src in _sources()]
+
+
+def _link(lib: str, futures) -> None:
+    objs = [f.result() for f in futures]
+    tmp = lib + f".tmp{os.getpid()}"
+    r = subprocess.run([nvcc()] + ARCH + ["-shared", "-o", tmp] + objs, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
+
+
+def build(force: bool = False, verbose: bool = False, debug: bool = True) -> str:
+    """Builds libdash.so and, with `debug`, the bounds-checked variant
+    libdash_debug.so (-DDASH_DEBUG: every point-row index is checked before
+    it is used), compiling both sets of translation units in parallel."""
+    todo = []
+    if force or not up_to_date(LIB):
+        todo.append((OUT_DIR, LIB, []))
+    if debug and (force or not up_to_date(DEBUG_LIB)):
+        todo.append((DEBUG_DIR, DEBUG_LIB, ["-DDASH_DEBUG"]))
+    if not todo:
+        return LIB
+    workers = max(1, min(len(_sources()) * len(todo), os.cpu_count() or 4))
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        jobs = [(lib, _build_variant(d, lib, extra, verbose, ex)) for d, lib, extra in todo]
+        for lib, futures in jobs:
+            _link(lib, futures)
     return LIB
 
 

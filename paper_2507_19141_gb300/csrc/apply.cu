@@ -15,6 +15,9 @@ __global__ void __launch_bounds__(kThreads) apply_bwd_kernel(Pts pts, int O, con
   const long long k = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (k >= n) return;
   const long long i = point_row(pts, k);
+#ifdef DASH_DEBUG
+  if (i < 0) return;
+#endif
   for (int j = 0; j < O; ++j) __stcs(ddelta + (long long)j * pts.n + k, __ldg(dattrs + (long long)j * n_all + i));
 }
 

@@ -95,6 +95,16 @@ int make_geom(const dash_layout* lo, Geom* g) {
   return DASH_OK;
 }
 
+// Point-row bounds of DASH_DEBUG builds (dash_debug_set_point_rows).
+static long long g_point_rows = -1;
+__device__ unsigned int g_bounds_flags;
+
+unsigned int* bounds_flags_ptr() {
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_bounds_flags) != cudaSuccess) return nullptr;
+  return static_cast<unsigned int*>(p);
+}
+
 int make_pts(const dash_points* p, Pts* out) {
   if (p == nullptr) return fail(DASH_ERR_INVALID_ARG, "points is NULL");
   if (p->n < 0) return fail(DASH_ERR_INVALID_ARG, "n=%lld < 0", (long long)p->n);
@@ -110,6 +120,15 @@ int make_pts(const dash_points* p, Pts* out) {
   out->idx = p->idx;
   out->n = p->n;
   out->n_dev = reinterpret_cast<const long long*>(p->n_dev);
+  out->rows = -1;
+  out->bounds = nullptr;
+#ifdef DASH_DEBUG
+  if (g_point_rows >= 0) {
+    out->bounds = bounds_flags_ptr();
+    if (out->bounds == nullptr) return fail(DASH_ERR_CUDA, "cannot resolve the bounds flag word");
+    out->rows = g_point_rows;
+  }
+#endif
   return DASH_OK;
 }
 
@@ -149,6 +168,17 @@ int dash_debug_fail_cuda_call(int64_t n) {
 
 int64_t dash_debug_cuda_call_count(void) { return (int64_t)dash::g_rt_calls.load(std::memory_order_relaxed); }
 
+int dash_debug_set_point_rows(int64_t rows) {
+#ifdef DASH_DEBUG
+  if (rows < -1) return dash::fail(DASH_ERR_INVALID_ARG, "rows=%lld < -1", (long long)rows);
+  dash::g_point_rows = rows;
+  return DASH_OK;
+#else
+  (void)rows;
+  return dash::fail(DASH_ERR_UNSUPPORTED, "point-row bounds checks need the DASH_DEBUG build (libdash_debug.so)");
+#endif
+}
+
 int dash_version(void) { return 102; }
 
 int dash_set_option(int option, int value) {
@@ -186,6 +216,17 @@ int dash_device_status(void* stream) {
   DASH_NVTX_RANGE("dash_device_status");
   using namespace dash;
   if (int s = cuda_status(DASH_RT(cudaStreamSynchronize(as_stream(stream))), "cudaStreamSynchronize")) return s;
+  {
+    // a point row out of range (DASH_DEBUG builds) is reported first
+    unsigned int* b = bounds_flags_ptr();
+    if (b == nullptr) return fail(DASH_ERR_CUDA, "cannot resolve the bounds flag word");
+    unsigned int v = 0u;
+    if (int s = cuda_status(DASH_RT(cudaMemcpy(&v, b, sizeof(v), cudaMemcpyDeviceToHost)), "cudaMemcpy(bounds)")) return s;
+    if (v != 0u) {
+      if (int s = cuda_status(DASH_RT(cudaMemset(b, 0, sizeof(v))), "cudaMemset(bounds)")) return s;
+      return fail(DASH_ERR_BOUNDS, "a point row index was outside [0, rows); those points were skipped");
+    }
+  }
   unsigned int* words[5] = {fused::fwd_flags_ptr(), fused::bwd_flags_ptr(), fused::batch_flags_ptr(),
                             fused::selftest_flags_ptr(), fused::decomp_flags_ptr()};
   unsigned int seen = 0u;

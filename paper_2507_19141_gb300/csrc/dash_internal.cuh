@@ -76,9 +76,13 @@ struct Pts {
   const int* idx;
   long long n;
   const long long* n_dev;
+  long long rows;         // DASH_DEBUG builds: point rows must be < rows (-1: unchecked)
+  unsigned int* bounds;   // DASH_DEBUG builds: flag word set by a row index out of range
 };
 
 int make_pts(const dash_points* p, Pts* out);
+// The device word the bounds checks of DASH_DEBUG builds set (dash_host.cu).
+unsigned int* bounds_flags_ptr();
 
 __device__ __forceinline__ long long point_count(const Pts& p) {
   long long n = p.n;
@@ -93,13 +97,26 @@ __device__ __forceinline__ long long point_count(const Pts& p) {
 // Clamp to [0,1]; NaN maps to 0 (fmaxf returns the non-NaN operand).
 __device__ __forceinline__ float clamp01(float v) { return fminf(fmaxf(v, 0.0f), 1.0f); }
 
+// The row of compact point i in the full arrays.  In DASH_DEBUG builds a row
+// outside [0, rows) sets the bounds flag and comes back as -1, and every
+// caller then skips the access (the check runs before it).
 __device__ __forceinline__ long long point_row(const Pts& p, long long i) {
-  return p.idx != nullptr ? (long long)__ldcs(p.idx + i) : i;
+  const long long j = p.idx != nullptr ? (long long)__ldcs(p.idx + i) : i;
+#ifdef DASH_DEBUG
+  if (p.rows >= 0 && (j < 0 || j >= p.rows)) {
+    atomicOr(p.bounds, 1u);
+    return -1;
+  }
+#endif
+  return j;
 }
 
 // Clamped (x, y, z, t) of compact point i.
 __device__ __forceinline__ float4 load_point(const Pts& p, long long i) {
   const long long j = point_row(p, i);
+#ifdef DASH_DEBUG
+  if (j < 0) return make_float4(0.f, 0.f, 0.f, 0.f);
+#endif
   float4 r;
   // coordinates are read once per kernel: streaming loads (evict first)
   r.x = clamp01(__ldcs(p.x + j));
@@ -462,6 +479,9 @@ struct Entry2<float> {
 // 0 outside and for NaN; one entry per axis x, y, z, t of compact point i.
 __device__ __forceinline__ float4 coord_inside(const Pts& p, long long i) {
   const long long j = point_row(p, i);
+#ifdef DASH_DEBUG
+  if (j < 0) return make_float4(0.f, 0.f, 0.f, 0.f);
+#endif
   const float v[4] = {__ldg(p.x + j), __ldg(p.y + j), __ldg(p.z + j),
                       p.t_stride != 0 ? __ldg(p.t + j * p.t_stride) : __ldg(p.t)};
   float m[4];

@@ -143,6 +143,9 @@ __global__ void __launch_bounds__(G * kRows, 1) deform_fwd_kernel(const __grid_c
       for (int j = 0; j < a.O; ++j) a.delta[(long long)j * a.n_cap + row] = o[j];
       if (a.attrs_out != nullptr) {
         const long long gi = point_row(a.pts, row);
+#ifdef DASH_DEBUG
+        if (gi >= 0)
+#endif
         for (int j = 0; j < a.O; ++j)
           a.attrs_out[(long long)j * a.n_all + gi] = a.attrs_in[(long long)j * a.n_all + gi] + o[j];
       }
@@ -293,6 +296,9 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_fwd_ws_kernel(const
         for (int k = 0; k < a.O; ++k) __stcs(a.delta + (long long)k * a.n_cap + row, o[k]);
         if (a.attrs_out != nullptr) {
           const long long gi = point_row(a.pts, row);
+#ifdef DASH_DEBUG
+          if (gi >= 0)
+#endif
           for (int k = 0; k < a.O; ++k)
             __stcs(a.attrs_out + (long long)k * a.n_all + gi, __ldcs(a.attrs_in + (long long)k * a.n_all + gi) + o[k]);
         }

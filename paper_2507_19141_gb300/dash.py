@@ -14,10 +14,14 @@ import os
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libdash.so")
+# DASH_LIBRARY=debug selects the bounds-checked build (libdash_debug.so,
+# compiled with -DDASH_DEBUG); a process loads one of the two, never both.
+LIB_PATH = (os.path.join(_HERE, "_build_debug", "libdash_debug.so") if os.environ.get("DASH_LIBRARY") == "debug"
+            else os.path.join(_HERE, "_build", "libdash.so"))
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError(f"libdash.so not built ({LIB_PATH}); run `python -c 'import __graft_entry__ as g; g.build()'`")
+    raise ImportError(f"{os.path.basename(LIB_PATH)} not built ({LIB_PATH}); "
+                      "run `python -c 'import __graft_entry__ as g; g.build()'`")
 
 _lib = ctypes.CDLL(LIB_PATH)
 
@@ -125,6 +129,7 @@ _SIGS = {
     "dash_selftest_wait": ([_I64, _P], _I),
     "dash_debug_fail_cuda_call": ([_I64], _I),
     "dash_debug_cuda_call_count": ([], _I64),
+    "dash_debug_set_point_rows": ([_I64], _I),
     "dash_probe_threads": ([_I], _I),
     "dash_probe_rate": ([_I, _P, _SZ, _I, _P, _P, _P], _I),
     "dash_get_option": ([_I], _I),
@@ -228,6 +233,12 @@ def dash_debug_fail_cuda_call(n: int) -> None:
     """Host fault injection: the n-th checked CUDA runtime call from now on
     is not made and fails (n = 0 disarms); restarts the call count."""
     _check(_lib.dash_debug_fail_cuda_call(int(n)), "dash_debug_fail_cuda_call")
+
+
+def dash_debug_set_point_rows(rows: int) -> None:
+    """Bounds-checked build only: the length of the point arrays that point
+    row indices are checked against (-1 = unchecked)."""
+    _check(_lib.dash_debug_set_point_rows(int(rows)), "dash_debug_set_point_rows")
 
 
 def dash_debug_cuda_call_count() -> int:

@@ -37,6 +37,22 @@ def test_every_declared_symbol_is_exported(lib):
     assert not missing, missing
 
 
+def test_debug_library_exports_the_same_abi(lib):
+    """libdash_debug.so (the -DDASH_DEBUG bounds-checked build) exports every
+    declared function; only it accepts dash_debug_set_point_rows (host-only
+    calls, no GPU needed)."""
+    assert os.path.exists(dash_build.DEBUG_LIB), dash_build.DEBUG_LIB
+    dbg = ctypes.CDLL(dash_build.DEBUG_LIB)
+    missing = [n for n in _declared_functions() if not hasattr(dbg, n)]
+    assert not missing, missing
+    dbg.dash_debug_set_point_rows.argtypes = [ctypes.c_int64]
+    lib.dash_debug_set_point_rows.argtypes = [ctypes.c_int64]
+    assert dbg.dash_debug_set_point_rows(1000) == 0
+    assert dbg.dash_debug_set_point_rows(-2) == -1      # DASH_ERR_INVALID_ARG
+    assert dbg.dash_debug_set_point_rows(-1) == 0
+    assert lib.dash_debug_set_point_rows(1000) == -2    # DASH_ERR_UNSUPPORTED in the release build
+
+
 def test_binding_names_match_the_abi():
     from paper_2507_19141_gb300 import dash
     declared = set(_declared_functions())
