@@ -94,6 +94,11 @@ __device__ __forceinline__ bool decoder_tile(const Tiles& t, const Ids& id, uint
                                              uint32_t bar, uint32_t& phase, unsigned int* flags,
                                              volatile int* abort_flag, const uint8_t* srow, const float* dd,
                                              long long dd_stride, bool valid, bool had_tile) {
+  // the upstream gradient is loaded with the state, so that its latency
+  // overlaps the state's and the first two layers instead of following them
+  float d[16];
+#pragma unroll
+  for (int jj = 0; jj < 16; ++jj) d[jj] = (valid && jj < t.O) ? __ldcs(dd + (long long)jj * dd_stride) : 0.0f;
   // f_h [hi | 1 | 0] from the state, masks from the forward
   const __nv_bfloat16* fs = reinterpret_cast<const __nv_bfloat16*>(srow);
   for (int c = 0; c < t.Dp / 8; ++c) {
@@ -179,10 +184,6 @@ __device__ __forceinline__ bool decoder_tile(const Tiles& t, const Ids& id, uint
   }
   write_ones(t.X, r, kHidden, kKH);
   {
-    float d[16];
-#pragma unroll
-    for (int jj = 0; jj < 16; ++jj)
-      d[jj] = (valid && jj < t.O) ? __ldcs(dd + (long long)jj * dd_stride) : 0.0f;
     uint32_t h[8];
 #pragma unroll
     for (int jj = 0; jj < 8; ++jj) h[jj] = pack_bf16x2(d[2 * jj], d[2 * jj + 1]);

@@ -245,6 +245,16 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_fwd_ws_kernel(const
       const uint32_t round = (uint32_t)(j / S);
       const long long row = (blockIdx.x + j * gridDim.x) * kRows + r;
       const bool valid = row < n;
+      // Eq. 10 inputs of this row, loaded before the wait so that the index
+      // and attribute latencies overlap the wait and the three layers
+      bool apply = valid && a.attrs_out != nullptr;
+      const long long gi = apply ? point_row(a.pts, row) : 0;
+#ifdef DASH_DEBUG
+      apply = apply && gi >= 0;
+#endif
+      float ain[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) ain[k] = (apply && k < a.O) ? __ldcs(a.attrs_in + (long long)k * a.n_all + gi) : 0.0f;
       if (!tc::mbar_wait(tc::smem_addr(&full[s]), round & 1u, kWaitIters)) {
         atomicOr(a.flags, 1u);
         *abort_flag = 1;
@@ -293,14 +303,13 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_fwd_ws_kernel(const
       float o[16];
       tc::tmem_ld16(trow, o);
       if (valid) {
-        for (int k = 0; k < a.O; ++k) __stcs(a.delta + (long long)k * a.n_cap + row, o[k]);
-        if (a.attrs_out != nullptr) {
-          const long long gi = point_row(a.pts, row);
-#ifdef DASH_DEBUG
-          if (gi >= 0)
-#endif
-          for (int k = 0; k < a.O; ++k)
-            __stcs(a.attrs_out + (long long)k * a.n_all + gi, __ldcs(a.attrs_in + (long long)k * a.n_all + gi) + o[k]);
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+          if (k < a.O) __stcs(a.delta + (long long)k * a.n_cap + row, o[k]);
+        if (apply) {
+#pragma unroll
+          for (int k = 0; k < 16; ++k)
+            if (k < a.O) __stcs(a.attrs_out + (long long)k * a.n_all + gi, ain[k] + o[k]);
         }
       }
       tc::fence_before_sync();
