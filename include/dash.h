@@ -210,11 +210,11 @@ int dash_debug_set_point_rows(int64_t rows);
 /* Process-wide kernel-form options (host; take effect at the next launch).
  * DASH_OPT_FWD_FORM selects the fused forward kernel: 0 = warp-specialised
  * (one decoder group fed by gather groups through a shared-memory ring;
- * default, two groups x two stages for F = 2, L*F <= 32: the small ring
- * leaves the L1 more room for the gathers), 1 / 2 / 4 = that many
+ * default, five groups x five stages for F = 2, L*F <= 32: enough gather
+ * warps to keep the L1's miss path busy), 1 / 2 / 4 = that many
  * independent gather+decoder groups per CTA, and for F = 2, L*F <= 32 the
  * warp-specialised shapes (gather groups, ring stages) 10 = (3, 6),
- * 11 = (3, 3), 12 = (2, 4), 13 = (5, 5), 14 = (4, 4).  DASH_OPT_BWD_FORM
+ * 11 = (3, 3), 12 = (2, 4), 13 = (5, 5), 14 = (4, 4), 15 = (2, 2).  DASH_OPT_BWD_FORM
  * selects the fused backward: 0 = warp-specialised (a decoder group feeding
  * scatter groups; three groups; used when a forward state is given),
  * 1 = one combined group per CTA, 10..13 = the shapes (3, 6), (4, 4),
@@ -611,7 +611,7 @@ int64_t* dash_batch_counts(dash_batch_plan* plan);
 int dash_batch_run(dash_batch_plan* plan, void* stream);
 /* Kernel forms in use: f + 16 * b, f the forward form (index into the
  * compiled (gather groups, ring stages) forms {(4,4), (3,6), (3,3), (2,4),
- * (2,2)}), b the backward form (into the (scatter groups, ring stages) forms
+ * (2,2), (5,5)}), b the backward form (into the (scatter groups, ring stages) forms
  * {(3,3), (2,2), (2,4), (3,4)}; 0 without a backward). */
 int dash_batch_form(const dash_batch_plan* plan);
 /* Autotuner: if cache_json_path holds an entry for this plan's signature

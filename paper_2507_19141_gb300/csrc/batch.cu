@@ -405,7 +405,7 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) batch_bwd_kernel(const __g
 struct Form {
   int P, S;
 };
-constexpr Form kForms[] = {{4, 4}, {3, 6}, {3, 3}, {2, 4}, {2, 2}};
+constexpr Form kForms[] = {{4, 4}, {3, 6}, {3, 3}, {2, 4}, {2, 2}, {5, 5}};
 constexpr int kNumForms = sizeof(kForms) / sizeof(kForms[0]);
 
 size_t smem_for(int P, int S, int Dp, BatchArgs* a) {
@@ -440,6 +440,7 @@ int launch_tt_f(int form, BatchArgs& a, cudaStream_t st) {
     case 1: return launch_form<TT, F, 3, 6>(a, st);
     case 2: return launch_form<TT, F, 3, 3>(a, st);
     case 3: return launch_form<TT, F, 2, 4>(a, st);
+    case 5: return launch_form<TT, F, 5, 5>(a, st);
     default: return launch_form<TT, F, 2, 2>(a, st);
   }
 }

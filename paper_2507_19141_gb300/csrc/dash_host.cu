@@ -184,8 +184,8 @@ int dash_version(void) { return 102; }
 int dash_set_option(int option, int value) {
   switch (option) {
     case DASH_OPT_FWD_FORM:
-      if (!(value == 0 || value == 1 || value == 2 || value == 4 || (value >= 10 && value <= 14)))
-        return dash::fail(DASH_ERR_INVALID_ARG, "forward form %d not in {0, 1, 2, 4, 10..14}", value);
+      if (!(value == 0 || value == 1 || value == 2 || value == 4 || (value >= 10 && value <= 15)))
+        return dash::fail(DASH_ERR_INVALID_ARG, "forward form %d not in {0, 1, 2, 4, 10..15}", value);
       dash::g_opt_fwd_form = value;
       return DASH_OK;
     case DASH_OPT_BWD_FORM:

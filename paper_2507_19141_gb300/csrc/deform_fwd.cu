@@ -404,12 +404,14 @@ int launch(FwdArgs a, cudaStream_t st) {
 
 template <typename TT>
 int dispatch_f(int F, int Dp, int variant, FwdArgs& a, cudaStream_t st) {
-  // variant 0: warp-specialised (3 producer groups; 6-stage ring, 3 stages when D > 32);
-  // 1, 2, 4: the simple form with that many independent groups per CTA
+  // variant 0: warp-specialised (5 gather groups and 5 stages for F = 2, L*F <= 32;
+  // otherwise 3 groups, 6 stages, 3 when D > 32); 1, 2, 4: the simple form
+  // with that many independent groups per CTA
   if (F == 2 && Dp <= 32) {
     // warp-specialised shapes (gather groups, ring stages); 0 = the measured best
     switch (variant) {
-      case 0: return launch_ws<TT, 2, 2, 2>(a, st);
+      case 0: return launch_ws<TT, 2, 5, 5>(a, st);
+      case 15: return launch_ws<TT, 2, 2, 2>(a, st);
       case 10: return launch_ws<TT, 2, 3, 6>(a, st);
       case 11: return launch_ws<TT, 2, 3, 3>(a, st);
       case 12: return launch_ws<TT, 2, 2, 4>(a, st);

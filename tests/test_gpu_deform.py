@@ -261,7 +261,7 @@ def test_forward_kernel_forms_agree(dashlib, grid, mlpc, tdtype):
     outs = []
     old = dashlib.dash_get_option(dashlib.OPT_FWD_FORM)
     try:
-        for form in (0, 1, 2, 4, 10, 11, 12, 13, 14):
+        for form in (0, 1, 2, 4, 10, 11, 12, 13, 14, 15):
             dashlib.dash_set_option(dashlib.OPT_FWD_FORM, form)
             st = dashlib.deform_state(mlp, n, "cuda")
             d = dashlib.dash_deform_mlp_fwd(lay, pts, tab, mlp, fwd_state=st)
