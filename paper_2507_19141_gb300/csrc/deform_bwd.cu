@@ -620,12 +620,17 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_bwd_ws_kernel(const
     // ------------------------------------------------------ scatter groups
     const int pg = tid / kRows - 1, r = tid % kRows;
     const TT* table = static_cast<const TT*>(a.table);
+    // the point of this group's next tile is loaded one tile ahead, so the
+    // index and coordinate latencies overlap the current tile's reductions
+    long long next_row = (blockIdx.x + pg * gridDim.x) * kRows + r;
+    float4 p_next = (pg < my_tiles && next_row < n) ? load_point(a.pts, next_row) : make_float4(0.f, 0.f, 0.f, 0.f);
     for (long long j = pg; j < my_tiles; j += P) {
       const int s = (int)(j % S);
       const uint32_t round = (uint32_t)(j / S);
-      const long long row = (blockIdx.x + j * gridDim.x) * kRows + r;
-      // the point's loads are in flight while this group waits for the tile's gradients
-      const float4 p = row < n ? load_point(a.pts, row) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const long long row = next_row;
+      const float4 p = p_next;
+      next_row = (blockIdx.x + (j + P) * gridDim.x) * kRows + r;
+      if (j + P < my_tiles && next_row < n) p_next = load_point(a.pts, next_row);
       if (!tc::mbar_wait(tc::smem_addr(&full[s]), round & 1u, kWaitIters)) {
         atomicOr(a.flags, 1u);
         *abort_flag = 1;
