@@ -216,9 +216,13 @@ int dash_debug_set_point_rows(int64_t rows);
  * warp-specialised shapes (gather groups, ring stages) 10 = (3, 6),
  * 11 = (3, 3), 12 = (2, 4), 13 = (5, 5), 14 = (4, 4), 15 = (2, 2).  DASH_OPT_BWD_FORM
  * selects the fused backward: 0 = warp-specialised (a decoder group feeding
- * scatter groups; three groups; used when a forward state is given),
- * 1 = one combined group per CTA, 10..13 = the shapes (3, 6), (4, 4),
- * (2, 4), (5, 5).  Every shape has at least one ring stage per group.  Forward forms agree bit for bit, backward forms up to the
+ * scatter groups; default four groups x five stages for F = 2, L*F <= 32;
+ * used when a forward state is given), 1 = one combined group per CTA,
+ * 10..14 = the shapes (3, 6), (4, 4), (2, 4), (5, 5), (3, 3).  When the
+ * number of scatter groups divides L (and there is no coordinate gradient),
+ * every group scatters every tile, each its own share of the levels;
+ * otherwise the groups take whole tiles in turn.  Every shape has at least
+ * one ring stage per group.  Forward forms agree bit for bit, backward forms up to the
  * order of the atomic additions.  DASH_OPT_ACCESS_FORM selects how the
  * warp-specialised forward and backward kernels issue their F = 2 table
  * accesses: 0 = lane pairs (default; lanes 2j and 2j+1 take the lower and
@@ -612,7 +616,7 @@ int dash_batch_run(dash_batch_plan* plan, void* stream);
 /* Kernel forms in use: f + 16 * b, f the forward form (index into the
  * compiled (gather groups, ring stages) forms {(4,4), (3,6), (3,3), (2,4),
  * (2,2), (5,5)}), b the backward form (into the (scatter groups, ring stages) forms
- * {(3,3), (2,2), (2,4), (3,4)}; 0 without a backward). */
+ * {(4,5), (2,2), (2,4), (3,4), (3,3)}; 0 without a backward). */
 int dash_batch_form(const dash_batch_plan* plan);
 /* Autotuner: if cache_json_path holds an entry for this plan's signature
  * (GPU, grid shape, scenes, counts, timestamps, with or without backward)

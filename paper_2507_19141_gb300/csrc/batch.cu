@@ -299,11 +299,15 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) batch_bwd_kernel(const __g
   long long* item_off = reinterpret_cast<long long*>(smem + a.off_tab);  // [n_scenes + 1]
   long long* tiles = item_off + kMaxScenes + 1;                           // [n_scenes]
   const int stage_floats = a.Dp * kRows;
+  // as in the single-scene backward: when P divides L every scatter group
+  // takes every tile and scatters its share of the levels, else whole tiles
+  // in turn
+  const bool split = a.g.L % P == 0;
   if (tid == 0) {
     build_item_table(a.scenes, a.counts, a.n_scenes, item_off, tiles);
     for (int s = 0; s < S; ++s) {
       tc::mbar_init(tc::smem_addr(&full[s]), kRows);
-      tc::mbar_init(tc::smem_addr(&empty[s]), kRows);
+      tc::mbar_init(tc::smem_addr(&empty[s]), split ? P * kRows : kRows);
     }
     tc::mbar_init(tc::smem_addr(mma_bar), 1);
     tc::mbar_init_fence();
@@ -365,7 +369,8 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) batch_bwd_kernel(const __g
   } else {
     // ------------------------------------------------------ scatter groups
     const int pg = tid / kRows - 1, r = tid % kRows;
-    for (long long j = pg; j < my_items; j += P) {
+    const int l0 = split ? pg * a.g.L / P : 0, l1 = split ? (pg + 1) * a.g.L / P : a.g.L;
+    for (long long j = split ? 0 : pg; j < my_items; j += split ? 1 : P) {
       const int s = (int)(j % S);
       const uint32_t round = (uint32_t)(j / S);
       const Item it = decode_item(blockIdx.x + j * gridDim.x, item_off, tiles, a.n_scenes);
@@ -391,7 +396,7 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) batch_bwd_kernel(const __g
       if (rep.base == nullptr) rep.levels = 0;
       if (row_a < cnt)
         bwdk::scatter_levels_paired(a.g, sc.table_grad, rep, p, ring + (size_t)s * stage_floats + (r & ~1),
-                                    (uint32_t)(r & 1), true, row_a + 1 < cnt, 3u << (r & 30));
+                                    (uint32_t)(r & 1), true, row_a + 1 < cnt, 3u << (r & 30), l0, l1);
       tc::mbar_arrive(tc::smem_addr(&empty[s]));
     }
   }
@@ -464,7 +469,7 @@ int launch_batch(int form, int table_dtype, BatchArgs& a, cudaStream_t st) {
 
 // Compiled forms of the batched backward: (scatter groups P, ring stages S);
 // the first is the single-scene default.
-constexpr Form kBwdForms[] = {{3, 3}, {2, 2}, {2, 4}, {3, 4}};
+constexpr Form kBwdForms[] = {{4, 5}, {2, 2}, {2, 4}, {3, 4}, {3, 3}};
 constexpr int kNumBwdForms = sizeof(kBwdForms) / sizeof(kBwdForms[0]);
 
 template <typename TT, int P, int S>
@@ -500,10 +505,11 @@ int launch_bwd_form(BatchBwdArgs a, cudaStream_t st) {
 template <typename TT>
 int launch_bwd_tt(int form, const BatchBwdArgs& a, cudaStream_t st) {
   switch (form) {
-    case 0: return launch_bwd_form<TT, 3, 3>(a, st);
+    case 0: return launch_bwd_form<TT, 4, 5>(a, st);
     case 1: return launch_bwd_form<TT, 2, 2>(a, st);
     case 2: return launch_bwd_form<TT, 2, 4>(a, st);
-    default: return launch_bwd_form<TT, 3, 4>(a, st);
+    case 3: return launch_bwd_form<TT, 3, 4>(a, st);
+    default: return launch_bwd_form<TT, 3, 3>(a, st);
   }
 }
 

@@ -189,8 +189,8 @@ int dash_set_option(int option, int value) {
       dash::g_opt_fwd_form = value;
       return DASH_OK;
     case DASH_OPT_BWD_FORM:
-      if (!(value == 0 || value == 1 || (value >= 10 && value <= 13)))
-        return dash::fail(DASH_ERR_INVALID_ARG, "backward form %d not in {0, 1, 10..13}", value);
+      if (!(value == 0 || value == 1 || (value >= 10 && value <= 14)))
+        return dash::fail(DASH_ERR_INVALID_ARG, "backward form %d not in {0, 1, 10..14}", value);
       dash::g_opt_bwd_form = value;
       return DASH_OK;
     case DASH_OPT_ACCESS_FORM:

@@ -527,15 +527,22 @@ __global__ void __launch_bounds__(kRows, 1) deform_bwd_kernel(const __grid_const
 // P scatter groups drain the ring: each thread takes one Gaussian, recomputes
 // its corners and issues the vector reductions into the tables; with the
 // smoothness term on they also encode p, p + e_s, p + e_t and scatter the
-// perturbed points' gradients.  With P = 0 (no ring) the decoder group
+// perturbed points' gradients.  When P divides L (lane pairs, no coordinate
+// gradient) every group takes every tile and scatters levels
+// [g L / P, (g + 1) L / P) of it, and a stage is released once all P groups
+// are done with it; this spreads each tile's reductions over the groups and
+// keeps all of them busy on the last tiles.  Otherwise group g takes tiles
+// g, g + P, ...  With P = 0 (no ring) the decoder group
 // stores dL/df_h to a.dfh_out for the Eq. 11 kernel to scatter; that form's
 // 110 KB of shared memory lets two CTAs share an SM.  Requires the forward
 // state.
 // ---------------------------------------------------------------------------
 template <typename TT, int F, int P, int S>
 __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_bwd_ws_kernel(const __grid_constant__ BwdArgs a) {
-  // tile j uses stage j % S and group j % P; the mbarrier waits tell phases
-  // apart only by parity, so no two groups may wait on one stage at once
+  // tile j uses stage j % S.  The mbarrier waits tell phases apart only by
+  // parity: with whole tiles in turn (group j % P) no two groups may wait on
+  // one stage at once; with the levels split all groups wait on the same
+  // phase, and the decoder refills a stage only after every group released it
   static_assert(S >= P, "the ring needs at least one stage per scatter group");
   static_assert(P > 0 || S == 0, "the store-only form has no ring");
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -558,10 +565,15 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_bwd_ws_kernel(const
 
   const bwdk::Tiles tl{w1, w2, w3, Ft, H1, X, G3, KF, a.D, a.Dp, a.O};
   if (tid < kRows) bwdk::build_weights(tl, a.params, tid, kRows);
+  // With lane pairs and no coordinate gradient, when the groups divide the
+  // levels evenly, every scatter group takes every tile and scatters its own
+  // share of the levels (so the last tiles are shared by all groups);
+  // otherwise the groups take whole tiles in turn.
+  const bool split = F == 2 && P > 0 && a.paired && a.coord_grad == nullptr && a.g.L % (P > 0 ? P : 1) == 0;
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
       tc::mbar_init(tc::smem_addr(&full[s]), kRows);
-      tc::mbar_init(tc::smem_addr(&empty[s]), kRows);
+      tc::mbar_init(tc::smem_addr(&empty[s]), split ? P * kRows : kRows);
     }
     tc::mbar_init(tc::smem_addr(mma_bar), 1);
     tc::mbar_init_fence();
@@ -620,17 +632,20 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_bwd_ws_kernel(const
     // ------------------------------------------------------ scatter groups
     const int pg = tid / kRows - 1, r = tid % kRows;
     const TT* table = static_cast<const TT*>(a.table);
+    const long long j0 = split ? 0 : pg, jstep = split ? 1 : P;
+    const int l0 = split ? pg * a.g.L / (P > 0 ? P : 1) : 0;
+    const int l1 = split ? (pg + 1) * a.g.L / (P > 0 ? P : 1) : a.g.L;
     // the point of this group's next tile is loaded one tile ahead, so the
     // index and coordinate latencies overlap the current tile's reductions
-    long long next_row = (blockIdx.x + pg * gridDim.x) * kRows + r;
-    float4 p_next = (pg < my_tiles && next_row < n) ? load_point(a.pts, next_row) : make_float4(0.f, 0.f, 0.f, 0.f);
-    for (long long j = pg; j < my_tiles; j += P) {
+    long long next_row = (blockIdx.x + j0 * gridDim.x) * kRows + r;
+    float4 p_next = (j0 < my_tiles && next_row < n) ? load_point(a.pts, next_row) : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (long long j = j0; j < my_tiles; j += jstep) {
       const int s = (int)(j % S);
       const uint32_t round = (uint32_t)(j / S);
       const long long row = next_row;
       const float4 p = p_next;
-      next_row = (blockIdx.x + (j + P) * gridDim.x) * kRows + r;
-      if (j + P < my_tiles && next_row < n) p_next = load_point(a.pts, next_row);
+      next_row = (blockIdx.x + (j + jstep) * gridDim.x) * kRows + r;
+      if (j + jstep < my_tiles && next_row < n) p_next = load_point(a.pts, next_row);
       if (!tc::mbar_wait(tc::smem_addr(&full[s]), round & 1u, kWaitIters)) {
         atomicOr(a.flags, 1u);
         *abort_flag = 1;
@@ -647,7 +662,8 @@ __global__ void __launch_bounds__((P + 1) * kRows, 1) deform_bwd_ws_kernel(const
           const unsigned int pm = 3u << (r & 30);
           if (row_a < n) {
             if (a.coord_grad == nullptr) {
-              scatter_levels_paired(a.g, a.table_grad, a.rep, p, stage + (r & ~1), xb, true, row_a + 1 < n, pm);
+              scatter_levels_paired(a.g, a.table_grad, a.rep, p, stage + (r & ~1), xb, true, row_a + 1 < n, pm, l0,
+                                    l1);
             } else {
               const float4 cg = scatter_coord_levels_paired<TT>(a.g, table, a.table_grad, a.rep, p, stage + (r & ~1), xb,
                                                                 row_a + 1 < n, pm);
@@ -770,11 +786,12 @@ int dispatch(int F, bool ws, BwdArgs& a, cudaStream_t st) {
   if (ws && F == 2 && a.Dp <= 32) {
     // warp-specialised shapes (scatter groups, ring stages); 0 = the measured best
     switch (g_opt_bwd_form) {
-      case 0: return launch_ws<TT, 2, 3, 3>(a, st);
+      case 0: return launch_ws<TT, 2, 4, 5>(a, st);
       case 10: return launch_ws<TT, 2, 3, 6>(a, st);
       case 11: return launch_ws<TT, 2, 4, 4>(a, st);
       case 12: return launch_ws<TT, 2, 2, 4>(a, st);
       case 13: return launch_ws<TT, 2, 5, 5>(a, st);
+      case 14: return launch_ws<TT, 2, 3, 3>(a, st);
       default: break;
     }
   }

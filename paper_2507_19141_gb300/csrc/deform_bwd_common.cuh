@@ -321,15 +321,17 @@ __device__ __forceinline__ void flush_dw(uint32_t trow, int r, int D, int Dp, in
 }
 
 // The F = 2 table-gradient scatter of a lane pair's two Gaussians over all
-// levels (scatter2_level_paired).  p is this lane's own Gaussian; dfp points
-// at A's column of the transposed [D][kRows] dL/df_h stage (B's is the next
-// one); va / vb say whether A / B exist; pm names the pair's lanes.
+// levels l0 .. l1-1 (scatter2_level_paired; l1 < 0: to the last level).  p
+// is this lane's own Gaussian; dfp points at A's column of the transposed
+// [D][kRows] dL/df_h stage (B's is the next one); va / vb say whether A / B
+// exist; pm names the pair's lanes.
 __device__ __forceinline__ void scatter_levels_paired(const Geom& g, float* __restrict__ grad, const Replicas& rp,
                                                       float4 p, const float* dfp, uint32_t xb, bool va, bool vb,
-                                                      unsigned int pm) {
+                                                      unsigned int pm, int l0 = 0, int l1 = -1) {
   float4 pa, pb;
   pair_points(p, xb, pm, pa, pb);
-  for (int l = 0; l < g.L; ++l) {
+  if (l1 < 0) l1 = g.L;
+  for (int l = l0; l < l1; ++l) {
     const float2 f0 = *reinterpret_cast<const float2*>(dfp + (2 * l) * kRows);      // (A, B) feature 0
     const float2 f1 = *reinterpret_cast<const float2*>(dfp + (2 * l + 1) * kRows);  // (A, B) feature 1
     scatter2_level_paired(g, l, pa, pb, xb, va, vb, rp.level_base(grad, g, l), f0.x, f1.x, f0.y, f1.y);

@@ -291,7 +291,10 @@ def test_backward_kernel_forms_agree(dashlib, smooth):
     res = []
     old = dashlib.dash_get_option(dashlib.OPT_BWD_FORM)
     try:
-        for form in (0, 1):
+        # 1: single group; 10, 13, 14: scatter groups taking whole tiles in
+        # turn; 0, 11, 12: every group on every tile, each its own share of
+        # the levels
+        for form in (0, 1, 10, 11, 12, 13, 14):
             dashlib.dash_set_option(dashlib.OPT_BWD_FORM, form)
             tg = torch.zeros((g.total, 2), dtype=torch.float32, device="cuda")
             pg = torch.zeros(mlpc.n_params, dtype=torch.float32, device="cuda")
@@ -301,9 +304,11 @@ def test_backward_kernel_forms_agree(dashlib, smooth):
             res.append((tg.cpu().numpy(), pg.cpu().numpy(), float(lo.item())))
     finally:
         dashlib.dash_set_option(dashlib.OPT_BWD_FORM, old)
-    assert rel_err(res[0][0], res[1][0]) < 1e-5
+    for other in res[1:]:
+        assert rel_err(res[0][0], other[0]) < 1e-5
     if smooth is None:
-        assert rel_err(res[0][1], res[1][1]) < 1e-5
+        for other in res[1:]:
+            assert rel_err(res[0][1], other[1]) < 1e-5
     else:
         # with Eq. 11 on, the single-group form recomputes the decoder from a
         # fresh FP32 f_h, the warp-specialised one from the state's BF16 f_h:
