@@ -47,10 +47,10 @@ STEP_BYTES = 2 + 4 + FWD_BYTES + BWD_BYTES
 # benchmark reports no traffic.  A changed kernel is re-captured before its
 # record changes: the record and the summary of its capture change together.
 NCU_TRAFFIC = {
-    "bwd": {"bytes": (214.2 + 8.5) * 1e6, "n": 1_000_000, "sha256_16": "1fde28dc2a1affc5",
+    "bwd": {"bytes": (214.4 + 7.0) * 1e6, "n": 1_000_000, "sha256_16": "751b2ae1b27781ca",
             "sources": ("deform_bwd.cu", "deform_bwd_common.cuh", "deform_common.cuh", "dash_internal.cuh",
                         "tc_ptx.cuh", "replicas.cu")},
-    "fwd": {"bytes": (45.4 + 71.9) * 1e6, "n": 1_000_000, "sha256_16": "51bbff9c0c10f931",
+    "fwd": {"bytes": (46.6 + 70.7) * 1e6, "n": 1_000_000, "sha256_16": "085fff1754c90dab",
             "sources": ("deform_fwd.cu", "deform_common.cuh", "dash_internal.cuh", "tc_ptx.cuh")},
 }
 
