@@ -210,8 +210,9 @@ int dash_debug_set_point_rows(int64_t rows);
 /* Process-wide kernel-form options (host; take effect at the next launch).
  * DASH_OPT_FWD_FORM selects the fused forward kernel: 0 = warp-specialised
  * (one decoder group fed by gather groups through a shared-memory ring;
- * default, five groups x five stages for F = 2, L*F <= 32: enough gather
- * warps to keep the L1's miss path busy), 1 / 2 / 4 = that many
+ * default for F = 2, L*F <= 32: five groups x five stages with FP16
+ * tables, enough gather warps to keep the L1's miss path busy; three x three
+ * with FP32 tables, whose 8-byte entries need more registers), 1 / 2 / 4 = that many
  * independent gather+decoder groups per CTA, and for F = 2, L*F <= 32 the
  * warp-specialised shapes (gather groups, ring stages) 10 = (3, 6),
  * 11 = (3, 3), 12 = (2, 4), 13 = (5, 5), 14 = (4, 4), 15 = (2, 2).  DASH_OPT_BWD_FORM

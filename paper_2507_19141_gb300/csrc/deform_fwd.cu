@@ -404,13 +404,15 @@ int launch(FwdArgs a, cudaStream_t st) {
 
 template <typename TT>
 int dispatch_f(int F, int Dp, int variant, FwdArgs& a, cudaStream_t st) {
-  // variant 0: warp-specialised (5 gather groups and 5 stages for F = 2, L*F <= 32;
-  // otherwise 3 groups, 6 stages, 3 when D > 32); 1, 2, 4: the simple form
-  // with that many independent groups per CTA
+  // variant 0: warp-specialised (for F = 2, L*F <= 32: 5 gather groups and 5
+  // stages with FP16 tables, 3 and 3 with FP32 tables; otherwise 3 groups, 6
+  // stages, 3 when D > 32); 1, 2, 4: the simple form with that many
+  // independent groups per CTA
   if (F == 2 && Dp <= 32) {
     // warp-specialised shapes (gather groups, ring stages); 0 = the measured best
     switch (variant) {
-      case 0: return launch_ws<TT, 2, 5, 5>(a, st);
+      case 0:  // FP32 tables' 8-byte entries need more registers: five groups would spill
+        return sizeof(TT) == 4 ? launch_ws<TT, 2, 3, 3>(a, st) : launch_ws<TT, 2, 5, 5>(a, st);
       case 15: return launch_ws<TT, 2, 2, 2>(a, st);
       case 10: return launch_ws<TT, 2, 3, 6>(a, st);
       case 11: return launch_ws<TT, 2, 3, 3>(a, st);
