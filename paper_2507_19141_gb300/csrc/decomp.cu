@@ -1024,7 +1024,7 @@ namespace dfw {
 
 using fused::kRows;
 using fused::tile_off;
-constexpr int kWorkers = 3;
+constexpr int kWorkers = 4;
 constexpr int kThreadsWs = (kWorkers + 1) * kRows;
 constexpr uint32_t kCols = 64;  // z
 constexpr int kMaxDp = 48;
