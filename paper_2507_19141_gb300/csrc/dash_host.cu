@@ -96,7 +96,9 @@ int make_geom(const dash_layout* lo, Geom* g) {
 }
 
 // Point-row bounds of DASH_DEBUG builds (dash_debug_set_point_rows).
+#ifdef DASH_DEBUG
 static long long g_point_rows = -1;
+#endif
 __device__ unsigned int g_bounds_flags;
 
 unsigned int* bounds_flags_ptr() {

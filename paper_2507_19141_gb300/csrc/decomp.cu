@@ -1027,7 +1027,6 @@ using fused::tile_off;
 constexpr int kWorkers = 4;
 constexpr int kThreadsWs = (kWorkers + 1) * kRows;
 constexpr uint32_t kCols = 64;  // z
-constexpr int kMaxDp = 48;
 
 struct Args {
   Geom g;
